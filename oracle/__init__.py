@@ -1,0 +1,14 @@
+"""FP64 CPU oracle of the conservative Allen-Cahn phase-field LBM.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The product library never imports,
+links or executes anything in this package.  It shares no code with the CUDA
+path; both sides only take the same seeded inputs.
+
+``Oracle`` wraps ``pflbm_oracle.cpp`` (plain loops, two-array streaming, full
+moment matrices) through ctypes.  See that file's header for the equations and
+the readings it follows.
+"""
+from .oracle import Oracle, from_params, tables, mrt_collide, build_oracle, COLL_MRT, COLL_BGK, COLL_MRT_ALL_EQUAL
+
+__all__ = ["Oracle", "from_params", "tables", "mrt_collide", "build_oracle", "COLL_MRT", "COLL_BGK", "COLL_MRT_ALL_EQUAL"]

@@ -1,0 +1,559 @@
+// Plain FP64 CPU oracle of the conservative Allen-Cahn phase-field LBM (PFLBM).
+//
+// TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, includes or
+// calls this file; only the tests, the smoke check and the CPU-baseline leg of
+// the benchmark load it.  It shares no code, header or table with the CUDA path.
+//
+// What it computes (section "Conservative Allen-Cahn model" of the paper, and
+// the LBM basics of section "The lattice Boltzmann method"):
+//   * phase-field PDFs h_i on D3Q15, hydrodynamic PDFs g_i on D3Q27;
+//   * phi = sum_i h_i (zeroth moment), p* = sum_i g_i (normalised pressure);
+//   * weighted-orthogonal MRT collision  Omega = M^-1 S M (f^eq - f)  (Eq. mrt),
+//     with the moment matrices built here by Gram-Schmidt under the lattice
+//     weights from a list of monomials, graded by polynomial degree;
+//   * Guo forcing applied in moment space, (I - S/2) M F;
+//   * forces F = F_s + F_b + F_p + F_mu with F_s = mu_phi grad(phi), F_b = rho g,
+//     F_p = -p* c_s^2 (rho_H - rho_L) grad(phi),
+//     F_mu = nu (rho_H - rho_L) [grad u + grad u^T] . grad(phi), the strain rate
+//     taken from the non-equilibrium second moment of g (no finite differences
+//     on u);
+//   * rho(phi) and tau(phi) linear interpolation between the phases;
+//   * conservative Allen-Cahn forcing F^phi = 4 phi (1 - phi) / xi * n;
+//   * streaming with periodic wrap or halfway bounce-back at no-slip faces.
+//
+// Readings where the paper is silent or garbled (each is listed in the design doc):
+//   tau_phi = M / c_s^2 is the shifted relaxation time, omega_phi = 1/(3M + 1/2);
+//   mu_phi = 4 beta phi (phi - 1)(phi - 1/2) - kappa lap(phi), beta = 12 sigma / xi,
+//     kappa = 3 sigma xi / 2;
+//   grad/laplacian of phi: D3Q27-weighted central stencil, phi mirrored at walls;
+//   h^eq_i = w_i phi (1 + c_i.u / c_s^2);  h source S_i = w_i c_i . (F^phi);
+//   g source G_i = w_i c_i . F / (rho c_s^2);  u = sum c g + F / (2 rho);
+//   F_mu uses the non-equilibrium part relative to g^eq(p*, u0) with
+//     u0 = sum c g + (F_s + F_b + F_p) / (2 rho);
+//   rates: g -- degree 2 at omega(phi), degree >= 3 at 1; h -- degrees 1 and 2
+//     at omega_phi, degree >= 3 at 1; conserved moments at 0 / 1 (irrelevant);
+//   n = grad(phi) / (|grad(phi)| + 1e-12).
+//
+// Schedule per step: both collisions use phi^t and its stencil, u^t from g in
+// the same cell; then both sets stream; then phi^{t+1} = sum h.
+//
+// Built with -O2 -ffp-contract=off so the arithmetic is plain IEEE FP64.
+#include <cmath>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+const double CS2 = 1.0 / 3.0;
+
+// ---------------------------------------------------------------- lattices --
+struct Lattice {
+  int q = 0;
+  std::vector<int> c;        // q x 3
+  std::vector<double> w;     // q
+  std::vector<int> opp;      // q
+  std::vector<int> degree;   // q, polynomial degree of moment k
+  std::vector<double> M;     // q x q, row k = moment polynomial k at c_i
+  std::vector<double> Minv;  // q x q
+};
+
+// Canonical velocity order: loop cz, cy, cx over -1, 0, 1 (cx fastest) and
+// keep the members of the set.  D3Q27 keeps all, D3Q15 keeps |c|^2 in {0,1,3}.
+void make_velocities(Lattice& L, bool q15) {
+  L.c.clear();
+  L.w.clear();
+  for (int cz = -1; cz <= 1; ++cz)
+    for (int cy = -1; cy <= 1; ++cy)
+      for (int cx = -1; cx <= 1; ++cx) {
+        int n2 = cx * cx + cy * cy + cz * cz;
+        double w;
+        if (q15) {
+          if (n2 == 2) continue;
+          w = (n2 == 0) ? 2.0 / 9.0 : (n2 == 1) ? 1.0 / 9.0 : 1.0 / 72.0;
+        } else {
+          w = (n2 == 0) ? 8.0 / 27.0 : (n2 == 1) ? 2.0 / 27.0 : (n2 == 2) ? 1.0 / 54.0 : 1.0 / 216.0;
+        }
+        L.c.push_back(cx);
+        L.c.push_back(cy);
+        L.c.push_back(cz);
+        L.w.push_back(w);
+      }
+  L.q = (int)L.w.size();
+  L.opp.assign(L.q, -1);
+  for (int i = 0; i < L.q; ++i)
+    for (int j = 0; j < L.q; ++j)
+      if (L.c[3 * j] == -L.c[3 * i] && L.c[3 * j + 1] == -L.c[3 * i + 1] && L.c[3 * j + 2] == -L.c[3 * i + 2])
+        L.opp[i] = j;
+}
+
+// Monomials x^a y^b z^c, listed by increasing degree.  Gram-Schmidt under
+// <u, v> = sum_i w_i u(c_i) v(c_i) turns them into weighted-orthogonal moment
+// polynomials; M^-1 = W M^T N^-1 with N_k = <P_k, P_k>.
+void build_moments(Lattice& L, const std::vector<int>& mono /* triples a,b,c */) {
+  const int q = L.q;
+  std::vector<double> P((size_t)q * q);
+  L.degree.assign(q, 0);
+  for (int k = 0; k < q; ++k) {
+    int a = mono[3 * k], b = mono[3 * k + 1], cc = mono[3 * k + 2];
+    L.degree[k] = a + b + cc;
+    for (int i = 0; i < q; ++i)
+      P[(size_t)k * q + i] = std::pow((double)L.c[3 * i], a) * std::pow((double)L.c[3 * i + 1], b) *
+                             std::pow((double)L.c[3 * i + 2], cc);
+  }
+  for (int k = 0; k < q; ++k) {
+    for (int j = 0; j < k; ++j) {
+      double num = 0, den = 0;
+      for (int i = 0; i < q; ++i) {
+        num += L.w[i] * P[(size_t)k * q + i] * P[(size_t)j * q + i];
+        den += L.w[i] * P[(size_t)j * q + i] * P[(size_t)j * q + i];
+      }
+      for (int i = 0; i < q; ++i) P[(size_t)k * q + i] -= num / den * P[(size_t)j * q + i];
+    }
+  }
+  L.M = P;
+  L.Minv.assign((size_t)q * q, 0.0);
+  for (int k = 0; k < q; ++k) {
+    double nk = 0;
+    for (int i = 0; i < q; ++i) nk += L.w[i] * P[(size_t)k * q + i] * P[(size_t)k * q + i];
+    for (int i = 0; i < q; ++i) L.Minv[(size_t)i * q + k] = L.w[i] * P[(size_t)k * q + i] / nk;
+  }
+}
+
+Lattice make_d3q27() {
+  Lattice L;
+  make_velocities(L, false);
+  std::vector<int> mono;
+  for (int deg = 0; deg <= 6; ++deg)
+    for (int a = 0; a <= 2; ++a)
+      for (int b = 0; b <= 2; ++b)
+        for (int cc = 0; cc <= 2; ++cc)
+          if (a + b + cc == deg) {
+            mono.push_back(a);
+            mono.push_back(b);
+            mono.push_back(cc);
+          }
+  build_moments(L, mono);
+  return L;
+}
+
+Lattice make_d3q15() {
+  Lattice L;
+  make_velocities(L, true);
+  // degree 0..2 complete; degree 3: xyz, x y^2, y z^2, z x^2; degree 4: x^2 y^2.
+  const int m[15][3] = {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {2, 0, 0}, {0, 2, 0}, {0, 0, 2}, {1, 1, 0},
+                        {0, 1, 1}, {1, 0, 1}, {1, 1, 1}, {1, 2, 0}, {0, 1, 2}, {2, 0, 1}, {2, 2, 0}};
+  std::vector<int> mono;
+  for (auto& r : m) {
+    mono.push_back(r[0]);
+    mono.push_back(r[1]);
+    mono.push_back(r[2]);
+  }
+  build_moments(L, mono);
+  return L;
+}
+
+const Lattice& Q27() {
+  static Lattice L = make_d3q27();
+  return L;
+}
+const Lattice& Q15() {
+  static Lattice L = make_d3q15();
+  return L;
+}
+
+// ------------------------------------------------------------------ model --
+enum { COLL_MRT = 0, COLL_BGK = 1, COLL_MRT_ALL_EQUAL = 2 };
+
+struct Params {
+  int nx, ny, nz;
+  int bc[6];  // -x,+x,-y,+y,-z,+z : 0 periodic, 1 no-slip
+  int collision;
+  double rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, g[3];
+};
+
+struct Sim {
+  Params P;
+  long N;
+  std::vector<double> h, g, hn, gn, phi;  // populations SoA [i][cell]
+  long step = 0;
+};
+
+inline long cell_index(const Params& P, int x, int y, int z) { return x + (long)P.nx * (y + (long)P.ny * z); }
+
+// Neighbour coordinate along one axis; returns false when the link leaves the
+// domain through a no-slip face.
+inline bool neighbour(int x, int d, int n, int bc_lo, int bc_hi, int& out) {
+  int t = x + d;
+  if (t < 0) {
+    if (bc_lo == 1) return false;
+    t += n;
+  } else if (t >= n) {
+    if (bc_hi == 1) return false;
+    t -= n;
+  }
+  out = t;
+  return true;
+}
+
+// Index of the cell used for the phi stencil: periodic wrap, or mirror
+// (phi outside a wall equals phi in the adjacent cell).
+inline int stencil_coord(int x, int d, int n, int bc_lo, int bc_hi) {
+  int t = x + d;
+  if (t < 0) t = (bc_lo == 1) ? 0 : t + n;
+  if (t >= n) t = (bc_hi == 1) ? n - 1 : t - n;
+  return t;
+}
+
+struct CellState {
+  double phi, gradphi[3], lapphi, rho, tau, omega, nu, mu, pstar, j[3], F[3], u[3];
+  double Fs[3], Fb[3], Fp[3], Fmu[3];
+};
+
+void geq_of(double pstar, const double u[3], double* out) {
+  const Lattice& L = Q27();
+  double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  for (int i = 0; i < L.q; ++i) {
+    double cu = L.c[3 * i] * u[0] + L.c[3 * i + 1] * u[1] + L.c[3 * i + 2] * u[2];
+    out[i] = L.w[i] * (pstar + cu / CS2 + cu * cu / (2 * CS2 * CS2) - uu / (2 * CS2));
+  }
+}
+
+double rate_g(const Params& P, int degree, double omega) {
+  if (P.collision != COLL_MRT) return omega;
+  if (degree == 0) return 0.0;
+  if (degree == 1) return 1.0;
+  if (degree == 2) return omega;
+  return 1.0;
+}
+
+double rate_h(const Params& P, int degree, double omega_phi) {
+  if (P.collision != COLL_MRT) return omega_phi;
+  if (degree == 0) return 0.0;
+  if (degree <= 2) return omega_phi;
+  return 1.0;
+}
+
+// Collision in moment space, Eq. (mrt) plus Guo forcing in collision space:
+//   f+ = f + M^-1 [ S M (f^eq - f) + (I - S/2) M src ].
+void mrt_collide(const Lattice& L, const double* f, const double* feq, const double* src, const double* s,
+                 double* out) {
+  const int q = L.q;
+  double r[27];
+  for (int k = 0; k < q; ++k) {
+    double d = 0, ms = 0;
+    for (int i = 0; i < q; ++i) {
+      d += L.M[(size_t)k * q + i] * (feq[i] - f[i]);
+      ms += L.M[(size_t)k * q + i] * src[i];
+    }
+    r[k] = s[k] * d + (1.0 - 0.5 * s[k]) * ms;
+  }
+  for (int i = 0; i < q; ++i) {
+    double v = 0;
+    for (int k = 0; k < q; ++k) v += L.Minv[(size_t)i * q + k] * r[k];
+    out[i] = f[i] + v;
+  }
+}
+
+// v = M^-1 S M d  (the relaxed non-equilibrium part).
+void mrt_relax(const Lattice& L, const double* d, const double* s, double* out) {
+  const int q = L.q;
+  double r[27];
+  for (int k = 0; k < q; ++k) {
+    double m = 0;
+    for (int i = 0; i < q; ++i) m += L.M[(size_t)k * q + i] * d[i];
+    r[k] = s[k] * m;
+  }
+  for (int i = 0; i < q; ++i) {
+    double v = 0;
+    for (int k = 0; k < q; ++k) v += L.Minv[(size_t)i * q + k] * r[k];
+    out[i] = v;
+  }
+}
+
+// Macroscopic state of one cell at the current time level: stencil, forces
+// and velocity (steps before the collision).  Needs phi of the neighbours.
+void cell_macro(const Sim& S, int x, int y, int z, const double* gcell, CellState& cs) {
+  const Params& P = S.P;
+  const Lattice& L27 = Q27();
+  long c0 = cell_index(P, x, y, z);
+  cs.phi = S.phi[c0];
+  cs.gradphi[0] = cs.gradphi[1] = cs.gradphi[2] = 0;
+  cs.lapphi = 0;
+  for (int i = 0; i < L27.q; ++i) {
+    int xs = stencil_coord(x, L27.c[3 * i], P.nx, P.bc[0], P.bc[1]);
+    int ys = stencil_coord(y, L27.c[3 * i + 1], P.ny, P.bc[2], P.bc[3]);
+    int zs = stencil_coord(z, L27.c[3 * i + 2], P.nz, P.bc[4], P.bc[5]);
+    double pn = S.phi[cell_index(P, xs, ys, zs)];
+    for (int a = 0; a < 3; ++a) cs.gradphi[a] += L27.w[i] * L27.c[3 * i + a] * pn;
+    cs.lapphi += L27.w[i] * (pn - cs.phi);
+  }
+  for (int a = 0; a < 3; ++a) cs.gradphi[a] /= CS2;
+  cs.lapphi *= 2.0 / CS2;
+
+  const double phiL = 0.0, phiH = 1.0, phi0 = 0.5;
+  double tauH = P.nu_h / CS2 + 0.5, tauL = P.nu_l / CS2 + 0.5;
+  cs.rho = P.rho_l + (cs.phi - phiL) * (P.rho_h - P.rho_l);
+  cs.tau = tauL + (cs.phi - phiL) * (tauH - tauL);
+  cs.omega = 1.0 / cs.tau;
+  cs.nu = CS2 * (cs.tau - 0.5);
+  double beta = 12.0 * P.sigma / P.xi, kappa = 1.5 * P.sigma * P.xi;
+  cs.mu = 4.0 * beta * (cs.phi - phiL) * (cs.phi - phiH) * (cs.phi - phi0) - kappa * cs.lapphi;
+
+  cs.pstar = 0;
+  cs.j[0] = cs.j[1] = cs.j[2] = 0;
+  for (int i = 0; i < L27.q; ++i) {
+    cs.pstar += gcell[i];
+    for (int a = 0; a < 3; ++a) cs.j[a] += L27.c[3 * i + a] * gcell[i];
+  }
+  double drho = P.rho_h - P.rho_l;
+  double u0[3];
+  for (int a = 0; a < 3; ++a) {
+    cs.Fs[a] = cs.mu * cs.gradphi[a];
+    cs.Fb[a] = cs.rho * P.g[a];
+    cs.Fp[a] = -cs.pstar * CS2 * drho * cs.gradphi[a];
+    u0[a] = cs.j[a] + (cs.Fs[a] + cs.Fb[a] + cs.Fp[a]) / (2.0 * cs.rho);
+  }
+  // Viscous force from the non-equilibrium moments, M^-1 S M (g - g^eq(p*, u0)).
+  double geq0[27], dneq[27], relaxed[27], s[27];
+  geq_of(cs.pstar, u0, geq0);
+  for (int k = 0; k < L27.q; ++k) s[k] = rate_g(P, L27.degree[k], cs.omega);
+  for (int i = 0; i < L27.q; ++i) dneq[i] = gcell[i] - geq0[i];
+  mrt_relax(L27, dneq, s, relaxed);
+  double Pi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int i = 0; i < L27.q; ++i)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) Pi[a][b] += L27.c[3 * i + a] * L27.c[3 * i + b] * relaxed[i];
+  for (int a = 0; a < 3; ++a) {
+    double acc = 0;
+    for (int b = 0; b < 3; ++b) acc += Pi[a][b] * cs.gradphi[b];
+    // [grad u + grad u^T] ~= -(1/c_s^2) (M^-1 S M g^neq)_2
+    cs.Fmu[a] = cs.nu * drho * (-acc / CS2);
+  }
+  for (int a = 0; a < 3; ++a) {
+    cs.F[a] = cs.Fs[a] + cs.Fb[a] + cs.Fp[a] + cs.Fmu[a];
+    cs.u[a] = cs.j[a] + cs.F[a] / (2.0 * cs.rho);
+  }
+}
+
+void compute_phi(Sim& S) {
+  const Lattice& L15 = Q15();
+  for (long c = 0; c < S.N; ++c) {
+    double s = 0;
+    for (int i = 0; i < L15.q; ++i) s += S.h[(size_t)i * S.N + c];
+    S.phi[c] = s;
+  }
+}
+
+void do_step(Sim& S) {
+  const Params& P = S.P;
+  const Lattice& L27 = Q27();
+  const Lattice& L15 = Q15();
+  const long N = S.N;
+  const double omega_phi = 1.0 / (P.mobility / CS2 + 0.5);
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < P.nz; ++z) {
+    for (int y = 0; y < P.ny; ++y)
+      for (int x = 0; x < P.nx; ++x) {
+        long c0 = cell_index(P, x, y, z);
+        double gc[27], hc[15];
+        for (int i = 0; i < 27; ++i) gc[i] = S.g[(size_t)i * N + c0];
+        for (int i = 0; i < 15; ++i) hc[i] = S.h[(size_t)i * N + c0];
+        CellState cs;
+        cell_macro(S, x, y, z, gc, cs);
+
+        // hydrodynamic collision
+        double geq[27], G[27], gpost[27], s27[27];
+        geq_of(cs.pstar, cs.u, geq);
+        for (int i = 0; i < 27; ++i) {
+          double cF = L27.c[3 * i] * cs.F[0] + L27.c[3 * i + 1] * cs.F[1] + L27.c[3 * i + 2] * cs.F[2];
+          G[i] = L27.w[i] * cF / (CS2 * cs.rho);
+        }
+        if (P.collision == COLL_BGK) {
+          for (int i = 0; i < 27; ++i)
+            gpost[i] = gc[i] - cs.omega * (gc[i] - geq[i]) + (1.0 - 0.5 * cs.omega) * G[i];
+        } else {
+          for (int k = 0; k < 27; ++k) s27[k] = rate_g(P, L27.degree[k], cs.omega);
+          mrt_collide(L27, gc, geq, G, s27, gpost);
+        }
+
+        // phase-field collision
+        double gnorm = std::sqrt(cs.gradphi[0] * cs.gradphi[0] + cs.gradphi[1] * cs.gradphi[1] +
+                                 cs.gradphi[2] * cs.gradphi[2]);
+        double n[3];
+        for (int a = 0; a < 3; ++a) n[a] = cs.gradphi[a] / (gnorm + 1e-12);
+        double theta = 4.0 * cs.phi * (1.0 - cs.phi) / P.xi;
+        double heq[15], Sh[15], hpost[15], s15[15];
+        for (int i = 0; i < 15; ++i) {
+          double cu = L15.c[3 * i] * cs.u[0] + L15.c[3 * i + 1] * cs.u[1] + L15.c[3 * i + 2] * cs.u[2];
+          double cn = L15.c[3 * i] * n[0] + L15.c[3 * i + 1] * n[1] + L15.c[3 * i + 2] * n[2];
+          heq[i] = L15.w[i] * cs.phi * (1.0 + cu / CS2);
+          Sh[i] = L15.w[i] * theta * cn;
+        }
+        if (P.collision == COLL_BGK) {
+          for (int i = 0; i < 15; ++i)
+            hpost[i] = hc[i] - omega_phi * (hc[i] - heq[i]) + (1.0 - 0.5 * omega_phi) * Sh[i];
+        } else {
+          for (int k = 0; k < 15; ++k) s15[k] = rate_h(P, L15.degree[k], omega_phi);
+          mrt_collide(L15, hc, heq, Sh, s15, hpost);
+        }
+
+        // streaming (push) with periodic wrap / halfway bounce-back
+        for (int i = 0; i < 27; ++i) {
+          int xt, yt, zt;
+          bool ok = neighbour(x, L27.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
+                    neighbour(y, L27.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
+                    neighbour(z, L27.c[3 * i + 2], P.nz, P.bc[4], P.bc[5], zt);
+          if (ok)
+            S.gn[(size_t)i * N + cell_index(P, xt, yt, zt)] = gpost[i];
+          else
+            S.gn[(size_t)L27.opp[i] * N + c0] = gpost[i];
+        }
+        for (int i = 0; i < 15; ++i) {
+          int xt, yt, zt;
+          bool ok = neighbour(x, L15.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
+                    neighbour(y, L15.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
+                    neighbour(z, L15.c[3 * i + 2], P.nz, P.bc[4], P.bc[5], zt);
+          if (ok)
+            S.hn[(size_t)i * N + cell_index(P, xt, yt, zt)] = hpost[i];
+          else
+            S.hn[(size_t)L15.opp[i] * N + c0] = hpost[i];
+        }
+      }
+  }
+  std::swap(S.g, S.gn);
+  std::swap(S.h, S.hn);
+  compute_phi(S);
+  S.step += 1;
+}
+
+}  // namespace
+
+extern "C" {
+
+// iparams: nx, ny, nz, bc[6], collision       (10 ints)
+// dparams: rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, gx, gy, gz (10 doubles)
+// phi0 (N), u0 (3N SoA, nullable), p0 (N, nullable): initial state; the
+// populations start at their equilibria h^eq(phi0, u0), g^eq(p0, u0).
+void* ora_new(const int* ip, const double* dp, const double* phi0, const double* u0, const double* p0) {
+  Sim* S = new Sim();
+  Params& P = S->P;
+  P.nx = ip[0];
+  P.ny = ip[1];
+  P.nz = ip[2];
+  for (int k = 0; k < 6; ++k) P.bc[k] = ip[3 + k];
+  P.collision = ip[9];
+  P.rho_h = dp[0];
+  P.rho_l = dp[1];
+  P.nu_h = dp[2];
+  P.nu_l = dp[3];
+  P.sigma = dp[4];
+  P.mobility = dp[5];
+  P.xi = dp[6];
+  P.g[0] = dp[7];
+  P.g[1] = dp[8];
+  P.g[2] = dp[9];
+  S->N = (long)P.nx * P.ny * P.nz;
+  const long N = S->N;
+  S->h.assign((size_t)15 * N, 0.0);
+  S->hn.assign((size_t)15 * N, 0.0);
+  S->g.assign((size_t)27 * N, 0.0);
+  S->gn.assign((size_t)27 * N, 0.0);
+  S->phi.assign(N, 0.0);
+  const Lattice& L15 = Q15();
+  for (long c = 0; c < N; ++c) {
+    double u[3] = {0, 0, 0};
+    if (u0)
+      for (int a = 0; a < 3; ++a) u[a] = u0[a * N + c];
+    double ps = p0 ? p0[c] : 0.0;
+    double geq[27];
+    geq_of(ps, u, geq);
+    for (int i = 0; i < 27; ++i) S->g[(size_t)i * N + c] = geq[i];
+    for (int i = 0; i < 15; ++i) {
+      double cu = L15.c[3 * i] * u[0] + L15.c[3 * i + 1] * u[1] + L15.c[3 * i + 2] * u[2];
+      S->h[(size_t)i * N + c] = L15.w[i] * phi0[c] * (1.0 + cu / CS2);
+    }
+  }
+  compute_phi(*S);
+  return S;
+}
+
+void ora_free(void* s) { delete (Sim*)s; }
+
+void ora_step(void* s, int n, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  for (int k = 0; k < n; ++k) do_step(*(Sim*)s);
+}
+
+long ora_time(void* s) { return ((Sim*)s)->step; }
+
+// Populations in canonical order, SoA [i][cell].
+void ora_get_pops(void* s, double* h, double* g) {
+  Sim* S = (Sim*)s;
+  if (h) std::memcpy(h, S->h.data(), sizeof(double) * S->h.size());
+  if (g) std::memcpy(g, S->g.data(), sizeof(double) * S->g.size());
+}
+
+void ora_set_pops(void* s, const double* h, const double* g) {
+  Sim* S = (Sim*)s;
+  if (h) std::memcpy(S->h.data(), h, sizeof(double) * S->h.size());
+  if (g) std::memcpy(S->g.data(), g, sizeof(double) * S->g.size());
+  compute_phi(*S);
+}
+
+// Macroscopic fields at the current time level (any output may be NULL):
+// phi, rho(phi), p = p* rho c_s^2, u = sum c g + F/(2 rho) (3N SoA).
+void ora_fields(void* s, double* phi, double* rho, double* p, double* u) {
+  Sim* S = (Sim*)s;
+  const Params& P = S->P;
+  const long N = S->N;
+#pragma omp parallel for collapse(2) schedule(static)
+  for (int z = 0; z < P.nz; ++z)
+    for (int y = 0; y < P.ny; ++y)
+      for (int x = 0; x < P.nx; ++x) {
+        long c0 = cell_index(P, x, y, z);
+        double gc[27];
+        for (int i = 0; i < 27; ++i) gc[i] = S->g[(size_t)i * N + c0];
+        CellState cs;
+        cell_macro(*S, x, y, z, gc, cs);
+        if (phi) phi[c0] = cs.phi;
+        if (rho) rho[c0] = cs.rho;
+        if (p) p[c0] = cs.pstar * cs.rho * CS2;
+        if (u)
+          for (int a = 0; a < 3; ++a) u[a * N + c0] = cs.u[a];
+      }
+}
+
+// Lattice tables for the pin tests: q = 15 or 27.
+int ora_tables(int q, int* c, double* w, int* opp, int* degree, double* M, double* Minv) {
+  const Lattice* L = (q == 15) ? &Q15() : (q == 27) ? &Q27() : nullptr;
+  if (!L) return -1;
+  for (int i = 0; i < L->q; ++i) {
+    for (int a = 0; a < 3; ++a) c[3 * i + a] = L->c[3 * i + a];
+    w[i] = L->w[i];
+    opp[i] = L->opp[i];
+    degree[i] = L->degree[i];
+  }
+  for (int k = 0; k < L->q * L->q; ++k) {
+    M[k] = L->M[k];
+    Minv[k] = L->Minv[k];
+  }
+  return L->q;
+}
+
+// One collision of a single g cell through the MRT machinery, for pin tests:
+// f, feq, src, rates (q each) -> out.
+void ora_mrt_collide(int q, const double* f, const double* feq, const double* src, const double* s, double* out) {
+  const Lattice& L = (q == 15) ? Q15() : Q27();
+  mrt_collide(L, f, feq, src, s, out);
+}
+
+}  // extern "C"

@@ -1,0 +1,180 @@
+"""Seeded synthetic inputs for the PFLBM workloads.
+
+This module builds initial fields (phi0, u0, p0) and parameter sets only; it
+holds none of the method's arithmetic (no equilibria, collisions or forces).
+Both the CUDA path and the CPU oracle take its arrays as inputs.
+
+Geometry follows the paper's setups: the diffuse interface is initialised with
+the tanh profile phi = 1/2 +- 1/2 tanh(d / (xi/2)) across the interface
+(section "Numerical experiments", initialisation of the PFLBM), heavy phase at
+phi = 1.  Cell i sits at coordinate i; walls (halfway bounce-back) sit at -1/2
+and n - 1/2.  Arrays are x-fastest: shape (nz, ny, nx); vectors (3, nz, ny, nx).
+"""
+from dataclasses import dataclass, field, asdict
+import math
+
+import numpy as np
+
+PERIODIC, NOSLIP = 0, 1
+
+
+@dataclass
+class Params:
+    nx: int
+    ny: int
+    nz: int
+    bc: tuple = (PERIODIC,) * 6          # -x,+x,-y,+y,-z,+z
+    rho_h: float = 1.0
+    rho_l: float = 1e-3
+    nu_h: float = 1.0 / 60.0
+    nu_l: float = 1.0 / 60.0
+    sigma: float = 1e-4
+    mobility: float = 0.02
+    xi: float = 5.0
+    gravity: tuple = (0.0, 0.0, 0.0)
+    collision: int = 0                    # 0 weighted-orthogonal MRT, 1 BGK
+
+    @property
+    def shape(self):
+        return (self.nz, self.ny, self.nx)
+
+    @property
+    def cells(self):
+        return self.nx * self.ny * self.nz
+
+    def oracle_kwargs(self):
+        d = asdict(self)
+        return d
+
+
+def coords(p):
+    z, y, x = np.meshgrid(np.arange(p.nz, dtype=np.float64), np.arange(p.ny, dtype=np.float64),
+                          np.arange(p.nx, dtype=np.float64), indexing="ij")
+    return x, y, z
+
+
+def tanh_profile(signed_distance, xi):
+    """phi across an interface; positive distance -> light phase (phi -> 0)."""
+    return 0.5 - 0.5 * np.tanh(signed_distance / (xi / 2.0))
+
+
+def sphere(p, center, radius, heavy_inside=True):
+    x, y, z = coords(p)
+    r = np.sqrt((x - center[0]) ** 2 + (y - center[1]) ** 2 + (z - center[2]) ** 2)
+    d = r - radius
+    return tanh_profile(d if heavy_inside else -d, p.xi)
+
+
+def cylinder_z(p, center, radius, heavy_inside=True):
+    x, y, _ = coords(p)
+    r = np.sqrt((x - center[0]) ** 2 + (y - center[1]) ** 2)
+    d = r - radius
+    return tanh_profile(d if heavy_inside else -d, p.xi)
+
+
+def wave(p, depth, amplitude, wavelength):
+    """Heavy phase below y = depth + amplitude cos(2 pi x / wavelength)."""
+    x, y, _ = coords(p)
+    ys = depth + amplitude * np.cos(2.0 * math.pi * x / wavelength)
+    return tanh_profile(y - ys, p.xi)
+
+
+def flat(p, y0):
+    _, y, _ = coords(p)
+    return tanh_profile(y - y0, p.xi)
+
+
+def noise(shape, seed, amplitude):
+    """Seeded uniform noise in [-amplitude, amplitude] (PCG64)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return amplitude * (2.0 * rng.random(shape) - 1.0)
+
+
+# ------------------------------------------------------------ workloads ----
+
+def static_drop(n=32, R=10.0, xi=5.0, sigma=1e-4, mobility=0.02, nu=1.0 / 60.0, rho_ratio=1000.0,
+                u_noise=0.0, seed=1234, collision=0):
+    """Static heavy drop of radius R centred in a periodic n^3 box."""
+    p = Params(n, n, n, (PERIODIC,) * 6, 1.0, 1.0 / rho_ratio, nu, nu, sigma, mobility, xi,
+               (0.0, 0.0, 0.0), collision)
+    c = (n - 1) / 2.0
+    phi0 = sphere(p, (c, c, c), R, heavy_inside=True)
+    u0 = noise((3,) + p.shape, seed, u_noise) if u_noise > 0 else None
+    return p, phi0, u0, None
+
+
+def static_cylinder(n=64, R=16.0, xi=5.0, sigma=1e-4, mobility=0.02, nu=1.0 / 60.0, rho_ratio=1000.0,
+                    collision=0):
+    """Quasi-2D static heavy column (n x n x 1, periodic); Laplace jump sigma/R."""
+    p = Params(n, n, 1, (PERIODIC,) * 6, 1.0, 1.0 / rho_ratio, nu, nu, sigma, mobility, xi,
+               (0.0, 0.0, 0.0), collision)
+    c = (n - 1) / 2.0
+    return p, cylinder_z(p, (c, c), R, heavy_inside=True), None, None
+
+
+def capillary_wave(L=200, ny=None, a0=None, xi=5.0, M=0.02, sigma=1e-4, nu=0.01, rho_ratio=1000.0,
+                   depth=None, collision=0):
+    """Standing capillary wave: L x ny x 1, periodic x and z, no-slip walls in y."""
+    ny = 2 * L if ny is None else ny
+    a0 = 0.01 * L if a0 is None else a0
+    depth = (ny - 1) / 2.0 if depth is None else depth
+    bc = (PERIODIC, PERIODIC, NOSLIP, NOSLIP, PERIODIC, PERIODIC)
+    p = Params(L, ny, 1, bc, 1.0, 1.0 / rho_ratio, nu, nu, sigma, M, xi, (0.0, 0.0, 0.0), collision)
+    return p, wave(p, depth, a0, float(L)), None, None
+
+
+def flat_interface(ny=64, xi=5.0, M=0.02, sigma=1e-4, nu=1.0 / 60.0, rho_ratio=1000.0, y0=None,
+                   collision=0):
+    """1 x ny x 1 column, walls in y, heavy phase below y0."""
+    y0 = (ny - 1) / 2.0 if y0 is None else y0
+    bc = (PERIODIC, PERIODIC, NOSLIP, NOSLIP, PERIODIC, PERIODIC)
+    p = Params(1, ny, 1, bc, 1.0, 1.0 / rho_ratio, nu, nu, sigma, M, xi, (0.0, 0.0, 0.0), collision)
+    return p, flat(p, y0), None, None
+
+
+def poiseuille(H=16, nx=1, g=1e-6, nu=1.0 / 8.0, collision=0):
+    """Single-phase channel (phi = 1), walls in y, body force along x."""
+    bc = (PERIODIC, PERIODIC, NOSLIP, NOSLIP, PERIODIC, PERIODIC)
+    p = Params(nx, H, 1, bc, 1.0, 1e-3, nu, nu, 1e-4, 0.02, 5.0, (g, 0.0, 0.0), collision)
+    return p, np.ones(p.shape), None, None
+
+
+def rising_bubble(nx=128, ny=384, nz=128, D=32.0, xi=4.0, M=0.02, rho_ratio=1000.0, mu_ratio=100.0,
+                  Eo=10.0, Mo=1e-3, nu_h=1.0 / 60.0, collision=0):
+    """Gas bubble of diameter D at 1.5 D above the bottom (y up), walls on all sides.
+
+    Gravity and sigma from the Eotvos and Morton numbers with the heavy-phase
+    viscosity fixed: g = nu_h^2 Eo^{3/2} / (D^3 sqrt(Mo)), sigma = g D^2 / Eo
+    (rho_h = 1); nu_l = nu_h rho_ratio / mu_ratio (dynamic viscosity ratio).
+    """
+    g = nu_h ** 2 * Eo ** 1.5 / (D ** 3 * math.sqrt(Mo))
+    sigma = g * D * D / Eo
+    nu_l = nu_h * rho_ratio / mu_ratio
+    p = Params(nx, ny, nz, (NOSLIP,) * 6, 1.0, 1.0 / rho_ratio, nu_h, nu_l, sigma, M, xi,
+               (0.0, -g, 0.0), collision)
+    c = ((nx - 1) / 2.0, 1.5 * D, (nz - 1) / 2.0)
+    return p, sphere(p, c, D / 2.0, heavy_inside=False), None, None
+
+
+def drop_impact(nx=512, ny=384, nz=512, D=64.0, depth=128.0, gap=8.0, We=200.0, Fr=200.0, U=0.05,
+                omega_h=1.988, rho_ratio=1000.0, mu_ratio=50.0, xi=5.0, M=0.02, collision=0):
+    """Vertical drop impact into a pool (y up), no-slip walls on all sides.
+
+    sigma = rho_h U^2 D / We, g = U^2 / (Fr D), nu_h from omega_h,
+    nu_l = nu_h rho_ratio / mu_ratio; the drop moves down with speed U.
+    """
+    sigma = U * U * D / We
+    g = U * U / (Fr * D)
+    nu_h = (1.0 / omega_h - 0.5) / 3.0
+    nu_l = nu_h * rho_ratio / mu_ratio
+    p = Params(nx, ny, nz, (NOSLIP,) * 6, 1.0, 1.0 / rho_ratio, nu_h, nu_l, sigma, M, xi,
+               (0.0, -g, 0.0), collision)
+    x, y, z = coords(p)
+    cy = depth + gap + D / 2.0
+    c = ((nx - 1) / 2.0, cy, (nz - 1) / 2.0)
+    drop = sphere(p, c, D / 2.0, heavy_inside=True)
+    pool = tanh_profile(y - depth, xi)
+    phi0 = np.maximum(drop, pool)
+    u0 = np.zeros((3,) + p.shape)
+    u0[1] = -U * drop * (y > depth + gap / 2.0)
+    return p, phi0, u0, None

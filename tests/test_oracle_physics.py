@@ -1,0 +1,201 @@
+"""Physics pins of the FP64 oracle (no GPU).
+
+Each test checks the oracle against something the paper or the mathematics
+fixes, chosen so that a plausible mistake in one part fails one of them:
+
+  mass            -- the conservative Allen-Cahn model conserves sum(phi)
+                     (section "Conservation of mass"); collision and streaming
+                     only redistribute h.
+  diffusion       -- with xi -> infinity the interface term vanishes and the
+                     phase-field LBE is pure diffusion with coefficient M
+                     (Eq. pflbm-tau read as the shifted time): pins omega_phi.
+  advection       -- a slab in uniform flow moves at u: pins c.u in h^eq.
+  tanh profile    -- a flat interface keeps the initial tanh profile of width
+                     xi (initialisation formula of the PFLBM): pins F^phi and
+                     its normalisation together with omega_phi.
+  Laplace         -- static column: p_in - p_out = sigma / R: pins beta, kappa
+                     of the chemical potential and F_s, F_p.
+  Poiseuille      -- single phase, body force, halfway bounce-back walls: with
+                     degree-2 rate omega and degree >= 3 rate 1 the wall sits
+                     exactly half-way at nu = 1/8 (Lambda = 3/16): pins nu(tau),
+                     F_b, Guo forcing and bounce-back to round-off.
+  two-layer flow  -- density and viscosity contrast: continuity of the dynamic
+                     shear stress needs F_mu; pins F_mu, rho(phi), tau(phi).
+  capillary wave  -- half-period against Prosperetti's model (section
+                     "Capillary wave"); loose at this small L (diffuse
+                     interface of Cn = xi/L = 0.125).
+  symmetry        -- a centred drop stays mirror- and permutation-symmetric:
+                     catches transposed components and index errors.
+  BGK special case-- the full simulation with MRT rates all equal equals BGK.
+"""
+import numpy as np
+import pytest
+from scipy.optimize import curve_fit
+
+import analytic as A
+import oracle
+from paper_2206_11637_gb300 import workloads as W
+
+THREADS = 8
+
+
+def run(p, phi0, u0=None, p0=None, n=0):
+    o = oracle.from_params(p, phi0, u0, p0)
+    o.step(n, THREADS)
+    return o
+
+
+def test_mass_conservation_3d_drop():
+    p, phi0, u0, _ = W.static_drop(24, 7.0, u_noise=1e-3, seed=1234)
+    o = run(p, phi0, u0, n=60)
+    phi = o.fields()[0]
+    assert abs(phi.sum() - phi0.sum()) / phi0.sum() < 1e-12
+
+
+def test_mass_conservation_walls():
+    p, phi0, _, _ = W.capillary_wave(24, ny=24, a0=1.0, xi=4.0)
+    o = run(p, phi0, n=200)
+    assert abs(o.fields()[0].sum() - phi0.sum()) / phi0.sum() < 1e-12
+
+
+def test_diffusion_rate_is_mobility():
+    M = 0.05
+    p = W.Params(64, 1, 1, (0,) * 6, 1.0, 1.0, 1 / 6, 1 / 6, 0.0, M, 1e9)
+    x = np.arange(64.0)
+    k = 2 * np.pi / 64
+    phi0 = (0.5 + 0.1 * np.sin(k * x)).reshape(1, 1, 64)
+    n = 400
+    phi = run(p, phi0, n=n).fields()[0].ravel()
+    amp = np.abs(np.fft.rfft(phi - 0.5)[1]) * 2 / 64
+    D_measured = -np.log(amp / 0.1) / (k * k * n)
+    assert abs(D_measured / M - 1) < 0.01
+
+
+def test_advection_speed():
+    p = W.Params(128, 1, 1, (0,) * 6, 1.0, 1e-3, 1 / 6, 1 / 6, 1e-4, 0.02, 5.0)
+    xx = np.arange(128.0)
+    phi0 = W.tanh_profile(np.abs(xx - 40.0) - 15.0, 5.0).reshape(1, 1, 128)
+    u0 = np.zeros((3, 1, 1, 128))
+    u0[0] = 0.02
+    phi = run(p, phi0, u0, n=1000).fields()[0].ravel()
+    centre = np.angle(np.sum(phi * np.exp(2j * np.pi * xx / 128))) * 128 / (2 * np.pi)
+    assert abs((centre - 40.0) / 20.0 - 1) < 5e-3
+
+
+def test_flat_interface_keeps_tanh_width():
+    xi = 5.0
+    p, phi0, _, _ = W.flat_interface(64, xi=xi)
+    phi = run(p, phi0, n=3000).fields()[0][0, :, 0]
+    f = lambda y, y0, w: 0.5 - 0.5 * np.tanh((y - y0) / (w / 2))
+    (y0, w), _ = curve_fit(f, np.arange(64.0), phi, p0=[31.5, xi])
+    assert abs(w / xi - 1) < 0.015
+    assert abs(y0 - 31.5) < 1e-4
+
+
+def test_laplace_pressure_column():
+    R = 16.0
+    p, phi0, _, _ = W.static_cylinder(64, R, nu=1 / 6)
+    _, _, pr, u = run(p, phi0, n=2500).fields()
+    dp = pr[0, 30:34, 30:34].mean() - pr[0, 0:2, 0:2].mean()
+    assert abs(dp / (p.sigma / R) - 1) < 0.02
+    assert np.abs(u).max() < 1e-5
+
+
+@pytest.mark.parametrize("H", [8, 16])
+def test_poiseuille_exact(H):
+    g, nu = 1e-6, 1 / 8
+    p, phi0, _, _ = W.poiseuille(H, g=g, nu=nu)
+    u = run(p, phi0, n=int(6 * H * H / nu)).fields()[3][0, 0, :, 0]
+    ua = A.poiseuille(np.arange(H), H, g, nu)
+    assert np.linalg.norm(u - ua) / np.linalg.norm(ua) < 1e-10
+
+
+def test_two_layer_flow_needs_dynamic_stress_continuity():
+    H, g = 32, 1e-6
+    p = W.Params(1, H, 1, (0, 0, 1, 1, 0, 0), 1.0, 0.1, 1 / 6, 1 / 6, 1e-4, 0.02, 4.0, (g, 0.0, 0.0))
+    u = run(p, W.flat(p, 15.5), n=30000).fields()[3][0, 0, :, 0]
+    right = A.two_layer_poiseuille(np.arange(H), H, 16.0, g, 1.0, 1 / 6, 0.1, 0.1 / 6)
+    wrong = A.two_layer_poiseuille(np.arange(H), H, 16.0, g, 1.0, 1 / 6, 0.1, 1 / 6)
+    assert np.linalg.norm(u - right) / np.linalg.norm(right) < 0.06
+    assert np.linalg.norm(u - wrong) / np.linalg.norm(wrong) > 0.5
+
+
+def test_capillary_wave_half_period():
+    L, sigma, nu, a0 = 32, 1e-4, 0.002, 0.5
+    k = 2 * np.pi / L
+    p, phi0, _, _ = W.capillary_wave(L, ny=L, a0=a0, xi=4.0, M=0.02, sigma=sigma, nu=nu)
+    o = oracle.from_params(p, phi0)
+    T = 2 * np.pi / A.capillary_omega0(sigma, k, 1.0, 1e-3)
+    dt = int(T / 80)
+    ts, amps = [], []
+    while o.time < 1.6 * T:
+        ts.append(o.time)
+        amps.append(A.interface_height(o.fields()[0][0, :, 0]) - (L - 1) / 2)
+        o.step(dt, THREADS)
+    ts, amps = np.array(ts), np.array(amps)
+    an = A.prosperetti(ts, k, nu, 1.0, 1e-3, sigma, a0)
+
+    def crossings(a):
+        return np.array([ts[i] + a[i] / (a[i] - a[i + 1]) * (ts[i + 1] - ts[i])
+                         for i in range(len(a) - 1) if (a[i] > 0) != (a[i + 1] > 0)])
+
+    cs, ca = crossings(amps), crossings(an)
+    assert len(cs) >= 2
+    ratio = (cs[1] - cs[0]) / (ca[1] - ca[0])
+    assert 1.0 < ratio < 1.12
+    # the wave is damped: the first trough is shallower than a0
+    assert -a0 < amps.min() < -0.5 * a0
+
+
+def test_drop_symmetry():
+    n = 16
+    p, phi0, _, _ = W.static_drop(n, 5.0)
+    # break the cubic symmetry only by a symmetric velocity along x
+    u0 = np.zeros((3, n, n, n))
+    x = np.arange(n) - (n - 1) / 2
+    u0[0] = 1e-3 * np.sin(2 * np.pi * x / n)[None, None, :] * 0 + 1e-3 * x[None, None, :] / n
+    o = run(p, phi0, u0, n=40)
+    phi, rho, pr, u = o.fields()
+    # mirror in x: phi even, u_x odd; mirror in y and z as well
+    assert np.abs(phi - phi[:, :, ::-1]).max() < 1e-13
+    assert np.abs(u[0] + u[0][:, :, ::-1]).max() < 1e-13
+    assert np.abs(phi - phi[:, ::-1, :]).max() < 1e-13
+    assert np.abs(u[1] + u[1][:, ::-1, :]).max() < 1e-13
+    # y <-> z exchange symmetry (u0 has no y/z parts)
+    assert np.abs(phi - phi.transpose(1, 0, 2)).max() < 1e-13
+    assert np.abs(u[1] - u[2].transpose(1, 0, 2)).max() < 1e-13
+
+
+def test_bgk_special_case_full_step():
+    p, phi0, u0, _ = W.static_drop(12, 4.0, rho_ratio=10.0, u_noise=1e-3, seed=5)
+    a = run(p, phi0, u0, n=20)
+    p.collision = oracle.COLL_BGK
+    b = run(p, phi0, u0, n=20)
+    p.collision = oracle.COLL_MRT_ALL_EQUAL
+    c = run(p, phi0, u0, n=20)
+    hb, gb = b.populations()
+    hc, gc = c.populations()
+    assert np.abs(hb - hc).max() < 1e-13 and np.abs(gb - gc).max() < 1e-13
+    ha, ga = a.populations()
+    assert np.abs(ha - hb).max() > 1e-9   # the weighted MRT is a different operator
+
+
+def test_prosperetti_limits():
+    k, a0 = 2 * np.pi / 32, 0.5
+    assert abs(A.prosperetti(np.array([0.0]), k, 0.01, 1.0, 1e-3, 1e-3, a0)[0] - a0) < 1e-12
+    t = np.linspace(0, 3000, 7)
+    w0 = A.capillary_omega0(1e-3, k, 1.0, 1e-3)
+    inviscid = A.prosperetti(t, k, 1e-10, 1.0, 1e-3, 1e-3, a0)
+    assert np.abs(inviscid - a0 * np.cos(w0 * t)).max() < 1e-5
+    # weak viscosity: close to the damped oscillator a0 exp(-2 nu k^2 t) cos(w0 t)
+    nu = 1e-4
+    weak = A.prosperetti(t, k, nu, 1.0, 0.0, 1e-3, a0)
+    w0s = A.capillary_omega0(1e-3, k, 1.0, 0.0)
+    assert np.abs(weak - a0 * np.exp(-2 * nu * k * k * t) * np.cos(w0s * t)).max() < 0.02 * a0
+
+
+def test_two_layer_closed_form_reduces_to_poiseuille():
+    y = np.arange(32)
+    a = A.two_layer_poiseuille(y, 32, 11.0, 1e-6, 1.0, 0.2, 1.0, 0.2)
+    b = A.poiseuille(y, 32, 1e-6, 0.2)
+    assert np.abs(a - b).max() < 1e-15
