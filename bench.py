@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Benchmark of the PFLBM hot path on GB300: MLUPS and fraction of HBM peak.
+
+One benchmark step = one segment of S lattice time steps of the workload (the
+fused stream-collide of h and g plus the phi pass per time step), run through
+the C interface.  Default workload: the standing capillary wave, 200 x 400 x 1
+cells (periodic x, z; no-slip walls in y), rho ratio 1000, nu = 0.01,
+sigma = 1e-4, xi = 5, M = 0.02; S = 2000 so ten steps cover its 20000 time
+steps.  The headline precision is the shifted-FP16 storage (FP32 arithmetic);
+FP64 and FP32 are timed in the same run.
+
+  value     MLUPS with the state resident in HBM (device timing, CUDA events);
+  e2e       MLUPS through the public API with host buffers: pfl_init from a
+            pinned host phi0 (H2D), S steps, pfl_fields of phi to the host (D2H);
+  roofline  the stream-collide kernel's algorithmic bytes per launch over its
+            CUDA-event duration, against the measured HBM copy bandwidth;
+  cpu_baseline  the FP64 CPU oracle on the host cores over a bounded sample.
+
+--impl reference times that oracle as the reference arm.  Under torchrun every
+rank runs an independent replica (the path is a single domain per GPU).
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PFLBM MLUPS & % HBM peak, mixed vs FP64 at stated error; adjoint/forward"
+UNIT = "MLUPS"
+L2_BYTES = 129 * 2 ** 20
+
+PREC_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2}
+PHI_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 4}
+
+
+def step_kernel_bytes(prec):
+    """Algorithmic bytes per cell of one stream-collide launch: every h and g
+    population read once and written once, phi read once (stencil), plus the
+    phi shift of the FP16S format."""
+    b = 2 * (15 + 27) * PREC_BYTES[prec] + PHI_BYTES[prec]
+    if prec == "fp16s":
+        b += PHI_BYTES[prec]
+    return b
+
+
+def ideal_step_bytes(prec):
+    """Algorithmic bytes per cell update of the whole step: 2 (15 + 27) S + phi read + phi write."""
+    return 2 * (15 + 27) * PREC_BYTES[prec] + 2 * PHI_BYTES[prec]
+
+
+def workload(name):
+    from paper_2206_11637_gb300 import workloads as W
+    if name == "capillary_wave":
+        p, phi0, u0, p0 = W.capillary_wave(200)
+        return dict(p=p, phi0=phi0, u0=u0, p0=p0, S=2000, total=20000, prec="fp16s",
+                    desc="standing capillary wave 200x400x1, walls in y, rho ratio 1000, nu 0.01, sigma 1e-4, xi 5, M 0.02")
+    if name == "static_drop":
+        p, phi0, u0, p0 = W.static_drop(32, 10.0)
+        return dict(p=p, phi0=phi0, u0=u0, p0=p0, S=100, total=1000, prec="fp64",
+                    desc="static drop 32^3 periodic, R 10, xi 5, rho ratio 1000, sigma 1e-4, M 0.02")
+    if name == "rising_bubble":
+        p, phi0, u0, p0 = W.rising_bubble()
+        return dict(p=p, phi0=phi0, u0=u0, p0=p0, S=200, total=4000, prec="fp32",
+                    desc="rising bubble 128x384x128, walls, D 32, Eo 10, Mo 1e-3, xi 4, M 0.02")
+    if name == "drop_impact":
+        p, phi0, u0, p0 = W.drop_impact()
+        return dict(p=p, phi0=phi0, u0=u0, p0=p0, S=100, total=10000, prec="fp16s",
+                    desc="drop impact 512x384x512, walls, D 64, We 200, Fr 200, xi 5, M 0.02")
+    raise SystemExit("unknown workload " + name)
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in ("kernels.cuh", "lattice.cuh"):
+        with open(os.path.join(ROOT, "paper_2206_11637_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+# DRAM bytes per launch of the stream-collide kernel from ncu captures
+# (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload, precision
+# and the hash of the kernel sources they were taken on.  A capture of another
+# kernel version does not apply.
+NCU_TRAFFIC = {}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi clock and throttle sampling during the timed region."""
+
+    def __init__(self):
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, device_index=0):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != device_index:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for k, nm in enumerate(names):
+                    if parts[5 + k].lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def mlups(cells, steps, seconds):
+    return cells * steps / seconds / 1e6
+
+
+def cpu_oracle_rate(wl, budget_s=12.0):
+    """FP64 oracle MLUPS on the host cores over a bounded sample of the workload."""
+    import oracle
+    oracle.build_oracle()
+    p = wl["p"]
+    o = oracle.from_params(p, wl["phi0"], wl["u0"], wl["p0"])
+    threads = os.cpu_count() or 1
+    o.step(1, threads)                      # warm-up (thread pool, caches)
+    t0 = time.perf_counter()
+    o.step(2, threads)
+    per = (time.perf_counter() - t0) / 2
+    n = max(2, min(2000, int(budget_s / max(per, 1e-9))))
+    t0 = time.perf_counter()
+    o.step(n, threads)
+    dt = time.perf_counter() - t0
+    return dict(value=mlups(p.cells, n, dt), unit=UNIT, cores=threads, kind="oracle",
+                sample="%d time steps of the full %dx%dx%d lattice (FP64, %d threads, %.1f s)"
+                       % (n, p.nx, p.ny, p.nz, threads, dt))
+
+
+def run_reference(args, wl):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build_oracle()
+    p = wl["p"]
+    threads = os.cpu_count() or 1
+    o = oracle.from_params(p, wl["phi0"], wl["u0"], wl["p0"])
+    o.step(1, threads)
+    t0 = time.perf_counter()
+    o.step(1, threads)
+    per = time.perf_counter() - t0
+    # one benchmark step = a bounded sample of lattice steps (about 3 s)
+    n_per = max(1, min(wl["S"], int(3.0 / max(per, 1e-9))))
+    for _ in range(args.warmup):
+        o.step(n_per, threads)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(n_per, threads)
+    dt = time.perf_counter() - t0
+    v = mlups(p.cells, n_per * args.steps, dt)
+    sample = "%d lattice steps of the full %dx%dx%d lattice per benchmark step (FP64 oracle, %d threads)" % (
+        n_per, p.nx, p.ny, p.nz, threads)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": wl["desc"], "cells": p.cells,
+                       "lattice_steps_per_step": n_per},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="capillary_wave",
+                    choices=["capillary_wave", "static_drop", "rising_bubble", "drop_impact"])
+    ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "fp16s"])
+    ap.add_argument("--lattice-steps", type=int, default=None, help="lattice steps per benchmark step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    wl = workload(args.workload)
+    if args.lattice_steps:
+        wl["S"] = args.lattice_steps
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        dist = None
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_2206_11637_gb300 import build as B
+    if rank == 0 or ws == 1:
+        B.build_library()
+    if dist:
+        dist.barrier()
+    from paper_2206_11637_gb300.pflbm import Simulation
+
+    p = wl["p"]
+    N = p.cells
+    S = wl["S"]
+    prec = args.precision or wl["prec"]
+    work_bytes = N * (2 * 42 * PREC_BYTES[prec] // 2 + 2 * PHI_BYTES[prec])
+    flush = work_bytes < 4 * L2_BYTES
+    flush_buf = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev) if flush else None
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def timed_device(precision, K, Wm):
+        sim = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision=precision, device=dev)
+        for _ in range(Wm):
+            sim.step(S)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier()
+        clk = Clocks()
+        if precision == prec:
+            clk.start()
+        t0 = time.perf_counter()
+        for k in range(K):
+            if flush:
+                flush_buf.fill_(float(k))
+            evs[k][0].record(stream)
+            sim.step(S)
+            evs[k][1].record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        clocks = clk.stop(dev.index or 0) if precision == prec else None
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        out, nf = sim.diag(check=False)
+        return sim, ms, wall, clocks, nf
+
+    K, Wm = args.steps, args.warmup
+    sim, ms, wall, clocks, nf = timed_device(prec, K, Wm)
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = mlups(N, S * K, ms / 1e3) * ws
+
+    # roofline of the stream-collide kernel (CUDA events around each launch)
+    n_rt = min(S, 400)
+    kms, pms = sim.kernel_times(n_rt)
+    avg_s = kms / n_rt / 1e3
+    peak, peak_kind = peaks()
+    achieved = N * step_kernel_bytes(prec) / avg_s / 1e9
+    traffic = NCU_TRAFFIC.get((args.workload, prec, kernel_hash()))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_step (fused h+g stream-collide)",
+                "bytes_per_cell": step_kernel_bytes(prec), "peak_source": peak_kind,
+                "kernel_share": kms / (kms + pms),
+                "whole_step_ideal_frac": mlups(N, n_rt, (kms + pms) / 1e3) * 1e6 * ideal_step_bytes(prec) / 1e9 / peak,
+                "working_set_bytes": work_bytes, "l2_resident": work_bytes < L2_BYTES}
+    del sim
+
+    # e2e through the public API with host buffers
+    phi0_pin = torch.from_numpy(np.ascontiguousarray(wl["phi0"], dtype=np.float64).reshape(-1)).pin_memory()
+    phi_out = torch.empty(N, dtype=torch.float64).pin_memory()
+    from paper_2206_11637_gb300 import _lib as L
+    import ctypes
+
+    def e2e_once():
+        s = Simulation(p, phi0_pin, None, None, precision=prec, device=dev)
+        s.step(S)
+        L.check(s.lib.pfl_fields(s.ctx, ctypes.c_void_p(phi_out.data_ptr()), None, None, None))
+        s.close()
+
+    for _ in range(2):
+        e2e_once()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K):
+        e2e_once()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": mlups(N, S * K, e2e_s) * ws, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+           "d2h_bytes_per_step": N * 8}
+
+    # the other precisions and the error of the headline precision against FP64
+    compare = {}
+    if not args.no_compare and rank == 0:
+        for other in ("fp64", "fp32", "fp16s"):
+            if other == prec:
+                continue
+            s2, ms2, _, _, _ = timed_device(other, max(2, K // 3), 3)
+            compare[other + "_mlups"] = mlups(N, S * max(2, K // 3), ms2 / 1e3)
+            del s2
+        compare["speedup_vs_fp64"] = value / ws / compare["fp64_mlups"] if "fp64_mlups" in compare else None
+        n_acc = min(wl["total"], 2000)
+        ref = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision="fp64", device=dev)
+        ref.step(n_acc)
+        tst = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision=prec, device=dev)
+        tst.step(n_acc)
+        f64 = ref.fields()
+        ftst = tst.fields()
+        umax = max(np.abs(f64[3]).max(), 1e-300)
+        compare["error_vs_fp64"] = {"lattice_steps": n_acc,
+                                    "phi_max_abs": float(np.abs(ftst[0] - f64[0]).max()),
+                                    "u_max_over_umax": float(np.abs(ftst[3] - f64[3]).max() / umax)}
+        del ref, tst
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate(wl)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
+                "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f16 storage / f32 arithmetic" if prec == "fp16s" else ("f32" if prec == "fp32" else "f64"),
+                "data": "synthetic",
+                "config": {"workload": args.workload, "description": wl["desc"], "precision": prec,
+                           "cells": N, "lattice_steps_per_step": S, "parallelism": "replicas" if ws > 1 else "1 GPU",
+                           "l2": "flushed between timed steps" if flush else "working set larger than L2"},
+                "e2e": e2e, "gpu_launches": 2 * S * K, "clocks": clocks, "roofline": roofline,
+                "cpu_baseline": cpu, "nonfinite_cells": nf, "wall_s": wall}
+        line.update(compare)
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+/*
+ * pflbm.h -- C interface of the GB300 conservative Allen-Cahn phase-field
+ * lattice Boltzmann method (PFLBM) library, libpflbm.so.
+ *
+ * The method (section "Conservative Allen-Cahn model" of Schwarzmeier et al.,
+ * "Comparison of free-surface and conservative Allen-Cahn phase-field lattice
+ * Boltzmann method"):
+ *   - phase-field PDFs h_i on D3Q15 with phi = sum_i h_i (Eq. zeroth_moment_phase),
+ *     relaxation time tau_phi = M / c_s^2 (Eq. pflbm-tau, read as the shifted
+ *     time: omega_phi = 1 / (3 M + 1/2)) and the Allen-Cahn forcing
+ *     F^phi = 4 phi (1 - phi) / xi * n applied with Guo's scheme;
+ *   - hydrodynamic PDFs g_i on D3Q27 with normalised pressure p* = sum_i g_i
+ *     (Eq. zeroth_moment_hydro), incompressible equilibrium (Eq. feq with
+ *     rho_0 = 1), forces F = F_s + F_b + F_p + F_mu;
+ *   - rho(phi) and tau(phi) linearly interpolated between the phases;
+ *   - weighted-orthogonal MRT collision (Eq. mrt) fused with streaming (Eq. LBE).
+ *
+ * Conventions
+ *   - Cells are x-fastest: cell = x + nx * (y + ny * z).  Scalar fields are N
+ *     doubles, vector fields are 3N doubles SoA (all x, then all y, then all z).
+ *   - Population order ("canonical"): loop cz, cy, cx over -1, 0, 1 with cx
+ *     fastest; D3Q27 keeps all 27 (index 9(cz+1) + 3(cy+1) + (cx+1)), D3Q15
+ *     keeps the 15 with |c|^2 in {0, 1, 3}.  Populations are SoA [i][cell].
+ *   - Faces are ordered -x, +x, -y, +y, -z, +z.  Both faces of one axis must
+ *     carry the same kind.  No-slip faces use halfway bounce-back; the phi
+ *     stencil mirrors phi across them.
+ *   - Heavy phase phi = 1 (rho_h), light phase phi = 0 (rho_l).
+ *   - All device work is queued on the stream passed to pfl_init; calls that
+ *     return data to the host synchronise that stream.
+ *
+ * Memory ownership: the library never allocates device memory.  The caller
+ * allocates one device buffer of pfl_workspace_bytes() bytes (for example a
+ * torch uint8 tensor), passes it to pfl_init and keeps it alive until
+ * pfl_destroy.  The context itself is a small host object owned by the library.
+ *
+ * Errors: every call returns a pfl_status.  PFL_ERR_ARG leaves the context
+ * untouched; PFL_ERR_CUDA means a CUDA call failed (the context should be
+ * destroyed); pfl_last_error() returns a message for the calling thread.
+ */
+#ifndef PFLBM_H
+#define PFLBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pfl_ctx pfl_ctx;
+
+typedef enum {
+  PFL_OK = 0,
+  PFL_ERR_ARG = 1,      /* invalid argument or parameter set                  */
+  PFL_ERR_CUDA = 2,     /* a CUDA runtime call failed                          */
+  PFL_ERR_OOM = 3,      /* workspace too small                                 */
+  PFL_ERR_UNSTABLE = 4, /* the last diagnostic found NaN/Inf in phi            */
+  PFL_ERR_STATE = 5     /* call not valid in the context's current state       */
+} pfl_status;
+
+/* Storage precision of the populations.  PFL_FP64: FP64 storage and arithmetic
+ * (reference mode).  PFL_FP32: FP32 storage and arithmetic.  PFL_FP16S
+ * (shifted FP16 storage): each population is stored in FP16 as its deviation
+ * from a rest equilibrium -- h_i from w_i phi of the cell that wrote it, g_i
+ * from zero (the rest equilibrium of p* = 0) -- divided by its lattice weight
+ * and scaled by a power of two; arithmetic in FP32; phi kept in FP32. */
+typedef enum { PFL_FP64 = 0, PFL_FP32 = 1, PFL_FP16S = 2 } pfl_precision;
+
+typedef enum { PFL_PERIODIC = 0, PFL_NOSLIP = 1 } pfl_bc;
+
+/* PFL_MRT: weighted-orthogonal MRT (degree-2 moments of g at omega(phi), of h
+ * at omega_phi together with degree 1; all higher moments at rate 1).
+ * PFL_BGK: single rate per lattice (Eq. BGK), a special case kept for testing. */
+typedef enum { PFL_MRT = 0, PFL_BGK = 1 } pfl_collision;
+
+typedef struct {
+  int nx, ny, nz;      /* lattice cells, each >= 1                                  */
+  int bc[6];           /* pfl_bc per face -x,+x,-y,+y,-z,+z                          */
+  double rho_h, rho_l; /* phase densities (> 0), rho_h is the reference density     */
+  double nu_h, nu_l;   /* kinematic viscosities; tau = 3 nu + 1/2 per phase (Eq. kin-viscosity) */
+  double sigma;        /* surface tension (>= 0)                                     */
+  double mobility;     /* M > 0                                                      */
+  double xi;           /* interface width (> 0), lattice units                       */
+  double gravity[3];   /* body-force acceleration g, F_b = rho g                      */
+  int precision;       /* pfl_precision                                              */
+  int collision;       /* pfl_collision                                              */
+} pfl_params;
+
+/* Device bytes the workspace must hold for these parameters (0 if invalid). */
+size_t pfl_workspace_bytes(const pfl_params* p);
+
+/* Create a context and write the initial state.
+ *   phi0: N doubles, required.  u0: 3N doubles SoA or NULL (zero).  p0: N
+ *   doubles of initial normalised pressure p* or NULL (zero).  Each may be a
+ *   host or a device pointer.  The populations start at their equilibria
+ *   h^eq(phi0, u0) and g^eq(p0, u0); phi is then recomputed as sum_i h_i.
+ *   workspace: device pointer, >= pfl_workspace_bytes(p) bytes, 256-byte aligned.
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ * Rejects (PFL_ERR_ARG) omega_h, omega_l or omega_phi outside (0, 2), M <= 0,
+ * xi <= 0, densities <= 0, dims < 1, mixed face kinds on one axis. */
+pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, const double* p0,
+                    void* workspace, size_t workspace_bytes, void* stream, pfl_ctx** out);
+
+/* Advance n_steps >= 0 time steps.  Asynchronous: only queues kernels. */
+pfl_status pfl_step(pfl_ctx* ctx, int n_steps);
+
+/* Macroscopic fields at the current time: phi, rho(phi), p = p* rho c_s^2
+ * (Eq. zeroth_moment_hydro and the definition of p*) and u = sum_i c_i g_i +
+ * F / (2 rho) (3N SoA).  Any pointer may be NULL; each may be host or device.
+ * Synchronises the stream. */
+pfl_status pfl_fields(pfl_ctx* ctx, double* phi, double* rho, double* p, double* u);
+
+/* Populations at the current time in canonical order and layout, converted to
+ * FP64: h is 15N, g is 27N doubles (either may be NULL; host or device).
+ * Synchronises. */
+pfl_status pfl_populations(pfl_ctx* ctx, double* h, double* g);
+
+/* Overwrite the populations (canonical order, FP64, host or device; rounded
+ * to the storage precision) and recompute phi.  Synchronises. */
+pfl_status pfl_set_populations(pfl_ctx* ctx, const double* h, const double* g);
+
+/* FP64 reductions over the domain (section "Rising bubble": centre of mass):
+ *   out[0] = sum phi, out[1..3] = sum phi * (x, y, z),
+ *   out[4] = sum (1 - phi), out[5..7] = sum (1 - phi) * (x, y, z).
+ * nonfinite (may be NULL) receives the number of cells whose phi is NaN/Inf.
+ * Returns PFL_ERR_UNSTABLE when that number is non-zero.  Synchronises. */
+pfl_status pfl_diag(pfl_ctx* ctx, double out[8], long long* nonfinite);
+
+/* Advance n_steps > 0 steps like pfl_step, recording a CUDA event pair on the
+ * context's stream around every kernel launch; ms[0] receives the summed
+ * device time of the stream-collide kernel, ms[1] that of the phi pass
+ * (section "The lattice Boltzmann method": the fused collide-stream, then
+ * phi = sum h).  Measurement aid; synchronises. */
+pfl_status pfl_kernel_times(pfl_ctx* ctx, int n_steps, double ms[2]);
+
+/* Time steps taken since pfl_init (or -1 for a NULL context). */
+long long pfl_time(const pfl_ctx* ctx);
+
+/* Release the host context (the caller frees the workspace afterwards). */
+void pfl_destroy(pfl_ctx* ctx);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* pfl_last_error(void);
+
+/* Library interface version (1). */
+int pfl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFLBM_H */

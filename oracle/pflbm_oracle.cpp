@@ -32,7 +32,9 @@
 //     u0 = sum c g + (F_s + F_b + F_p) / (2 rho);
 //   rates: g -- degree 2 at omega(phi), degree >= 3 at 1; h -- degrees 1 and 2
 //     at omega_phi, degree >= 3 at 1; conserved moments at 0 / 1 (irrelevant);
-//   n = grad(phi) / (|grad(phi)| + 1e-12).
+//   n = grad(phi) / (|grad(phi)| + 1e-6): the regularisation sits far below the
+//     gradients of the interface region and far above the rounding noise of
+//     the stencil, so that n stays well conditioned where grad(phi) -> 0.
 //
 // Schedule per step: both collisions use phi^t and its stencil, u^t from g in
 // the same cell; then both sets stream; then phi^{t+1} = sum h.
@@ -385,7 +387,7 @@ void do_step(Sim& S) {
         double gnorm = std::sqrt(cs.gradphi[0] * cs.gradphi[0] + cs.gradphi[1] * cs.gradphi[1] +
                                  cs.gradphi[2] * cs.gradphi[2]);
         double n[3];
-        for (int a = 0; a < 3; ++a) n[a] = cs.gradphi[a] / (gnorm + 1e-12);
+        for (int a = 0; a < 3; ++a) n[a] = cs.gradphi[a] / (gnorm + 1e-6);
         double theta = 4.0 * cs.phi * (1.0 - cs.phi) / P.xi;
         double heq[15], Sh[15], hpost[15], s15[15];
         for (int i = 0; i < 15; ++i) {

@@ -1,0 +1,89 @@
+"""ctypes binding of libpflbm.so (include/pflbm.h): argument marshalling only.
+
+Every step of the PFLBM path runs in the library's CUDA kernels.  Loading fails
+loudly when the library has not been built; there is no CPU fallback.
+"""
+import ctypes
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpflbm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pflbm.h")
+
+PFL_OK, PFL_ERR_ARG, PFL_ERR_CUDA, PFL_ERR_OOM, PFL_ERR_UNSTABLE, PFL_ERR_STATE = range(6)
+PFL_FP64, PFL_FP32, PFL_FP16S = 0, 1, 2
+PFL_PERIODIC, PFL_NOSLIP = 0, 1
+PFL_MRT, PFL_BGK = 0, 1
+STATUS_NAMES = {0: "PFL_OK", 1: "PFL_ERR_ARG", 2: "PFL_ERR_CUDA", 3: "PFL_ERR_OOM", 4: "PFL_ERR_UNSTABLE",
+                5: "PFL_ERR_STATE"}
+
+
+class pfl_params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("bc", ctypes.c_int * 6),
+                ("rho_h", ctypes.c_double), ("rho_l", ctypes.c_double),
+                ("nu_h", ctypes.c_double), ("nu_l", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("mobility", ctypes.c_double), ("xi", ctypes.c_double),
+                ("gravity", ctypes.c_double * 3),
+                ("precision", ctypes.c_int), ("collision", ctypes.c_int)]
+
+
+class PFLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libpflbm.so is not built (run __graft_entry__.build() or "
+                           "python -m paper_2206_11637_gb300.build); there is no CPU fallback")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, D, I, S = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
+    PP = ctypes.POINTER(pfl_params)
+    lib.pfl_workspace_bytes.restype = S
+    lib.pfl_workspace_bytes.argtypes = [PP]
+    lib.pfl_init.restype = I
+    lib.pfl_init.argtypes = [PP, P, P, P, P, S, P, ctypes.POINTER(P)]
+    lib.pfl_step.restype = I
+    lib.pfl_step.argtypes = [P, I]
+    lib.pfl_fields.restype = I
+    lib.pfl_fields.argtypes = [P, P, P, P, P]
+    lib.pfl_populations.restype = I
+    lib.pfl_populations.argtypes = [P, P, P]
+    lib.pfl_set_populations.restype = I
+    lib.pfl_set_populations.argtypes = [P, P, P]
+    lib.pfl_diag.restype = I
+    lib.pfl_diag.argtypes = [P, P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.pfl_kernel_times.restype = I
+    lib.pfl_kernel_times.argtypes = [P, I, P]
+    lib.pfl_time.restype = ctypes.c_longlong
+    lib.pfl_time.argtypes = [P]
+    lib.pfl_destroy.restype = None
+    lib.pfl_destroy.argtypes = [P]
+    lib.pfl_last_error.restype = ctypes.c_char_p
+    lib.pfl_last_error.argtypes = []
+    lib.pfl_version.restype = I
+    lib.pfl_version.argtypes = []
+    _lib = lib
+    return lib
+
+
+def check(status):
+    if status != PFL_OK:
+        raise PFLError(status, load().pfl_last_error().decode())
+    return status
+
+
+def declared_symbols():
+    """Names of the functions declared in include/pflbm.h."""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pfl_[a-z_]+)\s*\(", text)))

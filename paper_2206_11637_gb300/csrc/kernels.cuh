@@ -1,0 +1,517 @@
+// PFLBM device kernels: fused stream-collide of h (D3Q15) and g (D3Q27) with
+// in-place AA streaming, the phi = sum h pass, initialisation, field output
+// and FP64 reductions.
+//
+// Time step t (section "Conservative Allen-Cahn model"; schedule: both
+// collisions at t use phi^t and its stencil, u^t from g in the same cell;
+// then both sets stream; then phi^{t+1} = sum_i h_i):
+//   stencil   grad phi = 3 sum w_i c_i phi(x + c_i), lap phi = 6 sum w_i (phi(x + c_i) - phi(x))
+//             over D3Q27 weights; phi mirrored across no-slip faces.
+//   forces    mu = 4 beta phi (phi - 1)(phi - 1/2) - kappa lap phi, F_s = mu grad phi,
+//             F_b = rho g, F_p = -p* c_s^2 (rho_H - rho_L) grad phi,
+//             F_mu = nu (rho_H - rho_L)[grad u + grad u^T] grad phi with the strain
+//             rate -(omega / c_s^2) Pi^neq from the non-equilibrium second
+//             moment of g taken against g^eq(p*, u0), u0 = j + (F_s+F_b+F_p)/(2 rho).
+//   velocity  u = sum c_i g_i + F / (2 rho).
+//   g         weighted-orthogonal MRT with degree 2 at omega(phi) and degree >= 3
+//             at 1.  With moments graded by degree and w-orthogonal, M^-1 S M
+//             acts as a projector sum, and the post-collision state reduces to
+//               g+_i = g^eq_i + (1 - omega) w_i 9/2 (c_i c_i - I/3) : Pi^d + 1/2 G_i,
+//             Pi^d = sum c c (g - g^eq(p*, u)), G_i = 3 w_i c_i . F / rho (Guo
+//             source; its (I - S/2) factor is 1/2 on the conserved degree 1).
+//   h         degrees 1 and 2 at omega_phi, degree >= 3 at 1:
+//               h+_i = h^eq_i + (1 - omega_phi)[3 w_i c_i . J^d + w_i 9/2 (c_i c_i - I/3) : Pi^dh]
+//                      + (1 - omega_phi / 2) w_i c_i . (theta n),
+//             h^eq_i = w_i phi (1 + 3 c_i . u), theta = 4 phi (1 - phi) / xi,
+//             n = grad phi / (|grad phi| + 1e-6).
+//
+// AA pattern (one array per set, updated in place):
+//   even step: read f_i at x from slot i, write f+_i to slot opp(i) at x;
+//   odd step:  read f_i at x from slot opp(i) of x - c_i (slot i of x itself when
+//              x - c_i lies behind a no-slip face: halfway bounce-back), write
+//              f+_i to slot i of x + c_i (slot opp(i) of x behind a wall).
+//   Every location is read and then written by the same thread, so the update
+//   is race-free without a second array.  In both parities the population read
+//   at x for direction i was written by x - c_i (by x itself after a bounce).
+//
+// phi is double-buffered: a step reads phi^t from `phi` (stencil) and, for the
+// FP16S format, the shifts phi^{t-1} of the populations it loads from `shift`;
+// it writes populations shifted by phi^t of the writing cell.  The phi pass
+// then writes phi^{t+1} into the buffer that held phi^{t-1}.
+#pragma once
+#include "lattice.cuh"
+
+namespace pfl {
+
+struct Geo {
+  int nx, ny, nz;
+  int wall[3];  // per axis: 1 = no-slip faces, 0 = periodic
+  long long N;
+};
+
+struct Phys {
+  double rho_h, rho_l, tau_h, tau_l, beta, kappa, inv_xi, omega_phi, gx, gy, gz;
+};
+
+// Coordinates of x-1, x, x+1 along one axis.  pop[]: -1 behind a wall.
+// sten[]: clamped at walls (mirror of phi), wrapped when periodic.
+__device__ __forceinline__ void axis_nb(int x, int n, int wall, int pop[3], int sten[3]) {
+  int xm = x - 1, xp = x + 1;
+  if (wall) {
+    pop[0] = xm;
+    pop[2] = (xp < n) ? xp : -1;
+    sten[0] = xm < 0 ? 0 : xm;
+    sten[2] = xp >= n ? n - 1 : xp;
+  } else {
+    xm = xm < 0 ? xm + n : xm;
+    xp = xp >= n ? xp - n : xp;
+    pop[0] = xm;
+    pop[2] = xp;
+    sten[0] = xm;
+    sten[2] = xp;
+  }
+  pop[1] = x;
+  sten[1] = x;
+}
+
+struct Nb {
+  int px[3], py[3], pz[3];
+  int sx[3], sy[3], sz[3];
+};
+
+__device__ __forceinline__ void cell_coords(const Geo& geo, long long cell, int& x, int& y, int& z) {
+  long long yz = cell / geo.nx;
+  x = (int)(cell - yz * geo.nx);
+  z = (int)(yz / geo.ny);
+  y = (int)(yz - (long long)z * geo.ny);
+}
+
+__device__ __forceinline__ void make_nb(const Geo& geo, int x, int y, int z, Nb& nb) {
+  axis_nb(x, geo.nx, geo.wall[0], nb.px, nb.sx);
+  axis_nb(y, geo.ny, geo.wall[1], nb.py, nb.sy);
+  axis_nb(z, geo.nz, geo.wall[2], nb.pz, nb.sz);
+}
+
+__device__ __forceinline__ long long lin(const Geo& geo, int x, int y, int z) {
+  return (long long)x + (long long)geo.nx * ((long long)y + (long long)geo.ny * (long long)z);
+}
+
+// Location of population i (opposite oi) arriving at `cell` for the next
+// collision, and the cell that wrote it.  READ_ODD = state left by an even
+// step (gather from x - c with bounce-back); otherwise the normal state.
+template <int READ_ODD>
+__device__ __forceinline__ size_t src_index(const Geo& geo, const Nb& nb, long long cell, int i, int oi, int cx,
+                                            int cy, int cz, long long& from) {
+  int ax = nb.px[1 - cx], ay = nb.py[1 - cy], az = nb.pz[1 - cz];
+  const bool inside = ax >= 0 && ay >= 0 && az >= 0;
+  from = inside ? lin(geo, ax, ay, az) : cell;
+  if (!READ_ODD) return (size_t)i * geo.N + cell;
+  if (inside) return (size_t)oi * geo.N + from;
+  return (size_t)i * geo.N + cell;
+}
+
+// Destination of the post-collision population i of `cell`.
+template <int ODD>
+__device__ __forceinline__ size_t dst_index(const Geo& geo, const Nb& nb, long long cell, int i, int oi, int cx,
+                                            int cy, int cz) {
+  if (!ODD) return (size_t)oi * geo.N + cell;
+  int ax = nb.px[1 + cx], ay = nb.py[1 + cy], az = nb.pz[1 + cz];
+  if (ax >= 0 && ay >= 0 && az >= 0) return (size_t)i * geo.N + lin(geo, ax, ay, az);
+  return (size_t)oi * geo.N + cell;
+}
+
+// Everything a cell needs before its collisions.
+template <typename R>
+struct Macro {
+  R phi, gx, gy, gz, lap;
+  R rho, omega, nu;
+  R pst, jx, jy, jz;                  // p*, sum c g
+  R pxx, pyy, pzz, pxy, pyz, pxz;     // sum c c g
+  R Fx, Fy, Fz, ux, uy, uz;
+};
+
+template <int PREC>
+__device__ __forceinline__ void stencil(const Geo& geo, const Nb& nb, long long cell,
+                                        const typename Store<PREC>::PhiT* __restrict__ phi,
+                                        Macro<typename Store<PREC>::R>& m) {
+  typedef typename Store<PREC>::R R;
+  R pc = (R)__ldg(phi + cell);
+  R gx = 0, gy = 0, gz = 0, lap = 0;
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    if (i == 13) continue;
+    const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+    R v = (R)__ldg(phi + lin(geo, nb.sx[1 + cx], nb.sy[1 + cy], nb.sz[1 + cz]));
+    const R w = (R)q27_w(i);
+    if (cx) gx += (cx > 0 ? w : -w) * v;
+    if (cy) gy += (cy > 0 ? w : -w) * v;
+    if (cz) gz += (cz > 0 ? w : -w) * v;
+    lap += w * (v - pc);
+  }
+  m.phi = pc;
+  m.gx = (R)3 * gx;
+  m.gy = (R)3 * gy;
+  m.gz = (R)3 * gz;
+  m.lap = (R)6 * lap;
+}
+
+// Hydrodynamic moments, forces and velocity.  gv receives the 27 values (used
+// by the BGK mode; dead code otherwise).
+template <int PREC, int READ_ODD>
+__device__ __forceinline__ void hydro_macro(const Geo& geo, const Phys& ph, const Nb& nb, long long cell,
+                                            const typename Store<PREC>::S* __restrict__ g,
+                                            Macro<typename Store<PREC>::R>& m, typename Store<PREC>::R gv[27]) {
+  typedef typename Store<PREC>::R R;
+  R pst = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+    long long from;
+    R v = ld_g<PREC>(g, src_index<READ_ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz, from), i);
+    gv[i] = v;
+    pst += v;
+    if (cx) jx += cx > 0 ? v : -v;
+    if (cy) jy += cy > 0 ? v : -v;
+    if (cz) jz += cz > 0 ? v : -v;
+    if (cx) pxx += v;
+    if (cy) pyy += v;
+    if (cz) pzz += v;
+    if (cx && cy) pxy += (cx * cy > 0) ? v : -v;
+    if (cy && cz) pyz += (cy * cz > 0) ? v : -v;
+    if (cx && cz) pxz += (cx * cz > 0) ? v : -v;
+  }
+  m.pst = pst;
+  m.jx = jx;
+  m.jy = jy;
+  m.jz = jz;
+  m.pxx = pxx;
+  m.pyy = pyy;
+  m.pzz = pzz;
+  m.pxy = pxy;
+  m.pyz = pyz;
+  m.pxz = pxz;
+
+  const R phi = m.phi;
+  const R drho = (R)(ph.rho_h - ph.rho_l);
+  m.rho = (R)ph.rho_l + phi * drho;
+  const R tau = (R)ph.tau_l + phi * (R)(ph.tau_h - ph.tau_l);
+  m.omega = (R)1 / tau;
+  m.nu = (tau - (R)0.5) * (R)(1.0 / 3.0);
+  const R mu = (R)4 * (R)ph.beta * phi * (phi - (R)1) * (phi - (R)0.5) - (R)ph.kappa * m.lap;
+  const R inv2rho = (R)0.5 / m.rho;
+  const R cp = -pst * (R)(1.0 / 3.0) * drho;
+  // F_s + F_b + F_p
+  R Fx = mu * m.gx + m.rho * (R)ph.gx + cp * m.gx;
+  R Fy = mu * m.gy + m.rho * (R)ph.gy + cp * m.gy;
+  R Fz = mu * m.gz + m.rho * (R)ph.gz + cp * m.gz;
+  const R u0x = jx + Fx * inv2rho, u0y = jy + Fy * inv2rho, u0z = jz + Fz * inv2rho;
+  const R p3 = pst * (R)(1.0 / 3.0);
+  const R nxx = pxx - p3 - u0x * u0x, nyy = pyy - p3 - u0y * u0y, nzz = pzz - p3 - u0z * u0z;
+  const R nxy = pxy - u0x * u0y, nyz = pyz - u0y * u0z, nxz = pxz - u0x * u0z;
+  const R cm = (R)-3 * m.nu * m.omega * drho;
+  Fx += cm * (nxx * m.gx + nxy * m.gy + nxz * m.gz);
+  Fy += cm * (nxy * m.gx + nyy * m.gy + nyz * m.gz);
+  Fz += cm * (nxz * m.gx + nyz * m.gy + nzz * m.gz);
+  m.Fx = Fx;
+  m.Fy = Fy;
+  m.Fz = Fz;
+  m.ux = jx + Fx * inv2rho;
+  m.uy = jy + Fy * inv2rho;
+  m.uz = jz + Fz * inv2rho;
+}
+
+// h population k arriving at `cell` (shift from `shift` for FP16S).
+template <int PREC, int READ_ODD>
+__device__ __forceinline__ typename Store<PREC>::R load_h(const Geo& geo, const Nb& nb, long long cell, int k,
+                                                          const typename Store<PREC>::S* __restrict__ h,
+                                                          const typename Store<PREC>::PhiT* __restrict__ shift) {
+  typedef typename Store<PREC>::R R;
+  long long from;
+  const size_t idx = src_index<READ_ODD>(geo, nb, cell, k, q15_opp(k), q15_cx(k), q15_cy(k), q15_cz(k), from);
+  R sh = 0;
+  if constexpr (PREC == 2) sh = __ldg(shift + from);
+  return ld_h<PREC>(h, idx, k, sh);
+}
+
+// One time step: collide both sets at every cell and stream them in place.
+template <int PREC, int ODD, int BGK>
+__global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<PREC>::S* __restrict__ h,
+                                              typename Store<PREC>::S* __restrict__ g,
+                                              const typename Store<PREC>::PhiT* __restrict__ phi,
+                                              const typename Store<PREC>::PhiT* __restrict__ shift) {
+  typedef typename Store<PREC>::R R;
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= geo.N) return;
+  int x, y, z;
+  cell_coords(geo, cell, x, y, z);
+  Nb nb;
+  make_nb(geo, x, y, z, nb);
+  Macro<R> m;
+  stencil<PREC>(geo, nb, cell, phi, m);
+  R gv[27];
+  hydro_macro<PREC, ODD>(geo, ph, nb, cell, g, m, gv);
+
+  // ---- g collision and streaming
+  {
+    const R ux = m.ux, uy = m.uy, uz = m.uz;
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R p3 = m.pst * (R)(1.0 / 3.0);
+    const R dxx = m.pxx - p3 - ux * ux, dyy = m.pyy - p3 - uy * uy, dzz = m.pzz - p3 - uz * uz;
+    const R dxy = m.pxy - ux * uy, dyz = m.pyz - uy * uz, dxz = m.pxz - ux * uz;
+    const R tr3 = (dxx + dyy + dzz) * (R)(1.0 / 3.0);
+    const R a2 = ((R)1 - m.omega) * (R)4.5;
+    const R inv_rho = (R)1 / m.rho;
+    const R fx = (R)1.5 * m.Fx * inv_rho, fy = (R)1.5 * m.Fy * inv_rho, fz = (R)1.5 * m.Fz * inv_rho;
+    // BGK: (1 - omega/2) G_i with G_i = 2 w_i (1.5 c.F / rho)
+    const R om = m.omega, fbgk = ((R)1 - (R)0.5 * om) * (R)2;
+#pragma unroll
+    for (int i = 0; i < 27; ++i) {
+      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+      const R w = (R)q27_w(i);
+      const R cu = (R)cx * ux + (R)cy * uy + (R)cz * uz;
+      const R geq = w * (m.pst + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
+      const R cf = (R)cx * fx + (R)cy * fy + (R)cz * fz;  // 1.5 c.F / rho
+      R post;
+      if (BGK) {
+        post = gv[i] - om * (gv[i] - geq) + fbgk * w * cf;
+      } else {
+        const R hd = (R)(cx * cx) * dxx + (R)(cy * cy) * dyy + (R)(cz * cz) * dzz +
+                     (R)2 * ((R)(cx * cy) * dxy + (R)(cy * cz) * dyz + (R)(cx * cz) * dxz) - tr3;
+        post = geq + w * (a2 * hd + cf);
+      }
+      st_g<PREC>(g, dst_index<ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz), i, post);
+    }
+  }
+
+  // ---- h collision and streaming
+  {
+    R hv[15];
+    R phl = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+      const R v = load_h<PREC, ODD>(geo, nb, cell, k, h, shift);
+      hv[k] = v;
+      phl += v;
+      if (cx) jx += cx > 0 ? v : -v;
+      if (cy) jy += cy > 0 ? v : -v;
+      if (cz) jz += cz > 0 ? v : -v;
+      if (cx) pxx += v;
+      if (cy) pyy += v;
+      if (cz) pzz += v;
+      if (cx && cy) pxy += (cx * cy > 0) ? v : -v;
+      if (cy && cz) pyz += (cy * cz > 0) ? v : -v;
+      if (cx && cz) pxz += (cx * cz > 0) ? v : -v;
+    }
+    const R ux = m.ux, uy = m.uy, uz = m.uz;
+    const R omp = (R)ph.omega_phi;
+    const R gn = sqrt(m.gx * m.gx + m.gy * m.gy + m.gz * m.gz);
+    const R theta = (R)4 * m.phi * ((R)1 - m.phi) * (R)ph.inv_xi;
+    const R tn = theta / (gn + (R)1e-6);
+    const R tx = tn * m.gx, ty = tn * m.gy, tz = tn * m.gz;  // theta * n
+    const R src = (R)1 - (R)0.5 * omp;
+    const R a1 = ((R)1 - omp) * (R)3, a2 = ((R)1 - omp) * (R)4.5;
+    const R Jx = jx - phl * ux, Jy = jy - phl * uy, Jz = jz - phl * uz;
+    const R p3 = phl * (R)(1.0 / 3.0);
+    const R dxx = pxx - p3, dyy = pyy - p3, dzz = pzz - p3;
+    const R tr3 = (dxx + dyy + dzz) * (R)(1.0 / 3.0);
+    // populations are written as q = h+ / w - shift; the shift is this cell's phi
+    const R sh = (PREC == 2) ? m.phi : (R)0;
+#pragma unroll
+    for (int k = 0; k < 15; ++k) {
+      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+      const R cu = (R)cx * ux + (R)cy * uy + (R)cz * uz;
+      const R ct = (R)cx * tx + (R)cy * ty + (R)cz * tz;
+      R q;
+      if (BGK) {
+        const R w = (R)q15_w(k);
+        const R heq = w * phl * ((R)1 + (R)3 * cu);
+        q = (hv[k] - omp * (hv[k] - heq)) * (R)(1.0 / q15_w(k)) + src * ct - sh;
+      } else {
+        const R cJ = (R)cx * Jx + (R)cy * Jy + (R)cz * Jz;
+        const R hd = (R)(cx * cx) * dxx + (R)(cy * cy) * dyy + (R)(cz * cz) * dzz +
+                     (R)2 * ((R)(cx * cy) * pxy + (R)(cy * cz) * pyz + (R)(cx * cz) * pxz) - tr3;
+        q = (phl - sh) + phl * (R)3 * cu + a1 * cJ + a2 * hd + src * ct;
+      }
+      st_h_q<PREC>(h, dst_index<ODD>(geo, nb, cell, k, q15_opp(k), cx, cy, cz), k, q);
+    }
+  }
+}
+
+// phi = sum_i h_i of the state left by the last step (READ_ODD after an even
+// step); `shift` holds the shifts of the stored populations.
+template <int PREC, int READ_ODD>
+__global__ void __launch_bounds__(256) k_phi(Geo geo, const typename Store<PREC>::S* __restrict__ h,
+                                             const typename Store<PREC>::PhiT* __restrict__ shift,
+                                             typename Store<PREC>::PhiT* __restrict__ phi) {
+  typedef typename Store<PREC>::R R;
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= geo.N) return;
+  int x, y, z;
+  cell_coords(geo, cell, x, y, z);
+  Nb nb;
+  make_nb(geo, x, y, z, nb);
+  R s = 0;
+#pragma unroll
+  for (int k = 0; k < 15; ++k) s += load_h<PREC, READ_ODD>(geo, nb, cell, k, h, shift);
+  phi[cell] = s;
+}
+
+// Equilibrium initial state (normal layout, zero shifts) for cells
+// [c0, c0 + count).  Inputs are FP64 arrays indexed from c0 (phi0, u0x, u0y,
+// u0z, p0; u and p may be NULL).
+template <int PREC>
+__global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typename Store<PREC>::S* __restrict__ g,
+                       long long c0, long long count, const double* __restrict__ phi0,
+                       const double* __restrict__ u0x, const double* __restrict__ u0y,
+                       const double* __restrict__ u0z, const double* __restrict__ p0) {
+  typedef typename Store<PREC>::R R;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const long long cell = c0 + t;
+  const R ph = (R)phi0[t];
+  const R ux = u0x ? (R)u0x[t] : (R)0, uy = u0y ? (R)u0y[t] : (R)0, uz = u0z ? (R)u0z[t] : (R)0;
+  const R ps = p0 ? (R)p0[t] : (R)0;
+  const R uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    const R cu = (R)q27_cx(i) * ux + (R)q27_cy(i) * uy + (R)q27_cz(i) * uz;
+    st_g<PREC>(g, (size_t)i * geo.N + cell, i, (R)q27_w(i) * (ps + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu));
+  }
+#pragma unroll
+  for (int k = 0; k < 15; ++k) {
+    const R cu = (R)q15_cx(k) * ux + (R)q15_cy(k) * uy + (R)q15_cz(k) * uz;
+    st_h_q<PREC>(h, (size_t)k * geo.N + cell, k, ph * ((R)1 + (R)3 * cu));
+  }
+}
+
+// Macroscopic output: any of phi, rho, p, ux, uy, uz (device FP64, may be NULL).
+template <int PREC, int READ_ODD>
+__global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename Store<PREC>::S* __restrict__ g,
+                                                const typename Store<PREC>::PhiT* __restrict__ phi,
+                                                double* o_phi, double* o_rho, double* o_p, double* o_ux,
+                                                double* o_uy, double* o_uz) {
+  typedef typename Store<PREC>::R R;
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= geo.N) return;
+  int x, y, z;
+  cell_coords(geo, cell, x, y, z);
+  Nb nb;
+  make_nb(geo, x, y, z, nb);
+  Macro<R> m;
+  stencil<PREC>(geo, nb, cell, phi, m);
+  R gv[27];
+  hydro_macro<PREC, READ_ODD>(geo, ph, nb, cell, g, m, gv);
+  if (o_phi) o_phi[cell] = (double)m.phi;
+  if (o_rho) o_rho[cell] = (double)m.rho;
+  if (o_p) o_p[cell] = (double)m.pst * (double)m.rho / 3.0;
+  if (o_ux) o_ux[cell] = (double)m.ux;
+  if (o_uy) o_uy[cell] = (double)m.uy;
+  if (o_uz) o_uz[cell] = (double)m.uz;
+}
+
+// Population export in canonical layout (FP64): q = 15 (h) or 27 (g).
+template <int PREC, int READ_ODD>
+__global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
+                         const typename Store<PREC>::PhiT* __restrict__ shift, int q, int i,
+                         double* __restrict__ out) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= geo.N) return;
+  int x, y, z;
+  cell_coords(geo, cell, x, y, z);
+  Nb nb;
+  make_nb(geo, x, y, z, nb);
+  if (q == 27) {
+#pragma unroll
+    for (int j = 0; j < 27; ++j)
+      if (j == i) {
+        long long from;
+        out[cell] = (double)ld_g<PREC>(
+            f, src_index<READ_ODD>(geo, nb, cell, j, q27_opp(j), q27_cx(j), q27_cy(j), q27_cz(j), from), j);
+      }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 15; ++j)
+      if (j == i) out[cell] = (double)load_h<PREC, READ_ODD>(geo, nb, cell, j, f, shift);
+  }
+}
+
+// Population import (normal layout, zero shifts).
+template <int PREC>
+__global__ void k_import(Geo geo, typename Store<PREC>::S* __restrict__ f, int q, int i, const double* __restrict__ in) {
+  typedef typename Store<PREC>::R R;
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= geo.N) return;
+  const size_t idx = (size_t)i * geo.N + cell;
+  if constexpr (PREC != 2) {
+    f[idx] = (R)in[cell];
+  } else if (q == 27) {
+#pragma unroll
+    for (int j = 0; j < 27; ++j)
+      if (j == i) st_g<PREC>(f, idx, j, (R)in[cell]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < 15; ++j)
+      if (j == i) st_h_q<PREC>(f, idx, j, (R)(in[cell] / q15_w(j)));
+  }
+}
+
+// FP64 reductions: per-block partial sums of
+//   [phi, phi x, phi y, phi z, 1-phi, (1-phi) x, (1-phi) y, (1-phi) z, nonfinite]
+// written to part[block * 9 + k]; k_diag_final sums them in a fixed order.
+constexpr int DIAG_BLOCKS = 1216;  // 8 x 152 SMs
+constexpr int DIAG_THREADS = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename PhiT>
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag(Geo geo, const PhiT* __restrict__ phi, double* __restrict__ part) {
+  double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < geo.N;
+       cell += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    cell_coords(geo, cell, x, y, z);
+    const double p = (double)phi[cell];
+    if (!isfinite(p)) {
+      acc[8] += 1.0;
+      continue;
+    }
+    const double q = 1.0 - p;
+    acc[0] += p;
+    acc[1] += p * x;
+    acc[2] += p * y;
+    acc[3] += p * z;
+    acc[4] += q;
+    acc[5] += q * x;
+    acc[6] += q * y;
+    acc[7] += q * z;
+  }
+  __shared__ double sm[DIAG_THREADS / 32][9];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    double v = warp_sum(acc[k]);
+    if (lane == 0) sm[wid][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double s = 0;
+    for (int w = 0; w < DIAG_THREADS / 32; ++w) s += sm[w][threadIdx.x];
+    part[(size_t)blockIdx.x * 9 + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  // one warp per quantity, fixed order
+  const int k = blockIdx.x;
+  double s = 0;
+  for (int b = threadIdx.x; b < nblocks; b += 32) s += part[(size_t)b * 9 + k];
+  s = warp_sum(s);
+  if (threadIdx.x == 0) out[k] = s;
+}
+
+}  // namespace pfl

@@ -1,0 +1,110 @@
+// Lattice constants and population storage formats of the PFLBM kernels.
+//
+// D3Q27 (hydrodynamics g) and D3Q15 (phase field h) in the canonical order of
+// the C interface: cz, cy, cx each over -1, 0, 1 with cx fastest.  For D3Q27
+// this gives i = (cx+1) + 3(cy+1) + 9(cz+1), so velocities, weights and
+// opposites are closed-form functions of i that fold to constants inside
+// fully unrolled loops.  D3Q15 keeps the members with |c|^2 in {0, 1, 3};
+// member k sits at D3Q27 index 2k (k < 7), 13 (k = 7) or 2k - 2 (k > 7), and
+// its opposite is 14 - k.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pfl {
+
+__host__ __device__ constexpr int q27_cx(int i) { return i % 3 - 1; }
+__host__ __device__ constexpr int q27_cy(int i) { return (i / 3) % 3 - 1; }
+__host__ __device__ constexpr int q27_cz(int i) { return i / 9 - 1; }
+__host__ __device__ constexpr int q27_n2(int i) {
+  return q27_cx(i) * q27_cx(i) + q27_cy(i) * q27_cy(i) + q27_cz(i) * q27_cz(i);
+}
+__host__ __device__ constexpr int q27_opp(int i) { return 26 - i; }
+// weights 8/27, 2/27, 1/54, 1/216 by |c|^2 = 0, 1, 2, 3
+__host__ __device__ constexpr double q27_w(int i) {
+  return q27_n2(i) == 0 ? 8.0 / 27.0 : q27_n2(i) == 1 ? 2.0 / 27.0 : q27_n2(i) == 2 ? 1.0 / 54.0 : 1.0 / 216.0;
+}
+
+__host__ __device__ constexpr int q15_to27(int k) { return k < 7 ? 2 * k : (k == 7 ? 13 : 2 * k - 2); }
+__host__ __device__ constexpr int q15_cx(int k) { return q27_cx(q15_to27(k)); }
+__host__ __device__ constexpr int q15_cy(int k) { return q27_cy(q15_to27(k)); }
+__host__ __device__ constexpr int q15_cz(int k) { return q27_cz(q15_to27(k)); }
+__host__ __device__ constexpr int q15_opp(int k) { return 14 - k; }
+// weights 2/9, 1/9, 1/72 by |c|^2 = 0, 1, 3
+__host__ __device__ constexpr double q15_w(int k) {
+  return q27_n2(q15_to27(k)) == 0 ? 2.0 / 9.0 : q27_n2(q15_to27(k)) == 1 ? 1.0 / 9.0 : 1.0 / 72.0;
+}
+
+// FP16S format (shifted FP16 storage, FP32 arithmetic):
+//   h: stored = fp16(KH16 * (h_i / w_i - phi_src)), phi_src = phi at the cell the
+//      population was written by (its value at the time of writing), so the
+//      stored number is the population's deviation from w_i phi -- the rest
+//      equilibrium of the local phase -- and stays small in both bulk phases;
+//   g: stored = fp16(KG16 * g_i / w_i); the rest equilibrium of g is zero
+//      (p* = 0 gauge), so g_i itself is the deviation.
+// The power-of-two scales lift small deviations out of the FP16 subnormal
+// range while keeping |deviation / w| up to 64 (h) and 256 (g) representable.
+constexpr double KH16 = 1024.0;
+constexpr double KG16 = 256.0;
+
+template <int PREC>
+struct Store;
+
+template <>
+struct Store<0> {  // FP64 storage and arithmetic
+  typedef double S;
+  typedef double R;
+  typedef double PhiT;
+};
+
+template <>
+struct Store<1> {  // FP32 storage and arithmetic
+  typedef float S;
+  typedef float R;
+  typedef float PhiT;
+};
+
+template <>
+struct Store<2> {  // shifted FP16 storage, FP32 arithmetic
+  typedef __half S;
+  typedef float R;
+  typedef float PhiT;
+};
+
+// g population i: load / store in the arithmetic type.
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::R ld_g(const typename Store<PREC>::S* a, size_t idx, int i) {
+  if constexpr (PREC == 2)
+    return __half2float(a[idx]) * (float)(q27_w(i) / KG16);
+  else
+    return a[idx];
+}
+template <int PREC>
+__device__ __forceinline__ void st_g(typename Store<PREC>::S* a, size_t idx, int i, typename Store<PREC>::R v) {
+  if constexpr (PREC == 2)
+    a[idx] = __float2half_rn(v * (float)(KG16 / q27_w(i)));
+  else
+    a[idx] = v;
+}
+
+// h population k: load adds back the shift phi_src (FP16S only).
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::R ld_h(const typename Store<PREC>::S* a, size_t idx, int k,
+                                                        typename Store<PREC>::R phi_src) {
+  if constexpr (PREC == 2)
+    return (__half2float(a[idx]) * (float)(1.0 / KH16) + phi_src) * (float)q15_w(k);
+  else
+    return a[idx];
+}
+// Store of h from q = h_i / w_i - shift (the shift is zero for FP64 / FP32).
+template <int PREC>
+__device__ __forceinline__ void st_h_q(typename Store<PREC>::S* a, size_t idx, int k, typename Store<PREC>::R q) {
+  typedef typename Store<PREC>::R R;
+  if constexpr (PREC == 2)
+    a[idx] = __float2half_rn(q * (float)KH16);
+  else
+    a[idx] = (R)q15_w(k) * q;
+}
+
+}  // namespace pfl

@@ -1,0 +1,63 @@
+"""The C-ABI library loads and exports every declared symbol; host-side
+argument checks (no GPU needed)."""
+import ctypes
+
+import pytest
+
+from paper_2206_11637_gb300 import _lib as L
+from paper_2206_11637_gb300 import build as B
+from paper_2206_11637_gb300 import workloads as W
+from paper_2206_11637_gb300 import pflbm
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build_library()
+    return L.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = L.declared_symbols()
+    assert {"pfl_init", "pfl_step", "pfl_fields", "pfl_diag"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert lib.pfl_version() == 1
+
+
+def test_workspace_size(lib):
+    p, _, _, _ = W.static_drop(16, 5.0)
+    n = p.cells
+    b64 = pflbm.workspace_bytes(p, L.PFL_FP64)
+    b32 = pflbm.workspace_bytes(p, L.PFL_FP32)
+    b16 = pflbm.workspace_bytes(p, L.PFL_FP16S)
+    assert b64 >= 42 * n * 8 + n * 8
+    assert b32 >= 42 * n * 4 + n * 4
+    assert b16 >= 42 * n * 2 + n * 4
+    assert b16 < b32 < b64
+
+
+@pytest.mark.parametrize("field,value", [("mobility", 0.0), ("xi", -1.0), ("rho_l", 0.0), ("nu_h", -0.2),
+                                         ("nu_l", -0.1), ("nx", 0)])
+def test_rejects_bad_parameters(lib, field, value):
+    p, phi0, _, _ = W.static_drop(8, 3.0)
+    setattr(p, field, value)
+    s = pflbm._params_struct(p, 0)
+    assert lib.pfl_workspace_bytes(ctypes.byref(s)) == 0
+    ctx = ctypes.c_void_p()
+    st = lib.pfl_init(ctypes.byref(s), None, None, None, None, 0, None, ctypes.byref(ctx))
+    assert st == L.PFL_ERR_ARG
+    assert lib.pfl_last_error().decode() != ""
+
+
+def test_rejects_mixed_faces(lib):
+    p, _, _, _ = W.static_drop(8, 3.0)
+    p.bc = (0, 1, 0, 0, 0, 0)
+    s = pflbm._params_struct(p, 0)
+    assert lib.pfl_workspace_bytes(ctypes.byref(s)) == 0
+
+
+def test_null_context_calls(lib):
+    assert lib.pfl_step(None, 1) == L.PFL_ERR_ARG
+    assert lib.pfl_fields(None, None, None, None, None) == L.PFL_ERR_ARG
+    assert lib.pfl_time(None) == -1
+    lib.pfl_destroy(None)

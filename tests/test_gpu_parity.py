@@ -1,0 +1,164 @@
+"""GPU path vs the FP64 oracle, element by element, through the C-ABI.
+
+Tolerances: FP64 storage and arithmetic agree with the oracle to 1e-10 (max
+relative error: max |gpu - oracle| / max |oracle| per field) after many steps;
+FP32 to 1e-5 on phi and u / u_max; FP16-shifted storage with FP32 arithmetic
+to 1e-3.  Sizes span many 256-cell blocks and a ragged tail; the edge cases
+are single-cell-thick (quasi-2D) lattices, walls on every face, BGK mode and
+the set/get population round trip.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_11637_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+THREADS = 0  # oracle: all host cores
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_11637_gb300 import build
+    build.build_library()
+
+
+def sim(p, phi0, u0=None, p0=None, precision="fp64"):
+    from paper_2206_11637_gb300.pflbm import Simulation
+    return Simulation(p, phi0, u0, p0, precision=precision)
+
+
+def rel(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def compare_fields(s, o, tol_phi, tol_u, tol_p=None):
+    phi, rho, pr, u = s.fields()
+    ophi, orho, opr, ou = o.fields()
+    assert np.all(np.isfinite(phi)) and np.all(np.isfinite(u))
+    e = {"phi": rel(phi, ophi), "u": rel(u, ou), "p": rel(pr, opr), "rho": rel(rho, orho)}
+    assert e["phi"] <= tol_phi, e
+    assert e["u"] <= tol_u, e
+    if tol_p is not None:
+        assert e["p"] <= tol_p, e
+    return e
+
+
+CASES = {
+    # name: (builder, steps)
+    "static_drop_32": (lambda: W.static_drop(32, 10.0, u_noise=1e-3, seed=1234), 1000),
+    "wave_walls_y": (lambda: W.capillary_wave(40, ny=48, a0=1.5, xi=5.0, sigma=1e-4, nu=0.01), 400),
+    "bubble_all_walls": (lambda: W.rising_bubble(24, 40, 20, D=10.0, xi=4.0, M=0.05), 200),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_parity(name):
+    build, steps = CASES[name]
+    p, phi0, u0, p0 = build()
+    s = sim(p, phi0, u0, p0, "fp64")
+    o = oracle.from_params(p, phi0, u0, p0)
+    s.step(steps)
+    o.step(steps, THREADS)
+    compare_fields(s, o, 1e-10, 1e-10, 1e-10)
+    h, g = s.populations()
+    oh, og = o.populations()
+    assert rel(h, oh) < 1e-10 and rel(g, og) < 1e-10
+
+
+def test_fp64_ragged_mixed_boundaries():
+    # 37 x 23 x 11 = 9361 cells: not a multiple of the 256-thread block
+    p = W.Params(37, 23, 11, (0, 0, 1, 1, 0, 0), 1.0, 0.01, 0.02, 0.05, 2e-4, 0.03, 4.0, (1e-6, -2e-6, 0.0))
+    c = (18.0, 11.0, 5.0)
+    phi0 = W.sphere(p, c, 6.0, heavy_inside=True)
+    u0 = W.noise((3,) + p.shape, 99, 1e-3)
+    s = sim(p, phi0, u0, None, "fp64")
+    o = oracle.from_params(p, phi0, u0, None)
+    for chunk in (1, 2, 97):   # odd and even step counts
+        s.step(chunk)
+        o.step(chunk, THREADS)
+        compare_fields(s, o, 1e-10, 1e-10, 1e-10)
+
+
+def test_fp64_bgk_parity():
+    p, phi0, u0, _ = W.static_drop(20, 6.0, rho_ratio=10.0, u_noise=1e-3, seed=3, collision=1)
+    s = sim(p, phi0, u0, None, "fp64")
+    o = oracle.from_params(p, phi0, u0, None)
+    s.step(300)
+    o.step(300, THREADS)
+    compare_fields(s, o, 1e-10, 1e-10, 1e-10)
+
+
+def test_single_cell_thick_directions():
+    # quasi-2D in each orientation: nz = 1, ny = 1 and nx = 1
+    for shape in ((40, 30, 1), (40, 1, 30), (1, 40, 30)):
+        nx, ny, nz = shape
+        p = W.Params(nx, ny, nz, (0,) * 6, 1.0, 1e-3, 1 / 60, 1 / 60, 1e-4, 0.02, 4.0)
+        x, y, z = W.coords(p)
+        r = np.sqrt((x - (nx - 1) / 2) ** 2 + (y - (ny - 1) / 2) ** 2 + (z - (nz - 1) / 2) ** 2)
+        phi0 = W.tanh_profile(r - 8.0, 4.0)
+        s = sim(p, phi0)
+        o = oracle.from_params(p, phi0)
+        s.step(150)
+        o.step(150, THREADS)
+        compare_fields(s, o, 1e-10, 1e-10, 1e-10)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16s", 1e-3)])
+def test_reduced_precision_parity(precision, tol):
+    p, phi0, u0, _ = W.static_drop(32, 10.0, u_noise=1e-3, seed=1234)
+    s = sim(p, phi0, u0, None, precision)
+    o = oracle.from_params(p, phi0, u0, None)
+    s.step(1000)
+    o.step(1000, THREADS)
+    phi, _, _, u = s.fields()
+    ophi, _, _, ou = o.fields()
+    assert rel(phi, ophi) <= tol
+    assert rel(u, ou) <= tol * 10   # u / u_max: spurious currents are tiny here
+
+
+def test_mass_conservation_gpu_fp64():
+    p, phi0, u0, _ = W.static_drop(32, 10.0, u_noise=1e-3, seed=1234)
+    s = sim(p, phi0, u0, None, "fp64")
+    m0 = s.mass()
+    s.step(1000)
+    out, nf = s.diag()
+    assert nf == 0
+    assert abs(out[0] - m0) / m0 < 1e-12
+
+
+def test_diag_matches_fields():
+    p, phi0, u0, _ = W.rising_bubble(24, 40, 20, D=10.0, xi=4.0, M=0.05)
+    s = sim(p, phi0, None, None, "fp64")
+    s.step(10)
+    out, nf = s.diag()
+    phi = s.fields()[0]
+    x, y, z = W.coords(p)
+    expect = [phi.sum(), (phi * x).sum(), (phi * y).sum(), (phi * z).sum(),
+              (1 - phi).sum(), ((1 - phi) * x).sum(), ((1 - phi) * y).sum(), ((1 - phi) * z).sum()]
+    assert nf == 0
+    assert np.allclose(out, expect, rtol=1e-12, atol=1e-9)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
+def test_population_roundtrip_and_one_step(precision):
+    """Set the oracle's state into the GPU, take one step on each side."""
+    p, phi0, u0, _ = W.capillary_wave(48, ny=40, a0=2.0, xi=4.0, sigma=1e-3, nu=0.01)
+    o = oracle.from_params(p, phi0)
+    o.step(31, THREADS)
+    h, g = o.populations()
+    s = sim(p, phi0, None, None, precision)
+    s.set_populations(h, g)
+    h2, g2 = s.populations()
+    rt = {"fp64": 0.0, "fp32": 1e-7, "fp16s": 1e-3}[precision]
+    assert rel(h2, h) <= rt and rel(g2, g) <= rt * 10 + 1e-300
+    s.step(1)
+    o.set_populations(h2, g2)   # same rounded start on both sides
+    o.step(1, THREADS)
+    tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16s": 1e-3}[precision]
+    compare_fields(s, o, tol, tol * 10, None)
