@@ -79,7 +79,7 @@ def workload(name):
 
 def kernel_hash():
     h = hashlib.sha256()
-    for f in ("kernels.cuh", "lattice.cuh"):
+    for f in ("kernels.cuh", "lattice.cuh", "step.cuh"):
         with open(os.path.join(ROOT, "paper_2206_11637_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -12,6 +12,7 @@
 
 #include "../../include/pflbm.h"
 #include "kernels.cuh"
+#include "step.cuh"
 
 using namespace pfl;
 
@@ -106,6 +107,8 @@ unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads -
 struct pfl_ctx {
   pfl_params p;
   Geo geo;
+  Geo32 g32;
+  bool idx32;    // 27 N < 2^32: the 32-bit indexed kernels apply
   Phys ph;
   Layout L;
   char* ws;
@@ -146,7 +149,12 @@ double* stage(pfl_ctx* c) { return (double*)(c->ws + c->L.stage); }
 template <int PREC>
 void launch_phi(pfl_ctx* c) {
   const unsigned nb = blocks_for(c->geo.N, 256);
-  if (c->swapped)
+  if (c->idx32) {
+    if (c->swapped)
+      k_phi32<PREC, 1><<<nb, 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
+    else
+      k_phi32<PREC, 0><<<nb, 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
+  } else if (c->swapped)
     k_phi<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
   else
     k_phi<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
@@ -154,15 +162,27 @@ void launch_phi(pfl_ctx* c) {
 }
 
 // One collide-stream launch (without the phi pass that completes the step).
+// MRT runs the pair-based kernel; the BGK test mode, and lattices too large
+// for 32-bit indices, the generic one.
 template <int PREC, int BGK>
 void step_only(pfl_ctx* c) {
   const unsigned nb = blocks_for(c->geo.N, 256);
-  if (c->swapped)
-    k_step<PREC, 1, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
+  if (BGK || !c->idx32) {
+    if (c->swapped)
+      k_step<PREC, 1, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
                                                      phishift<PREC>(c));
-  else
-    k_step<PREC, 0, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
+    else
+      k_step<PREC, 0, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
                                                      phishift<PREC>(c));
+  } else {
+    const unsigned nbm = blocks_for(c->geo.N, PFL_STEP_THREADS);
+    if (c->swapped)
+      k_step_mrt<PREC, 1><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
+                                                      phishift<PREC>(c));
+    else
+      k_step_mrt<PREC, 0><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
+                                                      phishift<PREC>(c));
+  }
   c->swapped ^= 1;
   c->t += 1;
 }
@@ -288,6 +308,19 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
   c->geo.nz = p->nz;
   for (int a = 0; a < 3; ++a) c->geo.wall[a] = p->bc[2 * a] == PFL_NOSLIP ? 1 : 0;
   c->geo.N = (long long)p->nx * p->ny * p->nz;
+  c->idx32 = 27ull * (unsigned long long)c->geo.N < (1ull << 32);
+  c->g32.nx = p->nx;
+  c->g32.ny = p->ny;
+  c->g32.nz = p->nz;
+  c->g32.N = (unsigned)(c->idx32 ? c->geo.N : 0);
+  c->g32.dx = make_fastdiv((unsigned)p->nx);
+  c->g32.dy = make_fastdiv((unsigned)p->ny);
+  for (int a = 0; a < 3; ++a) c->g32.wall[a] = c->geo.wall[a];
+  if (c->idx32 && (!fastdiv_ok((unsigned)p->nx, (unsigned)c->geo.N) ||
+                   !fastdiv_ok((unsigned)p->ny, (unsigned)(c->geo.N / p->nx)))) {
+    delete c;
+    return fail(PFL_ERR_STATE, "integer divider self-check failed");
+  }
   c->ph.rho_h = p->rho_h;
   c->ph.rho_l = p->rho_l;
   c->ph.tau_h = 3.0 * p->nu_h + 0.5;

@@ -1,0 +1,422 @@
+// Fused stream-collide kernel of the MRT path, written around opposite-velocity
+// pairs.
+//
+// The collisions reduce to moments (see kernels.cuh): with degree-2 moments
+// relaxed at omega and all higher ones at 1 (g), or degrees 1 and 2 at
+// omega_phi and higher at 1 (h), every post-collision population is a
+// quadratic polynomial of its velocity,
+//   f+_i / w_i = alpha + beta . c_i + c_i . Gamma . c_i,
+// so a pair (c, -c) shares E = alpha + c.Gamma.c and differs only in the sign
+// of L = beta . c.  Moments are gathered the same way: S = f_c + f_-c feeds the
+// even moments (p*, phi, second moments), D = f_c - f_-c the odd ones.
+//   g:  alpha = p* - 3/2 u.u - a2 tr(Pi^d)/3,  beta = 3 u + 3/2 F / rho,
+//       Gamma = 9/2 u u^T + a2 Pi^d,           a2 = 9/2 (1 - omega)
+//   h:  alpha = phi - a2 tr(Pi^dh)/3,           beta = 3 phi u + a1 J^d + (1 - omega_phi/2) theta n,
+//       Gamma = a2 Pi^dh,                       a1 = 3 (1 - omega_phi), a2 = 9/2 (1 - omega_phi)
+// For the shifted FP16 format the coefficients are pre-scaled by the format's
+// power-of-two factor and alpha_h carries the shift, so a stored value is
+// E +- L without a per-population multiply by 1 / w.
+//
+// Neighbour addressing: per cell, the cell-index offsets of the -1 / +1
+// neighbours along each axis (periodic wrap folded in) and whether the link
+// crosses a no-slip face; offsets of a direction are sums of these, fixed at
+// compile time inside the unrolled loops.
+#pragma once
+#include "kernels.cuh"
+
+#ifndef PFL_STEP_THREADS
+#define PFL_STEP_THREADS 128
+#endif
+#ifndef PFL_STEP_MINB
+#define PFL_STEP_MINB 4
+#endif
+
+namespace pfl {
+
+// Exact q = n / d for 32-bit unsigned n and a divisor fixed for the launch
+// (division by an invariant integer using multiplication, Granlund and
+// Montgomery 1994, round-up multiplier form): with l = ceil(log2 d) and
+// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n), q = (t + ((n - t) >> s1)) >> s2,
+// s1 = min(l, 1), s2 = max(l - 1, 0).
+struct FastDiv {
+  unsigned d, m;
+  int s1, s2;
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d;
+  int l = 0;
+  while ((1ull << l) < d) ++l;
+  f.m = (unsigned)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+  f.s1 = l < 1 ? l : 1;
+  f.s2 = l - 1 > 0 ? l - 1 : 0;
+  return f;
+}
+
+__host__ __device__ __forceinline__ unsigned fdiv(unsigned n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+  const unsigned t = __umulhi(n, f.m);
+#else
+  const unsigned t = (unsigned)(((unsigned long long)n * f.m) >> 32);
+#endif
+  return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
+// Host check of the divider on the boundary cases and a spread of numerators.
+inline bool fastdiv_ok(unsigned d, unsigned nmax) {
+  const FastDiv f = make_fastdiv(d);
+  const unsigned probe[] = {0u, 1u, d - 1, d, d + 1, 2 * d - 1, 2 * d, nmax - 1, nmax};
+  for (unsigned n : probe)
+    if (n <= nmax && fdiv(n, f) != n / d) return false;
+  unsigned long long x = 0x9e3779b97f4a7c15ull;
+  for (int k = 0; k < 4096; ++k) {
+    x ^= x << 13;
+    x ^= x >> 7;
+    x ^= x << 17;
+    const unsigned n = (unsigned)(x % ((unsigned long long)nmax + 1));
+    if (fdiv(n, f) != n / d) return false;
+  }
+  return true;
+}
+
+// Launch geometry of the 32-bit-indexed kernels (27 N < 2^32).
+struct Geo32 {
+  unsigned nx, ny, nz, N;
+  FastDiv dx, dy;   // division by nx and by ny
+  int wall[3];
+};
+
+struct AxisOff {
+  int om, op;    // population neighbour offsets of x-1, x+1
+  bool vm, vp;   // the link to x-1 / x+1 stays inside (false behind a wall)
+  int sm, sp;    // phi-stencil offsets (mirror at walls)
+};
+
+__device__ __forceinline__ AxisOff axis_off(unsigned x, unsigned n, int stride, int wall) {
+  AxisOff a;
+  if (wall) {
+    a.vm = x > 0;
+    a.vp = x + 1 < n;
+    a.om = -stride;
+    a.op = stride;
+    a.sm = a.vm ? a.om : 0;
+    a.sp = a.vp ? a.op : 0;
+  } else {
+    a.vm = a.vp = true;
+    a.om = x > 0 ? -stride : (int)(n - 1) * stride;
+    a.op = x + 1 < n ? stride : -(int)(n - 1) * stride;
+    a.sm = a.om;
+    a.sp = a.op;
+  }
+  return a;
+}
+
+
+struct CellOff {
+  AxisOff X, Y, Z;
+  // population offset and validity of direction (cx, cy, cz)
+  __device__ __forceinline__ int off(int cx, int cy, int cz) const {
+    return (cx < 0 ? X.om : cx > 0 ? X.op : 0) + (cy < 0 ? Y.om : cy > 0 ? Y.op : 0) +
+           (cz < 0 ? Z.om : cz > 0 ? Z.op : 0);
+  }
+  __device__ __forceinline__ bool valid(int cx, int cy, int cz) const {
+    return (cx < 0 ? X.vm : cx > 0 ? X.vp : true) && (cy < 0 ? Y.vm : cy > 0 ? Y.vp : true) &&
+           (cz < 0 ? Z.vm : cz > 0 ? Z.vp : true);
+  }
+  __device__ __forceinline__ int soff(int cx, int cy, int cz) const {
+    return (cx < 0 ? X.sm : cx > 0 ? X.sp : 0) + (cy < 0 ? Y.sm : cy > 0 ? Y.sp : 0) +
+           (cz < 0 ? Z.sm : cz > 0 ? Z.sp : 0);
+  }
+};
+
+// Raw stored value as the arithmetic type (FP16: the stored number, unscaled).
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::R raw(typename Store<PREC>::S v) {
+  if constexpr (PREC == 2)
+    return __half2float(v);
+  else
+    return v;
+}
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::S pack(typename Store<PREC>::R v) {
+  if constexpr (PREC == 2)
+    return __float2half_rn(v);
+  else
+    return v;
+}
+
+__device__ __forceinline__ void cell_off(const Geo32& geo, unsigned c, CellOff& o) {
+  const unsigned yz = fdiv(c, geo.dx);
+  const unsigned x = c - yz * geo.nx;
+  const unsigned z = fdiv(yz, geo.dy);
+  const unsigned y = yz - z * geo.ny;
+  o.X = axis_off(x, geo.nx, 1, geo.wall[0]);
+  o.Y = axis_off(y, geo.ny, (int)geo.nx, geo.wall[1]);
+  o.Z = axis_off(z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
+}
+
+// Load the pair (i: direction c, oi: direction -c) arriving at `cell`.
+// a, b: raw stored values; fa, fb: the cells that wrote them.  Indices are
+// 32-bit (unsigned wrap-around arithmetic; the final index is in range).
+template <int PREC, int READ_ODD>
+__device__ __forceinline__ void load_pair(const typename Store<PREC>::S* __restrict__ f, unsigned N, unsigned cell,
+                                          const CellOff& o, int i, int oi, int cx, int cy, int cz,
+                                          typename Store<PREC>::R& a, typename Store<PREC>::R& b, unsigned& fa,
+                                          unsigned& fb) {
+  const bool vmc = o.valid(-cx, -cy, -cz), vc = o.valid(cx, cy, cz);
+  const unsigned nm = cell + (unsigned)o.off(-cx, -cy, -cz), np = cell + (unsigned)o.off(cx, cy, cz);
+  fa = vmc ? nm : cell;
+  fb = vc ? np : cell;
+  if (!READ_ODD) {
+    a = raw<PREC>(f[(unsigned)i * N + cell]);
+    b = raw<PREC>(f[(unsigned)oi * N + cell]);
+  } else {
+    a = raw<PREC>(f[vmc ? (unsigned)oi * N + nm : (unsigned)i * N + cell]);
+    b = raw<PREC>(f[vc ? (unsigned)i * N + np : (unsigned)oi * N + cell]);
+  }
+}
+
+// Store the post-collision pair (A: direction c, B: direction -c) of `cell`.
+template <int PREC, int ODD>
+__device__ __forceinline__ void store_pair(typename Store<PREC>::S* __restrict__ f, unsigned N, unsigned cell,
+                                           const CellOff& o, int i, int oi, int cx, int cy, int cz,
+                                           typename Store<PREC>::R A, typename Store<PREC>::R B) {
+  if (!ODD) {
+    f[(unsigned)oi * N + cell] = pack<PREC>(A);
+    f[(unsigned)i * N + cell] = pack<PREC>(B);
+  } else {
+    const bool vc = o.valid(cx, cy, cz), vmc = o.valid(-cx, -cy, -cz);
+    f[vc ? (unsigned)i * N + cell + (unsigned)o.off(cx, cy, cz) : (unsigned)oi * N + cell] = pack<PREC>(A);
+    f[vmc ? (unsigned)oi * N + cell + (unsigned)o.off(-cx, -cy, -cz) : (unsigned)i * N + cell] = pack<PREC>(B);
+  }
+}
+
+template <int PREC, int ODD>
+__global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB) k_step_mrt(Geo32 geo, Phys ph, typename Store<PREC>::S* __restrict__ h,
+                                                  typename Store<PREC>::S* __restrict__ g,
+                                                  const typename Store<PREC>::PhiT* __restrict__ phi,
+                                                  const typename Store<PREC>::PhiT* __restrict__ shift) {
+  typedef typename Store<PREC>::R R;
+  constexpr bool F16 = PREC == 2;
+  const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= geo.N) return;
+  const unsigned N = geo.N;
+  CellOff o;
+  cell_off(geo, cell, o);
+
+  // ---- phi stencil over D3Q27 weights, by pairs
+  const R pc = (R)__ldg(phi + cell);
+  R gx = 0, gy = 0, gz = 0, lap = 0;
+#pragma unroll
+  for (int i = 0; i < 13; ++i) {
+    const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+    const R a = (R)__ldg(phi + cell + o.soff(cx, cy, cz));
+    const R b = (R)__ldg(phi + cell + o.soff(-cx, -cy, -cz));
+    const R w = (R)q27_w(i);
+    const R d = w * (a - b);
+    if (cx) gx += cx > 0 ? d : -d;
+    if (cy) gy += cy > 0 ? d : -d;
+    if (cz) gz += cz > 0 ? d : -d;
+    lap += w * ((a + b) - (R)2 * pc);
+  }
+  gx *= (R)3;
+  gy *= (R)3;
+  gz *= (R)3;
+  lap *= (R)6;
+
+  // ---- g moments
+  R pst, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
+  {
+    const R rest = raw<PREC>(g[13u * N + cell]);
+    pst = F16 ? rest * (R)(q27_w(13) / KG16) : rest;
+  }
+#pragma unroll
+  for (int i = 0; i < 13; ++i) {
+    const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+    R a, b;
+    unsigned fa, fb;
+    load_pair<PREC, ODD>(g, N, cell, o, i, 26 - i, cx, cy, cz, a, b, fa, fb);
+    R S = a + b, D = a - b;
+    if (F16) {
+      S *= (R)(q27_w(i) / KG16);
+      D *= (R)(q27_w(i) / KG16);
+    }
+    pst += S;
+    if (cx) jx += cx > 0 ? D : -D;
+    if (cy) jy += cy > 0 ? D : -D;
+    if (cz) jz += cz > 0 ? D : -D;
+    if (cx) pxx += S;
+    if (cy) pyy += S;
+    if (cz) pzz += S;
+    if (cx && cy) pxy += (cx * cy > 0) ? S : -S;
+    if (cy && cz) pyz += (cy * cz > 0) ? S : -S;
+    if (cx && cz) pxz += (cx * cz > 0) ? S : -S;
+  }
+
+  // ---- forces and velocity (same expressions as hydro_macro)
+  const R drho = (R)(ph.rho_h - ph.rho_l);
+  const R rho = (R)ph.rho_l + pc * drho;
+  const R tau = (R)ph.tau_l + pc * (R)(ph.tau_h - ph.tau_l);
+  const R omega = (R)1 / tau;
+  const R nu = (tau - (R)0.5) * (R)(1.0 / 3.0);
+  const R mu = (R)4 * (R)ph.beta * pc * (pc - (R)1) * (pc - (R)0.5) - (R)ph.kappa * lap;
+  const R inv2rho = (R)0.5 / rho;
+  const R cp = -pst * (R)(1.0 / 3.0) * drho;
+  R Fx = (mu + cp) * gx + rho * (R)ph.gx;
+  R Fy = (mu + cp) * gy + rho * (R)ph.gy;
+  R Fz = (mu + cp) * gz + rho * (R)ph.gz;
+  const R p3 = pst * (R)(1.0 / 3.0);
+  {
+    const R u0x = jx + Fx * inv2rho, u0y = jy + Fy * inv2rho, u0z = jz + Fz * inv2rho;
+    const R nxx = pxx - p3 - u0x * u0x, nyy = pyy - p3 - u0y * u0y, nzz = pzz - p3 - u0z * u0z;
+    const R nxy = pxy - u0x * u0y, nyz = pyz - u0y * u0z, nxz = pxz - u0x * u0z;
+    const R cm = (R)-3 * nu * omega * drho;
+    Fx += cm * (nxx * gx + nxy * gy + nxz * gz);
+    Fy += cm * (nxy * gx + nyy * gy + nyz * gz);
+    Fz += cm * (nxz * gx + nyz * gy + nzz * gz);
+  }
+  const R ux = jx + Fx * inv2rho, uy = jy + Fy * inv2rho, uz = jz + Fz * inv2rho;
+
+  // ---- g post-collision coefficients and pair stores
+  {
+    const R uu = ux * ux + uy * uy + uz * uz;
+    const R a2 = ((R)1 - omega) * (R)4.5;
+    const R dxx = pxx - p3 - ux * ux, dyy = pyy - p3 - uy * uy, dzz = pzz - p3 - uz * uz;
+    const R K = F16 ? (R)KG16 : (R)1;
+    const R al = K * (pst - (R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
+    const R fr = (R)1.5 / rho;
+    const R bx = K * ((R)3 * ux + fr * Fx), by = K * ((R)3 * uy + fr * Fy), bz = K * ((R)3 * uz + fr * Fz);
+    const R Gxx = K * ((R)4.5 * ux * ux + a2 * dxx), Gyy = K * ((R)4.5 * uy * uy + a2 * dyy),
+            Gzz = K * ((R)4.5 * uz * uz + a2 * dzz);
+    const R Gxy = K * (R)2 * ((R)4.5 * ux * uy + a2 * (pxy - ux * uy));
+    const R Gyz = K * (R)2 * ((R)4.5 * uy * uz + a2 * (pyz - uy * uz));
+    const R Gxz = K * (R)2 * ((R)4.5 * ux * uz + a2 * (pxz - ux * uz));
+    g[13u * N + cell] = pack<PREC>(F16 ? al : (R)q27_w(13) * al);
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+      R E = al;
+      if (cx) E += Gxx;
+      if (cy) E += Gyy;
+      if (cz) E += Gzz;
+      if (cx && cy) E += (cx * cy > 0) ? Gxy : -Gxy;
+      if (cy && cz) E += (cy * cz > 0) ? Gyz : -Gyz;
+      if (cx && cz) E += (cx * cz > 0) ? Gxz : -Gxz;
+      R L = 0;
+      if (cx) L += cx > 0 ? bx : -bx;
+      if (cy) L += cy > 0 ? by : -by;
+      if (cz) L += cz > 0 ? bz : -bz;
+      R A = E + L, B = E - L;
+      if (!F16) {
+        A *= (R)q27_w(i);
+        B *= (R)q27_w(i);
+      }
+      store_pair<PREC, ODD>(g, N, cell, o, i, 26 - i, cx, cy, cz, A, B);
+    }
+  }
+
+  // ---- h moments (shifted FP16: value = w (s / K + phi_src))
+  R phl, hjx = 0, hjy = 0, hjz = 0, hxx = 0, hyy = 0, hzz = 0, hxy = 0, hyz = 0, hxz = 0;
+  {
+    const R rest = raw<PREC>(h[7u * N + cell]);
+    phl = F16 ? (rest * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7) : rest;
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+    R a, b;
+    unsigned fa, fb;
+    load_pair<PREC, ODD>(h, N, cell, o, k, 14 - k, cx, cy, cz, a, b, fa, fb);
+    R S, D;
+    if (F16) {
+      const R sa = (R)__ldg(shift + fa), sb = (R)__ldg(shift + fb);
+      const R w = (R)q15_w(k);
+      S = w * ((a + b) * (R)(1.0 / KH16) + (sa + sb));
+      D = w * ((a - b) * (R)(1.0 / KH16) + (sa - sb));
+    } else {
+      S = a + b;
+      D = a - b;
+    }
+    phl += S;
+    if (cx) hjx += cx > 0 ? D : -D;
+    if (cy) hjy += cy > 0 ? D : -D;
+    if (cz) hjz += cz > 0 ? D : -D;
+    if (cx) hxx += S;
+    if (cy) hyy += S;
+    if (cz) hzz += S;
+    if (cx && cy) hxy += (cx * cy > 0) ? S : -S;
+    if (cy && cz) hyz += (cy * cz > 0) ? S : -S;
+    if (cx && cz) hxz += (cx * cz > 0) ? S : -S;
+  }
+
+  // ---- h post-collision coefficients and pair stores
+  {
+    const R omp = (R)ph.omega_phi;
+    const R gn = sqrt(gx * gx + gy * gy + gz * gz);
+    const R theta = (R)4 * pc * ((R)1 - pc) * (R)ph.inv_xi;
+    const R tn = theta / (gn + (R)1e-6) * ((R)1 - (R)0.5 * omp);  // (1 - omega_phi/2) theta / |grad phi|
+    const R a1 = ((R)1 - omp) * (R)3, a2 = ((R)1 - omp) * (R)4.5;
+    const R ph3 = phl * (R)(1.0 / 3.0);
+    const R dxx = hxx - ph3, dyy = hyy - ph3, dzz = hzz - ph3;
+    const R K = F16 ? (R)KH16 : (R)1;
+    const R sh = F16 ? pc : (R)0;   // this cell's phi: the shift of everything it writes
+    const R al = K * ((phl - sh) - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
+    const R bx = K * ((R)3 * phl * ux + a1 * (hjx - phl * ux) + tn * gx);
+    const R by = K * ((R)3 * phl * uy + a1 * (hjy - phl * uy) + tn * gy);
+    const R bz = K * ((R)3 * phl * uz + a1 * (hjz - phl * uz) + tn * gz);
+    const R Gxx = K * a2 * dxx, Gyy = K * a2 * dyy, Gzz = K * a2 * dzz;
+    const R Gxy = K * (R)2 * a2 * hxy, Gyz = K * (R)2 * a2 * hyz, Gxz = K * (R)2 * a2 * hxz;
+    h[7u * N + cell] = pack<PREC>(F16 ? al : (R)q15_w(7) * al);
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+      R E = al;
+      if (cx) E += Gxx;
+      if (cy) E += Gyy;
+      if (cz) E += Gzz;
+      if (cx && cy) E += (cx * cy > 0) ? Gxy : -Gxy;
+      if (cy && cz) E += (cy * cz > 0) ? Gyz : -Gyz;
+      if (cx && cz) E += (cx * cz > 0) ? Gxz : -Gxz;
+      R L = 0;
+      if (cx) L += cx > 0 ? bx : -bx;
+      if (cy) L += cy > 0 ? by : -by;
+      if (cz) L += cz > 0 ? bz : -bz;
+      R A = E + L, B = E - L;
+      if (!F16) {
+        A *= (R)q15_w(k);
+        B *= (R)q15_w(k);
+      }
+      store_pair<PREC, ODD>(h, N, cell, o, k, 14 - k, cx, cy, cz, A, B);
+    }
+  }
+}
+
+// phi = sum_i h_i of the state left by the last step (READ_ODD after an even
+// step); `shift` holds the shifts of the stored populations (FP16S).
+template <int PREC, int READ_ODD>
+__global__ void __launch_bounds__(256) k_phi32(Geo32 geo, const typename Store<PREC>::S* __restrict__ h,
+                                               const typename Store<PREC>::PhiT* __restrict__ shift,
+                                               typename Store<PREC>::PhiT* __restrict__ phi) {
+  typedef typename Store<PREC>::R R;
+  constexpr bool F16 = PREC == 2;
+  const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= geo.N) return;
+  CellOff o;
+  cell_off(geo, cell, o);
+  R s = F16 ? (raw<PREC>(h[7u * geo.N + cell]) * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7)
+            : raw<PREC>(h[7u * geo.N + cell]);
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    R a, b;
+    unsigned fa, fb;
+    load_pair<PREC, READ_ODD>(h, geo.N, cell, o, k, 14 - k, q15_cx(k), q15_cy(k), q15_cz(k), a, b, fa, fb);
+    if (F16)
+      s += (R)q15_w(k) * ((a + b) * (R)(1.0 / KH16) + ((R)__ldg(shift + fa) + (R)__ldg(shift + fb)));
+    else
+      s += a + b;
+  }
+  phi[cell] = s;
+}
+
+}  // namespace pfl

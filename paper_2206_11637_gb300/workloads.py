@@ -139,8 +139,25 @@ def poiseuille(H=16, nx=1, g=1e-6, nu=1.0 / 8.0, collision=0):
     return p, np.ones(p.shape), None, None
 
 
+def hydrostatic_pstar(p, phi0, level, inclusions=()):
+    """Initial normalised pressure p* = p / (rho(phi) c_s^2) of a liquid at rest
+    under gravity along -y (the paper initialises hydrostatic pressure in its
+    gravity cases): p = rho_h |g| (level - y) in the liquid, zero reference at
+    y = level; each inclusion (weight field, pressure) adds a region of uniform
+    pressure (a bubble at the liquid pressure of its centre plus its Laplace
+    jump, or a falling drop at its Laplace jump), blended by its weight."""
+    _, y, _ = coords(p)
+    g = abs(p.gravity[1])
+    p_liq = p.rho_h * g * (level - y)
+    pres = p_liq
+    for weight, value in inclusions:
+        pres = (1.0 - weight) * pres + weight * value
+    rho = p.rho_l + phi0 * (p.rho_h - p.rho_l)
+    return 3.0 * pres / rho
+
+
 def rising_bubble(nx=128, ny=384, nz=128, D=32.0, xi=4.0, M=0.02, rho_ratio=1000.0, mu_ratio=100.0,
-                  Eo=10.0, Mo=1e-3, nu_h=1.0 / 60.0, collision=0):
+                  Eo=10.0, Mo=1e-3, nu_h=1.0 / 60.0, collision=0, hydrostatic=True, level=None):
     """Gas bubble of diameter D at 1.5 D above the bottom (y up), walls on all sides.
 
     Gravity and sigma from the Eotvos and Morton numbers with the heavy-phase
@@ -153,11 +170,18 @@ def rising_bubble(nx=128, ny=384, nz=128, D=32.0, xi=4.0, M=0.02, rho_ratio=1000
     p = Params(nx, ny, nz, (NOSLIP,) * 6, 1.0, 1.0 / rho_ratio, nu_h, nu_l, sigma, M, xi,
                (0.0, -g, 0.0), collision)
     c = ((nx - 1) / 2.0, 1.5 * D, (nz - 1) / 2.0)
-    return p, sphere(p, c, D / 2.0, heavy_inside=False), None, None
+    phi0 = sphere(p, c, D / 2.0, heavy_inside=False)
+    p0 = None
+    if hydrostatic:
+        # zero pressure at the bubble's height keeps p* = 3 p / rho small in the gas
+        level = c[1] if level is None else level
+        p_bubble = p.rho_h * g * (level - c[1]) + 2.0 * sigma / (D / 2.0)
+        p0 = hydrostatic_pstar(p, phi0, level, [(1.0 - phi0, p_bubble)])
+    return p, phi0, None, p0
 
 
 def drop_impact(nx=512, ny=384, nz=512, D=64.0, depth=128.0, gap=8.0, We=200.0, Fr=200.0, U=0.05,
-                omega_h=1.988, rho_ratio=1000.0, mu_ratio=50.0, xi=5.0, M=0.02, collision=0):
+                omega_h=1.988, rho_ratio=1000.0, mu_ratio=50.0, xi=5.0, M=0.02, collision=0, hydrostatic=True):
     """Vertical drop impact into a pool (y up), no-slip walls on all sides.
 
     sigma = rho_h U^2 D / We, g = U^2 / (Fr D), nu_h from omega_h,
@@ -177,4 +201,13 @@ def drop_impact(nx=512, ny=384, nz=512, D=64.0, depth=128.0, gap=8.0, We=200.0, 
     phi0 = np.maximum(drop, pool)
     u0 = np.zeros((3,) + p.shape)
     u0[1] = -U * drop * (y > depth + gap / 2.0)
-    return p, phi0, u0, None
+    p0 = None
+    if hydrostatic:
+        # liquid below the pool surface at its hydrostatic pressure, gas at the
+        # surface pressure, the drop at its Laplace jump
+        _, yy, _ = coords(p)
+        p_pool = p.rho_h * g * np.maximum(depth - yy, 0.0) * pool
+        pres = p_pool + drop * 2.0 * sigma / (D / 2.0)
+        rho = p.rho_l + phi0 * (p.rho_h - p.rho_l)
+        p0 = 3.0 * pres / rho
+    return p, phi0, u0, p0

@@ -53,7 +53,7 @@ CASES = {
     # name: (builder, steps)
     "static_drop_32": (lambda: W.static_drop(32, 10.0, u_noise=1e-3, seed=1234), 1000),
     "wave_walls_y": (lambda: W.capillary_wave(40, ny=48, a0=1.5, xi=5.0, sigma=1e-4, nu=0.01), 400),
-    "bubble_all_walls": (lambda: W.rising_bubble(24, 40, 20, D=10.0, xi=4.0, M=0.05), 200),
+    "bubble_all_walls": (lambda: W.rising_bubble(24, 40, 20, D=10.0, xi=4.0, M=0.05, hydrostatic=False), 200),
 }
 
 
@@ -69,6 +69,28 @@ def test_fp64_parity(name):
     h, g = s.populations()
     oh, og = o.populations()
     assert rel(h, oh) < 1e-10 and rel(g, og) < 1e-10
+
+
+def test_fp64_parity_hydrostatic_bubble():
+    """Bubble under gravity with the hydrostatic initial pressure.  This case
+    amplifies rounding: two oracle runs whose phi0 differ by 1e-16 spread by
+    ~2e-10 in h after 200 steps.  The GPU must agree within 1e-10 or within
+    four times that spread, whichever is larger."""
+    p, phi0, u0, p0 = W.rising_bubble(24, 40, 20, D=10.0, xi=4.0, M=0.05)
+    steps = 200
+    o = oracle.from_params(p, phi0, u0, p0)
+    o2 = oracle.from_params(p, phi0 + 1e-16 * W.noise(phi0.shape, 7, 1.0), u0, p0)
+    o.step(steps, THREADS)
+    o2.step(steps, THREADS)
+    oh, og = o.populations()
+    oh2, og2 = o2.populations()
+    spread_h, spread_g = rel(oh2, oh), rel(og2, og)
+    s = sim(p, phi0, u0, p0, "fp64")
+    s.step(steps)
+    h, g = s.populations()
+    assert rel(h, oh) <= max(1e-10, 4 * spread_h)
+    assert rel(g, og) <= max(1e-10, 4 * spread_g)
+    compare_fields(s, o, max(1e-10, 4 * spread_h), 1e-9, 1e-9)
 
 
 def test_fp64_ragged_mixed_boundaries():
