@@ -132,6 +132,28 @@ pfl_status pfl_diag(pfl_ctx* ctx, double out[8], long long* nonfinite);
  * phi = sum h).  Measurement aid; synchronises. */
 pfl_status pfl_kernel_times(pfl_ctx* ctx, int n_steps, double ms[2]);
 
+/* Mass and centre-of-mass sums of a phase field the caller already holds,
+ * computed without any device memory from the caller: for callers that are
+ * not allowed to allocate device memory themselves -- an application whose
+ * GPU memory all belongs to its own pool or caching allocator, a plugin given
+ * fixed buffers and no right to allocate, a loop that cannot pay for the
+ * device synchronisation an allocation may cause.  The paper has no
+ * counterpart; this is a service of the library.
+ *   phi: device pointer to nx*ny*nz values, x-fastest; FP64 if phi_fp64 != 0,
+ *        else FP32 (the caller keeps ownership).
+ *   out: host array of 8 doubles, the same sums as pfl_diag; nonfinite (host,
+ *        may be NULL) the number of NaN/Inf values.  stream: a cudaStream_t.
+ * Scratch: a fixed array inside the library image (about 88 KB per device,
+ * held until the process exits); no cudaMalloc/cudaFree is called.  The first
+ * call on a device looks up that array's device address, so make it before
+ * any stream capture.  All calls on one device share the array: calls that
+ * overlap on the GPU race and must be ordered by the caller.
+ * Errors: PFL_ERR_ARG for NULL pointers, non-device phi, dims < 1 or more than
+ * 2^31 - 1 cells; PFL_ERR_UNSTABLE when NaN/Inf are present; PFL_ERR_CUDA.
+ * Synchronises the stream. */
+pfl_status pfl_phi_moments_static(const void* phi, int phi_fp64, int nx, int ny, int nz, double out[8],
+                                  long long* nonfinite, void* stream);
+
 /* Time steps taken since pfl_init (or -1 for a NULL context). */
 long long pfl_time(const pfl_ctx* ctx);
 

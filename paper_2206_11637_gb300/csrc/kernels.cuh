@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag(Geo geo, const PhiT* __re
   }
 }
 
-__global__ void k_diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+static __global__ void k_diag_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
   // one warp per quantity, fixed order
   const int k = blockIdx.x;
   double s = 0;

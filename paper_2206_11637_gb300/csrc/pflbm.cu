@@ -11,6 +11,7 @@
 #include <string>
 
 #include "../../include/pflbm.h"
+#include "errors.h"
 #include "kernels.cuh"
 #include "step.cuh"
 
@@ -24,6 +25,14 @@ pfl_status fail(pfl_status s, const std::string& msg) {
   g_err = msg;
   return s;
 }
+
+}  // namespace
+
+namespace pfl_internal {
+void set_error(const std::string& msg) { g_err = msg; }
+}  // namespace pfl_internal
+
+namespace {
 
 pfl_status cuda_fail(cudaError_t e, const char* what) {
   return fail(PFL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
