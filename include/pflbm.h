@@ -132,6 +132,32 @@ pfl_status pfl_diag(pfl_ctx* ctx, double out[8], long long* nonfinite);
  * phi = sum h).  Measurement aid; synchronises. */
 pfl_status pfl_kernel_times(pfl_ctx* ctx, int n_steps, double ms[2]);
 
+/* Device bytes of the adjoint workspace for an adjoint over n_steps steps
+ * (0 if ctx is NULL or n_steps < 1).  It holds ceil(n_steps / K) checkpoints
+ * and K recomputed states with K = ceil(sqrt(n_steps)), two adjoint
+ * population sets, the observation weights and the reduction scratch. */
+size_t pfl_adjoint_workspace_bytes(const pfl_ctx* ctx, int n_steps);
+
+/* Discrete adjoint of n_steps time steps from the current state: the gradient
+ * of J = sum_o sum_x W_o(x) phi(x, t0 + s_o) with respect to the mobility M,
+ * the interface width xi and the surface tension sigma -- the parameters the
+ * paper finds the PFLBM's accuracy sensitive to (sections "Rising bubble",
+ * mobility study).  Bubble rise velocity (the centroid of 1 - phi, linear in
+ * phi because sum(1 - phi) is conserved) and the amplitude of a wave mode are
+ * such functionals.
+ *   obs_steps: n_obs distinct steps in [0, n_steps], relative to the current
+ *   time; obs_weights: n_obs arrays of N doubles (host or device).
+ *   The forward run keeps a checkpoint every K = ceil(sqrt(n_steps)) steps,
+ *   and the reverse sweep recomputes one K-step segment at a time.
+ *   On return the context holds the state after n_steps steps (as pfl_step);
+ *   *J receives J, grad[0..2] = dJ/dM, dJ/dxi, dJ/dsigma.
+ *   adj_workspace: device memory of pfl_adjoint_workspace_bytes() bytes,
+ *   256-byte aligned, caller-owned.
+ * PFL_ERR_STATE for FP16S storage, the BGK mode or lattices with 27 N >= 2^32;
+ * PFL_ERR_ARG for bad observations (at most 8).  Synchronises. */
+pfl_status pfl_adjoint(pfl_ctx* ctx, int n_steps, int n_obs, const int* obs_steps, const double* const* obs_weights,
+                       void* adj_workspace, size_t adj_bytes, double* J, double grad[3]);
+
 /* Mass and centre-of-mass sums of a phase field the caller already holds,
  * computed without any device memory from the caller: for callers that are
  * not allowed to allocate device memory themselves -- an application whose

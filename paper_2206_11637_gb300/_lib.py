@@ -62,6 +62,12 @@ def load():
     lib.pfl_set_populations.argtypes = [P, P, P]
     lib.pfl_diag.restype = I
     lib.pfl_diag.argtypes = [P, P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.pfl_adjoint_workspace_bytes.restype = S
+    lib.pfl_adjoint_workspace_bytes.argtypes = [P, I]
+    lib.pfl_adjoint.restype = I
+    lib.pfl_adjoint.argtypes = [P, I, I, P, P, P, S, P, P]
+    lib.pfl_phi_moments_static.restype = I
+    lib.pfl_phi_moments_static.argtypes = [P, I, I, I, I, P, ctypes.POINTER(ctypes.c_longlong), P]
     lib.pfl_kernel_times.restype = I
     lib.pfl_kernel_times.argtypes = [P, I, P]
     lib.pfl_time.restype = ctypes.c_longlong

@@ -6,7 +6,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpflbm.so")
 SOURCES = ["pflbm.cu", "noalloc.cu"]
-DEPS = SOURCES + ["kernels.cuh", "lattice.cuh", "step.cuh", "errors.h"]
+DEPS = SOURCES + ["kernels.cuh", "lattice.cuh", "step.cuh", "adjoint.cuh", "errors.h"]
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pflbm.h")
 
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",

@@ -1,0 +1,524 @@
+// Discrete adjoint of the MRT stream-collide step (FP64 and FP32 storage).
+//
+// Forward step t maps the populations s^t = (h^t, g^t) to s^{t+1}: phi^t = sum h,
+// the D3Q27 stencil of phi^t, the local collision map P (moments -> forces ->
+// post-collision populations, see step.cuh) and streaming.  For an objective
+// J = sum_o sum_x W_o(x) phi^{t_o}(x) the adjoint recursion is
+//   lambda^t = (d s^{t+1} / d s^t)^T lambda^{t+1} + dJ / d s^t,
+//   dJ / d theta = sum_t (dP / d theta)^T lambda^+_t,   theta = (M, xi, sigma),
+// where lambda^+_t(x, i) is the adjoint of the post-collision population i of
+// cell x: lambda^{t+1} at the cell and slot that streaming delivered it to.
+//
+// k_adj_local (one thread per cell) recomputes P's intermediates from the saved
+// state s^t and runs P's reverse sweep: it writes the adjoint of the local
+// pre-collision populations through the moments, and per cell the adjoints of
+// the stencil outputs (grad phi, lap phi) and of phi(x) itself.  k_adj_phi then
+// gathers the stencil's transpose -- every (cell y, direction c) whose stencil
+// read phi at x, walls folded in -- and adds the resulting adjoint of phi(x) to
+// all 15 h adjoints of x (phi = sum h), together with W_o at observation steps.
+//
+// Adjoint populations are kept in the canonical layout [i][cell] (h: 15 N,
+// then g: 27 N) in the arithmetic type.
+#pragma once
+#include "step.cuh"
+
+namespace pfl {
+
+constexpr int ADJ_THREADS = 128;
+
+// Parameters of the reverse sweep that the forward step folds into Phys.
+struct AdjPar {
+  double M, xi, sigma;
+};
+
+template <typename R>
+__device__ __forceinline__ R block_sum3_to(R a, R b, R c, double* out3) {
+  // FP64 block reduction of three values; thread 0 writes out3[0..2].
+  __shared__ double sm[ADJ_THREADS / 32][3];
+  double v[3] = {(double)a, (double)b, (double)c};
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    double s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) sm[wid][k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double s = 0;
+    for (int w = 0; w < ADJ_THREADS / 32; ++w) s += sm[w][threadIdx.x];
+    out3[threadIdx.x] = s;
+  }
+  return a;
+}
+
+template <int PREC, int READ_ODD>
+__global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, AdjPar ap,
+                                                           const typename Store<PREC>::S* __restrict__ h,
+                                                           const typename Store<PREC>::S* __restrict__ g,
+                                                           const typename Store<PREC>::PhiT* __restrict__ phi,
+                                                           const typename Store<PREC>::R* __restrict__ lam_in,
+                                                           typename Store<PREC>::R* __restrict__ lam_out,
+                                                           typename Store<PREC>::R* __restrict__ aux,
+                                                           double* __restrict__ part) {
+  static_assert(PREC != 2, "the adjoint runs on FP64 or FP32 storage");
+  typedef typename Store<PREC>::R R;
+  const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = cell < geo.N;
+  R bM = 0, bXi = 0, bSig = 0;
+  if (active) {
+    const unsigned N = geo.N;
+    CellOff o;
+    cell_off(geo, cell, o);
+
+    // ---------------- forward recomputation (as in k_step_mrt)
+    const R pc = (R)phi[cell];
+    R gx = 0, gy = 0, gz = 0, lap = 0;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+      const R a = (R)phi[cell + o.soff(cx, cy, cz)];
+      const R b = (R)phi[cell + o.soff(-cx, -cy, -cz)];
+      const R w = (R)q27_w(i);
+      const R d = w * (a - b);
+      if (cx) gx += cx > 0 ? d : -d;
+      if (cy) gy += cy > 0 ? d : -d;
+      if (cz) gz += cz > 0 ? d : -d;
+      lap += w * ((a + b) - (R)2 * pc);
+    }
+    gx *= (R)3;
+    gy *= (R)3;
+    gz *= (R)3;
+    lap *= (R)6;
+
+    R pst = g[13u * N + cell], jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+      R a, b;
+      unsigned fa, fb;
+      load_pair<PREC, READ_ODD>(g, N, cell, o, i, 26 - i, cx, cy, cz, a, b, fa, fb);
+      const R S = a + b, D = a - b;
+      pst += S;
+      if (cx) jx += cx > 0 ? D : -D;
+      if (cy) jy += cy > 0 ? D : -D;
+      if (cz) jz += cz > 0 ? D : -D;
+      if (cx) pxx += S;
+      if (cy) pyy += S;
+      if (cz) pzz += S;
+      if (cx && cy) pxy += (cx * cy > 0) ? S : -S;
+      if (cy && cz) pyz += (cy * cz > 0) ? S : -S;
+      if (cx && cz) pxz += (cx * cz > 0) ? S : -S;
+    }
+    R phl = h[7u * N + cell], hjx = 0, hjy = 0, hjz = 0, hxx = 0, hyy = 0, hzz = 0, hxy = 0, hyz = 0, hxz = 0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+      R a, b;
+      unsigned fa, fb;
+      load_pair<PREC, READ_ODD>(h, N, cell, o, k, 14 - k, cx, cy, cz, a, b, fa, fb);
+      const R S = a + b, D = a - b;
+      phl += S;
+      if (cx) hjx += cx > 0 ? D : -D;
+      if (cy) hjy += cy > 0 ? D : -D;
+      if (cz) hjz += cz > 0 ? D : -D;
+      if (cx) hxx += S;
+      if (cy) hyy += S;
+      if (cz) hzz += S;
+      if (cx && cy) hxy += (cx * cy > 0) ? S : -S;
+      if (cy && cz) hyz += (cy * cz > 0) ? S : -S;
+      if (cx && cz) hxz += (cx * cz > 0) ? S : -S;
+    }
+
+    const R drho = (R)(ph.rho_h - ph.rho_l);
+    const R dtau = (R)(ph.tau_h - ph.tau_l);
+    const R rho = (R)ph.rho_l + pc * drho;
+    const R tau = (R)ph.tau_l + pc * dtau;
+    const R omega = (R)1 / tau;
+    const R nu = (tau - (R)0.5) * (R)(1.0 / 3.0);
+    const R beta = (R)ph.beta, kappa = (R)ph.kappa;
+    const R dw = pc * (pc - (R)1) * (pc - (R)0.5);
+    const R mu = (R)4 * beta * dw - kappa * lap;
+    const R inv2rho = (R)0.5 / rho;
+    const R cp = -pst * (R)(1.0 / 3.0) * drho;
+    const R Gx = (R)ph.gx, Gy = (R)ph.gy, Gz = (R)ph.gz;
+    const R F0x = (mu + cp) * gx + rho * Gx, F0y = (mu + cp) * gy + rho * Gy, F0z = (mu + cp) * gz + rho * Gz;
+    const R p3 = pst * (R)(1.0 / 3.0);
+    const R u0x = jx + F0x * inv2rho, u0y = jy + F0y * inv2rho, u0z = jz + F0z * inv2rho;
+    const R Nxx = pxx - p3 - u0x * u0x, Nyy = pyy - p3 - u0y * u0y, Nzz = pzz - p3 - u0z * u0z;
+    const R Nxy = pxy - u0x * u0y, Nyz = pyz - u0y * u0z, Nxz = pxz - u0x * u0z;
+    const R cm = (R)-3 * nu * omega * drho;
+    const R NGx = Nxx * gx + Nxy * gy + Nxz * gz;
+    const R NGy = Nxy * gx + Nyy * gy + Nyz * gz;
+    const R NGz = Nxz * gx + Nyz * gy + Nzz * gz;
+    const R Fx = F0x + cm * NGx, Fy = F0y + cm * NGy, Fz = F0z + cm * NGz;
+    const R ux = jx + Fx * inv2rho, uy = jy + Fy * inv2rho, uz = jz + Fz * inv2rho;
+    const R a2 = ((R)1 - omega) * (R)4.5;
+    const R dxx = pxx - p3 - ux * ux, dyy = pyy - p3 - uy * uy, dzz = pzz - p3 - uz * uz;
+    const R fr = (R)1.5 / rho;
+    // phase field
+    const R omp = (R)ph.omega_phi;
+    const R gn = sqrt(gx * gx + gy * gy + gz * gz);
+    const R den = gn + (R)1e-6;
+    const R theta = (R)4 * pc * ((R)1 - pc) * (R)ph.inv_xi;
+    const R sfac = (R)1 - (R)0.5 * omp;
+    const R tn = theta / den * sfac;
+    const R a1h = ((R)1 - omp) * (R)3, a2h = ((R)1 - omp) * (R)4.5;
+    const R ph3 = phl * (R)(1.0 / 3.0);
+    const R dhxx = hxx - ph3, dhyy = hyy - ph3, dhzz = hzz - ph3;
+
+    // ---------------- adjoints of the post-collision populations
+    // g: lambda+ of population i of this cell sits where streaming put it
+    R b_al = 0, b_bx = 0, b_by = 0, b_bz = 0, b_Gxx = 0, b_Gyy = 0, b_Gzz = 0, b_Gxy = 0, b_Gyz = 0, b_Gxz = 0;
+    const R* lg = lam_in + 15u * N;
+    b_al = (R)q27_w(13) * lg[13u * N + cell];
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+      const int oi = 26 - i;
+      // direction c (index i) went to x + c (slot i) or bounced into slot oi of x
+      const R la = o.valid(cx, cy, cz) ? lg[(unsigned)i * N + cell + (unsigned)o.off(cx, cy, cz)]
+                                       : lg[(unsigned)oi * N + cell];
+      const R lb = o.valid(-cx, -cy, -cz) ? lg[(unsigned)oi * N + cell + (unsigned)o.off(-cx, -cy, -cz)]
+                                          : lg[(unsigned)i * N + cell];
+      const R w = (R)q27_w(i);
+      const R S = w * (la + lb), D = w * (la - lb);
+      b_al += S;
+      if (cx) b_bx += cx > 0 ? D : -D;
+      if (cy) b_by += cy > 0 ? D : -D;
+      if (cz) b_bz += cz > 0 ? D : -D;
+      if (cx) b_Gxx += S;
+      if (cy) b_Gyy += S;
+      if (cz) b_Gzz += S;
+      if (cx && cy) b_Gxy += (cx * cy > 0) ? S : -S;
+      if (cy && cz) b_Gyz += (cy * cz > 0) ? S : -S;
+      if (cx && cz) b_Gxz += (cx * cz > 0) ? S : -S;
+    }
+    // h
+    R c_al = (R)q15_w(7) * lam_in[7u * N + cell], c_bx = 0, c_by = 0, c_bz = 0;
+    R c_Gxx = 0, c_Gyy = 0, c_Gzz = 0, c_Gxy = 0, c_Gyz = 0, c_Gxz = 0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+      const int ok = 14 - k;
+      const R la = o.valid(cx, cy, cz) ? lam_in[(unsigned)k * N + cell + (unsigned)o.off(cx, cy, cz)]
+                                       : lam_in[(unsigned)ok * N + cell];
+      const R lb = o.valid(-cx, -cy, -cz) ? lam_in[(unsigned)ok * N + cell + (unsigned)o.off(-cx, -cy, -cz)]
+                                          : lam_in[(unsigned)k * N + cell];
+      const R w = (R)q15_w(k);
+      const R S = w * (la + lb), D = w * (la - lb);
+      c_al += S;
+      if (cx) c_bx += cx > 0 ? D : -D;
+      if (cy) c_by += cy > 0 ? D : -D;
+      if (cz) c_bz += cz > 0 ? D : -D;
+      if (cx) c_Gxx += S;
+      if (cy) c_Gyy += S;
+      if (cz) c_Gzz += S;
+      if (cx && cy) c_Gxy += (cx * cy > 0) ? S : -S;
+      if (cy && cz) c_Gyz += (cy * cz > 0) ? S : -S;
+      if (cx && cz) c_Gxz += (cx * cz > 0) ? S : -S;
+    }
+
+    // ---------------- reverse sweep of the local map
+    // adjoint accumulators of the inputs
+    R b_pst = 0, b_jx = 0, b_jy = 0, b_jz = 0, b_pxx = 0, b_pyy = 0, b_pzz = 0, b_pxy = 0, b_pyz = 0, b_pxz = 0;
+    R b_phl = 0, b_hjx = 0, b_hjy = 0, b_hjz = 0, b_hxx = 0, b_hyy = 0, b_hzz = 0, b_hxy = 0, b_hyz = 0, b_hxz = 0;
+    R b_pc = 0, b_gx = 0, b_gy = 0, b_gz = 0, b_lap = 0;
+    // intermediates
+    R b_ux = 0, b_uy = 0, b_uz = 0, b_Fx = 0, b_Fy = 0, b_Fz = 0, b_rho = 0, b_omega = 0;
+
+    // g: al = pst - 1.5 uu - a2 (dxx + dyy + dzz) / 3 ; b = 3 u + fr F ;
+    //    Gaa = 4.5 ua^2 + a2 daa ; Gab = 2 (4.5 - a2) ua ub + 2 a2 pab
+    {
+      R b_a2 = 0, b_dxx = 0, b_dyy = 0, b_dzz = 0, b_fr = 0;
+      b_pst += b_al;
+      b_ux += (R)-3 * ux * b_al;
+      b_uy += (R)-3 * uy * b_al;
+      b_uz += (R)-3 * uz * b_al;
+      b_a2 += -b_al * (dxx + dyy + dzz) * (R)(1.0 / 3.0);
+      const R btr = -b_al * a2 * (R)(1.0 / 3.0);
+      b_dxx += btr;
+      b_dyy += btr;
+      b_dzz += btr;
+      // b
+      b_ux += (R)3 * b_bx;
+      b_uy += (R)3 * b_by;
+      b_uz += (R)3 * b_bz;
+      b_Fx += fr * b_bx;
+      b_Fy += fr * b_by;
+      b_Fz += fr * b_bz;
+      b_fr += Fx * b_bx + Fy * b_by + Fz * b_bz;
+      // diagonal G
+      b_ux += (R)9 * ux * b_Gxx;
+      b_uy += (R)9 * uy * b_Gyy;
+      b_uz += (R)9 * uz * b_Gzz;
+      b_a2 += dxx * b_Gxx + dyy * b_Gyy + dzz * b_Gzz;
+      b_dxx += a2 * b_Gxx;
+      b_dyy += a2 * b_Gyy;
+      b_dzz += a2 * b_Gzz;
+      // off-diagonal G (stored with the factor 2)
+      const R k2 = (R)2 * ((R)4.5 - a2);
+      b_ux += k2 * (uy * b_Gxy + uz * b_Gxz);
+      b_uy += k2 * (ux * b_Gxy + uz * b_Gyz);
+      b_uz += k2 * (uy * b_Gyz + ux * b_Gxz);
+      b_a2 += (R)2 * ((pxy - ux * uy) * b_Gxy + (pyz - uy * uz) * b_Gyz + (pxz - ux * uz) * b_Gxz);
+      b_pxy += (R)2 * a2 * b_Gxy;
+      b_pyz += (R)2 * a2 * b_Gyz;
+      b_pxz += (R)2 * a2 * b_Gxz;
+      // d_aa = p_aa - p3 - ua^2
+      b_pxx += b_dxx;
+      b_pyy += b_dyy;
+      b_pzz += b_dzz;
+      b_pst += -(b_dxx + b_dyy + b_dzz) * (R)(1.0 / 3.0);
+      b_ux += (R)-2 * ux * b_dxx;
+      b_uy += (R)-2 * uy * b_dyy;
+      b_uz += (R)-2 * uz * b_dzz;
+      b_rho += (R)-1.5 / (rho * rho) * b_fr;
+      b_omega += (R)-4.5 * b_a2;
+    }
+
+    // h: al = phl - a2h (sum dh) / 3 ; b = (3 - a1h) phl u + a1h hj + tn grad ;
+    //    Gaa = a2h dhaa ; Gab = 2 a2h hab
+    {
+      R b_a1h = 0, b_a2h = 0, b_tn = 0;
+      const R sdh = dhxx + dhyy + dhzz;
+      b_phl += c_al;
+      b_a2h += -c_al * sdh * (R)(1.0 / 3.0);
+      const R bsd = -c_al * a2h * (R)(1.0 / 3.0);
+      b_hxx += bsd;
+      b_hyy += bsd;
+      b_hzz += bsd;
+      b_phl += -bsd;
+      b_a2h += dhxx * c_Gxx + dhyy * c_Gyy + dhzz * c_Gzz;
+      b_hxx += a2h * c_Gxx;
+      b_hyy += a2h * c_Gyy;
+      b_hzz += a2h * c_Gzz;
+      b_phl += -a2h * (R)(1.0 / 3.0) * (c_Gxx + c_Gyy + c_Gzz);
+      b_a2h += (R)2 * (hxy * c_Gxy + hyz * c_Gyz + hxz * c_Gxz);
+      b_hxy += (R)2 * a2h * c_Gxy;
+      b_hyz += (R)2 * a2h * c_Gyz;
+      b_hxz += (R)2 * a2h * c_Gxz;
+      const R k3 = (R)3 - a1h;
+      b_phl += k3 * (ux * c_bx + uy * c_by + uz * c_bz);
+      b_ux += k3 * phl * c_bx;
+      b_uy += k3 * phl * c_by;
+      b_uz += k3 * phl * c_bz;
+      b_a1h += (hjx - phl * ux) * c_bx + (hjy - phl * uy) * c_by + (hjz - phl * uz) * c_bz;
+      b_hjx += a1h * c_bx;
+      b_hjy += a1h * c_by;
+      b_hjz += a1h * c_bz;
+      b_tn += gx * c_bx + gy * c_by + gz * c_bz;
+      b_gx += tn * c_bx;
+      b_gy += tn * c_by;
+      b_gz += tn * c_bz;
+      // tn = theta / den * sfac, den = |grad| + eps
+      const R b_theta = sfac / den * b_tn;
+      const R b_den = -theta * sfac / (den * den) * b_tn;
+      const R b_sfac = theta / den * b_tn;
+      if (gn > (R)0) {
+        b_gx += gx / gn * b_den;
+        b_gy += gy / gn * b_den;
+        b_gz += gz / gn * b_den;
+      }
+      // theta = 4 pc (1 - pc) / xi
+      b_pc += (R)4 * ((R)1 - (R)2 * pc) * (R)ph.inv_xi * b_theta;
+      const R b_invxi = (R)4 * pc * ((R)1 - pc) * b_theta;
+      bXi += -b_invxi / (R)(ap.xi * ap.xi);
+      // omega_phi -> M
+      const R b_omp = (R)-3 * b_a1h - (R)4.5 * b_a2h - (R)0.5 * b_sfac;
+      bM += (R)-3 * omp * omp * b_omp;
+    }
+
+    // u = j + F inv2rho ; F = F0 + cm NG ; NG = N grad ; u0 = j + F0 inv2rho
+    {
+      R b_inv2rho = 0;
+      b_jx += b_ux;
+      b_jy += b_uy;
+      b_jz += b_uz;
+      b_Fx += inv2rho * b_ux;
+      b_Fy += inv2rho * b_uy;
+      b_Fz += inv2rho * b_uz;
+      b_inv2rho += Fx * b_ux + Fy * b_uy + Fz * b_uz;
+      // F = F0 + cm NG
+      R b_F0x = b_Fx, b_F0y = b_Fy, b_F0z = b_Fz;
+      const R b_cm = NGx * b_Fx + NGy * b_Fy + NGz * b_Fz;
+      const R bNGx = cm * b_Fx, bNGy = cm * b_Fy, bNGz = cm * b_Fz;
+      // NG_a = sum_b N_ab g_b (N symmetric)
+      const R b_Nxx = bNGx * gx, b_Nyy = bNGy * gy, b_Nzz = bNGz * gz;
+      const R b_Nxy = bNGx * gy + bNGy * gx, b_Nyz = bNGy * gz + bNGz * gy, b_Nxz = bNGx * gz + bNGz * gx;
+      b_gx += Nxx * bNGx + Nxy * bNGy + Nxz * bNGz;
+      b_gy += Nxy * bNGx + Nyy * bNGy + Nyz * bNGz;
+      b_gz += Nxz * bNGx + Nyz * bNGy + Nzz * bNGz;
+      // cm = -3 nu omega drho
+      R b_nu = (R)-3 * omega * drho * b_cm;
+      b_omega += (R)-3 * nu * drho * b_cm;
+      // N_aa = p_aa - p3 - u0a^2 ; N_ab = p_ab - u0a u0b
+      b_pxx += b_Nxx;
+      b_pyy += b_Nyy;
+      b_pzz += b_Nzz;
+      b_pxy += b_Nxy;
+      b_pyz += b_Nyz;
+      b_pxz += b_Nxz;
+      b_pst += -(b_Nxx + b_Nyy + b_Nzz) * (R)(1.0 / 3.0);
+      const R b_u0x = (R)-2 * u0x * b_Nxx - u0y * b_Nxy - u0z * b_Nxz;
+      const R b_u0y = (R)-2 * u0y * b_Nyy - u0x * b_Nxy - u0z * b_Nyz;
+      const R b_u0z = (R)-2 * u0z * b_Nzz - u0y * b_Nyz - u0x * b_Nxz;
+      // u0 = j + F0 inv2rho
+      b_jx += b_u0x;
+      b_jy += b_u0y;
+      b_jz += b_u0z;
+      b_F0x += inv2rho * b_u0x;
+      b_F0y += inv2rho * b_u0y;
+      b_F0z += inv2rho * b_u0z;
+      b_inv2rho += F0x * b_u0x + F0y * b_u0y + F0z * b_u0z;
+      // F0 = (mu + cp) grad + rho G
+      const R b_mcp = gx * b_F0x + gy * b_F0y + gz * b_F0z;
+      b_gx += (mu + cp) * b_F0x;
+      b_gy += (mu + cp) * b_F0y;
+      b_gz += (mu + cp) * b_F0z;
+      b_rho += Gx * b_F0x + Gy * b_F0y + Gz * b_F0z;
+      // cp = -pst drho / 3
+      b_pst += -drho * (R)(1.0 / 3.0) * b_mcp;
+      // mu = 4 beta dw(pc) - kappa lap
+      b_pc += (R)4 * beta * ((R)3 * pc * pc - (R)3 * pc + (R)0.5) * b_mcp;
+      b_lap += -kappa * b_mcp;
+      const R b_beta = (R)4 * dw * b_mcp;
+      const R b_kappa = -lap * b_mcp;
+      // beta = 12 sigma / xi, kappa = 1.5 sigma xi
+      bSig += (R)(12.0 / ap.xi) * b_beta + (R)(1.5 * ap.xi) * b_kappa;
+      bXi += (R)(-12.0 * ap.sigma / (ap.xi * ap.xi)) * b_beta + (R)(1.5 * ap.sigma) * b_kappa;
+      // inv2rho = 0.5 / rho ; nu = (tau - 0.5) / 3 ; omega = 1 / tau
+      b_rho += (R)-0.5 / (rho * rho) * b_inv2rho;
+      R b_tau = b_nu * (R)(1.0 / 3.0) - omega * omega * b_omega;
+      b_pc += dtau * b_tau + drho * b_rho;
+    }
+
+    // ---------------- adjoints of the local pre-collision populations
+    R* og = lam_out + 15u * N;
+    og[13u * N + cell] = b_pst;
+#pragma unroll
+    for (int i = 0; i < 13; ++i) {
+      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+      R E = b_pst;
+      if (cx) E += b_pxx;
+      if (cy) E += b_pyy;
+      if (cz) E += b_pzz;
+      if (cx && cy) E += (cx * cy > 0) ? b_pxy : -b_pxy;
+      if (cy && cz) E += (cy * cz > 0) ? b_pyz : -b_pyz;
+      if (cx && cz) E += (cx * cz > 0) ? b_pxz : -b_pxz;
+      R L = 0;
+      if (cx) L += cx > 0 ? b_jx : -b_jx;
+      if (cy) L += cy > 0 ? b_jy : -b_jy;
+      if (cz) L += cz > 0 ? b_jz : -b_jz;
+      og[(unsigned)i * N + cell] = E + L;
+      og[(unsigned)(26 - i) * N + cell] = E - L;
+    }
+    lam_out[7u * N + cell] = b_phl;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+      R E = b_phl;
+      if (cx) E += b_hxx;
+      if (cy) E += b_hyy;
+      if (cz) E += b_hzz;
+      if (cx && cy) E += (cx * cy > 0) ? b_hxy : -b_hxy;
+      if (cy && cz) E += (cy * cz > 0) ? b_hyz : -b_hyz;
+      if (cx && cz) E += (cx * cz > 0) ? b_hxz : -b_hxz;
+      R L = 0;
+      if (cx) L += cx > 0 ? b_hjx : -b_hjx;
+      if (cy) L += cy > 0 ? b_hjy : -b_hjy;
+      if (cz) L += cz > 0 ? b_hjz : -b_hjz;
+      lam_out[(unsigned)k * N + cell] = E + L;
+      lam_out[(unsigned)(14 - k) * N + cell] = E - L;
+    }
+    aux[0u * N + cell] = b_gx;
+    aux[1u * N + cell] = b_gy;
+    aux[2u * N + cell] = b_gz;
+    aux[3u * N + cell] = b_lap;
+    aux[4u * N + cell] = b_pc;
+  }
+  block_sum3_to<R>(bM, bXi, bSig, part + 3u * blockIdx.x);
+}
+
+// Transpose of the phi stencil plus phi = sum h: adds the adjoint of phi(x)
+// to the 15 h adjoints of x, and the objective weight W(x) when this time is
+// an observation.
+template <typename R>
+__global__ void __launch_bounds__(256) k_adj_phi(Geo32 geo, const R* __restrict__ aux, R* __restrict__ lam,
+                                                 const double* __restrict__ W) {
+  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= geo.N) return;
+  const unsigned N = geo.N;
+  const unsigned yz = fdiv(x, geo.dx);
+  const int cxo = (int)(x - yz * geo.nx);
+  const unsigned zq = fdiv(yz, geo.dy);
+  const int cyo = (int)(yz - zq * geo.ny);
+  const int czo = (int)zq;
+  const int n[3] = {(int)geo.nx, (int)geo.ny, (int)geo.nz};
+  const int xc[3] = {cxo, cyo, czo};
+  R acc = aux[4u * N + x] - (R)(6.0 * 19.0 / 27.0) * aux[3u * N + x];
+#pragma unroll
+  for (int i = 0; i < 27; ++i) {
+    if (i == 13) continue;
+    const int c[3] = {q27_cx(i), q27_cy(i), q27_cz(i)};
+    const R w = (R)q27_w(i);
+    // per axis: the coordinates y_a whose stencil read, in direction c_a, lands on x_a
+    int cand[3][2], nc[3];
+    for (int a = 0; a < 3; ++a) {
+      nc[a] = 0;
+      int y = xc[a] - c[a];
+      if (geo.wall[a]) {
+        if (y >= 0 && y < n[a]) cand[a][nc[a]++] = y;
+        if ((c[a] == -1 && xc[a] == 0) || (c[a] == 1 && xc[a] == n[a] - 1)) cand[a][nc[a]++] = xc[a];
+      } else {
+        y = y < 0 ? y + n[a] : (y >= n[a] ? y - n[a] : y);
+        cand[a][nc[a]++] = y;
+      }
+    }
+    for (int ia = 0; ia < nc[0]; ++ia)
+      for (int ib = 0; ib < nc[1]; ++ib)
+        for (int ic = 0; ic < nc[2]; ++ic) {
+          const unsigned y = (unsigned)cand[0][ia] + geo.nx * ((unsigned)cand[1][ib] + geo.ny * (unsigned)cand[2][ic]);
+          R v = (R)6 * aux[3u * N + y];
+          if (c[0]) v += (R)(3 * c[0]) * aux[0u * N + y];
+          if (c[1]) v += (R)(3 * c[1]) * aux[1u * N + y];
+          if (c[2]) v += (R)(3 * c[2]) * aux[2u * N + y];
+          acc += w * v;
+        }
+  }
+  if (W) acc += (R)W[x];
+#pragma unroll
+  for (int k = 0; k < 15; ++k) lam[(unsigned)k * N + x] += acc;
+}
+
+// dot = sum_x W(x) phi(x) in FP64 (per-block partials, fixed order).
+template <typename PhiT>
+__global__ void __launch_bounds__(256) k_dot(unsigned N, const double* __restrict__ W, const PhiT* __restrict__ phi,
+                                             double* __restrict__ part) {
+  double s = 0;
+  for (unsigned c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x)
+    s += W[c] * (double)phi[c];
+  __shared__ double sm[8];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < 8; ++w) t += sm[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+// Sum of n partials of stride `stride` (component k) into out[k], one warp.
+static __global__ void k_sum_parts(const double* __restrict__ part, int n, int stride, double* __restrict__ out) {
+  const int k = blockIdx.x;
+  double s = 0;
+  for (int b = threadIdx.x; b < n; b += 32) s += part[(size_t)b * stride + k];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) out[k] += s;
+}
+
+}  // namespace pfl

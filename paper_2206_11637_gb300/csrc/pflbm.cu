@@ -9,11 +9,13 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/pflbm.h"
 #include "errors.h"
 #include "kernels.cuh"
 #include "step.cuh"
+#include "adjoint.cuh"
 
 using namespace pfl;
 
@@ -548,6 +550,235 @@ pfl_status pfl_kernel_times(pfl_ctx* c, int n, double ms[2]) {
 }
 
 long long pfl_time(const pfl_ctx* c) { return c ? c->t : -1; }
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- adjoint --
+namespace {
+
+constexpr int ADJ_MAX_OBS = 8;
+constexpr int DOT_BLOCKS = 1024;
+
+struct AdjLayout {
+  size_t state;      // bytes of one saved state (h, g, phi)
+  int K, nck;        // checkpoint interval, number of checkpoints
+  size_t ck, seg, fin, lam0, lam1, aux, W, part, res, total;
+};
+
+size_t rbytes(int prec) { return prec == PFL_FP64 ? 8 : 4; }
+
+AdjLayout adj_layout(const pfl_ctx* c, int n) {
+  AdjLayout A;
+  const size_t N = (size_t)c->geo.N;
+  const size_t S = pop_bytes(c->p.precision), P = phi_bytes(c->p.precision), R = rbytes(c->p.precision);
+  A.state = align256(15 * N * S) + align256(27 * N * S) + align256(N * P);
+  A.K = 1;
+  while ((long long)A.K * A.K < n) ++A.K;
+  A.nck = (n + A.K - 1) / A.K;
+  if (A.nck < 1) A.nck = 1;
+  size_t off = 0;
+  A.ck = off;
+  off += (size_t)A.nck * A.state;
+  A.seg = off;
+  off += (size_t)A.K * A.state;
+  A.fin = off;
+  off += A.state;
+  A.lam0 = off;
+  off = align256(off + 42 * N * R);
+  A.lam1 = off;
+  off = align256(off + 42 * N * R);
+  A.aux = off;
+  off = align256(off + 5 * N * R);
+  A.W = off;
+  off = align256(off + (size_t)ADJ_MAX_OBS * N * sizeof(double));
+  A.part = off;
+  const size_t nb = (N + ADJ_THREADS - 1) / ADJ_THREADS;
+  off = align256(off + (3 * nb + DOT_BLOCKS) * sizeof(double));
+  A.res = off;
+  off = align256(off + 8 * sizeof(double));
+  A.total = off;
+  return A;
+}
+
+struct Saved {
+  int swapped;
+};
+
+// copy the live state (h, g, current phi) into a slot, or back
+pfl_status copy_state(pfl_ctx* c, char* slot, bool save) {
+  const size_t N = (size_t)c->geo.N;
+  const size_t S = pop_bytes(c->p.precision), P = phi_bytes(c->p.precision);
+  const size_t hb = 15 * N * S, gb = 27 * N * S, pb = N * P;
+  char* live[3] = {c->ws + c->L.h, c->ws + c->L.g, c->ws + c->L.phi[c->cur]};
+  char* sl[3] = {slot, slot + align256(hb), slot + align256(hb) + align256(gb)};
+  const size_t by[3] = {hb, gb, pb};
+  for (int k = 0; k < 3; ++k)
+    CUDA_TRY(cudaMemcpyAsync(save ? sl[k] : live[k], save ? live[k] : sl[k], by[k], cudaMemcpyDeviceToDevice,
+                             c->stream));
+  return PFL_OK;
+}
+
+template <int PREC>
+void launch_dot(pfl_ctx* c, const double* W, double* part, double* out) {
+  k_dot<typename Store<PREC>::PhiT><<<DOT_BLOCKS, 256, 0, c->stream>>>((unsigned)c->geo.N, W, phicur<PREC>(c), part);
+  k_sum_parts<<<1, 32, 0, c->stream>>>(part, DOT_BLOCKS, 1, out);
+}
+
+template <int PREC>
+void launch_adj_step(pfl_ctx* c, const AdjLayout& A, char* aws, char* slot, int swapped, const void* lam_in,
+                     void* lam_out, const double* W, double* gradacc) {
+  typedef typename Store<PREC>::R R;
+  const size_t N = (size_t)c->geo.N;
+  const size_t S = pop_bytes(c->p.precision);
+  const typename Store<PREC>::S* h = (const typename Store<PREC>::S*)slot;
+  const typename Store<PREC>::S* g = (const typename Store<PREC>::S*)(slot + align256(15 * N * S));
+  const typename Store<PREC>::PhiT* phi =
+      (const typename Store<PREC>::PhiT*)(slot + align256(15 * N * S) + align256(27 * N * S));
+  AdjPar ap{c->p.mobility, c->p.xi, c->p.sigma};
+  double* part = (double*)(aws + A.part);
+  R* aux = (R*)(aws + A.aux);
+  const unsigned nb = blocks_for(c->geo.N, ADJ_THREADS);
+  if (swapped)
+    k_adj_local<PREC, 1><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
+                                                             (R*)lam_out, aux, part);
+  else
+    k_adj_local<PREC, 0><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
+                                                             (R*)lam_out, aux, part);
+  k_sum_parts<<<3, 32, 0, c->stream>>>(part, (int)nb, 3, gradacc);
+  k_adj_phi<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(c->g32, aux, (R*)lam_out, W);
+}
+
+// lambda = 0, then the h part of lambda += W (objective at the final time)
+template <typename R>
+__global__ void k_lam_init(unsigned N, R* __restrict__ lam, const double* __restrict__ W) {
+  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= N) return;
+  const R w = W ? (R)W[x] : (R)0;
+#pragma unroll
+  for (int k = 0; k < 15; ++k) lam[(unsigned)k * N + x] = w;
+#pragma unroll
+  for (int i = 0; i < 27; ++i) lam[(unsigned)(15 + i) * N + x] = (R)0;
+}
+
+template <int PREC>
+pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const double* const* Wd, char* aws,
+                       const AdjLayout& A, double* J, double grad[3]) {
+  typedef typename Store<PREC>::R R;
+  double* res = (double*)(aws + A.res);  // [0] J, [1..3] dJ/d(M, xi, sigma)
+  double* part = (double*)(aws + A.part);
+  CUDA_TRY(cudaMemsetAsync(res, 0, 8 * sizeof(double), c->stream));
+  auto obs_at = [&](int k) -> const double* {
+    for (int o = 0; o < nobs; ++o)
+      if (obs_steps[o] == k) return Wd[o];
+    return nullptr;
+  };
+  // several weights at one step are summed into the first by the caller side; here one per step
+  const long long t0 = c->t;
+  std::vector<int> ck_swapped(A.nck, 0), seg_swapped(A.K, 0);
+  // forward sweep with checkpoints
+  for (int k = 0; k < n; ++k) {
+    if (k % A.K == 0) {
+      ck_swapped[k / A.K] = c->swapped;
+      pfl_status s = copy_state(c, aws + A.ck + (size_t)(k / A.K) * A.state, true);
+      if (s != PFL_OK) return s;
+    }
+    if (const double* W = obs_at(k)) launch_dot<PREC>(c, W, part + 3 * ((c->geo.N + ADJ_THREADS - 1) / ADJ_THREADS), res);
+    const bool bgk = false;
+    (void)bgk;
+    step_only<PREC, 0>(c);
+    launch_phi<PREC>(c);
+  }
+  if (const double* W = obs_at(n)) launch_dot<PREC>(c, W, part + 3 * ((c->geo.N + ADJ_THREADS - 1) / ADJ_THREADS), res);
+  const int fin_swapped = c->swapped;
+  const long long t_end = c->t;
+  pfl_status st = copy_state(c, aws + A.fin, true);
+  if (st != PFL_OK) return st;
+  CUDA_TRY(cudaGetLastError());
+
+  // reverse sweep, one checkpoint segment at a time
+  void* lam = aws + A.lam0;
+  void* lam2 = aws + A.lam1;
+  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, (R*)lam, obs_at(n));
+  for (int sgm = A.nck - 1; sgm >= 0; --sgm) {
+    const int k0 = sgm * A.K, k1 = (k0 + A.K < n) ? k0 + A.K : n;
+    st = copy_state(c, aws + A.ck + (size_t)sgm * A.state, false);
+    if (st != PFL_OK) return st;
+    c->swapped = ck_swapped[sgm];
+    for (int k = k0; k < k1; ++k) {
+      seg_swapped[k - k0] = c->swapped;
+      st = copy_state(c, aws + A.seg + (size_t)(k - k0) * A.state, true);
+      if (st != PFL_OK) return st;
+      if (k + 1 < k1) {  // the last state of the segment is never stepped from here
+        step_only<PREC, 0>(c);
+        launch_phi<PREC>(c);
+      }
+    }
+    for (int k = k1 - 1; k >= k0; --k) {
+      launch_adj_step<PREC>(c, A, aws, aws + A.seg + (size_t)(k - k0) * A.state, seg_swapped[k - k0], lam, lam2,
+                            obs_at(k), res + 1);
+      std::swap(lam, lam2);
+    }
+    CUDA_TRY(cudaGetLastError());
+  }
+  // back to the end of the forward run
+  st = copy_state(c, aws + A.fin, false);
+  if (st != PFL_OK) return st;
+  c->swapped = fin_swapped;
+  c->t = t_end;
+  (void)t0;
+  double hres[4];
+  CUDA_TRY(cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (J) *J = hres[0];
+  if (grad)
+    for (int k = 0; k < 3; ++k) grad[k] = hres[1 + k];
+  return PFL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t pfl_adjoint_workspace_bytes(const pfl_ctx* c, int n_steps) {
+  if (!c || n_steps < 1) return 0;
+  return adj_layout(c, n_steps).total;
+}
+
+pfl_status pfl_adjoint(pfl_ctx* c, int n_steps, int n_obs, const int* obs_steps, const double* const* obs_weights,
+                       void* adj_workspace, size_t adj_bytes, double* J, double grad[3]) {
+  if (!c) return fail(PFL_ERR_ARG, "context is NULL");
+  if (n_steps < 1) return fail(PFL_ERR_ARG, "n_steps must be >= 1");
+  if (c->p.precision == PFL_FP16S) return fail(PFL_ERR_STATE, "the adjoint runs on FP64 or FP32 storage");
+  if (c->p.collision != PFL_MRT) return fail(PFL_ERR_STATE, "the adjoint covers the MRT collision");
+  if (!c->idx32) return fail(PFL_ERR_STATE, "lattice too large for the adjoint kernels (27 N >= 2^32)");
+  if (n_obs < 1 || n_obs > ADJ_MAX_OBS || !obs_steps || !obs_weights)
+    return fail(PFL_ERR_ARG, "need 1.." + std::to_string(ADJ_MAX_OBS) + " observations");
+  for (int o = 0; o < n_obs; ++o) {
+    if (obs_steps[o] < 0 || obs_steps[o] > n_steps || !obs_weights[o])
+      return fail(PFL_ERR_ARG, "observation step outside [0, n_steps] or NULL weights");
+    for (int q = 0; q < o; ++q)
+      if (obs_steps[q] == obs_steps[o]) return fail(PFL_ERR_ARG, "observation steps must be distinct");
+  }
+  if (!adj_workspace || !is_device_ptr(adj_workspace)) return fail(PFL_ERR_ARG, "adjoint workspace must be device memory");
+  if (((uintptr_t)adj_workspace & 255) != 0) return fail(PFL_ERR_ARG, "adjoint workspace must be 256-byte aligned");
+  const AdjLayout A = adj_layout(c, n_steps);
+  if (adj_bytes < A.total)
+    return fail(PFL_ERR_OOM, "adjoint workspace holds " + std::to_string(adj_bytes) + " bytes, needs " +
+                                 std::to_string(A.total));
+  CUDA_TRY(cudaSetDevice(c->device));
+  char* aws = (char*)adj_workspace;
+  const size_t N = (size_t)c->geo.N;
+  const double* Wd[ADJ_MAX_OBS];
+  for (int o = 0; o < n_obs; ++o) {
+    double* dst = (double*)(aws + A.W) + (size_t)o * N;
+    CUDA_TRY(cudaMemcpyAsync(dst, obs_weights[o], N * sizeof(double), cudaMemcpyDefault, c->stream));
+    Wd[o] = dst;
+  }
+  switch (c->p.precision) {
+    case PFL_FP64: return run_adjoint<0>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
+    default: return run_adjoint<1>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
+  }
+}
 
 void pfl_destroy(pfl_ctx* c) {
   if (!c) return;

@@ -104,6 +104,29 @@ class Simulation:
     def step(self, n=1):
         L.check(self.lib.pfl_step(self.ctx, int(n)))
 
+    def adjoint(self, n_steps, observations):
+        """Discrete adjoint over the next n_steps steps.
+
+        observations: list of (step, W) with W an (N,) FP64 array or CUDA
+        tensor; J = sum_o sum_x W_o(x) phi(x, t0 + step_o).  Returns
+        (J, [dJ/dM, dJ/dxi, dJ/dsigma]); the simulation advances n_steps.
+        """
+        torch = self.torch
+        nbytes = self.lib.pfl_adjoint_workspace_bytes(self.ctx, int(n_steps))
+        if nbytes == 0:
+            raise L.PFLError(L.PFL_ERR_ARG, "invalid adjoint request")
+        ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        steps = (ctypes.c_int * len(observations))(*[int(k) for k, _ in observations])
+        keep = [self._as_f64(w, self.N) for _, w in observations]
+        ptrs = (ctypes.c_void_p * len(keep))(*[_ptr(w).value for w in keep])
+        J = ctypes.c_double(0.0)
+        grad = np.zeros(3)
+        L.check(self.lib.pfl_adjoint(self.ctx, int(n_steps), len(observations), ctypes.cast(steps, ctypes.c_void_p),
+                                     ctypes.cast(ptrs, ctypes.c_void_p), ctypes.c_void_p(ws.data_ptr()), nbytes,
+                                     ctypes.byref(J), _ptr(grad)))
+        del ws
+        return J.value, grad
+
     def kernel_times(self, n):
         """Run n steps timing each kernel with CUDA events: (ms step kernel, ms phi pass)."""
         ms = np.zeros(2)

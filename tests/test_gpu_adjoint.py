@@ -1,0 +1,115 @@
+"""Discrete adjoint of the stream-collide step against central finite
+differences of the forward GPU path (FP64), and FP32 against FP64.
+
+J is a linear functional of phi at chosen steps (bubble rise velocity, wave
+mode amplitude); the gradient is taken with respect to M, xi and sigma.  The
+bar is 1e-3 relative error per component against central differences with a
+relative step of 1e-4 (truncation error of order 1e-8).
+"""
+import copy
+
+import numpy as np
+import pytest
+
+from paper_2206_11637_gb300 import objectives as O
+from paper_2206_11637_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PARAMS = ("mobility", "xi", "sigma")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_11637_gb300 import build
+    build.build_library()
+
+
+def forward_J(p, phi0, u0, p0, n, obs, precision="fp64"):
+    from paper_2206_11637_gb300.pflbm import Simulation
+    s = Simulation(p, phi0, u0, p0, precision=precision)
+    J = 0.0
+    for step, w in sorted(obs, key=lambda t: t[0]):
+        s.step(step - s.time)
+        J += float(np.dot(w, s.phi().reshape(-1)))
+    return J
+
+
+def fd_grad(p, phi0, u0, p0, n, obs, rel=1e-4):
+    g = []
+    for name in PARAMS:
+        v = getattr(p, name)
+        d = rel * v
+        pp, pm = copy.copy(p), copy.copy(p)
+        setattr(pp, name, v + d)
+        setattr(pm, name, v - d)
+        g.append((forward_J(pp, phi0, u0, p0, n, obs) - forward_J(pm, phi0, u0, p0, n, obs)) / (2 * d))
+    return np.array(g)
+
+
+def adjoint(p, phi0, u0, p0, n, obs, precision="fp64"):
+    from paper_2206_11637_gb300.pflbm import Simulation
+    s = Simulation(p, phi0, u0, p0, precision=precision)
+    J, g = s.adjoint(n, obs)
+    return J, g, s
+
+
+def bubble_case():
+    p, phi0, u0, p0 = W.rising_bubble(20, 36, 20, D=10.0, xi=4.0, M=0.05)
+    n = 50                      # K = 8: seven checkpoints, the last segment partial
+    return p, phi0, u0, p0, n, O.rise_velocity_weights(p, phi0, 20, n)
+
+
+def wave_case():
+    p, phi0, u0, p0 = W.capillary_wave(32, ny=32, a0=1.0, xi=4.0, M=0.02, sigma=1e-3, nu=0.02)
+    n = 64
+    return p, phi0, u0, p0, n, [(n, O.wave_mode_weights(p, 32.0)), (n // 2, 0.5 * O.wave_mode_weights(p, 32.0))]
+
+
+@pytest.mark.parametrize("case", [bubble_case, wave_case])
+def test_adjoint_matches_finite_differences(case):
+    p, phi0, u0, p0, n, obs = case()
+    J, g, s = adjoint(p, phi0, u0, p0, n, obs)
+    assert s.time == n
+    Jf = forward_J(p, phi0, u0, p0, n, obs)
+    assert abs(J - Jf) <= 1e-12 * max(1.0, abs(Jf))
+    gfd = fd_grad(p, phi0, u0, p0, n, obs)
+    assert np.all(np.abs(gfd) > 0)
+    rel = np.abs(g - gfd) / np.abs(gfd)
+    assert np.all(rel < 1e-3), (g, gfd, rel)
+
+
+def test_adjoint_leaves_forward_state():
+    p, phi0, u0, p0, n, obs = bubble_case()
+    _, _, s = adjoint(p, phi0, u0, p0, n, obs)
+    from paper_2206_11637_gb300.pflbm import Simulation
+    r = Simulation(p, phi0, u0, p0, precision="fp64")
+    r.step(n)
+    assert np.abs(s.phi() - r.phi()).max() < 1e-13
+    h1, g1 = s.populations()
+    h2, g2 = r.populations()
+    assert np.abs(h1 - h2).max() < 1e-13 and np.abs(g1 - g2).max() < 1e-13
+
+
+def test_fp32_adjoint_close_to_fp64():
+    p, phi0, u0, p0, n, obs = wave_case()
+    _, g64, _ = adjoint(p, phi0, u0, p0, n, obs, "fp64")
+    _, g32, _ = adjoint(p, phi0, u0, p0, n, obs, "fp32")
+    assert np.all(np.abs(g32 - g64) / np.abs(g64) < 1e-2), (g32, g64)
+
+
+def test_adjoint_rejects_fp16s_and_bad_observations():
+    from paper_2206_11637_gb300.pflbm import Simulation
+    from paper_2206_11637_gb300 import _lib as L
+    p, phi0, u0, p0, n, obs = wave_case()
+    s = Simulation(p, phi0, u0, p0, precision="fp16s")
+    with pytest.raises(L.PFLError) as e:
+        s.adjoint(n, obs)
+    assert e.value.status == L.PFL_ERR_STATE
+    s = Simulation(p, phi0, u0, p0, precision="fp64")
+    with pytest.raises(L.PFLError) as e:
+        s.adjoint(n, [(n + 1, obs[0][1])])
+    assert e.value.status == L.PFL_ERR_ARG
