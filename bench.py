@@ -364,6 +364,35 @@ def main():
                                     "u_max_over_umax": float(np.abs(ftst[3] - f64[3]).max() / umax)}
         del ref, tst
 
+    # adjoint / forward: one adjoint step (checkpoint recompute included) over
+    # one forward step, FP32 storage (the adjoint runs on FP64 or FP32)
+    adj = None
+    if not args.no_compare and rank == 0:
+        from paper_2206_11637_gb300 import objectives as O
+        n_adj = min(S, 400)
+        obs = [(n_adj, O.wave_mode_weights(p, float(p.nx)) if args.workload == "capillary_wave"
+                else np.ones(N) / N)]
+        fw = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision="fp32", device=dev)
+        fw.step(10)
+        barrier()
+        t0 = time.perf_counter()
+        fw.step(n_adj)
+        barrier()
+        t_fw = time.perf_counter() - t0
+        del fw
+        ad = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision="fp32", device=dev)
+        ad.adjoint(n_adj, obs)          # warm-up (workspace, caches)
+        barrier()
+        t0 = time.perf_counter()
+        J_adj, g_adj = ad.adjoint(n_adj, obs)
+        barrier()
+        t_ad = time.perf_counter() - t0
+        del ad
+        adj = {"precision": "fp32", "lattice_steps": n_adj, "forward_ms": t_fw * 1e3,
+               "adjoint_ms_incl_forward_and_recompute": t_ad * 1e3,
+               "adjoint_over_forward": (t_ad - t_fw) / t_fw,
+               "grad_M_xi_sigma": [float(v) for v in g_adj]}
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = cpu_oracle_rate(wl)
@@ -377,7 +406,7 @@ def main():
                            "cells": N, "lattice_steps_per_step": S, "parallelism": "replicas" if ws > 1 else "1 GPU",
                            "l2": "flushed between timed steps" if flush else "working set larger than L2"},
                 "e2e": e2e, "gpu_launches": 2 * S * K, "clocks": clocks, "roofline": roofline,
-                "cpu_baseline": cpu, "nonfinite_cells": nf, "wall_s": wall}
+                "cpu_baseline": cpu, "nonfinite_cells": nf, "wall_s": wall, "adjoint": adj}
         line.update(compare)
         print(json.dumps(line), flush=True)
     if dist:

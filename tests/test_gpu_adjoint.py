@@ -113,3 +113,18 @@ def test_adjoint_rejects_fp16s_and_bad_observations():
     with pytest.raises(L.PFLError) as e:
         s.adjoint(n, [(n + 1, obs[0][1])])
     assert e.value.status == L.PFL_ERR_ARG
+
+
+def test_autograd_function():
+    from paper_2206_11637_gb300.autograd import RolloutSetup, rollout
+    p, phi0, u0, p0, n, obs = wave_case()
+    setup = RolloutSetup(p, phi0, n, obs, u0, p0, precision="fp64")
+    M = torch.tensor(p.mobility, dtype=torch.float64, requires_grad=True)
+    xi = torch.tensor(p.xi, dtype=torch.float64, requires_grad=True)
+    sg = torch.tensor(p.sigma, dtype=torch.float64, requires_grad=True)
+    J = rollout(M, xi, sg, setup)
+    (3.0 * J).backward()
+    _, g, _ = adjoint(p, phi0, u0, p0, n, obs)
+    assert abs(J.item() - forward_J(p, phi0, u0, p0, n, obs)) < 1e-12
+    got = np.array([M.grad.item(), xi.grad.item(), sg.grad.item()])
+    assert np.allclose(got, 3.0 * g, rtol=1e-12, atol=0)

@@ -1,0 +1,110 @@
+"""Physics checks of the GPU path against what the paper fixes.
+
+- Laplace: static 3D drop, p_in - p_out = 2 sigma / R within 2 % at R = 16;
+  FP32 and shifted-FP16 storage within 1 % of the FP64 pressure jump.
+- Capillary wave (200 x 400 x 1, sigma 1e-4, nu 0.01, xi 5, M 0.02): the
+  oscillation frequency from zero crossings of the interface height at x = 0
+  (section "Capillary wave"), FP32 and FP16S within 1 % of FP64; FP64 against
+  Prosperetti's model.
+- Convergence at the paper's wave parameters (L x L, Re 10, omega_H 1.99,
+  xi 5, M 0.02): the period error against Prosperetti shrinks as L grows.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import analytic as A
+from paper_2206_11637_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_11637_gb300 import build
+    build.build_library()
+
+
+def sim(p, phi0, u0=None, p0=None, precision="fp64"):
+    from paper_2206_11637_gb300.pflbm import Simulation
+    return Simulation(p, phi0, u0, p0, precision=precision)
+
+
+def laplace_jump(precision, n=64, R=16.0, steps=2500):
+    p, phi0, _, _ = W.static_drop(n, R, nu=1.0 / 6.0)
+    s = sim(p, phi0, precision=precision)
+    s.step(steps)
+    _, _, pr, _ = s.fields()
+    c = n // 2
+    p_in = pr[c - 2:c + 2, c - 2:c + 2, c - 2:c + 2].mean()
+    p_out = pr[0:3, 0:3, 0:3].mean()
+    return p_in - p_out, p
+
+
+def test_laplace_3d_drop():
+    dp64, p = laplace_jump("fp64")
+    assert abs(dp64 / (2 * p.sigma / 16.0) - 1) < 0.02
+    for prec in ("fp32", "fp16s"):
+        dp, _ = laplace_jump(prec)
+        assert abs(dp / dp64 - 1) < 0.01, (prec, dp, dp64)
+
+
+def crossings(ts, a):
+    return np.array([ts[i] + a[i] / (a[i] - a[i + 1]) * (ts[i + 1] - ts[i])
+                     for i in range(len(a) - 1) if (a[i] > 0) != (a[i + 1] > 0)])
+
+
+def wave_history(p, phi0, precision, t_end, nsamp=160):
+    s = sim(p, phi0, precision=precision)
+    dt = max(1, int(t_end / nsamp))
+    ts, amp = [], []
+    depth = (p.ny - 1) / 2.0
+    while s.time <= t_end:
+        ts.append(s.time)
+        amp.append(A.interface_height(s.phi()[0, :, 0]) - depth)
+        s.step(dt)
+    return np.array(ts, float), np.array(amp)
+
+
+def test_capillary_wave_frequency_by_precision():
+    p, phi0, _, _ = W.capillary_wave(200)            # 200 x 400 x 1
+    k = 2 * math.pi / 200
+    T = 2 * math.pi / A.capillary_omega0(p.sigma, k, p.rho_h, p.rho_l)
+    periods = {}
+    for prec in ("fp64", "fp32", "fp16s"):
+        ts, amp = wave_history(p, phi0, prec, 2.2 * T)
+        c = crossings(ts, amp)
+        assert len(c) >= 4, prec
+        periods[prec] = 2 * (c[3] - c[1]) / 2.0      # two half-periods
+    for prec in ("fp32", "fp16s"):
+        assert abs(periods[prec] / periods["fp64"] - 1) < 0.01, periods
+    # FP64 against the model: the diffuse interface (Cn = 5/200) lengthens the period slightly
+    assert 0.97 < periods["fp64"] / T < 1.08, (periods, T)
+
+
+def paper_wave(L):
+    nu = (1.0 / 1.99 - 0.5) / 3.0
+    a0 = 0.01 * L
+    w0 = 10.0 * nu / (a0 * L)                        # Re = a0 w0 L / nu = 10
+    k = 2 * math.pi / L
+    sigma = w0 ** 2 * (1.0 + 1e-3) / k ** 3
+    p, phi0, _, _ = W.capillary_wave(L, ny=L, a0=a0, xi=5.0, M=0.02, sigma=sigma, nu=nu)
+    return p, phi0, w0, k, nu, a0
+
+
+def test_capillary_wave_converges_with_resolution():
+    errs = []
+    for L in (50, 100):
+        p, phi0, w0, k, nu, a0 = paper_wave(L)
+        T = 2 * math.pi / w0
+        ts, amp = wave_history(p, phi0, "fp64", 1.3 * T, nsamp=130)
+        an = A.prosperetti(ts, k, nu, p.rho_h, p.rho_l, p.sigma, a0)
+        c_sim, c_an = crossings(ts, amp), crossings(ts, an)
+        assert len(c_sim) >= 2 and len(c_an) >= 2
+        errs.append(abs((c_sim[1] - c_sim[0]) / (c_an[1] - c_an[0]) - 1))
+    assert errs[1] < errs[0], errs
+    assert errs[1] < 0.05, errs
