@@ -41,13 +41,14 @@ PREC_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2}
 PHI_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 4}
 
 
-def step_kernel_bytes(prec):
+def step_kernel_bytes(prec, engine=0):
     """Algorithmic bytes per cell of one stream-collide launch: every h and g
-    population read once and written once, phi read once (stencil), plus the
-    phi shift of the FP16S format."""
+    population read once and written once; the fused two-array step (engine 0)
+    also writes phi, the in-place step (engine 1) reads phi for its stencil;
+    FP16S adds the shift arrays (phi and p* of the writers read, p* written)."""
     b = 2 * (15 + 27) * PREC_BYTES[prec] + PHI_BYTES[prec]
     if prec == "fp16s":
-        b += PHI_BYTES[prec]
+        b += PHI_BYTES[prec] + 4 + 4
     return b
 
 
@@ -219,6 +220,70 @@ def run_reference(args, wl):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """512 seeded instances (drops n^3, n in 24..96; waves nx x 2nx, nx in
+    64..256) with their own M, xi, sigma, advanced together in FP32 by the
+    batched persistent launches (CUDA graph, tuned shapes).  value = aggregate
+    MLUPS; error_vs_fp64 compares 16 instances with the FP64 single-lattice
+    path (itself checked against the oracle to 1e-10)."""
+    import numpy as np
+    import torch
+    from paper_2206_11637_gb300 import workloads as W
+    from paper_2206_11637_gb300 import build as B
+    ws, rank, _ = dist_env()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    B.build_library()
+    from paper_2206_11637_gb300.batch import Batch
+    from paper_2206_11637_gb300.pflbm import Simulation
+    inst = W.batched_sweep(512)
+    cells = sum(p.cells for p, _, _, _ in inst)
+    t0 = time.perf_counter()
+    b = Batch(inst, precision="fp32", tune=True, device=dev)
+    t_init = time.perf_counter() - t0
+    S = args.lattice_steps or 100
+    for _ in range(args.warmup):
+        b.step(S)
+    torch.cuda.synchronize()
+    clk = Clocks()
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        b.step(S)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop(0)
+    ms = e0.elapsed_time(e1)
+    out, nf, _ = b.diag(check=False)
+    threads, grid, ntiles = b.shapes()
+    # error of 16 instances against FP64 after the same number of steps
+    n_done = b.time
+    errs = []
+    for i in range(0, 32, 2):                      # 8 drops and 8 waves
+        p, phi0, u0, p0 = inst[i + (i // 2) % 2]
+        j = i + (i // 2) % 2
+        ref = Simulation(p, phi0, u0, p0, precision="fp64", device=dev)
+        ref.step(n_done)
+        phi = b.fields(j)[0]
+        if nf[j] == 0:
+            errs.append(float(np.abs(phi - ref.phi()).max()))
+        del ref
+    v = mlups(cells, S * args.steps, ms / 1e3)
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched_sweep", "instances": len(inst), "cells": cells,
+                       "lattice_steps_per_step": S, "precision": "fp32",
+                       "l2": "working set larger than L2"},
+            "gpu_launches": 4 * S * args.steps, "clocks": clocks,
+            "batch": {"init_s": t_init, "shapes": {"threads": threads.tolist(), "grid": grid.tolist(),
+                                                    "tiles": ntiles.tolist()},
+                      "unstable_instances": int((nf > 0).sum()),
+                      "phi_max_abs_err_vs_fp64_16": errs}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -226,15 +291,20 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="capillary_wave",
-                    choices=["capillary_wave", "static_drop", "rising_bubble", "drop_impact"])
+                    choices=["capillary_wave", "static_drop", "rising_bubble", "drop_impact", "batched_sweep"])
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "fp16s"])
     ap.add_argument("--lattice-steps", type=int, default=None, help="lattice steps per benchmark step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
+    ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
+                    help="0: fused two-array step (default), 1: in-place AA step + phi pass")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
+    if args.workload == "batched_sweep":
+        return run_batched(args)
     wl = workload(args.workload)
+    wl["p"].engine = args.engine
     if args.lattice_steps:
         wl["S"] = args.lattice_steps
     if args.impl == "reference":
@@ -308,11 +378,12 @@ def main():
     kms, pms = sim.kernel_times(n_rt)
     avg_s = kms / n_rt / 1e3
     peak, peak_kind = peaks()
-    achieved = N * step_kernel_bytes(prec) / avg_s / 1e9
+    achieved = N * step_kernel_bytes(prec, args.engine) / avg_s / 1e9
     traffic = NCU_TRAFFIC.get((args.workload, prec, kernel_hash()))
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_step (fused h+g stream-collide)",
-                "bytes_per_cell": step_kernel_bytes(prec), "peak_source": peak_kind,
+                "traffic": traffic,
+                "kernel": "k_step_zm (fused two-array step)" if args.engine == 0 else "k_step_mrt (in-place step)",
+                "bytes_per_cell": step_kernel_bytes(prec, args.engine), "peak_source": peak_kind,
                 "kernel_share": kms / (kms + pms),
                 "whole_step_ideal_frac": mlups(N, n_rt, (kms + pms) / 1e3) * 1e6 * ideal_step_bytes(prec) / 1e9 / peak,
                 "working_set_bytes": work_bytes, "l2_resident": work_bytes < L2_BYTES}

@@ -83,7 +83,15 @@ typedef struct {
   double gravity[3];   /* body-force acceleration g, F_b = rho g                      */
   int precision;       /* pfl_precision                                              */
   int collision;       /* pfl_collision                                              */
+  int engine;          /* pfl_engine                                                 */
 } pfl_params;
+
+/* How a single lattice is stepped.  PFL_ENGINE_AUTO: the fused two-array step
+ * (stream-collide and phi stencil in one launch, populations in two array
+ * pairs) for the MRT collision on lattices with 27 N < 2^32, else the in-place
+ * one.  PFL_ENGINE_INPLACE: one array pair updated in place (AA pattern) and a
+ * separate phi = sum h pass.  Both give the same results. */
+typedef enum { PFL_ENGINE_AUTO = 0, PFL_ENGINE_INPLACE = 1 } pfl_engine;
 
 /* Device bytes the workspace must hold for these parameters (0 if invalid). */
 size_t pfl_workspace_bytes(const pfl_params* p);
@@ -157,6 +165,50 @@ size_t pfl_adjoint_workspace_bytes(const pfl_ctx* ctx, int n_steps);
  * PFL_ERR_ARG for bad observations (at most 8).  Synchronises. */
 pfl_status pfl_adjoint(pfl_ctx* ctx, int n_steps, int n_obs, const int* obs_steps, const double* const* obs_weights,
                        void* adj_workspace, size_t adj_bytes, double* J, double grad[3]);
+
+/* ------------------------------------------------------------------ batch --
+ * Many independent lattices of uneven size, each with its own parameters
+ * (M, xi, sigma, densities, ...), advanced together: every lattice step is
+ * one persistent grid-stride launch of the stream-collide over a work list of
+ * all instances' cells (plus one of the phi pass), and pfl_batch_step replays
+ * a CUDA graph of 16 steps.  All instances share the precision; MRT only;
+ * 27 N < 2^32 per instance. */
+typedef struct pfl_batch pfl_batch;
+
+/* Device bytes of the batch workspace (0 if a parameter set is invalid,
+ * precisions differ or the collision is not MRT). */
+size_t pfl_batch_workspace_bytes(const pfl_params* params, int count);
+
+/* Create the batch: params[count]; phi0[count] arrays (host or device, N_i
+ * doubles each, required); u0, p0: NULL or arrays of count pointers (entries
+ * may be NULL).  tune_shapes != 0 times the candidate launch shapes of each
+ * size class (below / above 65536 cells) on the initial state and keeps the
+ * fastest -- threads per block 128 or 256, grid 1, 2 or 4 x SMs x resident
+ * blocks -- then rebuilds the initial state.  Synchronises. */
+pfl_status pfl_batch_init(const pfl_params* params, int count, const double* const* phi0, const double* const* u0,
+                          const double* const* p0, void* workspace, size_t workspace_bytes, void* stream,
+                          int tune_shapes, pfl_batch** out);
+
+/* Advance every active instance n_steps steps (asynchronous). */
+pfl_status pfl_batch_step(pfl_batch* b, int n_steps);
+
+/* Fields of instance i, as pfl_fields.  Synchronises. */
+pfl_status pfl_batch_fields(pfl_batch* b, int i, double* phi, double* rho, double* p, double* u);
+
+/* pfl_diag of every instance: out[8 * count] (may be NULL), nonfinite[count]
+ * (may be NULL).  Instances whose phi holds NaN/Inf are stopped (skipped by
+ * later steps) and the call returns PFL_ERR_UNSTABLE.  Synchronises. */
+pfl_status pfl_batch_diag(pfl_batch* b, double* out, long long* nonfinite);
+
+/* Launch shape chosen for each of the two size classes: threads per block,
+ * grid blocks and work-list tiles (each array of 2, may be NULL). */
+pfl_status pfl_batch_shapes(const pfl_batch* b, int* threads, int* grid, int* ntiles);
+
+/* Steps taken by the batch (-1 for NULL). */
+long long pfl_batch_time(const pfl_batch* b);
+
+/* Release the batch (the caller frees the workspace afterwards). */
+void pfl_batch_destroy(pfl_batch* b);
 
 /* Mass and centre-of-mass sums of a phase field the caller already holds,
  * computed without any device memory from the caller: for callers that are

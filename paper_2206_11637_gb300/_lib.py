@@ -15,6 +15,7 @@ PFL_OK, PFL_ERR_ARG, PFL_ERR_CUDA, PFL_ERR_OOM, PFL_ERR_UNSTABLE, PFL_ERR_STATE 
 PFL_FP64, PFL_FP32, PFL_FP16S = 0, 1, 2
 PFL_PERIODIC, PFL_NOSLIP = 0, 1
 PFL_MRT, PFL_BGK = 0, 1
+PFL_ENGINE_AUTO, PFL_ENGINE_INPLACE = 0, 1
 STATUS_NAMES = {0: "PFL_OK", 1: "PFL_ERR_ARG", 2: "PFL_ERR_CUDA", 3: "PFL_ERR_OOM", 4: "PFL_ERR_UNSTABLE",
                 5: "PFL_ERR_STATE"}
 
@@ -26,7 +27,7 @@ class pfl_params(ctypes.Structure):
                 ("nu_h", ctypes.c_double), ("nu_l", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("mobility", ctypes.c_double), ("xi", ctypes.c_double),
                 ("gravity", ctypes.c_double * 3),
-                ("precision", ctypes.c_int), ("collision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("collision", ctypes.c_int), ("engine", ctypes.c_int)]
 
 
 class PFLError(RuntimeError):
@@ -68,6 +69,22 @@ def load():
     lib.pfl_adjoint.argtypes = [P, I, I, P, P, P, S, P, P]
     lib.pfl_phi_moments_static.restype = I
     lib.pfl_phi_moments_static.argtypes = [P, I, I, I, I, P, ctypes.POINTER(ctypes.c_longlong), P]
+    lib.pfl_batch_workspace_bytes.restype = S
+    lib.pfl_batch_workspace_bytes.argtypes = [P, I]
+    lib.pfl_batch_init.restype = I
+    lib.pfl_batch_init.argtypes = [P, I, P, P, P, P, S, P, I, ctypes.POINTER(P)]
+    lib.pfl_batch_step.restype = I
+    lib.pfl_batch_step.argtypes = [P, I]
+    lib.pfl_batch_fields.restype = I
+    lib.pfl_batch_fields.argtypes = [P, I, P, P, P, P]
+    lib.pfl_batch_diag.restype = I
+    lib.pfl_batch_diag.argtypes = [P, P, P]
+    lib.pfl_batch_shapes.restype = I
+    lib.pfl_batch_shapes.argtypes = [P, P, P, P]
+    lib.pfl_batch_time.restype = ctypes.c_longlong
+    lib.pfl_batch_time.argtypes = [P]
+    lib.pfl_batch_destroy.restype = None
+    lib.pfl_batch_destroy.argtypes = [P]
     lib.pfl_kernel_times.restype = I
     lib.pfl_kernel_times.argtypes = [P, I, P]
     lib.pfl_time.restype = ctypes.c_longlong

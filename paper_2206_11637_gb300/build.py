@@ -5,12 +5,12 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpflbm.so")
-SOURCES = ["pflbm.cu", "noalloc.cu"]
-DEPS = SOURCES + ["kernels.cuh", "lattice.cuh", "step.cuh", "adjoint.cuh", "errors.h"]
+SOURCES = ["pflbm.cu", "noalloc.cu", "batch.cu"]
+DEPS = SOURCES + ["kernels.cuh", "lattice.cuh", "step.cuh", "adjoint.cuh", "errors.h", "host_common.h"]
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pflbm.h")
 
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a",
-              "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]
+              "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
 
 def _nvcc():
@@ -28,14 +28,32 @@ def stale():
 
 
 def build_library(force=False, verbose=False, extra=()):
+    """Compile the translation units in parallel, then link the shared library."""
     if not force and not stale():
         return LIB
-    tmp = LIB + ".tmp.%d" % os.getpid()
-    cmd = [_nvcc()] + NVCC_FLAGS + list(extra) + [os.path.join(CSRC, s) for s in SOURCES] + ["-o", tmp]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    tag = ".%d" % os.getpid()
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(CSRC, src[:-3] + tag + ".o")
+        cmd = [_nvcc()] + NVCC_FLAGS + list(extra) + ["-c", os.path.join(CSRC, src), "-o", obj]
+        if verbose:
+            print(" ".join(cmd))
+        procs.append((subprocess.Popen(cmd), cmd))
+        objs.append(obj)
+    failed = [cmd for pr, cmd in procs if pr.wait() != 0]
+    try:
+        if failed:
+            raise subprocess.CalledProcessError(1, failed[0])
+        tmp = LIB + ".tmp" + tag
+        cmd = [_nvcc(), "-shared", "-gencode", "arch=compute_103a,code=sm_103a"] + objs + ["-o", tmp]
+        if verbose:
+            print(" ".join(cmd))
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

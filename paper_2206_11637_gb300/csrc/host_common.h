@@ -1,0 +1,63 @@
+// Host helpers shared by the library's translation units: parameter checks,
+// pointer kinds, sizes.
+#pragma once
+#include <cmath>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pflbm.h"
+
+namespace pfl_host {
+
+inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+inline size_t pop_bytes(int prec) { return prec == PFL_FP64 ? 8 : prec == PFL_FP32 ? 4 : 2; }
+inline size_t phi_bytes(int prec) { return prec == PFL_FP64 ? 8 : 4; }
+
+// The fused two-array step applies to MRT lattices with 32-bit indices.
+inline bool uses_two_arrays(const pfl_params* p) {
+  return p->engine == PFL_ENGINE_AUTO && p->collision == PFL_MRT &&
+         27ull * (unsigned long long)p->nx * p->ny * p->nz < (1ull << 32);
+}
+
+inline std::string check_params(const pfl_params* p) {
+  if (!p) return "params is NULL";
+  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "dimensions must be >= 1";
+  for (int a = 0; a < 3; ++a) {
+    int lo = p->bc[2 * a], hi = p->bc[2 * a + 1];
+    if ((lo != PFL_PERIODIC && lo != PFL_NOSLIP) || (hi != PFL_PERIODIC && hi != PFL_NOSLIP))
+      return "unknown boundary kind";
+    if (lo != hi) return "both faces of one axis must have the same kind";
+  }
+  if (!(p->rho_h > 0) || !(p->rho_l > 0)) return "densities must be > 0";
+  if (!(p->mobility > 0)) return "mobility must be > 0";
+  if (!(p->xi > 0)) return "interface width xi must be > 0";
+  if (!(p->sigma >= 0)) return "sigma must be >= 0";
+  const double wh = 1.0 / (3.0 * p->nu_h + 0.5), wl = 1.0 / (3.0 * p->nu_l + 0.5);
+  const double wp = 1.0 / (3.0 * p->mobility + 0.5);
+  if (!(wh > 0 && wh < 2) || !(wl > 0 && wl < 2)) return "relaxation rates of both phases must lie in (0, 2)";
+  if (!(wp > 0 && wp < 2)) return "phase-field relaxation rate must lie in (0, 2)";
+  if (p->precision < PFL_FP64 || p->precision > PFL_FP16S) return "unknown precision";
+  if (p->collision != PFL_MRT && p->collision != PFL_BGK) return "unknown collision model";
+  if (p->engine != PFL_ENGINE_AUTO && p->engine != PFL_ENGINE_INPLACE) return "unknown engine";
+  if (!std::isfinite(p->gravity[0]) || !std::isfinite(p->gravity[1]) || !std::isfinite(p->gravity[2]))
+    return "gravity must be finite";
+  return "";
+}
+
+inline bool is_device_ptr(const void* ptr, int* device = nullptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  if (device) *device = a.device;
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+}  // namespace pfl_host

@@ -35,9 +35,9 @@
 //   at x for direction i was written by x - c_i (by x itself after a bounce).
 //
 // phi is double-buffered: a step reads phi^t from `phi` (stencil) and, for the
-// FP16S format, the shifts phi^{t-1} of the populations it loads from `shift`;
-// it writes populations shifted by phi^t of the writing cell.  The phi pass
-// then writes phi^{t+1} into the buffer that held phi^{t-1}.
+// FP16S format, phi^{t-1} -- from which the shifts of the populations it loads
+// follow -- from `shift`; it writes populations shifted by phi^t values.  The
+// phi pass then writes phi^{t+1} into the buffer that held phi^{t-1}.
 #pragma once
 #include "lattice.cuh"
 
@@ -160,14 +160,16 @@ __device__ __forceinline__ void stencil(const Geo& geo, const Nb& nb, long long 
 template <int PREC, int READ_ODD>
 __device__ __forceinline__ void hydro_macro(const Geo& geo, const Phys& ph, const Nb& nb, long long cell,
                                             const typename Store<PREC>::S* __restrict__ g,
-                                            Macro<typename Store<PREC>::R>& m, typename Store<PREC>::R gv[27]) {
+                                            const float* __restrict__ pshift, Macro<typename Store<PREC>::R>& m,
+                                            typename Store<PREC>::R gv[27]) {
   typedef typename Store<PREC>::R R;
   R pst = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
 #pragma unroll
   for (int i = 0; i < 27; ++i) {
     const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
     long long from;
-    R v = ld_g<PREC>(g, src_index<READ_ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz, from), i);
+    const size_t idx = src_index<READ_ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz, from);
+    R v = ld_g<PREC>(g, idx, i, PREC == 2 ? (R)__ldg(pshift + from) : (R)0);
     gv[i] = v;
     pst += v;
     if (cx) jx += cx > 0 ? v : -v;
@@ -220,7 +222,8 @@ __device__ __forceinline__ void hydro_macro(const Geo& geo, const Phys& ph, cons
   m.uz = jz + Fz * inv2rho;
 }
 
-// h population k arriving at `cell` (shift from `shift` for FP16S).
+// h population k arriving at `cell` (FP16S: shifted by phi of the writing cell,
+// read from `shift`).
 template <int PREC, int READ_ODD>
 __device__ __forceinline__ typename Store<PREC>::R load_h(const Geo& geo, const Nb& nb, long long cell, int k,
                                                           const typename Store<PREC>::S* __restrict__ h,
@@ -238,7 +241,8 @@ template <int PREC, int ODD, int BGK>
 __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<PREC>::S* __restrict__ h,
                                               typename Store<PREC>::S* __restrict__ g,
                                               const typename Store<PREC>::PhiT* __restrict__ phi,
-                                              const typename Store<PREC>::PhiT* __restrict__ shift) {
+                                              const typename Store<PREC>::PhiT* __restrict__ shift,
+                                              const float* __restrict__ pshift, float* __restrict__ pout) {
   typedef typename Store<PREC>::R R;
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
@@ -249,7 +253,8 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
   Macro<R> m;
   stencil<PREC>(geo, nb, cell, phi, m);
   R gv[27];
-  hydro_macro<PREC, ODD>(geo, ph, nb, cell, g, m, gv);
+  hydro_macro<PREC, ODD>(geo, ph, nb, cell, g, pshift, m, gv);
+  if (PREC == 2) pout[cell] = (float)m.pst;
 
   // ---- g collision and streaming
   {
@@ -279,7 +284,7 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
                      (R)2 * ((R)(cx * cy) * dxy + (R)(cy * cz) * dyz + (R)(cx * cz) * dxz) - tr3;
         post = geq + w * (a2 * hd + cf);
       }
-      st_g<PREC>(g, dst_index<ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz), i, post);
+      st_g<PREC>(g, dst_index<ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz), i, post, (R)m.pst);
     }
   }
 
@@ -376,7 +381,8 @@ __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typenam
 #pragma unroll
   for (int i = 0; i < 27; ++i) {
     const R cu = (R)q27_cx(i) * ux + (R)q27_cy(i) * uy + (R)q27_cz(i) * uz;
-    st_g<PREC>(g, (size_t)i * geo.N + cell, i, (R)q27_w(i) * (ps + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu));
+    st_g<PREC>(g, (size_t)i * geo.N + cell, i, (R)q27_w(i) * (ps + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu),
+               (R)0);
   }
 #pragma unroll
   for (int k = 0; k < 15; ++k) {
@@ -389,8 +395,8 @@ __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typenam
 template <int PREC, int READ_ODD>
 __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename Store<PREC>::S* __restrict__ g,
                                                 const typename Store<PREC>::PhiT* __restrict__ phi,
-                                                double* o_phi, double* o_rho, double* o_p, double* o_ux,
-                                                double* o_uy, double* o_uz) {
+                                                const float* __restrict__ pshift, double* o_phi, double* o_rho,
+                                                double* o_p, double* o_ux, double* o_uy, double* o_uz) {
   typedef typename Store<PREC>::R R;
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
@@ -401,7 +407,7 @@ __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename
   Macro<R> m;
   stencil<PREC>(geo, nb, cell, phi, m);
   R gv[27];
-  hydro_macro<PREC, READ_ODD>(geo, ph, nb, cell, g, m, gv);
+  hydro_macro<PREC, READ_ODD>(geo, ph, nb, cell, g, pshift, m, gv);
   if (o_phi) o_phi[cell] = (double)m.phi;
   if (o_rho) o_rho[cell] = (double)m.rho;
   if (o_p) o_p[cell] = (double)m.pst * (double)m.rho / 3.0;
@@ -414,7 +420,7 @@ __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename
 template <int PREC, int READ_ODD>
 __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
                          const typename Store<PREC>::PhiT* __restrict__ shift, int q, int i,
-                         double* __restrict__ out) {
+                         double* __restrict__ out, const float* __restrict__ pshift) {
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
   int x, y, z;
@@ -426,8 +432,8 @@ __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
     for (int j = 0; j < 27; ++j)
       if (j == i) {
         long long from;
-        out[cell] = (double)ld_g<PREC>(
-            f, src_index<READ_ODD>(geo, nb, cell, j, q27_opp(j), q27_cx(j), q27_cy(j), q27_cz(j), from), j);
+        const size_t idx = src_index<READ_ODD>(geo, nb, cell, j, q27_opp(j), q27_cx(j), q27_cy(j), q27_cz(j), from);
+        out[cell] = (double)ld_g<PREC>(f, idx, j, PREC == 2 ? pshift[from] : 0.0f);
       }
   } else {
 #pragma unroll
@@ -448,7 +454,7 @@ __global__ void k_import(Geo geo, typename Store<PREC>::S* __restrict__ f, int q
   } else if (q == 27) {
 #pragma unroll
     for (int j = 0; j < 27; ++j)
-      if (j == i) st_g<PREC>(f, idx, j, (R)in[cell]);
+      if (j == i) st_g<PREC>(f, idx, j, (R)in[cell], (R)0);
   } else {
 #pragma unroll
     for (int j = 0; j < 15; ++j)

@@ -13,11 +13,13 @@
 
 #include "../../include/pflbm.h"
 #include "errors.h"
+#include "host_common.h"
 #include "kernels.cuh"
 #include "step.cuh"
 #include "adjoint.cuh"
 
 using namespace pfl;
+using namespace pfl_host;
 
 namespace {
 
@@ -46,13 +48,10 @@ pfl_status cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
   } while (0)
 
-size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-size_t pop_bytes(int prec) { return prec == PFL_FP64 ? 8 : prec == PFL_FP32 ? 4 : 2; }
-size_t phi_bytes(int prec) { return prec == PFL_FP64 ? 8 : 4; }
 
 struct Layout {
-  size_t h, g, phi[2], stage, red, total;
+  size_t h, g, h2, g2, phi[2], pst[2], stage, red, total;
 };
 
 Layout layout_of(const pfl_params* p) {
@@ -63,9 +62,20 @@ Layout layout_of(const pfl_params* p) {
   off = align256(off + 15 * N * pop_bytes(p->precision));
   L.g = off;
   off = align256(off + 27 * N * pop_bytes(p->precision));
+  L.h2 = L.g2 = 0;
+  if (uses_two_arrays(p)) {  // second array pair of the fused two-array step
+    L.h2 = off;
+    off = align256(off + 15 * N * pop_bytes(p->precision));
+    L.g2 = off;
+    off = align256(off + 27 * N * pop_bytes(p->precision));
+  }
   for (int b = 0; b < 2; ++b) {
     L.phi[b] = off;
     off = align256(off + N * phi_bytes(p->precision));
+  }
+  for (int b = 0; b < 2; ++b) {  // p* of the writing cells (shift of the FP16S g)
+    L.pst[b] = off;
+    off = align256(off + N * sizeof(float));
   }
   L.stage = off;
   off = align256(off + (N + 16) * sizeof(double));
@@ -75,43 +85,8 @@ Layout layout_of(const pfl_params* p) {
   return L;
 }
 
-std::string check_params(const pfl_params* p) {
-  if (!p) return "params is NULL";
-  if (p->nx < 1 || p->ny < 1 || p->nz < 1) return "dimensions must be >= 1";
-  for (int a = 0; a < 3; ++a) {
-    int lo = p->bc[2 * a], hi = p->bc[2 * a + 1];
-    if ((lo != PFL_PERIODIC && lo != PFL_NOSLIP) || (hi != PFL_PERIODIC && hi != PFL_NOSLIP))
-      return "unknown boundary kind";
-    if (lo != hi) return "both faces of one axis must have the same kind";
-  }
-  if (!(p->rho_h > 0) || !(p->rho_l > 0)) return "densities must be > 0";
-  if (!(p->mobility > 0)) return "mobility must be > 0";
-  if (!(p->xi > 0)) return "interface width xi must be > 0";
-  if (!(p->sigma >= 0)) return "sigma must be >= 0";
-  const double wh = 1.0 / (3.0 * p->nu_h + 0.5), wl = 1.0 / (3.0 * p->nu_l + 0.5);
-  const double wp = 1.0 / (3.0 * p->mobility + 0.5);
-  if (!(wh > 0 && wh < 2) || !(wl > 0 && wl < 2)) return "relaxation rates of both phases must lie in (0, 2)";
-  if (!(wp > 0 && wp < 2)) return "phase-field relaxation rate must lie in (0, 2)";
-  if (p->precision < PFL_FP64 || p->precision > PFL_FP16S) return "unknown precision";
-  if (p->collision != PFL_MRT && p->collision != PFL_BGK) return "unknown collision model";
-  if (!std::isfinite(p->gravity[0]) || !std::isfinite(p->gravity[1]) || !std::isfinite(p->gravity[2]))
-    return "gravity must be finite";
-  return "";
-}
 
-bool is_device_ptr(const void* ptr, int* device = nullptr) {
-  if (!ptr) return false;
-  cudaPointerAttributes a;
-  cudaError_t e = cudaPointerGetAttributes(&a, ptr);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  if (device) *device = a.device;
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
 
-unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 }  // namespace
 
@@ -126,19 +101,33 @@ struct pfl_ctx {
   cudaStream_t stream;
   int device;
   int cur;       // phi buffer holding phi^t; the other holds the shifts of the stored h
+  int pcur;      // p* buffer holding the shifts of the stored g (written by the last step)
+  bool zm;       // fused two-array step (else in-place AA + phi pass)
+  int ab;        // two-array step: 0 = first pair current, 1 = second
+  bool stale;    // two-array step: phi of the current state not yet materialised
+  int zc;        // two-array step: z planes per block
   long long t;   // steps taken
   int swapped;   // 1 after an even step (populations await the gather read)
 };
 
 namespace {
 
+// current populations (the two-array step alternates between two pairs)
 template <int PREC>
 typename Store<PREC>::S* hbuf(pfl_ctx* c) {
-  return (typename Store<PREC>::S*)(c->ws + c->L.h);
+  return (typename Store<PREC>::S*)(c->ws + (c->zm && c->ab ? c->L.h2 : c->L.h));
 }
 template <int PREC>
 typename Store<PREC>::S* gbuf(pfl_ctx* c) {
-  return (typename Store<PREC>::S*)(c->ws + c->L.g);
+  return (typename Store<PREC>::S*)(c->ws + (c->zm && c->ab ? c->L.g2 : c->L.g));
+}
+template <int PREC>
+typename Store<PREC>::S* hnext(pfl_ctx* c) {
+  return (typename Store<PREC>::S*)(c->ws + (c->ab ? c->L.h : c->L.h2));
+}
+template <int PREC>
+typename Store<PREC>::S* gnext(pfl_ctx* c) {
+  return (typename Store<PREC>::S*)(c->ws + (c->ab ? c->L.g : c->L.g2));
 }
 template <int PREC>
 typename Store<PREC>::PhiT* phibuf(pfl_ctx* c, int b) {
@@ -153,6 +142,11 @@ typename Store<PREC>::PhiT* phishift(pfl_ctx* c) {
   return phibuf<PREC>(c, 1 - c->cur);
 }
 double* stage(pfl_ctx* c) { return (double*)(c->ws + c->L.stage); }
+
+float* pshift(pfl_ctx* c) { return (float*)(c->ws + c->L.pst[c->pcur]); }
+// seed of the FP16 stochastic rounding of one step
+unsigned step_seed(const pfl_ctx* c) { return (unsigned)((unsigned long long)c->t * 0x9E3779B97F4A7C15ull >> 32); }
+float* pnext(pfl_ctx* c) { return (float*)(c->ws + c->L.pst[1 - c->pcur]); }
 
 // phi of the stored state into the spare buffer, then make it current.  The
 // stored h carry the shifts of buffer `cur` (after a step) -- the spare buffer
@@ -172,37 +166,76 @@ void launch_phi(pfl_ctx* c) {
   c->cur = 1 - c->cur;
 }
 
-// One collide-stream launch (without the phi pass that completes the step).
-// MRT runs the pair-based kernel; the BGK test mode, and lattices too large
-// for 32-bit indices, the generic one.
+// One collide-stream launch (without the phi pass that completes an in-place
+// step).  Two-array contexts run the fused kernel; MRT in place the pair-based
+// kernel; the BGK test mode, and lattices too large for 32-bit indices, the
+// generic one.
 template <int PREC, int BGK>
 void step_only(pfl_ctx* c) {
   const unsigned nb = blocks_for(c->geo.N, 256);
+  if (c->zm) {
+    const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
+    const dim3 block(ZM_TX, ZM_TY);
+    if (c->p.nz == 1)
+      k_step_zm<PREC, 1><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), hnext<PREC>(c),
+                                                         gnext<PREC>(c), phishift<PREC>(c), phicur<PREC>(c),
+                                                         pshift(c), pnext(c), c->zc, step_seed(c));
+    else
+      k_step_zm<PREC, 0><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), hnext<PREC>(c),
+                                                         gnext<PREC>(c), phishift<PREC>(c), phicur<PREC>(c),
+                                                         pshift(c), pnext(c), c->zc, step_seed(c));
+    // phicur now holds phi^t, the shift of the populations just written
+    c->ab ^= 1;
+    c->cur = 1 - c->cur;
+    c->pcur = 1 - c->pcur;
+    c->stale = true;
+    c->t += 1;
+    return;
+  }
   if (BGK || !c->idx32) {
     if (c->swapped)
-      k_step<PREC, 1, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
-                                                     phishift<PREC>(c));
+      k_step<PREC, 1, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
+                                                       phishift<PREC>(c), pshift(c), pnext(c));
     else
-      k_step<PREC, 0, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
-                                                     phishift<PREC>(c));
+      k_step<PREC, 0, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
+                                                       phishift<PREC>(c), pshift(c), pnext(c));
   } else {
     const unsigned nbm = blocks_for(c->geo.N, PFL_STEP_THREADS);
     if (c->swapped)
-      k_step_mrt<PREC, 1><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
-                                                      phishift<PREC>(c));
+      k_step_mrt<PREC, 1><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),
+                                                                    phicur<PREC>(c), phishift<PREC>(c), pshift(c),
+                                                                    pnext(c), step_seed(c));
     else
-      k_step_mrt<PREC, 0><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
-                                                      phishift<PREC>(c));
+      k_step_mrt<PREC, 0><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),
+                                                                    phicur<PREC>(c), phishift<PREC>(c), pshift(c),
+                                                                    pnext(c), step_seed(c));
   }
   c->swapped ^= 1;
+  c->pcur = 1 - c->pcur;
   c->t += 1;
+}
+
+// phi of the current state of a two-array context into the current buffer
+// (the same sum the next fused step forms in shared memory).
+template <int PREC>
+void ensure_phi(pfl_ctx* c) {
+  if (!c->zm || !c->stale) return;
+  k_phi32<PREC, 0><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phishift<PREC>(c),
+                                                                      phicur<PREC>(c));
+  c->stale = false;
+}
+
+// completes a step: the phi pass in place, nothing for the fused step
+template <int PREC>
+void after_step(pfl_ctx* c) {
+  if (!c->zm) launch_phi<PREC>(c);
 }
 
 template <int PREC, int BGK>
 void launch_steps(pfl_ctx* c, int n) {
   for (int s = 0; s < n; ++s) {
     step_only<PREC, BGK>(c);
-    launch_phi<PREC>(c);
+    after_step<PREC>(c);
   }
 }
 
@@ -211,6 +244,9 @@ void launch_steps(pfl_ctx* c, int n) {
 // write phi into buffer 0 and make that one current.
 template <int PREC>
 pfl_status fresh_phi(pfl_ctx* c) {
+  c->stale = false;
+  c->pcur = 0;
+  CUDA_TRY(cudaMemsetAsync(pshift(c), 0, c->geo.N * sizeof(float), c->stream));
   c->cur = 1;
   CUDA_TRY(cudaMemsetAsync(phicur<PREC>(c), 0, c->geo.N * sizeof(typename Store<PREC>::PhiT), c->stream));
   c->swapped = 0;
@@ -223,11 +259,11 @@ template <int PREC>
 void launch_fields(pfl_ctx* c, double* o[6]) {
   const unsigned nb = blocks_for(c->geo.N, 256);
   if (c->swapped)
-    k_fields<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0], o[1], o[2],
-                                                  o[3], o[4], o[5]);
+    k_fields<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), pshift(c), o[0],
+                                                  o[1], o[2], o[3], o[4], o[5]);
   else
-    k_fields<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0], o[1], o[2],
-                                                  o[3], o[4], o[5]);
+    k_fields<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), pshift(c), o[0],
+                                                  o[1], o[2], o[3], o[4], o[5]);
 }
 
 template <int PREC>
@@ -235,9 +271,9 @@ void launch_export(pfl_ctx* c, int q, int i, double* out) {
   const unsigned nb = blocks_for(c->geo.N, 256);
   const typename Store<PREC>::S* f = (q == 27) ? gbuf<PREC>(c) : hbuf<PREC>(c);
   if (c->swapped)
-    k_export<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), q, i, out);
+    k_export<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), q, i, out, pshift(c));
   else
-    k_export<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), q, i, out);
+    k_export<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), q, i, out, pshift(c));
 }
 
 template <int PREC>
@@ -314,6 +350,20 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
   c->t = 0;
   c->swapped = 0;
   c->cur = 0;
+  c->pcur = 0;
+  c->zm = uses_two_arrays(p);
+  c->ab = 0;
+  c->stale = false;
+  {
+    // z planes per block: about four waves of two blocks per SM, at least 4 planes
+    int sms = 152;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const long long bxy = (long long)((p->nx + ZM_TX - 1) / ZM_TX) * ((p->ny + ZM_TY - 1) / ZM_TY);
+    long long zc = (bxy * p->nz + 8LL * sms - 1) / (8LL * sms);
+    if (zc < 4) zc = 4;
+    if (zc > p->nz) zc = p->nz;
+    c->zc = (int)zc;
+  }
   c->geo.nx = p->nx;
   c->geo.ny = p->ny;
   c->geo.nz = p->nz;
@@ -425,6 +475,7 @@ pfl_status pfl_fields(pfl_ctx* c, double* phi, double* rho, double* p, double* u
     if (want[k] && !host[k]) dev[k] = want[k];
   }
   // device outputs in one pass
+  DISPATCH_PREC(c, ensure_phi, c);
   bool any_dev = false;
   for (int k = 0; k < 6; ++k) any_dev |= dev[k] != nullptr;
   if (any_dev) DISPATCH_PREC(c, launch_fields, c, dev);
@@ -446,6 +497,7 @@ pfl_status pfl_fields(pfl_ctx* c, double* phi, double* rho, double* p, double* u
 pfl_status pfl_populations(pfl_ctx* c, double* h, double* g) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
   CUDA_TRY(cudaSetDevice(c->device));
+  DISPATCH_PREC(c, ensure_phi, c);
   const long long N = c->geo.N;
   for (int set = 0; set < 2; ++set) {
     double* dst = set == 0 ? h : g;
@@ -499,6 +551,7 @@ pfl_status pfl_diag(pfl_ctx* c, double out[8], long long* nonfinite) {
   CUDA_TRY(cudaSetDevice(c->device));
   double* part = (double*)(c->ws + c->L.red);
   double* res = part + DIAG_BLOCKS * 9;
+  DISPATCH_PREC(c, ensure_phi, c);
   DISPATCH_PREC(c, launch_diag, c, part, res);
   CUDA_TRY(cudaGetLastError());
   double host[9];
@@ -529,7 +582,7 @@ pfl_status pfl_kernel_times(pfl_ctx* c, int n, double ms[2]) {
       default: bgk ? step_only<2, 1>(c) : step_only<2, 0>(c); break;
     }
     cudaEventRecord(ev[1], c->stream);
-    DISPATCH_PREC(c, launch_phi, c);
+    DISPATCH_PREC(c, after_step, c);
     cudaEventRecord(ev[2], c->stream);
     cudaError_t e = cudaEventSynchronize(ev[2]);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -609,12 +662,15 @@ pfl_status copy_state(pfl_ctx* c, char* slot, bool save) {
   const size_t N = (size_t)c->geo.N;
   const size_t S = pop_bytes(c->p.precision), P = phi_bytes(c->p.precision);
   const size_t hb = 15 * N * S, gb = 27 * N * S, pb = N * P;
-  char* live[3] = {c->ws + c->L.h, c->ws + c->L.g, c->ws + c->L.phi[c->cur]};
+  const bool second = c->zm && c->ab;
+  char* live[3] = {c->ws + (second ? c->L.h2 : c->L.h), c->ws + (second ? c->L.g2 : c->L.g),
+                   c->ws + c->L.phi[c->cur]};
   char* sl[3] = {slot, slot + align256(hb), slot + align256(hb) + align256(gb)};
   const size_t by[3] = {hb, gb, pb};
   for (int k = 0; k < 3; ++k)
     CUDA_TRY(cudaMemcpyAsync(save ? sl[k] : live[k], save ? live[k] : sl[k], by[k], cudaMemcpyDeviceToDevice,
                              c->stream));
+  if (!save) c->stale = false;  // the restored phi belongs to the restored populations
   return PFL_OK;
 }
 
@@ -676,6 +732,7 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
   const long long t0 = c->t;
   std::vector<int> ck_swapped(A.nck, 0), seg_swapped(A.K, 0);
   // forward sweep with checkpoints
+  ensure_phi<PREC>(c);
   for (int k = 0; k < n; ++k) {
     if (k % A.K == 0) {
       ck_swapped[k / A.K] = c->swapped;
@@ -686,7 +743,8 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
     const bool bgk = false;
     (void)bgk;
     step_only<PREC, 0>(c);
-    launch_phi<PREC>(c);
+    after_step<PREC>(c);
+    ensure_phi<PREC>(c);
   }
   if (const double* W = obs_at(n)) launch_dot<PREC>(c, W, part + 3 * ((c->geo.N + ADJ_THREADS - 1) / ADJ_THREADS), res);
   const int fin_swapped = c->swapped;
@@ -710,7 +768,8 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
       if (st != PFL_OK) return st;
       if (k + 1 < k1) {  // the last state of the segment is never stepped from here
         step_only<PREC, 0>(c);
-        launch_phi<PREC>(c);
+        after_step<PREC>(c);
+        ensure_phi<PREC>(c);
       }
     }
     for (int k = k1 - 1; k >= k0; --k) {

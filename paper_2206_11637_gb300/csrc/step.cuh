@@ -146,6 +146,41 @@ __device__ __forceinline__ typename Store<PREC>::S pack(typename Store<PREC>::R 
     return v;
 }
 
+// Stochastic rounding for the FP16 stores of the step.  Round-to-nearest
+// repeats the same error every step where a field changes slowly, and those
+// errors add up linearly in time (mass drift of phi); rounding up with the
+// probability given by the discarded bits makes every store unbiased.  The
+// random bits come from a per-cell stream: the 32-bit hash of (cell, step)
+// (lowbias32 by C. Wellons) seeds a linear congruential sequence (Numerical
+// Recipes constants), whose top 13 bits are added below the FP16 mantissa of
+// the FP32 value before truncation toward zero.
+__device__ __forceinline__ unsigned hash32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+struct Dither {
+  unsigned r;
+  __device__ __forceinline__ unsigned next() {
+    r = r * 1664525u + 1013904223u;
+    return r >> 19;
+  }
+};
+
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::S pack_sr(typename Store<PREC>::R v, Dither& d) {
+  if constexpr (PREC == 2) {
+    const unsigned b = __float_as_uint(v) + d.next();
+    return __float2half_rz(__uint_as_float(b));
+  } else {
+    return v;
+  }
+}
+
 __device__ __forceinline__ void cell_off(const Geo32& geo, unsigned c, CellOff& o) {
   const unsigned yz = fdiv(c, geo.dx);
   const unsigned x = c - yz * geo.nx;
@@ -181,38 +216,55 @@ __device__ __forceinline__ void load_pair(const typename Store<PREC>::S* __restr
 template <int PREC, int ODD>
 __device__ __forceinline__ void store_pair(typename Store<PREC>::S* __restrict__ f, unsigned N, unsigned cell,
                                            const CellOff& o, int i, int oi, int cx, int cy, int cz,
-                                           typename Store<PREC>::R A, typename Store<PREC>::R B) {
+                                           typename Store<PREC>::R A, typename Store<PREC>::R B, Dither& d) {
   if (!ODD) {
-    f[(unsigned)oi * N + cell] = pack<PREC>(A);
-    f[(unsigned)i * N + cell] = pack<PREC>(B);
+    f[(unsigned)oi * N + cell] = pack_sr<PREC>(A, d);
+    f[(unsigned)i * N + cell] = pack_sr<PREC>(B, d);
   } else {
     const bool vc = o.valid(cx, cy, cz), vmc = o.valid(-cx, -cy, -cz);
-    f[vc ? (unsigned)i * N + cell + (unsigned)o.off(cx, cy, cz) : (unsigned)oi * N + cell] = pack<PREC>(A);
-    f[vmc ? (unsigned)oi * N + cell + (unsigned)o.off(-cx, -cy, -cz) : (unsigned)i * N + cell] = pack<PREC>(B);
+    f[vc ? (unsigned)i * N + cell + (unsigned)o.off(cx, cy, cz) : (unsigned)oi * N + cell] = pack_sr<PREC>(A, d);
+    f[vmc ? (unsigned)oi * N + cell + (unsigned)o.off(-cx, -cy, -cz) : (unsigned)i * N + cell] = pack_sr<PREC>(B, d);
   }
 }
 
-template <int PREC, int ODD>
-__global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB) k_step_mrt(Geo32 geo, Phys ph, typename Store<PREC>::S* __restrict__ h,
-                                                  typename Store<PREC>::S* __restrict__ g,
-                                                  const typename Store<PREC>::PhiT* __restrict__ phi,
-                                                  const typename Store<PREC>::PhiT* __restrict__ shift) {
+// phi^t around a cell read from the current phi buffer (stencil offsets, so
+// mirrored across walls).
+template <int PREC>
+struct GlobalPhi {
+  const typename Store<PREC>::PhiT* __restrict__ phi;
+  const CellOff* o;
+  unsigned cell;
+  __device__ __forceinline__ typename Store<PREC>::R operator()(int cx, int cy, int cz) const {
+    return (typename Store<PREC>::R)__ldg(phi + cell + o->soff(cx, cy, cz));
+  }
+};
+
+// The collide-stream update of one cell, shared by every stream-collide
+// kernel: populations are read from (hin, gin) in the layout READ_ODD and
+// written to (hout, gout) in the layout WRITE_ODD (the same arrays and parity
+// for the in-place AA step; a second array pair and push streaming for the
+// two-array step).  phi_at(c) returns phi^t at the stencil neighbour c.
+template <int PREC, int READ_ODD, int WRITE_ODD, class PhiAt>
+__device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, const CellOff& o,
+                                             const typename Store<PREC>::S* hin,
+                                             const typename Store<PREC>::S* gin, typename Store<PREC>::S* hout,
+                                             typename Store<PREC>::S* gout, const PhiAt& phi_at,
+                                             const typename Store<PREC>::PhiT* __restrict__ shift,
+                                             const float* __restrict__ pshift, float* __restrict__ pout,
+                                             unsigned cell, unsigned seed) {
   typedef typename Store<PREC>::R R;
   constexpr bool F16 = PREC == 2;
-  const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= geo.N) return;
   const unsigned N = geo.N;
-  CellOff o;
-  cell_off(geo, cell, o);
+  Dither dith{F16 ? hash32(cell * 0x9E3779B1u + seed) : 0u};
 
   // ---- phi stencil over D3Q27 weights, by pairs
-  const R pc = (R)__ldg(phi + cell);
+  const R pc = phi_at(0, 0, 0);
   R gx = 0, gy = 0, gz = 0, lap = 0;
 #pragma unroll
   for (int i = 0; i < 13; ++i) {
     const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
-    const R a = (R)__ldg(phi + cell + o.soff(cx, cy, cz));
-    const R b = (R)__ldg(phi + cell + o.soff(-cx, -cy, -cz));
+    const R a = phi_at(cx, cy, cz);
+    const R b = phi_at(-cx, -cy, -cz);
     const R w = (R)q27_w(i);
     const R d = w * (a - b);
     if (cx) gx += cx > 0 ? d : -d;
@@ -226,21 +278,23 @@ __global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB) k_step_mrt(Ge
   lap *= (R)6;
 
   // ---- g moments
+  // shifted FP16: g_i = w_i (s / KG + p*_writer)
   R pst, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
   {
-    const R rest = raw<PREC>(g[13u * N + cell]);
-    pst = F16 ? rest * (R)(q27_w(13) / KG16) : rest;
+    const R rest = raw<PREC>(gin[13u * N + cell]);
+    pst = F16 ? (rest * (R)(1.0 / KG16) + (R)__ldg(pshift + cell)) * (R)q27_w(13) : rest;
   }
 #pragma unroll
   for (int i = 0; i < 13; ++i) {
     const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
     R a, b;
     unsigned fa, fb;
-    load_pair<PREC, ODD>(g, N, cell, o, i, 26 - i, cx, cy, cz, a, b, fa, fb);
+    load_pair<PREC, READ_ODD>(gin, N, cell, o, i, 26 - i, cx, cy, cz, a, b, fa, fb);
     R S = a + b, D = a - b;
     if (F16) {
-      S *= (R)(q27_w(i) / KG16);
-      D *= (R)(q27_w(i) / KG16);
+      const R qa = (R)__ldg(pshift + fa), qb = (R)__ldg(pshift + fb);
+      S = (R)q27_w(i) * (S * (R)(1.0 / KG16) + (qa + qb));
+      D = (R)q27_w(i) * (D * (R)(1.0 / KG16) + (qa - qb));
     }
     pst += S;
     if (cx) jx += cx > 0 ? D : -D;
@@ -284,7 +338,9 @@ __global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB) k_step_mrt(Ge
     const R a2 = ((R)1 - omega) * (R)4.5;
     const R dxx = pxx - p3 - ux * ux, dyy = pyy - p3 - uy * uy, dzz = pzz - p3 - uz * uz;
     const R K = F16 ? (R)KG16 : (R)1;
-    const R al = K * (pst - (R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
+    // FP16S stores g+ / w - p* of this cell: the p* term leaves alpha
+    const R al = K * ((F16 ? (R)0 : pst) - (R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
+    if (F16) pout[cell] = (float)pst;
     const R fr = (R)1.5 / rho;
     const R bx = K * ((R)3 * ux + fr * Fx), by = K * ((R)3 * uy + fr * Fy), bz = K * ((R)3 * uz + fr * Fz);
     const R Gxx = K * ((R)4.5 * ux * ux + a2 * dxx), Gyy = K * ((R)4.5 * uy * uy + a2 * dyy),
@@ -292,7 +348,7 @@ __global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB) k_step_mrt(Ge
     const R Gxy = K * (R)2 * ((R)4.5 * ux * uy + a2 * (pxy - ux * uy));
     const R Gyz = K * (R)2 * ((R)4.5 * uy * uz + a2 * (pyz - uy * uz));
     const R Gxz = K * (R)2 * ((R)4.5 * ux * uz + a2 * (pxz - ux * uz));
-    g[13u * N + cell] = pack<PREC>(F16 ? al : (R)q27_w(13) * al);
+    gout[13u * N + cell] = pack_sr<PREC>(F16 ? al : (R)q27_w(13) * al, dith);
 #pragma unroll
     for (int i = 0; i < 13; ++i) {
       const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
@@ -312,14 +368,14 @@ __global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB) k_step_mrt(Ge
         A *= (R)q27_w(i);
         B *= (R)q27_w(i);
       }
-      store_pair<PREC, ODD>(g, N, cell, o, i, 26 - i, cx, cy, cz, A, B);
+      store_pair<PREC, WRITE_ODD>(gout, N, cell, o, i, 26 - i, cx, cy, cz, A, B, dith);
     }
   }
 
-  // ---- h moments (shifted FP16: value = w (s / K + phi_src))
+  // ---- h moments (shifted FP16: h = w (s / KH + phi_writer))
   R phl, hjx = 0, hjy = 0, hjz = 0, hxx = 0, hyy = 0, hzz = 0, hxy = 0, hyz = 0, hxz = 0;
   {
-    const R rest = raw<PREC>(h[7u * N + cell]);
+    const R rest = raw<PREC>(hin[7u * N + cell]);
     phl = F16 ? (rest * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7) : rest;
   }
 #pragma unroll
@@ -327,7 +383,7 @@ __global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB) k_step_mrt(Ge
     const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
     R a, b;
     unsigned fa, fb;
-    load_pair<PREC, ODD>(h, N, cell, o, k, 14 - k, cx, cy, cz, a, b, fa, fb);
+    load_pair<PREC, READ_ODD>(hin, N, cell, o, k, 14 - k, cx, cy, cz, a, b, fa, fb);
     R S, D;
     if (F16) {
       const R sa = (R)__ldg(shift + fa), sb = (R)__ldg(shift + fb);
@@ -367,7 +423,7 @@ __global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB) k_step_mrt(Ge
     const R bz = K * ((R)3 * phl * uz + a1 * (hjz - phl * uz) + tn * gz);
     const R Gxx = K * a2 * dxx, Gyy = K * a2 * dyy, Gzz = K * a2 * dzz;
     const R Gxy = K * (R)2 * a2 * hxy, Gyz = K * (R)2 * a2 * hyz, Gxz = K * (R)2 * a2 * hxz;
-    h[7u * N + cell] = pack<PREC>(F16 ? al : (R)q15_w(7) * al);
+    hout[7u * N + cell] = pack_sr<PREC>(F16 ? al : (R)q15_w(7) * al, dith);
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
       const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
@@ -387,21 +443,44 @@ __global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB) k_step_mrt(Ge
         A *= (R)q15_w(k);
         B *= (R)q15_w(k);
       }
-      store_pair<PREC, ODD>(h, N, cell, o, k, 14 - k, cx, cy, cz, A, B);
+      store_pair<PREC, WRITE_ODD>(hout, N, cell, o, k, 14 - k, cx, cy, cz, A, B, dith);
     }
   }
 }
 
-// phi = sum_i h_i of the state left by the last step (READ_ODD after an even
-// step); `shift` holds the shifts of the stored populations (FP16S).
-template <int PREC, int READ_ODD>
-__global__ void __launch_bounds__(256) k_phi32(Geo32 geo, const typename Store<PREC>::S* __restrict__ h,
-                                               const typename Store<PREC>::PhiT* __restrict__ shift,
-                                               typename Store<PREC>::PhiT* __restrict__ phi) {
-  typedef typename Store<PREC>::R R;
-  constexpr bool F16 = PREC == 2;
+// In-place AA update of one cell with the stencil read from the phi buffer.
+template <int PREC, int ODD>
+__device__ __forceinline__ void step_cell(const Geo32& geo, const Phys& ph, typename Store<PREC>::S* __restrict__ h,
+                                          typename Store<PREC>::S* __restrict__ g,
+                                          const typename Store<PREC>::PhiT* __restrict__ phi,
+                                          const typename Store<PREC>::PhiT* __restrict__ shift,
+                                          const float* __restrict__ pshift, float* __restrict__ pout, unsigned cell,
+                                          unsigned seed) {
+  CellOff o;
+  cell_off(geo, cell, o);
+  GlobalPhi<PREC> at{phi, &o, cell};
+  collide_cell<PREC, ODD, ODD>(geo, ph, o, h, g, h, g, at, shift, pshift, pout, cell, seed);
+}
+
+template <int PREC, int ODD>
+__global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB)
+    k_step_mrt(Geo32 geo, Phys ph, typename Store<PREC>::S* __restrict__ h, typename Store<PREC>::S* __restrict__ g,
+               const typename Store<PREC>::PhiT* __restrict__ phi,
+               const typename Store<PREC>::PhiT* __restrict__ shift, const float* __restrict__ pshift,
+               float* __restrict__ pout, unsigned seed) {
   const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
+  step_cell<PREC, ODD>(geo, ph, h, g, phi, shift, pshift, pout, cell, seed);
+}
+
+// phi of one cell from the stored h (READ_ODD after an even step).
+template <int PREC, int READ_ODD>
+__device__ __forceinline__ typename Store<PREC>::R phi_cell(const Geo32& geo,
+                                                            const typename Store<PREC>::S* __restrict__ h,
+                                                            const typename Store<PREC>::PhiT* __restrict__ shift,
+                                                            unsigned cell) {
+  typedef typename Store<PREC>::R R;
+  constexpr bool F16 = PREC == 2;
   CellOff o;
   cell_off(geo, cell, o);
   R s = F16 ? (raw<PREC>(h[7u * geo.N + cell]) * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7)
@@ -416,7 +495,143 @@ __global__ void __launch_bounds__(256) k_phi32(Geo32 geo, const typename Store<P
     else
       s += a + b;
   }
-  phi[cell] = s;
+  return s;
+}
+
+// phi = sum_i h_i of the state left by the last step (READ_ODD after an even
+// step); `shift` holds the shifts of the stored populations (FP16S).
+template <int PREC, int READ_ODD>
+__global__ void __launch_bounds__(256) k_phi32(Geo32 geo, const typename Store<PREC>::S* __restrict__ h,
+                                               const typename Store<PREC>::PhiT* __restrict__ shift,
+                                               typename Store<PREC>::PhiT* __restrict__ phi) {
+  const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= geo.N) return;
+  phi[cell] = phi_cell<PREC, READ_ODD>(geo, h, shift, cell);
+}
+
+}  // namespace pfl
+
+namespace pfl {
+
+// ---------------------------------------------------------------------------
+// Fused two-array step: stream-collide and the phi stencil in one launch.
+//
+// The populations live in two array pairs; a step reads the current pair in
+// its own cell (every slot local, coalesced) and pushes the post-collision
+// populations to the other pair (x + c, or the opposite slot of x behind a
+// wall).  Nothing a step reads is overwritten during that step, so a block may
+// read its neighbours' populations: each block owns an xy tile of ZM_TX x
+// ZM_TY columns and marches through a chunk of z planes, computing phi^t =
+// sum_i h_i for its tile plus a one-cell ring into a three-plane shared-memory
+// ring before colliding a plane.  phi^t of every cell is written once (the
+// FP16S shift of the populations written this step and the phi output), so
+// the separate phi pass and its re-read of h disappear.  Ring and z-halo
+// planes repeat the phi sum of neighbouring tiles (from L2).
+constexpr int ZM_TX = 32;
+constexpr int ZM_TY = 8;
+
+template <int PREC>
+struct SmemPhi {
+  const typename Store<PREC>::PhiT* plane[3];  // planes z - 1, z, z + 1 of (ZM_TY + 2) x (ZM_TX + 2) values
+  int i0;                 // index of this thread's column in a plane
+  __device__ __forceinline__ typename Store<PREC>::R operator()(int cx, int cy, int cz) const {
+    return (typename Store<PREC>::R)plane[1 + cz][i0 + cy * (ZM_TX + 2) + cx];
+  }
+};
+
+__device__ __forceinline__ int wrap_or_clamp(int v, int n, int wall) {
+  if (wall) return v < 0 ? 0 : (v >= n ? n - 1 : v);
+  return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
+// phi at cell (x, y, z) of the current pair (normal layout).
+template <int PREC>
+__device__ __forceinline__ typename Store<PREC>::R phi_at_xyz(const Geo32& geo,
+                                                              const typename Store<PREC>::S* __restrict__ h,
+                                                              const typename Store<PREC>::PhiT* __restrict__ shift,
+                                                              unsigned x, unsigned y, unsigned z) {
+  typedef typename Store<PREC>::R R;
+  constexpr bool F16 = PREC == 2;
+  CellOff o;
+  o.X = axis_off(x, geo.nx, 1, geo.wall[0]);
+  o.Y = axis_off(y, geo.ny, (int)geo.nx, geo.wall[1]);
+  o.Z = axis_off(z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
+  const unsigned cell = x + geo.nx * (y + geo.ny * z);
+  R s = F16 ? (raw<PREC>(h[7u * geo.N + cell]) * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7)
+            : raw<PREC>(h[7u * geo.N + cell]);
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    R a, b;
+    unsigned fa, fb;
+    load_pair<PREC, 0>(h, geo.N, cell, o, k, 14 - k, q15_cx(k), q15_cy(k), q15_cz(k), a, b, fa, fb);
+    if (F16)
+      s += (R)q15_w(k) * ((a + b) * (R)(1.0 / KH16) + ((R)__ldg(shift + fa) + (R)__ldg(shift + fb)));
+    else
+      s += a + b;
+  }
+  return s;
+}
+
+// grid: (ceil(nx / ZM_TX), ceil(ny / ZM_TY), ceil(nz / zc)), block ZM_TX x ZM_TY.
+template <int PREC, int FLAT>
+__global__ void __launch_bounds__(ZM_TX * ZM_TY, 2)
+    k_step_zm(Geo32 geo, Phys ph, const typename Store<PREC>::S* __restrict__ hA,
+              const typename Store<PREC>::S* __restrict__ gA, typename Store<PREC>::S* __restrict__ hB,
+              typename Store<PREC>::S* __restrict__ gB, const typename Store<PREC>::PhiT* __restrict__ phi_shift,
+              typename Store<PREC>::PhiT* __restrict__ phi_out, const float* __restrict__ pshift,
+              float* __restrict__ pout, int zc, unsigned seed) {
+  constexpr int PW = ZM_TX + 2, PH = ZM_TY + 2, PS = PW * PH;
+  typedef typename Store<PREC>::PhiT PhiT;
+  __shared__ PhiT ring[FLAT ? 1 : 3][PS];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZM_TX + tx;
+  const int x0 = blockIdx.x * ZM_TX, y0 = blockIdx.y * ZM_TY;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, (int)geo.nz);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < (int)geo.nx && y < (int)geo.ny;
+
+  // phi of plane zp (wrapped / mirrored) over the tile and its ring into slot
+  auto fill = [&](int zp, int slot) {
+    const unsigned zq = (unsigned)wrap_or_clamp(zp, (int)geo.nz, geo.wall[2]);
+    for (int p = tid; p < PS; p += ZM_TX * ZM_TY) {
+      const int i = p % PW, j = p / PW;
+      const unsigned xq = (unsigned)wrap_or_clamp(x0 - 1 + i, (int)geo.nx, geo.wall[0]);
+      const unsigned yq = (unsigned)wrap_or_clamp(y0 - 1 + j, (int)geo.ny, geo.wall[1]);
+      ring[slot][p] = (PhiT)phi_at_xyz<PREC>(geo, hA, phi_shift, xq, yq, zq);
+    }
+  };
+
+  if (FLAT) {
+    fill(0, 0);
+  } else {
+    fill(z0 - 1, (z0 - 1 - (z0 - 1)) % 3);
+    fill(z0, 1);
+  }
+  for (int z = z0; z < z1; ++z) {
+    if (!FLAT) fill(z + 1, (z + 1 - (z0 - 1)) % 3);
+    __syncthreads();
+    if (active) {
+      const unsigned cell = (unsigned)x + geo.nx * ((unsigned)y + geo.ny * (unsigned)z);
+      CellOff o;
+      o.X = axis_off((unsigned)x, geo.nx, 1, geo.wall[0]);
+      o.Y = axis_off((unsigned)y, geo.ny, (int)geo.nx, geo.wall[1]);
+      o.Z = axis_off((unsigned)z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
+      SmemPhi<PREC> at;
+      if (FLAT) {
+        at.plane[0] = at.plane[1] = at.plane[2] = ring[0];
+      } else {
+        const int b = z - (z0 - 1);
+        at.plane[0] = ring[(b + 2) % 3];
+        at.plane[1] = ring[b % 3];
+        at.plane[2] = ring[(b + 1) % 3];
+      }
+      // with one z plane the z neighbours are the plane itself (periodic or mirrored)
+      at.i0 = (ty + 1) * PW + (tx + 1);
+      phi_out[cell] = (typename Store<PREC>::PhiT)at(0, 0, 0);
+      collide_cell<PREC, 0, 1>(geo, ph, o, hA, gA, hB, gB, at, phi_shift, pshift, pout, cell, seed);
+    }
+    __syncthreads();
+  }
 }
 
 }  // namespace pfl

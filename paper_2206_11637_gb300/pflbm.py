@@ -23,6 +23,7 @@ def _params_struct(p, precision):
         s.gravity[k] = float(p.gravity[k])
     s.precision = int(precision)
     s.collision = int(p.collision)
+    s.engine = int(getattr(p, "engine", 0))
     return s
 
 

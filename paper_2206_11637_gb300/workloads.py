@@ -33,6 +33,7 @@ class Params:
     xi: float = 5.0
     gravity: tuple = (0.0, 0.0, 0.0)
     collision: int = 0                    # 0 weighted-orthogonal MRT, 1 BGK
+    engine: int = 0                       # 0 auto (fused two-array step), 1 in-place AA + phi pass
 
     @property
     def shape(self):
@@ -211,3 +212,27 @@ def drop_impact(nx=512, ny=384, nz=512, D=64.0, depth=128.0, gap=8.0, We=200.0, 
         rho = p.rho_l + phi0 * (p.rho_h - p.rho_l)
         p0 = 3.0 * pres / rho
     return p, phi0, u0, p0
+
+
+def batched_sweep(count=512, seed=20240601, small=False):
+    """Seeded mix of static drops (cubes n^3) and capillary waves (nx x 2nx x 1).
+
+    Half the instances are cubes with n ~ U{24..96}, half quasi-2D waves with
+    nx ~ U{64..256}; M ~ U[0.005, 0.1], xi ~ U[3, 8], sigma ~ logU[1e-5, 1e-3],
+    rho ratio 1000, nu = 1/60.  Drops have R = n/4, waves a0 = 0.01 nx.
+    small=True shrinks the sizes (cubes 12..24, waves 32..64) for tests.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(count):
+        M = float(rng.uniform(0.005, 0.1))
+        xi = float(rng.uniform(3.0, 8.0))
+        sigma = float(10.0 ** rng.uniform(-5.0, -3.0))
+        if i % 2 == 0:
+            n = int(rng.integers(12, 25)) if small else int(rng.integers(24, 97))
+            p, phi0, u0, p0 = static_drop(n, n / 4.0, xi=xi, sigma=sigma, mobility=M)
+        else:
+            nx = int(rng.integers(32, 65)) if small else int(rng.integers(64, 257))
+            p, phi0, u0, p0 = capillary_wave(nx, ny=2 * nx, a0=0.01 * nx, xi=xi, M=M, sigma=sigma, nu=1.0 / 60.0)
+        out.append((p, phi0, u0, p0))
+    return out
