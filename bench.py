@@ -45,10 +45,10 @@ def step_kernel_bytes(prec, engine=0):
     """Algorithmic bytes per cell of one stream-collide launch: every h and g
     population read once and written once; the fused two-array step (engine 0)
     also writes phi, the in-place step (engine 1) reads phi for its stencil;
-    FP16S adds the shift arrays (phi and p* of the writers read, p* written)."""
+    FP16S adds the read of the h shifts (phi of the writing cells)."""
     b = 2 * (15 + 27) * PREC_BYTES[prec] + PHI_BYTES[prec]
     if prec == "fp16s":
-        b += PHI_BYTES[prec] + 4 + 4
+        b += PHI_BYTES[prec]
     return b
 
 
@@ -284,6 +284,108 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_leg(dev, barrier):
+    """Adjoint over forward on the 128 x 384 x 128 rising bubble (FP32, walls,
+    D 32, Eo 10, Mo 1e-3, xi 4, M 0.02): J = mean rise velocity over the last
+    quarter of n = 400 steps, gradient with respect to (M, xi, sigma), sqrt(n)
+    checkpoints.  The ratio counts everything the adjoint call adds to the
+    forward run it contains: (t_adjoint - t_forward) / t_forward."""
+    from paper_2206_11637_gb300 import objectives as O
+    from paper_2206_11637_gb300 import workloads as W
+    from paper_2206_11637_gb300.pflbm import Simulation
+    p, phi0, u0, p0 = W.rising_bubble()
+    n = 400
+    obs = O.rise_velocity_weights(p, phi0, 3 * n // 4, n)
+    fw = Simulation(p, phi0, u0, p0, precision="fp32", device=dev)
+    fw.step(10)
+    barrier()
+    t0 = time.perf_counter()
+    fw.step(n)
+    barrier()
+    t_fw = time.perf_counter() - t0
+    del fw
+    ad = Simulation(p, phi0, u0, p0, precision="fp32", device=dev)
+    ad.adjoint(20, [(20, obs[1][1])])         # warm-up (kernels, workspace)
+    ad = Simulation(p, phi0, u0, p0, precision="fp32", device=dev)
+    barrier()
+    t0 = time.perf_counter()
+    J, g = ad.adjoint(n, obs)
+    barrier()
+    t_ad = time.perf_counter() - t0
+    ws_gb = ad.lib.pfl_adjoint_workspace_bytes(ad.ctx, n) / 1e9
+    del ad
+    return {"workload": "rising_bubble 128x384x128", "precision": "fp32", "lattice_steps": n,
+            "objective": "mean rise velocity over steps %d..%d" % (3 * n // 4, n),
+            "forward_ms": t_fw * 1e3, "adjoint_ms_incl_forward_and_recompute": t_ad * 1e3,
+            "adjoint_over_forward": (t_ad - t_fw) / t_fw, "workspace_gb": ws_gb,
+            "J": J, "grad_M_xi_sigma": [float(v) for v in g]}
+
+
+# (workload, precision, lattice steps timed) of the per-config table
+CONFIG_LEGS = [("static_drop", "fp64", 1000),
+               ("capillary_wave", "fp64", 1000), ("capillary_wave", "fp32", 2000),
+               ("capillary_wave", "fp16s", 2000),
+               ("rising_bubble", "fp64", 20), ("rising_bubble", "fp32", 200), ("rising_bubble", "fp16s", 200),
+               ("drop_impact", "fp32", 40), ("drop_impact", "fp16s", 40)]
+
+
+def config_table(dev, barrier):
+    """MLUPS and fraction of the HBM peak of every single-lattice workload and
+    precision (CUDA events around S steps after three warm-up steps; the
+    fraction counts the fused step's algorithmic bytes per cell), plus the
+    batched sweep's aggregate."""
+    import torch
+    from paper_2206_11637_gb300.pflbm import Simulation
+    peak, _ = peaks()
+    rows = []
+    cache = {}
+    for name, prec, S in CONFIG_LEGS:
+        if name not in cache:
+            cache.clear()
+            cache[name] = workload(name)
+        wl = cache[name]
+        p = wl["p"]
+        sim = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision=prec, device=dev)
+        sim.step(3)
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sim.step(S)
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        _, nf = sim.diag(check=False)
+        del sim
+        r = mlups(p.cells, S, ms / 1e3)
+        bpc = step_kernel_bytes(prec, 0)
+        work = p.cells * (2 * 42 * PREC_BYTES[prec] + 2 * PHI_BYTES[prec])
+        rows.append({"workload": name, "cells": p.cells, "precision": prec, "lattice_steps": S, "mlups": r,
+                     "bytes_per_cell": bpc, "hbm_frac": r * 1e6 * bpc / 1e9 / peak,
+                     "l2_resident": work < L2_BYTES, "nonfinite_cells": nf})
+    cache.clear()
+    torch.cuda.empty_cache()
+    # batched sweep: 512 instances in one persistent launch per class, graph replay
+    from paper_2206_11637_gb300 import workloads as W
+    from paper_2206_11637_gb300.batch import Batch
+    inst = W.batched_sweep(512)
+    cells = sum(q.cells for q, _, _, _ in inst)
+    b = Batch(inst, precision="fp32", tune=True, device=dev)
+    b.step(16)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    b.step(96)
+    e1.record()
+    barrier()
+    r = mlups(cells, 96, e0.elapsed_time(e1) / 1e3)
+    bpc = 2 * 42 * 4 + 2 * 4     # in-place step + phi pass: populations, phi read and written
+    rows.append({"workload": "batched_sweep", "instances": len(inst), "cells": cells, "precision": "fp32",
+                 "lattice_steps": 96, "mlups": r, "bytes_per_cell": bpc, "hbm_frac": r * 1e6 * bpc / 1e9 / peak})
+    del b
+    torch.cuda.empty_cache()
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -435,34 +537,11 @@ def main():
                                     "u_max_over_umax": float(np.abs(ftst[3] - f64[3]).max() / umax)}
         del ref, tst
 
-    # adjoint / forward: one adjoint step (checkpoint recompute included) over
-    # one forward step, FP32 storage (the adjoint runs on FP64 or FP32)
     adj = None
+    configs = None
     if not args.no_compare and rank == 0:
-        from paper_2206_11637_gb300 import objectives as O
-        n_adj = min(S, 400)
-        obs = [(n_adj, O.wave_mode_weights(p, float(p.nx)) if args.workload == "capillary_wave"
-                else np.ones(N) / N)]
-        fw = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision="fp32", device=dev)
-        fw.step(10)
-        barrier()
-        t0 = time.perf_counter()
-        fw.step(n_adj)
-        barrier()
-        t_fw = time.perf_counter() - t0
-        del fw
-        ad = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision="fp32", device=dev)
-        ad.adjoint(n_adj, obs)          # warm-up (workspace, caches)
-        barrier()
-        t0 = time.perf_counter()
-        J_adj, g_adj = ad.adjoint(n_adj, obs)
-        barrier()
-        t_ad = time.perf_counter() - t0
-        del ad
-        adj = {"precision": "fp32", "lattice_steps": n_adj, "forward_ms": t_fw * 1e3,
-               "adjoint_ms_incl_forward_and_recompute": t_ad * 1e3,
-               "adjoint_over_forward": (t_ad - t_fw) / t_fw,
-               "grad_M_xi_sigma": [float(v) for v in g_adj]}
+        adj = adjoint_leg(dev, barrier)
+        configs = config_table(dev, barrier)
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -476,8 +555,9 @@ def main():
                 "config": {"workload": args.workload, "description": wl["desc"], "precision": prec,
                            "cells": N, "lattice_steps_per_step": S, "parallelism": "replicas" if ws > 1 else "1 GPU",
                            "l2": "flushed between timed steps" if flush else "working set larger than L2"},
-                "e2e": e2e, "gpu_launches": 2 * S * K, "clocks": clocks, "roofline": roofline,
-                "cpu_baseline": cpu, "nonfinite_cells": nf, "wall_s": wall, "adjoint": adj}
+                "e2e": e2e, "gpu_launches": (1 if args.engine == 0 else 2) * S * K, "clocks": clocks, "roofline": roofline,
+                "cpu_baseline": cpu, "nonfinite_cells": nf, "wall_s": wall, "adjoint": adj,
+                "configs": configs}
         line.update(compare)
         print(json.dumps(line), flush=True)
     if dist:

@@ -48,7 +48,6 @@ struct BInst {
   void* h;
   void* g;
   void* phi[2];
-  float* pst[2];
   int active;
   int frozen_cur, frozen_swapped;  // host bookkeeping: roles of the buffers when the instance stopped
 };
@@ -75,7 +74,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 2)
     const unsigned cell = tile.c0 + threadIdx.x;
     if (cell < I->geo.N)
       step_cell<PREC, ODD>(I->geo, I->ph, (S*)I->h, (S*)I->g, (const PhiT*)I->phi[cur], (const PhiT*)I->phi[1 - cur],
-                           I->pst[ODD], I->pst[1 - ODD], cell, *tstep * 0x9E3779B9u + (unsigned)tile.inst * 0x85EBCA6Bu);
+                           cell, *tstep * 0x9E3779B9u + (unsigned)tile.inst * 0x85EBCA6Bu);
   }
 }
 
@@ -156,7 +155,7 @@ struct BLayout {
 size_t inst_bytes(const pfl_params& p) {
   const size_t N = (size_t)p.nx * p.ny * p.nz;
   return align256(15 * N * pop_bytes(p.precision)) + align256(27 * N * pop_bytes(p.precision)) +
-         2 * align256(N * phi_bytes(p.precision)) + 2 * align256(N * sizeof(float));
+         2 * align256(N * phi_bytes(p.precision));
 }
 
 BLayout blayout(const pfl_params* p, int count) {
@@ -310,7 +309,6 @@ pfl_status initial_state(pfl_batch* b, const double* const* phi0, const double* 
       BTRY(cudaStreamSynchronize(b->stream));
     }
     BTRY(cudaMemsetAsync(b->inst[i].phi[1], 0, (size_t)N * phi_bytes(b->prec), b->stream));
-    BTRY(cudaMemsetAsync(b->inst[i].pst[0], 0, (size_t)N * sizeof(float), b->stream));
     switch (b->prec) {
       case PFL_FP64: launch_phi_one<0>(b, i); break;
       case PFL_FP32: launch_phi_one<1>(b, i); break;
@@ -508,8 +506,6 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
     I.g = base + align256(15 * (size_t)N * S);
     I.phi[0] = base + align256(15 * (size_t)N * S) + align256(27 * (size_t)N * S);
     I.phi[1] = (char*)I.phi[0] + align256((size_t)N * P);
-    I.pst[0] = (float*)((char*)I.phi[1] + align256((size_t)N * P));
-    I.pst[1] = (float*)((char*)I.pst[0] + align256((size_t)N * sizeof(float)));
     I.active = 1;
     I.frozen_cur = 0;
     I.frozen_swapped = 0;
@@ -585,11 +581,11 @@ pfl_status pfl_batch_fields(pfl_batch* b, int i, double* phi, double* rho, doubl
 #define BF(PREC)                                                                                                  \
   if (swapped)                                                                                                    \
     k_fields<PREC, 1><<<nb, 256, 0, b->stream>>>(geo, I.ph, (const Store<PREC>::S*)I.g,                           \
-                                                 (const Store<PREC>::PhiT*)I.phi[cur], I.pst[swapped], o[0], o[1], \
+                                                 (const Store<PREC>::PhiT*)I.phi[cur], o[0], o[1],                 \
                                                  o[2], o[3], o[4], o[5]);                                         \
   else                                                                                                            \
     k_fields<PREC, 0><<<nb, 256, 0, b->stream>>>(geo, I.ph, (const Store<PREC>::S*)I.g,                           \
-                                                 (const Store<PREC>::PhiT*)I.phi[cur], I.pst[swapped], o[0], o[1], \
+                                                 (const Store<PREC>::PhiT*)I.phi[cur], o[0], o[1],                 \
                                                  o[2], o[3], o[4], o[5]);
     switch (b->prec) {
       case PFL_FP64: BF(0) break;

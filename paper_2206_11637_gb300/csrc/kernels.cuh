@@ -159,8 +159,7 @@ __device__ __forceinline__ void stencil(const Geo& geo, const Nb& nb, long long 
 // by the BGK mode; dead code otherwise).
 template <int PREC, int READ_ODD>
 __device__ __forceinline__ void hydro_macro(const Geo& geo, const Phys& ph, const Nb& nb, long long cell,
-                                            const typename Store<PREC>::S* __restrict__ g,
-                                            const float* __restrict__ pshift, Macro<typename Store<PREC>::R>& m,
+                                            const typename Store<PREC>::S* __restrict__ g, Macro<typename Store<PREC>::R>& m,
                                             typename Store<PREC>::R gv[27]) {
   typedef typename Store<PREC>::R R;
   R pst = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
@@ -169,7 +168,7 @@ __device__ __forceinline__ void hydro_macro(const Geo& geo, const Phys& ph, cons
     const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
     long long from;
     const size_t idx = src_index<READ_ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz, from);
-    R v = ld_g<PREC>(g, idx, i, PREC == 2 ? (R)__ldg(pshift + from) : (R)0);
+    R v = ld_g<PREC>(g, idx, i);
     gv[i] = v;
     pst += v;
     if (cx) jx += cx > 0 ? v : -v;
@@ -241,8 +240,7 @@ template <int PREC, int ODD, int BGK>
 __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<PREC>::S* __restrict__ h,
                                               typename Store<PREC>::S* __restrict__ g,
                                               const typename Store<PREC>::PhiT* __restrict__ phi,
-                                              const typename Store<PREC>::PhiT* __restrict__ shift,
-                                              const float* __restrict__ pshift, float* __restrict__ pout) {
+                                              const typename Store<PREC>::PhiT* __restrict__ shift) {
   typedef typename Store<PREC>::R R;
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
@@ -253,8 +251,7 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
   Macro<R> m;
   stencil<PREC>(geo, nb, cell, phi, m);
   R gv[27];
-  hydro_macro<PREC, ODD>(geo, ph, nb, cell, g, pshift, m, gv);
-  if (PREC == 2) pout[cell] = (float)m.pst;
+  hydro_macro<PREC, ODD>(geo, ph, nb, cell, g, m, gv);
 
   // ---- g collision and streaming
   {
@@ -284,7 +281,7 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
                      (R)2 * ((R)(cx * cy) * dxy + (R)(cy * cz) * dyz + (R)(cx * cz) * dxz) - tr3;
         post = geq + w * (a2 * hd + cf);
       }
-      st_g<PREC>(g, dst_index<ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz), i, post, (R)m.pst);
+      st_g<PREC>(g, dst_index<ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz), i, post);
     }
   }
 
@@ -381,8 +378,7 @@ __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typenam
 #pragma unroll
   for (int i = 0; i < 27; ++i) {
     const R cu = (R)q27_cx(i) * ux + (R)q27_cy(i) * uy + (R)q27_cz(i) * uz;
-    st_g<PREC>(g, (size_t)i * geo.N + cell, i, (R)q27_w(i) * (ps + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu),
-               (R)0);
+    st_g<PREC>(g, (size_t)i * geo.N + cell, i, (R)q27_w(i) * (ps + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu));
   }
 #pragma unroll
   for (int k = 0; k < 15; ++k) {
@@ -394,8 +390,7 @@ __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typenam
 // Macroscopic output: any of phi, rho, p, ux, uy, uz (device FP64, may be NULL).
 template <int PREC, int READ_ODD>
 __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename Store<PREC>::S* __restrict__ g,
-                                                const typename Store<PREC>::PhiT* __restrict__ phi,
-                                                const float* __restrict__ pshift, double* o_phi, double* o_rho,
+                                                const typename Store<PREC>::PhiT* __restrict__ phi, double* o_phi, double* o_rho,
                                                 double* o_p, double* o_ux, double* o_uy, double* o_uz) {
   typedef typename Store<PREC>::R R;
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -407,7 +402,7 @@ __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename
   Macro<R> m;
   stencil<PREC>(geo, nb, cell, phi, m);
   R gv[27];
-  hydro_macro<PREC, READ_ODD>(geo, ph, nb, cell, g, pshift, m, gv);
+  hydro_macro<PREC, READ_ODD>(geo, ph, nb, cell, g, m, gv);
   if (o_phi) o_phi[cell] = (double)m.phi;
   if (o_rho) o_rho[cell] = (double)m.rho;
   if (o_p) o_p[cell] = (double)m.pst * (double)m.rho / 3.0;
@@ -420,7 +415,7 @@ __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename
 template <int PREC, int READ_ODD>
 __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
                          const typename Store<PREC>::PhiT* __restrict__ shift, int q, int i,
-                         double* __restrict__ out, const float* __restrict__ pshift) {
+                         double* __restrict__ out) {
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
   int x, y, z;
@@ -433,7 +428,7 @@ __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
       if (j == i) {
         long long from;
         const size_t idx = src_index<READ_ODD>(geo, nb, cell, j, q27_opp(j), q27_cx(j), q27_cy(j), q27_cz(j), from);
-        out[cell] = (double)ld_g<PREC>(f, idx, j, PREC == 2 ? pshift[from] : 0.0f);
+        out[cell] = (double)ld_g<PREC>(f, idx, j);
       }
   } else {
 #pragma unroll
@@ -442,7 +437,7 @@ __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
   }
 }
 
-// Population import (normal layout, zero shifts).
+// Population import (normal layout; h with zero shifts).
 template <int PREC>
 __global__ void k_import(Geo geo, typename Store<PREC>::S* __restrict__ f, int q, int i, const double* __restrict__ in) {
   typedef typename Store<PREC>::R R;
@@ -454,7 +449,7 @@ __global__ void k_import(Geo geo, typename Store<PREC>::S* __restrict__ f, int q
   } else if (q == 27) {
 #pragma unroll
     for (int j = 0; j < 27; ++j)
-      if (j == i) st_g<PREC>(f, idx, j, (R)in[cell], (R)0);
+      if (j == i) st_g<PREC>(f, idx, j, (R)in[cell]);
   } else {
 #pragma unroll
     for (int j = 0; j < 15; ++j)

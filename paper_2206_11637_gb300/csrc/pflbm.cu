@@ -51,7 +51,7 @@ pfl_status cuda_fail(cudaError_t e, const char* what) {
 
 
 struct Layout {
-  size_t h, g, h2, g2, phi[2], pst[2], stage, red, total;
+  size_t h, g, h2, g2, phi[2], stage, red, total;
 };
 
 Layout layout_of(const pfl_params* p) {
@@ -72,10 +72,6 @@ Layout layout_of(const pfl_params* p) {
   for (int b = 0; b < 2; ++b) {
     L.phi[b] = off;
     off = align256(off + N * phi_bytes(p->precision));
-  }
-  for (int b = 0; b < 2; ++b) {  // p* of the writing cells (shift of the FP16S g)
-    L.pst[b] = off;
-    off = align256(off + N * sizeof(float));
   }
   L.stage = off;
   off = align256(off + (N + 16) * sizeof(double));
@@ -101,7 +97,6 @@ struct pfl_ctx {
   cudaStream_t stream;
   int device;
   int cur;       // phi buffer holding phi^t; the other holds the shifts of the stored h
-  int pcur;      // p* buffer holding the shifts of the stored g (written by the last step)
   bool zm;       // fused two-array step (else in-place AA + phi pass)
   int ab;        // two-array step: 0 = first pair current, 1 = second
   bool stale;    // two-array step: phi of the current state not yet materialised
@@ -143,10 +138,8 @@ typename Store<PREC>::PhiT* phishift(pfl_ctx* c) {
 }
 double* stage(pfl_ctx* c) { return (double*)(c->ws + c->L.stage); }
 
-float* pshift(pfl_ctx* c) { return (float*)(c->ws + c->L.pst[c->pcur]); }
 // seed of the FP16 stochastic rounding of one step
 unsigned step_seed(const pfl_ctx* c) { return (unsigned)((unsigned long long)c->t * 0x9E3779B97F4A7C15ull >> 32); }
-float* pnext(pfl_ctx* c) { return (float*)(c->ws + c->L.pst[1 - c->pcur]); }
 
 // phi of the stored state into the spare buffer, then make it current.  The
 // stored h carry the shifts of buffer `cur` (after a step) -- the spare buffer
@@ -179,15 +172,14 @@ void step_only(pfl_ctx* c) {
     if (c->p.nz == 1)
       k_step_zm<PREC, 1><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), hnext<PREC>(c),
                                                          gnext<PREC>(c), phishift<PREC>(c), phicur<PREC>(c),
-                                                         pshift(c), pnext(c), c->zc, step_seed(c));
+                                                         c->zc, step_seed(c));
     else
       k_step_zm<PREC, 0><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), hnext<PREC>(c),
                                                          gnext<PREC>(c), phishift<PREC>(c), phicur<PREC>(c),
-                                                         pshift(c), pnext(c), c->zc, step_seed(c));
+                                                         c->zc, step_seed(c));
     // phicur now holds phi^t, the shift of the populations just written
     c->ab ^= 1;
     c->cur = 1 - c->cur;
-    c->pcur = 1 - c->pcur;
     c->stale = true;
     c->t += 1;
     return;
@@ -195,23 +187,20 @@ void step_only(pfl_ctx* c) {
   if (BGK || !c->idx32) {
     if (c->swapped)
       k_step<PREC, 1, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
-                                                       phishift<PREC>(c), pshift(c), pnext(c));
+                                                       phishift<PREC>(c));
     else
       k_step<PREC, 0, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
-                                                       phishift<PREC>(c), pshift(c), pnext(c));
+                                                       phishift<PREC>(c));
   } else {
     const unsigned nbm = blocks_for(c->geo.N, PFL_STEP_THREADS);
     if (c->swapped)
       k_step_mrt<PREC, 1><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),
-                                                                    phicur<PREC>(c), phishift<PREC>(c), pshift(c),
-                                                                    pnext(c), step_seed(c));
+                                                                    phicur<PREC>(c), phishift<PREC>(c), step_seed(c));
     else
       k_step_mrt<PREC, 0><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),
-                                                                    phicur<PREC>(c), phishift<PREC>(c), pshift(c),
-                                                                    pnext(c), step_seed(c));
+                                                                    phicur<PREC>(c), phishift<PREC>(c), step_seed(c));
   }
   c->swapped ^= 1;
-  c->pcur = 1 - c->pcur;
   c->t += 1;
 }
 
@@ -245,8 +234,6 @@ void launch_steps(pfl_ctx* c, int n) {
 template <int PREC>
 pfl_status fresh_phi(pfl_ctx* c) {
   c->stale = false;
-  c->pcur = 0;
-  CUDA_TRY(cudaMemsetAsync(pshift(c), 0, c->geo.N * sizeof(float), c->stream));
   c->cur = 1;
   CUDA_TRY(cudaMemsetAsync(phicur<PREC>(c), 0, c->geo.N * sizeof(typename Store<PREC>::PhiT), c->stream));
   c->swapped = 0;
@@ -259,10 +246,10 @@ template <int PREC>
 void launch_fields(pfl_ctx* c, double* o[6]) {
   const unsigned nb = blocks_for(c->geo.N, 256);
   if (c->swapped)
-    k_fields<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), pshift(c), o[0],
+    k_fields<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0],
                                                   o[1], o[2], o[3], o[4], o[5]);
   else
-    k_fields<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), pshift(c), o[0],
+    k_fields<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0],
                                                   o[1], o[2], o[3], o[4], o[5]);
 }
 
@@ -271,9 +258,9 @@ void launch_export(pfl_ctx* c, int q, int i, double* out) {
   const unsigned nb = blocks_for(c->geo.N, 256);
   const typename Store<PREC>::S* f = (q == 27) ? gbuf<PREC>(c) : hbuf<PREC>(c);
   if (c->swapped)
-    k_export<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), q, i, out, pshift(c));
+    k_export<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), q, i, out);
   else
-    k_export<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), q, i, out, pshift(c));
+    k_export<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), q, i, out);
 }
 
 template <int PREC>
@@ -350,7 +337,6 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
   c->t = 0;
   c->swapped = 0;
   c->cur = 0;
-  c->pcur = 0;
   c->zm = uses_two_arrays(p);
   c->ab = 0;
   c->stale = false;
@@ -635,7 +621,7 @@ AdjLayout adj_layout(const pfl_ctx* c, int n) {
   A.seg = off;
   off += (size_t)A.K * A.state;
   A.fin = off;
-  off += A.state;
+  if (!c->zm) off += A.state;  // the fused engine's reverse sweep leaves the live state alone
   A.lam0 = off;
   off = align256(off + 42 * N * R);
   A.lam1 = off;
@@ -716,6 +702,87 @@ __global__ void k_lam_init(unsigned N, R* __restrict__ lam, const double* __rest
   for (int i = 0; i < 27; ++i) lam[(unsigned)(15 + i) * N + x] = (R)0;
 }
 
+// slot layout: h, g, phi (each 256-byte aligned)
+template <int PREC>
+struct SlotPtr {
+  typename Store<PREC>::S* h;
+  typename Store<PREC>::S* g;
+  typename Store<PREC>::PhiT* phi;
+  SlotPtr(const pfl_ctx* c, char* slot) {
+    const size_t N = (size_t)c->geo.N, S = pop_bytes(c->p.precision);
+    h = (typename Store<PREC>::S*)slot;
+    g = (typename Store<PREC>::S*)(slot + align256(15 * N * S));
+    phi = (typename Store<PREC>::PhiT*)(slot + align256(15 * N * S) + align256(27 * N * S));
+  }
+};
+
+// One fused step from slot a into slot b; phi of a (the sum the kernel forms
+// in shared memory) goes to a's phi.  FP64 / FP32 only: no shifts.
+template <int PREC>
+void zm_step_slots(pfl_ctx* c, const SlotPtr<PREC>& a, const SlotPtr<PREC>& b) {
+  const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
+  const dim3 block(ZM_TX, ZM_TY);
+  if (c->p.nz == 1)
+    k_step_zm<PREC, 1><<<grid, block, 0, c->stream>>>(c->g32, c->ph, a.h, a.g, b.h, b.g, nullptr, a.phi, c->zc, 0u);
+  else
+    k_step_zm<PREC, 0><<<grid, block, 0, c->stream>>>(c->g32, c->ph, a.h, a.g, b.h, b.g, nullptr, a.phi, c->zc, 0u);
+}
+
+// Adjoint with the fused two-array engine.  Forward sweep: checkpoints every K
+// steps, phi formed only where a checkpoint or an observation needs it.
+// Reverse sweep, per segment: the checkpoint is copied into slot 0 and each
+// recomputed step writes the next slot directly, so the live state (t_end) is
+// never touched and no per-step copy is made.
+template <int PREC, class ObsAt>
+pfl_status run_adjoint_zm(pfl_ctx* c, int n, const ObsAt& obs_at, char* aws, const AdjLayout& A, double* J,
+                          double grad[3]) {
+  typedef typename Store<PREC>::R R;
+  double* res = (double*)(aws + A.res);
+  double* part = (double*)(aws + A.part);
+  double* dot_part = part + 3 * ((c->geo.N + ADJ_THREADS - 1) / ADJ_THREADS);
+  for (int k = 0; k < n; ++k) {
+    const double* W = obs_at(k);
+    if (k % A.K == 0 || W) ensure_phi<PREC>(c);
+    if (k % A.K == 0) {
+      pfl_status s = copy_state(c, aws + A.ck + (size_t)(k / A.K) * A.state, true);
+      if (s != PFL_OK) return s;
+    }
+    if (W) launch_dot<PREC>(c, W, dot_part, res);
+    step_only<PREC, 0>(c);
+  }
+  ensure_phi<PREC>(c);
+  if (const double* W = obs_at(n)) launch_dot<PREC>(c, W, dot_part, res);
+  CUDA_TRY(cudaGetLastError());
+
+  void* lam = aws + A.lam0;
+  void* lam2 = aws + A.lam1;
+  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, (R*)lam, obs_at(n));
+  for (int sgm = A.nck - 1; sgm >= 0; --sgm) {
+    const int k0 = sgm * A.K, k1 = (k0 + A.K < n) ? k0 + A.K : n;
+    char* seg = aws + A.seg;
+    CUDA_TRY(cudaMemcpyAsync(seg, aws + A.ck + (size_t)sgm * A.state, A.state, cudaMemcpyDeviceToDevice, c->stream));
+    for (int k = k0; k + 1 < k1; ++k)
+      zm_step_slots<PREC>(c, SlotPtr<PREC>(c, seg + (size_t)(k - k0) * A.state),
+                          SlotPtr<PREC>(c, seg + (size_t)(k + 1 - k0) * A.state));
+    if (k1 - 1 > k0) {  // phi of the last slot (the others were formed by the steps out of them)
+      const SlotPtr<PREC> last(c, seg + (size_t)(k1 - 1 - k0) * A.state);
+      k_phi32<PREC, 0><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(c->g32, last.h, nullptr, last.phi);
+    }
+    for (int k = k1 - 1; k >= k0; --k) {
+      launch_adj_step<PREC>(c, A, aws, seg + (size_t)(k - k0) * A.state, 0, lam, lam2, obs_at(k), res + 1);
+      std::swap(lam, lam2);
+    }
+    CUDA_TRY(cudaGetLastError());
+  }
+  double hres[4];
+  CUDA_TRY(cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (J) *J = hres[0];
+  if (grad)
+    for (int k = 0; k < 3; ++k) grad[k] = hres[1 + k];
+  return PFL_OK;
+}
+
 template <int PREC>
 pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const double* const* Wd, char* aws,
                        const AdjLayout& A, double* J, double grad[3]) {
@@ -728,6 +795,7 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
       if (obs_steps[o] == k) return Wd[o];
     return nullptr;
   };
+  if (c->zm) return run_adjoint_zm<PREC>(c, n, obs_at, aws, A, J, grad);
   // several weights at one step are summed into the first by the caller side; here one per step
   const long long t0 = c->t;
   std::vector<int> ck_swapped(A.nck, 0), seg_swapped(A.K, 0);

@@ -244,14 +244,14 @@ struct GlobalPhi {
 // written to (hout, gout) in the layout WRITE_ODD (the same arrays and parity
 // for the in-place AA step; a second array pair and push streaming for the
 // two-array step).  phi_at(c) returns phi^t at the stencil neighbour c.
-template <int PREC, int READ_ODD, int WRITE_ODD, class PhiAt>
+template <int PREC, int READ_ODD, int WRITE_ODD, class PhiAt, int HM = 0>
 __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, const CellOff& o,
                                              const typename Store<PREC>::S* hin,
                                              const typename Store<PREC>::S* gin, typename Store<PREC>::S* hout,
                                              typename Store<PREC>::S* gout, const PhiAt& phi_at,
                                              const typename Store<PREC>::PhiT* __restrict__ shift,
-                                             const float* __restrict__ pshift, float* __restrict__ pout,
-                                             unsigned cell, unsigned seed) {
+                                             unsigned cell, unsigned seed,
+                                             const typename Store<PREC>::R* hmom = nullptr, int hstride = 0) {
   typedef typename Store<PREC>::R R;
   constexpr bool F16 = PREC == 2;
   const unsigned N = geo.N;
@@ -277,12 +277,11 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
   gz *= (R)3;
   lap *= (R)6;
 
-  // ---- g moments
-  // shifted FP16: g_i = w_i (s / KG + p*_writer)
+  // ---- g moments (FP16: g_i = w_i s / KG)
   R pst, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
   {
     const R rest = raw<PREC>(gin[13u * N + cell]);
-    pst = F16 ? (rest * (R)(1.0 / KG16) + (R)__ldg(pshift + cell)) * (R)q27_w(13) : rest;
+    pst = F16 ? rest * (R)(q27_w(13) / KG16) : rest;
   }
 #pragma unroll
   for (int i = 0; i < 13; ++i) {
@@ -292,9 +291,8 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     load_pair<PREC, READ_ODD>(gin, N, cell, o, i, 26 - i, cx, cy, cz, a, b, fa, fb);
     R S = a + b, D = a - b;
     if (F16) {
-      const R qa = (R)__ldg(pshift + fa), qb = (R)__ldg(pshift + fb);
-      S = (R)q27_w(i) * (S * (R)(1.0 / KG16) + (qa + qb));
-      D = (R)q27_w(i) * (D * (R)(1.0 / KG16) + (qa - qb));
+      S *= (R)(q27_w(i) / KG16);
+      D *= (R)(q27_w(i) / KG16);
     }
     pst += S;
     if (cx) jx += cx > 0 ? D : -D;
@@ -338,9 +336,7 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     const R a2 = ((R)1 - omega) * (R)4.5;
     const R dxx = pxx - p3 - ux * ux, dyy = pyy - p3 - uy * uy, dzz = pzz - p3 - uz * uz;
     const R K = F16 ? (R)KG16 : (R)1;
-    // FP16S stores g+ / w - p* of this cell: the p* term leaves alpha
-    const R al = K * ((F16 ? (R)0 : pst) - (R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
-    if (F16) pout[cell] = (float)pst;
+    const R al = K * (pst - (R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
     const R fr = (R)1.5 / rho;
     const R bx = K * ((R)3 * ux + fr * Fx), by = K * ((R)3 * uy + fr * Fy), bz = K * ((R)3 * uz + fr * Fz);
     const R Gxx = K * ((R)4.5 * ux * ux + a2 * dxx), Gyy = K * ((R)4.5 * uy * uy + a2 * dyy),
@@ -372,14 +368,25 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     }
   }
 
-  // ---- h moments (shifted FP16: h = w (s / KH + phi_writer))
+  // ---- h moments (shifted FP16: h = w (s / KH + phi_writer)), or given by the caller
   R phl, hjx = 0, hjy = 0, hjz = 0, hxx = 0, hyy = 0, hzz = 0, hxy = 0, hyz = 0, hxz = 0;
-  {
+  if (HM) {
+    phl = hmom[0];
+    hjx = hmom[hstride];
+    hjy = hmom[2 * hstride];
+    hjz = hmom[3 * hstride];
+    hxx = hmom[4 * hstride];
+    hyy = hmom[5 * hstride];
+    hzz = hmom[6 * hstride];
+    hxy = hmom[7 * hstride];
+    hyz = hmom[8 * hstride];
+    hxz = hmom[9 * hstride];
+  } else {
     const R rest = raw<PREC>(hin[7u * N + cell]);
     phl = F16 ? (rest * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7) : rest;
   }
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
+  for (int k = 0; k < (HM ? 0 : 7); ++k) {
     const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
     R a, b;
     unsigned fa, fb;
@@ -453,24 +460,22 @@ template <int PREC, int ODD>
 __device__ __forceinline__ void step_cell(const Geo32& geo, const Phys& ph, typename Store<PREC>::S* __restrict__ h,
                                           typename Store<PREC>::S* __restrict__ g,
                                           const typename Store<PREC>::PhiT* __restrict__ phi,
-                                          const typename Store<PREC>::PhiT* __restrict__ shift,
-                                          const float* __restrict__ pshift, float* __restrict__ pout, unsigned cell,
+                                          const typename Store<PREC>::PhiT* __restrict__ shift, unsigned cell,
                                           unsigned seed) {
   CellOff o;
   cell_off(geo, cell, o);
   GlobalPhi<PREC> at{phi, &o, cell};
-  collide_cell<PREC, ODD, ODD>(geo, ph, o, h, g, h, g, at, shift, pshift, pout, cell, seed);
+  collide_cell<PREC, ODD, ODD>(geo, ph, o, h, g, h, g, at, shift, cell, seed);
 }
 
 template <int PREC, int ODD>
 __global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB)
     k_step_mrt(Geo32 geo, Phys ph, typename Store<PREC>::S* __restrict__ h, typename Store<PREC>::S* __restrict__ g,
                const typename Store<PREC>::PhiT* __restrict__ phi,
-               const typename Store<PREC>::PhiT* __restrict__ shift, const float* __restrict__ pshift,
-               float* __restrict__ pout, unsigned seed) {
+               const typename Store<PREC>::PhiT* __restrict__ shift, unsigned seed) {
   const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
-  step_cell<PREC, ODD>(geo, ph, h, g, phi, shift, pshift, pout, cell, seed);
+  step_cell<PREC, ODD>(geo, ph, h, g, phi, shift, cell, seed);
 }
 
 // phi of one cell from the stored h (READ_ODD after an even step).
@@ -544,7 +549,67 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, int wall) {
   return v < 0 ? v + n : (v >= n ? v - n : v);
 }
 
-// phi at cell (x, y, z) of the current pair (normal layout).
+// The 10 h moments (phi, sum c h, sum c c h) of cell (x, y, z) of the current
+// pair (normal layout), accumulated by pairs in the same order as the
+// collision does, so moms[0] equals its phi bitwise.
+template <int PREC>
+__device__ __forceinline__ void h_moments_xyz(const Geo32& geo, const typename Store<PREC>::S* __restrict__ h,
+                                              const typename Store<PREC>::PhiT* __restrict__ shift, unsigned x,
+                                              unsigned y, unsigned z, typename Store<PREC>::R m[10]) {
+  typedef typename Store<PREC>::R R;
+  constexpr bool F16 = PREC == 2;
+  CellOff o;
+  o.X = axis_off(x, geo.nx, 1, geo.wall[0]);
+  o.Y = axis_off(y, geo.ny, (int)geo.nx, geo.wall[1]);
+  o.Z = axis_off(z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
+  const unsigned cell = x + geo.nx * (y + geo.ny * z);
+  const unsigned N = geo.N;
+  R phl, hjx = 0, hjy = 0, hjz = 0, hxx = 0, hyy = 0, hzz = 0, hxy = 0, hyz = 0, hxz = 0;
+  {
+    const R rest = raw<PREC>(h[7u * N + cell]);
+    phl = F16 ? (rest * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7) : rest;
+  }
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+    R a, b;
+    unsigned fa, fb;
+    load_pair<PREC, 0>(h, N, cell, o, k, 14 - k, cx, cy, cz, a, b, fa, fb);
+    R S, D;
+    if (F16) {
+      const R sa = (R)__ldg(shift + fa), sb = (R)__ldg(shift + fb);
+      const R w = (R)q15_w(k);
+      S = w * ((a + b) * (R)(1.0 / KH16) + (sa + sb));
+      D = w * ((a - b) * (R)(1.0 / KH16) + (sa - sb));
+    } else {
+      S = a + b;
+      D = a - b;
+    }
+    phl += S;
+    if (cx) hjx += cx > 0 ? D : -D;
+    if (cy) hjy += cy > 0 ? D : -D;
+    if (cz) hjz += cz > 0 ? D : -D;
+    if (cx) hxx += S;
+    if (cy) hyy += S;
+    if (cz) hzz += S;
+    if (cx && cy) hxy += (cx * cy > 0) ? S : -S;
+    if (cy && cz) hyz += (cy * cz > 0) ? S : -S;
+    if (cx && cz) hxz += (cx * cz > 0) ? S : -S;
+  }
+  m[0] = phl;
+  m[1] = hjx;
+  m[2] = hjy;
+  m[3] = hjz;
+  m[4] = hxx;
+  m[5] = hyy;
+  m[6] = hzz;
+  m[7] = hxy;
+  m[8] = hyz;
+  m[9] = hxz;
+}
+
+// phi at cell (x, y, z) of the current pair (normal layout), same sum as the
+// phi pass.
 template <int PREC>
 __device__ __forceinline__ typename Store<PREC>::R phi_at_xyz(const Geo32& geo,
                                                               const typename Store<PREC>::S* __restrict__ h,
@@ -572,43 +637,71 @@ __device__ __forceinline__ typename Store<PREC>::R phi_at_xyz(const Geo32& geo,
   return s;
 }
 
+// position r in [0, 2 (W + H) - 4) of the frame of a W x H plane -> (i, j)
+__device__ __forceinline__ void frame_pos(int r, int W, int H, int& i, int& j) {
+  if (r < W) {
+    i = r;
+    j = 0;
+  } else if (r < 2 * W) {
+    i = r - W;
+    j = H - 1;
+  } else if (r < 2 * W + (H - 2)) {
+    i = 0;
+    j = 1 + (r - 2 * W);
+  } else {
+    i = W - 1;
+    j = 1 + (r - 2 * W - (H - 2));
+  }
+}
+
 // grid: (ceil(nx / ZM_TX), ceil(ny / ZM_TY), ceil(nz / zc)), block ZM_TX x ZM_TY.
 template <int PREC, int FLAT>
 __global__ void __launch_bounds__(ZM_TX * ZM_TY, 2)
     k_step_zm(Geo32 geo, Phys ph, const typename Store<PREC>::S* __restrict__ hA,
               const typename Store<PREC>::S* __restrict__ gA, typename Store<PREC>::S* __restrict__ hB,
               typename Store<PREC>::S* __restrict__ gB, const typename Store<PREC>::PhiT* __restrict__ phi_shift,
-              typename Store<PREC>::PhiT* __restrict__ phi_out, const float* __restrict__ pshift,
-              float* __restrict__ pout, int zc, unsigned seed) {
-  constexpr int PW = ZM_TX + 2, PH = ZM_TY + 2, PS = PW * PH;
+              typename Store<PREC>::PhiT* __restrict__ phi_out, int zc, unsigned seed) {
   typedef typename Store<PREC>::PhiT PhiT;
+  typedef typename Store<PREC>::R R;
+  constexpr int NT = ZM_TX * ZM_TY;
+  constexpr int PW = ZM_TX + 2, PH = ZM_TY + 2, PS = PW * PH;
+  constexpr int NRING = 2 * (PW + PH) - 4;
+  static_assert(NRING <= NT, "one thread per ring position");
   __shared__ PhiT ring[FLAT ? 1 : 3][PS];
+  __shared__ R hmom[FLAT ? 1 : 2][10 * NT];  // h moments of the tile's own cells
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZM_TX + tx;
   const int x0 = blockIdx.x * ZM_TX, y0 = blockIdx.y * ZM_TY;
   const int z0 = blockIdx.z * zc;
   const int z1 = min(z0 + zc, (int)geo.nz);
   const int x = x0 + tx, y = y0 + ty;
   const bool active = x < (int)geo.nx && y < (int)geo.ny;
+  const unsigned xq = (unsigned)wrap_or_clamp(x, (int)geo.nx, geo.wall[0]);
+  const unsigned yq = (unsigned)wrap_or_clamp(y, (int)geo.ny, geo.wall[1]);
+  int ri = 0, rj = 0;
+  if (tid < NRING) frame_pos(tid, PW, PH, ri, rj);
+  const unsigned rxq = (unsigned)wrap_or_clamp(x0 - 1 + ri, (int)geo.nx, geo.wall[0]);
+  const unsigned ryq = (unsigned)wrap_or_clamp(y0 - 1 + rj, (int)geo.ny, geo.wall[1]);
 
-  // phi of plane zp (wrapped / mirrored) over the tile and its ring into slot
-  auto fill = [&](int zp, int slot) {
+  // phi of plane zp over the tile (with the h moments of the own cells) and its ring
+  auto fill = [&](int zp, int slot, int mslot) {
     const unsigned zq = (unsigned)wrap_or_clamp(zp, (int)geo.nz, geo.wall[2]);
-    for (int p = tid; p < PS; p += ZM_TX * ZM_TY) {
-      const int i = p % PW, j = p / PW;
-      const unsigned xq = (unsigned)wrap_or_clamp(x0 - 1 + i, (int)geo.nx, geo.wall[0]);
-      const unsigned yq = (unsigned)wrap_or_clamp(y0 - 1 + j, (int)geo.ny, geo.wall[1]);
-      ring[slot][p] = (PhiT)phi_at_xyz<PREC>(geo, hA, phi_shift, xq, yq, zq);
-    }
+    R m[10];
+    h_moments_xyz<PREC>(geo, hA, phi_shift, xq, yq, zq, m);
+    ring[slot][(ty + 1) * PW + tx + 1] = (PhiT)m[0];
+#pragma unroll
+    for (int k = 0; k < 10; ++k) hmom[mslot][k * NT + tid] = m[k];
+    if (tid < NRING) ring[slot][rj * PW + ri] = (PhiT)phi_at_xyz<PREC>(geo, hA, phi_shift, rxq, ryq, zq);
   };
 
   if (FLAT) {
-    fill(0, 0);
+    fill(0, 0, 0);
   } else {
-    fill(z0 - 1, (z0 - 1 - (z0 - 1)) % 3);
-    fill(z0, 1);
+    fill(z0 - 1, 0, 1);  // moments of plane z0 - 1 are never used (written to the spare slot)
+    fill(z0, 1, 0);
   }
   for (int z = z0; z < z1; ++z) {
-    if (!FLAT) fill(z + 1, (z + 1 - (z0 - 1)) % 3);
+    const int b = z - (z0 - 1);
+    if (!FLAT) fill(z + 1, (b + 1) % 3, (z + 1 - z0) & 1);
     __syncthreads();
     if (active) {
       const unsigned cell = (unsigned)x + geo.nx * ((unsigned)y + geo.ny * (unsigned)z);
@@ -620,15 +713,15 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, 2)
       if (FLAT) {
         at.plane[0] = at.plane[1] = at.plane[2] = ring[0];
       } else {
-        const int b = z - (z0 - 1);
         at.plane[0] = ring[(b + 2) % 3];
         at.plane[1] = ring[b % 3];
         at.plane[2] = ring[(b + 1) % 3];
       }
       // with one z plane the z neighbours are the plane itself (periodic or mirrored)
       at.i0 = (ty + 1) * PW + (tx + 1);
-      phi_out[cell] = (typename Store<PREC>::PhiT)at(0, 0, 0);
-      collide_cell<PREC, 0, 1>(geo, ph, o, hA, gA, hB, gB, at, phi_shift, pshift, pout, cell, seed);
+      phi_out[cell] = (PhiT)at(0, 0, 0);
+      collide_cell<PREC, 0, 1, SmemPhi<PREC>, 1>(geo, ph, o, hA, gA, hB, gB, at, phi_shift, cell, seed,
+                                                 &hmom[FLAT ? 0 : ((z - z0) & 1)][tid], NT);
     }
     __syncthreads();
   }

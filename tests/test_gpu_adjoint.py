@@ -82,6 +82,18 @@ def test_adjoint_matches_finite_differences(case):
     assert np.all(rel < 1e-3), (g, gfd, rel)
 
 
+def test_adjoint_same_on_both_engines():
+    """The in-place engine's reverse sweep replays through the live arrays and
+    copies each state; the fused engine's steps from slot to slot."""
+    import dataclasses
+    p, phi0, u0, p0, n, obs = bubble_case()
+    J0, g0, s0 = adjoint(p, phi0, u0, p0, n, obs)
+    J1, g1, s1 = adjoint(dataclasses.replace(p, engine=1), phi0, u0, p0, n, obs)
+    assert abs(J0 - J1) <= 1e-13 * abs(J0)
+    assert np.all(np.abs(g0 - g1) <= 1e-12 * np.abs(g0)), (g0, g1)
+    assert np.array_equal(s0.phi(), s1.phi())
+
+
 def test_adjoint_leaves_forward_state():
     p, phi0, u0, p0, n, obs = bubble_case()
     _, _, s = adjoint(p, phi0, u0, p0, n, obs)
@@ -92,6 +104,9 @@ def test_adjoint_leaves_forward_state():
     h1, g1 = s.populations()
     h2, g2 = r.populations()
     assert np.abs(h1 - h2).max() < 1e-13 and np.abs(g1 - g2).max() < 1e-13
+    s.step(3)                        # the context steps on from where the forward run ended
+    r.step(3)
+    assert np.abs(s.phi() - r.phi()).max() < 1e-13
 
 
 def test_fp32_adjoint_close_to_fp64():
