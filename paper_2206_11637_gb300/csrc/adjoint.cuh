@@ -14,11 +14,14 @@
 // pre-collision populations through the moments, and per cell the adjoints of
 // the stencil outputs (grad phi, lap phi) and of phi(x) itself.  k_adj_phi then
 // gathers the stencil's transpose -- every (cell y, direction c) whose stencil
-// read phi at x, walls folded in -- and adds the resulting adjoint of phi(x) to
-// all 15 h adjoints of x (phi = sum h), together with W_o at observation steps.
+// read phi at x, walls folded in -- into the adjoint of phi(x), plus W_o at
+// observation steps.  Since phi = sum h, that value belongs to all 15 h
+// adjoints of x; it is kept once per cell (array `acc`) and added by the next
+// reverse step as it reads lambda, instead of being written into 15 arrays.
 //
 // Adjoint populations are kept in the canonical layout [i][cell] (h: 15 N,
-// then g: 27 N) in the arithmetic type.
+// then g: 27 N) in the arithmetic type; lambda^t = (local part) + acc^t on the
+// h entries.
 #pragma once
 #include "step.cuh"
 
@@ -33,7 +36,8 @@ struct AdjPar {
 
 template <typename R>
 __device__ __forceinline__ R block_sum3_to(R a, R b, R c, double* out3) {
-  // FP64 block reduction of three values; thread 0 writes out3[0..2].
+  // FP64 block reduction of three values, added to out3[0..2]: each block owns
+  // its three slots and accumulates over the reverse sweep's steps.
   __shared__ double sm[ADJ_THREADS / 32][3];
   double v[3] = {(double)a, (double)b, (double)c};
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -48,7 +52,7 @@ __device__ __forceinline__ R block_sum3_to(R a, R b, R c, double* out3) {
   if (threadIdx.x < 3) {
     double s = 0;
     for (int w = 0; w < ADJ_THREADS / 32; ++w) s += sm[w][threadIdx.x];
-    out3[threadIdx.x] = s;
+    out3[threadIdx.x] += s;
   }
   return a;
 }
@@ -59,6 +63,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
                                                            const typename Store<PREC>::S* __restrict__ g,
                                                            const typename Store<PREC>::PhiT* __restrict__ phi,
                                                            const typename Store<PREC>::R* __restrict__ lam_in,
+                                                           const typename Store<PREC>::R* __restrict__ acc_in,
                                                            typename Store<PREC>::R* __restrict__ lam_out,
                                                            typename Store<PREC>::R* __restrict__ aux,
                                                            double* __restrict__ part) {
@@ -196,16 +201,18 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
       if (cx && cz) b_Gxz += (cx * cz > 0) ? S : -S;
     }
     // h
-    R c_al = (R)q15_w(7) * lam_in[7u * N + cell], c_bx = 0, c_by = 0, c_bz = 0;
+    R c_al = (R)q15_w(7) * (lam_in[7u * N + cell] + acc_in[cell]), c_bx = 0, c_by = 0, c_bz = 0;
     R c_Gxx = 0, c_Gyy = 0, c_Gzz = 0, c_Gxy = 0, c_Gyz = 0, c_Gxz = 0;
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
       const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
       const int ok = 14 - k;
-      const R la = o.valid(cx, cy, cz) ? lam_in[(unsigned)k * N + cell + (unsigned)o.off(cx, cy, cz)]
-                                       : lam_in[(unsigned)ok * N + cell];
-      const R lb = o.valid(-cx, -cy, -cz) ? lam_in[(unsigned)ok * N + cell + (unsigned)o.off(-cx, -cy, -cz)]
-                                          : lam_in[(unsigned)k * N + cell];
+      // the slot read and the cell holding it (whose acc belongs to every h slot)
+      const bool va = o.valid(cx, cy, cz), vb = o.valid(-cx, -cy, -cz);
+      const unsigned ya = va ? cell + (unsigned)o.off(cx, cy, cz) : cell;
+      const unsigned yb = vb ? cell + (unsigned)o.off(-cx, -cy, -cz) : cell;
+      const R la = lam_in[(va ? (unsigned)k : (unsigned)ok) * N + ya] + acc_in[ya];
+      const R lb = lam_in[(vb ? (unsigned)ok : (unsigned)k) * N + yb] + acc_in[yb];
       const R w = (R)q15_w(k);
       const R S = w * (la + lb), D = w * (la - lb);
       c_al += S;
@@ -441,55 +448,101 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
   block_sum3_to<R>(bM, bXi, bSig, part + 3u * blockIdx.x);
 }
 
-// Transpose of the phi stencil plus phi = sum h: adds the adjoint of phi(x)
-// to the 15 h adjoints of x, and the objective weight W(x) when this time is
-// an observation.
+// Transpose of the phi stencil: acc(x) = adjoint of phi(x) = aux_pc(x) -
+// 6 (1 - w_0) aux_lap(x) + sum over (y, c) whose stencil read x of
+// w_c (6 aux_lap(y) + 3 c . aux_grad(y)), plus W(x) at an observation step.
+//
+// On a periodic lattice the reader of x in direction c is y = x - c.  The
+// forward stencil mirrors across a no-slip face (a read beyond the face cell
+// returns the face cell itself), so a face cell x also receives, for each
+// direction c that leaves through the face, the term of its own reading
+// cell y = x - c with the normal component of c reversed.  Both cases become
+// one plain gather over a halo one cell wide whose ghost beyond a face holds
+// the face cell's values with the normal gradient component negated (an even
+// reflection of aux_lap and of the tangential components, an odd one of the
+// normal component, about the face cell): the ghost's term for c then equals
+// the mirrored term for c with its normal component reversed, the weights
+// being equal.
+//
+// Blocks of ZM_TX x ZM_TY threads march zc planes along z and keep three
+// planes of the four gathered aux fields (tile plus halo) in shared memory.
 template <typename R>
-__global__ void __launch_bounds__(256) k_adj_phi(Geo32 geo, const R* __restrict__ aux, R* __restrict__ lam,
-                                                 const double* __restrict__ W) {
-  const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= geo.N) return;
+__global__ void __launch_bounds__(ZM_TX * ZM_TY) k_adj_phi(Geo32 geo, const R* __restrict__ aux,
+                                                           R* __restrict__ acc_out, const double* __restrict__ W,
+                                                           int zc) {
+  constexpr int NT = ZM_TX * ZM_TY;
+  constexpr int PW = ZM_TX + 2, PH = ZM_TY + 2, PS = PW * PH;
+  __shared__ R ring[3][4][PS];
   const unsigned N = geo.N;
-  const unsigned yz = fdiv(x, geo.dx);
-  const int cxo = (int)(x - yz * geo.nx);
-  const unsigned zq = fdiv(yz, geo.dy);
-  const int cyo = (int)(yz - zq * geo.ny);
-  const int czo = (int)zq;
-  const int n[3] = {(int)geo.nx, (int)geo.ny, (int)geo.nz};
-  const int xc[3] = {cxo, cyo, czo};
-  R acc = aux[4u * N + x] - (R)(6.0 * 19.0 / 27.0) * aux[3u * N + x];
-#pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    if (i == 13) continue;
-    const int c[3] = {q27_cx(i), q27_cy(i), q27_cz(i)};
-    const R w = (R)q27_w(i);
-    // per axis: the coordinates y_a whose stencil read, in direction c_a, lands on x_a
-    int cand[3][2], nc[3];
-    for (int a = 0; a < 3; ++a) {
-      nc[a] = 0;
-      int y = xc[a] - c[a];
-      if (geo.wall[a]) {
-        if (y >= 0 && y < n[a]) cand[a][nc[a]++] = y;
-        if ((c[a] == -1 && xc[a] == 0) || (c[a] == 1 && xc[a] == n[a] - 1)) cand[a][nc[a]++] = xc[a];
-      } else {
-        y = y < 0 ? y + n[a] : (y >= n[a] ? y - n[a] : y);
-        cand[a][nc[a]++] = y;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZM_TX + tx;
+  const int x0 = blockIdx.x * ZM_TX, y0 = blockIdx.y * ZM_TY;
+  const int z0 = blockIdx.z * zc;
+  const int z1 = min(z0 + zc, (int)geo.nz);
+  const int x = x0 + tx, y = y0 + ty;
+  const bool active = x < (int)geo.nx && y < (int)geo.ny;
+
+  // source coordinate of a (possibly ghost) position along one axis, and
+  // whether the normal component flips (ghost beyond a no-slip face)
+  auto src = [](int p, int n, int wall, bool& flip) -> unsigned {
+    flip = false;
+    if (wall) {
+      if (p < 0) {
+        flip = true;
+        return 0u;
       }
+      if (p >= n) {
+        flip = p == n;
+        return (unsigned)(n - 1);
+      }
+      return (unsigned)p;
     }
-    for (int ia = 0; ia < nc[0]; ++ia)
-      for (int ib = 0; ib < nc[1]; ++ib)
-        for (int ic = 0; ic < nc[2]; ++ic) {
-          const unsigned y = (unsigned)cand[0][ia] + geo.nx * ((unsigned)cand[1][ib] + geo.ny * (unsigned)cand[2][ic]);
-          R v = (R)6 * aux[3u * N + y];
-          if (c[0]) v += (R)(3 * c[0]) * aux[0u * N + y];
-          if (c[1]) v += (R)(3 * c[1]) * aux[1u * N + y];
-          if (c[2]) v += (R)(3 * c[2]) * aux[2u * N + y];
-          acc += w * v;
-        }
-  }
-  if (W) acc += (R)W[x];
+    return (unsigned)(((p % n) + n) % n);
+  };
+
+  auto fill = [&](int zp, int slot) {
+    bool fz;
+    const unsigned sz = src(zp, (int)geo.nz, geo.wall[2], fz);
+    for (int r = tid; r < PS; r += NT) {
+      const int i = r % PW, j = r / PW;
+      bool fx, fy;
+      const unsigned sx = src(x0 - 1 + i, (int)geo.nx, geo.wall[0], fx);
+      const unsigned sy = src(y0 - 1 + j, (int)geo.ny, geo.wall[1], fy);
+      const unsigned c = sx + geo.nx * (sy + geo.ny * sz);
+      const R a0 = aux[c], a1 = aux[N + c], a2 = aux[2u * N + c];
+      ring[slot][0][r] = fx ? -a0 : a0;
+      ring[slot][1][r] = fy ? -a1 : a1;
+      ring[slot][2][r] = fz ? -a2 : a2;
+      ring[slot][3][r] = aux[3u * N + c];
+    }
+  };
+
+  fill(z0 - 1, 0);
+  fill(z0, 1);
+  for (int z = z0; z < z1; ++z) {
+    const int b = z - (z0 - 1);
+    fill(z + 1, (b + 1) % 3);
+    __syncthreads();
+    if (active) {
+      const unsigned cell = (unsigned)x + geo.nx * ((unsigned)y + geo.ny * (unsigned)z);
+      const int i0 = (ty + 1) * PW + (tx + 1);
+      const int sl[3] = {(b + 2) % 3, b % 3, (b + 1) % 3};  // planes z - 1, z, z + 1
+      R acc = aux[4u * N + cell] - (R)(6.0 * 19.0 / 27.0) * ring[sl[1]][3][i0];
 #pragma unroll
-  for (int k = 0; k < 15; ++k) lam[(unsigned)k * N + x] += acc;
+      for (int q = 0; q < 27; ++q) {
+        if (q == 13) continue;
+        const int cx = q27_cx(q), cy = q27_cy(q), cz = q27_cz(q);
+        const int s = sl[1 - cz], r = i0 - cx - cy * PW;   // reader y = x - c
+        R v = (R)6 * ring[s][3][r];
+        if (cx) v += (R)(3 * cx) * ring[s][0][r];
+        if (cy) v += (R)(3 * cy) * ring[s][1][r];
+        if (cz) v += (R)(3 * cz) * ring[s][2][r];
+        acc += (R)q27_w(q) * v;
+      }
+      if (W) acc += (R)W[cell];
+      acc_out[cell] = acc;
+    }
+    __syncthreads();
+  }
 }
 
 // dot = sum_x W(x) phi(x) in FP64 (per-block partials, fixed order).

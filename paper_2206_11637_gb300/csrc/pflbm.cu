@@ -341,14 +341,33 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
   c->ab = 0;
   c->stale = false;
   {
-    // z planes per block: about four waves of two blocks per SM, at least 4 planes
-    int sms = 152;
+    // z planes per block.  Every block marches zc planes and fills two more
+    // (the planes below and above its first) before it starts, about half a
+    // plane's work; blocks run in waves of `slots` resident blocks.  Take the
+    // zc with the least modelled time: waves x (zc + 0.5).
+    int sms = 152, per_sm = 2;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    const dim3 blk(ZM_TX, ZM_TY);
+    if (p->precision == PFL_FP64)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_zm<0, 0>, (int)(blk.x * blk.y), 0);
+    else if (p->precision == PFL_FP32)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_zm<1, 0>, (int)(blk.x * blk.y), 0);
+    else
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_zm<2, 0>, (int)(blk.x * blk.y), 0);
+    if (per_sm < 1) per_sm = 1;
+    const long long slots = (long long)sms * per_sm;
     const long long bxy = (long long)((p->nx + ZM_TX - 1) / ZM_TX) * ((p->ny + ZM_TY - 1) / ZM_TY);
-    long long zc = (bxy * p->nz + 8LL * sms - 1) / (8LL * sms);
-    if (zc < 4) zc = 4;
-    if (zc > p->nz) zc = p->nz;
-    c->zc = (int)zc;
+    int best = p->nz;
+    double best_cost = 1e300;
+    for (int zc = p->nz; zc >= 1; --zc) {
+      const long long blocks = bxy * ((p->nz + zc - 1) / zc);
+      const double cost = (double)((blocks + slots - 1) / slots) * (zc + 0.5);
+      if (cost < best_cost * (1 - 1e-9)) {
+        best_cost = cost;
+        best = zc;
+      }
+    }
+    c->zc = best;
   }
   c->geo.nx = p->nx;
   c->geo.ny = p->ny;
@@ -601,7 +620,7 @@ constexpr int DOT_BLOCKS = 1024;
 struct AdjLayout {
   size_t state;      // bytes of one saved state (h, g, phi)
   int K, nck;        // checkpoint interval, number of checkpoints
-  size_t ck, seg, fin, lam0, lam1, aux, W, part, res, total;
+  size_t ck, seg, fin, lam0, lam1, aux, acc, W, part, res, total;
 };
 
 size_t rbytes(int prec) { return prec == PFL_FP64 ? 8 : 4; }
@@ -628,6 +647,8 @@ AdjLayout adj_layout(const pfl_ctx* c, int n) {
   off = align256(off + 42 * N * R);
   A.aux = off;
   off = align256(off + 5 * N * R);
+  A.acc = off;
+  off = align256(off + N * R);
   A.W = off;
   off = align256(off + (size_t)ADJ_MAX_OBS * N * sizeof(double));
   A.part = off;
@@ -668,7 +689,7 @@ void launch_dot(pfl_ctx* c, const double* W, double* part, double* out) {
 
 template <int PREC>
 void launch_adj_step(pfl_ctx* c, const AdjLayout& A, char* aws, char* slot, int swapped, const void* lam_in,
-                     void* lam_out, const double* W, double* gradacc) {
+                     void* lam_out, const double* W) {
   typedef typename Store<PREC>::R R;
   const size_t N = (size_t)c->geo.N;
   const size_t S = pop_bytes(c->p.precision);
@@ -679,27 +700,27 @@ void launch_adj_step(pfl_ctx* c, const AdjLayout& A, char* aws, char* slot, int 
   AdjPar ap{c->p.mobility, c->p.xi, c->p.sigma};
   double* part = (double*)(aws + A.part);
   R* aux = (R*)(aws + A.aux);
+  R* acc = (R*)(aws + A.acc);
   const unsigned nb = blocks_for(c->geo.N, ADJ_THREADS);
   if (swapped)
     k_adj_local<PREC, 1><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
-                                                             (R*)lam_out, aux, part);
+                                                             acc, (R*)lam_out, aux, part);
   else
     k_adj_local<PREC, 0><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
-                                                             (R*)lam_out, aux, part);
-  k_sum_parts<<<3, 32, 0, c->stream>>>(part, (int)nb, 3, gradacc);
-  k_adj_phi<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(c->g32, aux, (R*)lam_out, W);
+                                                             acc, (R*)lam_out, aux, part);
+  const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
+  k_adj_phi<R><<<grid, dim3(ZM_TX, ZM_TY), 0, c->stream>>>(c->g32, aux, acc, W, c->zc);
 }
 
-// lambda = 0, then the h part of lambda += W (objective at the final time)
+// lambda at the final time: local part 0, acc = W (the objective's weight on
+// phi, which the h entries share)
 template <typename R>
-__global__ void k_lam_init(unsigned N, R* __restrict__ lam, const double* __restrict__ W) {
+__global__ void k_lam_init(unsigned N, R* __restrict__ lam, R* __restrict__ acc, const double* __restrict__ W) {
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= N) return;
-  const R w = W ? (R)W[x] : (R)0;
 #pragma unroll
-  for (int k = 0; k < 15; ++k) lam[(unsigned)k * N + x] = w;
-#pragma unroll
-  for (int i = 0; i < 27; ++i) lam[(unsigned)(15 + i) * N + x] = (R)0;
+  for (int i = 0; i < 42; ++i) lam[(unsigned)i * N + x] = (R)0;
+  acc[x] = W ? (R)W[x] : (R)0;
 }
 
 // slot layout: h, g, phi (each 256-byte aligned)
@@ -756,7 +777,10 @@ pfl_status run_adjoint_zm(pfl_ctx* c, int n, const ObsAt& obs_at, char* aws, con
 
   void* lam = aws + A.lam0;
   void* lam2 = aws + A.lam1;
-  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, (R*)lam, obs_at(n));
+  const unsigned nbl = blocks_for(c->geo.N, ADJ_THREADS);  // per-block gradient partials, summed at the end
+  CUDA_TRY(cudaMemsetAsync(part, 0, 3 * (size_t)nbl * sizeof(double), c->stream));
+  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, (R*)lam,
+                                                                   (R*)(aws + A.acc), obs_at(n));
   for (int sgm = A.nck - 1; sgm >= 0; --sgm) {
     const int k0 = sgm * A.K, k1 = (k0 + A.K < n) ? k0 + A.K : n;
     char* seg = aws + A.seg;
@@ -769,11 +793,12 @@ pfl_status run_adjoint_zm(pfl_ctx* c, int n, const ObsAt& obs_at, char* aws, con
       k_phi32<PREC, 0><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(c->g32, last.h, nullptr, last.phi);
     }
     for (int k = k1 - 1; k >= k0; --k) {
-      launch_adj_step<PREC>(c, A, aws, seg + (size_t)(k - k0) * A.state, 0, lam, lam2, obs_at(k), res + 1);
+      launch_adj_step<PREC>(c, A, aws, seg + (size_t)(k - k0) * A.state, 0, lam, lam2, obs_at(k));
       std::swap(lam, lam2);
     }
     CUDA_TRY(cudaGetLastError());
   }
+  k_sum_parts<<<3, 32, 0, c->stream>>>(part, (int)nbl, 3, res + 1);
   double hres[4];
   CUDA_TRY(cudaMemcpyAsync(hres, res, sizeof(hres), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -824,7 +849,10 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
   // reverse sweep, one checkpoint segment at a time
   void* lam = aws + A.lam0;
   void* lam2 = aws + A.lam1;
-  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, (R*)lam, obs_at(n));
+  const unsigned nbl = blocks_for(c->geo.N, ADJ_THREADS);  // per-block gradient partials, summed at the end
+  CUDA_TRY(cudaMemsetAsync(part, 0, 3 * (size_t)nbl * sizeof(double), c->stream));
+  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, (R*)lam,
+                                                                   (R*)(aws + A.acc), obs_at(n));
   for (int sgm = A.nck - 1; sgm >= 0; --sgm) {
     const int k0 = sgm * A.K, k1 = (k0 + A.K < n) ? k0 + A.K : n;
     st = copy_state(c, aws + A.ck + (size_t)sgm * A.state, false);
@@ -842,11 +870,12 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
     }
     for (int k = k1 - 1; k >= k0; --k) {
       launch_adj_step<PREC>(c, A, aws, aws + A.seg + (size_t)(k - k0) * A.state, seg_swapped[k - k0], lam, lam2,
-                            obs_at(k), res + 1);
+                            obs_at(k));
       std::swap(lam, lam2);
     }
     CUDA_TRY(cudaGetLastError());
   }
+  k_sum_parts<<<3, 32, 0, c->stream>>>(part, (int)nbl, 3, res + 1);
   // back to the end of the forward run
   st = copy_state(c, aws + A.fin, false);
   if (st != PFL_OK) return st;

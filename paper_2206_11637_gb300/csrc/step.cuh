@@ -217,13 +217,15 @@ template <int PREC, int ODD>
 __device__ __forceinline__ void store_pair(typename Store<PREC>::S* __restrict__ f, unsigned N, unsigned cell,
                                            const CellOff& o, int i, int oi, int cx, int cy, int cz,
                                            typename Store<PREC>::R A, typename Store<PREC>::R B, Dither& d) {
+  const typename Store<PREC>::S a = pack_sr<PREC>(A, d);
+  const typename Store<PREC>::S b = pack_sr<PREC>(B, d);
   if (!ODD) {
-    f[(unsigned)oi * N + cell] = pack_sr<PREC>(A, d);
-    f[(unsigned)i * N + cell] = pack_sr<PREC>(B, d);
+    f[(unsigned)oi * N + cell] = a;
+    f[(unsigned)i * N + cell] = b;
   } else {
     const bool vc = o.valid(cx, cy, cz), vmc = o.valid(-cx, -cy, -cz);
-    f[vc ? (unsigned)i * N + cell + (unsigned)o.off(cx, cy, cz) : (unsigned)oi * N + cell] = pack_sr<PREC>(A, d);
-    f[vmc ? (unsigned)oi * N + cell + (unsigned)o.off(-cx, -cy, -cz) : (unsigned)i * N + cell] = pack_sr<PREC>(B, d);
+    f[vc ? (unsigned)i * N + cell + (unsigned)o.off(cx, cy, cz) : (unsigned)oi * N + cell] = a;
+    f[vmc ? (unsigned)oi * N + cell + (unsigned)o.off(-cx, -cy, -cz) : (unsigned)i * N + cell] = b;
   }
 }
 
@@ -667,7 +669,13 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, 2)
   constexpr int PW = ZM_TX + 2, PH = ZM_TY + 2, PS = PW * PH;
   constexpr int NRING = 2 * (PW + PH) - 4;
   static_assert(NRING <= NT, "one thread per ring position");
-  __shared__ PhiT ring[FLAT ? 1 : 3][PS];
+  // phi planes z - 1, z, z + 1 and the one being filled: with four slots the
+  // fill of plane z + 1 overwrites plane z - 3, which every thread finished
+  // reading before the barrier of the previous plane, so one barrier per plane
+  // suffices.  The h moments are per thread and need none.  FP64 keeps three
+  // slots (static shared memory stays under 48 KB) and a second barrier.
+  constexpr int NS = FLAT ? 1 : (sizeof(R) == 8 ? 3 : 4);
+  __shared__ PhiT ring[NS][PS];
   __shared__ R hmom[FLAT ? 1 : 2][10 * NT];  // h moments of the tile's own cells
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZM_TX + tx;
   const int x0 = blockIdx.x * ZM_TX, y0 = blockIdx.y * ZM_TY;
@@ -701,7 +709,7 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, 2)
   }
   for (int z = z0; z < z1; ++z) {
     const int b = z - (z0 - 1);
-    if (!FLAT) fill(z + 1, (b + 1) % 3, (z + 1 - z0) & 1);
+    if (!FLAT) fill(z + 1, (b + 1) % NS, (z + 1 - z0) & 1);
     __syncthreads();
     if (active) {
       const unsigned cell = (unsigned)x + geo.nx * ((unsigned)y + geo.ny * (unsigned)z);
@@ -713,9 +721,9 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, 2)
       if (FLAT) {
         at.plane[0] = at.plane[1] = at.plane[2] = ring[0];
       } else {
-        at.plane[0] = ring[(b + 2) % 3];
-        at.plane[1] = ring[b % 3];
-        at.plane[2] = ring[(b + 1) % 3];
+        at.plane[0] = ring[(b - 1) % NS];
+        at.plane[1] = ring[b % NS];
+        at.plane[2] = ring[(b + 1) % NS];
       }
       // with one z plane the z neighbours are the plane itself (periodic or mirrored)
       at.i0 = (ty + 1) * PW + (tx + 1);
@@ -723,7 +731,7 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, 2)
       collide_cell<PREC, 0, 1, SmemPhi<PREC>, 1>(geo, ph, o, hA, gA, hB, gB, at, phi_shift, cell, seed,
                                                  &hmom[FLAT ? 0 : ((z - z0) & 1)][tid], NT);
     }
-    __syncthreads();
+    if (NS == 3) __syncthreads();
   }
 }
 
