@@ -44,6 +44,8 @@ def _load():
         lib.ora_tables.restype = ctypes.c_int
         lib.ora_tables.argtypes = [ctypes.c_int, P, P, P, P, P, P]
         lib.ora_mrt_collide.argtypes = [ctypes.c_int, P, P, P, P, P]
+        lib.ora_tangent.argtypes = [P, P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int,
+                                    P, P]
         _lib = lib
     return _lib
 
@@ -142,3 +144,27 @@ def from_params(p, phi0, u0=None, p0=None):
     """Oracle built from a ``workloads.Params``-like object (duck-typed)."""
     return Oracle(p.nx, p.ny, p.nz, p.bc, p.rho_h, p.rho_l, p.nu_h, p.nu_l, p.sigma, p.mobility, p.xi,
                   p.gravity, phi0, u0, p0, collision=p.collision)
+
+
+PARAM_INDEX = {"mobility": 0, "xi": 1, "sigma": 2}
+
+
+def tangent(p, phi0, u0, p0, n, obs, param, threads=0):
+    """Exact dJ/d(param) by forward-mode (dual-number) differentiation of the
+    oracle, J = sum over (step, W) in obs of W . phi(step) after n steps;
+    param is "mobility", "xi" or "sigma".  Returns (J, dJ)."""
+    lib = _load()
+    N = p.nx * p.ny * p.nz
+    ip = np.array([p.nx, p.ny, p.nz] + list(p.bc) + [p.collision], dtype=np.int32)
+    dp = np.array([p.rho_h, p.rho_l, p.nu_h, p.nu_l, p.sigma, p.mobility, p.xi] + list(p.gravity),
+                  dtype=np.float64)
+    steps = np.array([int(t) for t, _ in obs], dtype=np.int32)
+    if np.any(steps < 0) or np.any(steps > n):
+        raise ValueError("observation step outside [0, n]")
+    W = np.ascontiguousarray(np.stack([_f64(w, N) for _, w in obs]))
+    phi0, u0, p0 = _f64(phi0, N), _f64(u0, 3 * N), _f64(p0, N)
+    J = ctypes.c_double(0.0)
+    dJ = ctypes.c_double(0.0)
+    lib.ora_tangent(_ptr(ip), _ptr(dp), _ptr(phi0), _ptr(u0), _ptr(p0), PARAM_INDEX[param], int(n), len(obs),
+                    _ptr(steps), _ptr(W), int(threads), ctypes.byref(J), ctypes.byref(dJ))
+    return J.value, dJ.value

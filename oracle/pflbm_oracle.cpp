@@ -53,6 +53,35 @@ namespace {
 
 const double CS2 = 1.0 / 3.0;
 
+// ------------------------------------------------------------ dual numbers --
+// Forward-mode differentiation (dual numbers, Wengert 1964): a value and its
+// derivative with respect to one chosen parameter, carried through every
+// operation by the chain rule.  The simulation below is written once for a
+// scalar type T; T = double is the oracle, T = Dual gives the exact
+// derivative of any result with respect to M, xi or sigma (the tangent of the
+// same arithmetic, no finite-difference truncation).
+struct Dual {
+  double v, d;
+  Dual(double a = 0.0, double b = 0.0) : v(a), d(b) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v * b.d) / (b.v * b.v)); }
+inline Dual& operator+=(Dual& a, Dual b) { return a = a + b; }
+inline Dual& operator-=(Dual& a, Dual b) { return a = a - b; }
+inline Dual& operator*=(Dual& a, Dual b) { return a = a * b; }
+inline Dual& operator/=(Dual& a, Dual b) { return a = a / b; }
+inline Dual sqrt(Dual a) {
+  const double r = std::sqrt(a.v);
+  return Dual(r, a.v > 0 ? a.d / (2.0 * r) : 0.0);
+}
+inline double value(double a) { return a; }
+inline double value(Dual a) { return a.v; }
+inline double deriv(double) { return 0.0; }
+inline double deriv(Dual a) { return a.d; }
+
 // ---------------------------------------------------------------- lattices --
 struct Lattice {
   int q = 0;
@@ -178,10 +207,12 @@ struct Params {
   double rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, g[3];
 };
 
+template <typename T>
 struct Sim {
   Params P;
+  T sigma, mobility, xi;  // P's values, as T (seeded for a derivative)
   long N;
-  std::vector<double> h, g, hn, gn, phi;  // populations SoA [i][cell]
+  std::vector<T> h, g, hn, gn, phi;  // populations SoA [i][cell]
   long step = 0;
 };
 
@@ -211,21 +242,24 @@ inline int stencil_coord(int x, int d, int n, int bc_lo, int bc_hi) {
   return t;
 }
 
+template <typename T>
 struct CellState {
-  double phi, gradphi[3], lapphi, rho, tau, omega, nu, mu, pstar, j[3], F[3], u[3];
-  double Fs[3], Fb[3], Fp[3], Fmu[3];
+  T phi, gradphi[3], lapphi, rho, tau, omega, nu, mu, pstar, j[3], F[3], u[3];
+  T Fs[3], Fb[3], Fp[3], Fmu[3];
 };
 
-void geq_of(double pstar, const double u[3], double* out) {
+template <typename T>
+void geq_of(T pstar, const T u[3], T* out) {
   const Lattice& L = Q27();
-  double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   for (int i = 0; i < L.q; ++i) {
-    double cu = L.c[3 * i] * u[0] + L.c[3 * i + 1] * u[1] + L.c[3 * i + 2] * u[2];
+    T cu = L.c[3 * i] * u[0] + L.c[3 * i + 1] * u[1] + L.c[3 * i + 2] * u[2];
     out[i] = L.w[i] * (pstar + cu / CS2 + cu * cu / (2 * CS2 * CS2) - uu / (2 * CS2));
   }
 }
 
-double rate_g(const Params& P, int degree, double omega) {
+template <typename T>
+T rate_g(const Params& P, int degree, T omega) {
   if (P.collision != COLL_MRT) return omega;
   if (degree == 0) return 0.0;
   if (degree == 1) return 1.0;
@@ -233,7 +267,8 @@ double rate_g(const Params& P, int degree, double omega) {
   return 1.0;
 }
 
-double rate_h(const Params& P, int degree, double omega_phi) {
+template <typename T>
+T rate_h(const Params& P, int degree, T omega_phi) {
   if (P.collision != COLL_MRT) return omega_phi;
   if (degree == 0) return 0.0;
   if (degree <= 2) return omega_phi;
@@ -242,12 +277,12 @@ double rate_h(const Params& P, int degree, double omega_phi) {
 
 // Collision in moment space, Eq. (mrt) plus Guo forcing in collision space:
 //   f+ = f + M^-1 [ S M (f^eq - f) + (I - S/2) M src ].
-void mrt_collide(const Lattice& L, const double* f, const double* feq, const double* src, const double* s,
-                 double* out) {
+template <typename T>
+void mrt_collide(const Lattice& L, const T* f, const T* feq, const T* src, const T* s, T* out) {
   const int q = L.q;
-  double r[27];
+  T r[27];
   for (int k = 0; k < q; ++k) {
-    double d = 0, ms = 0;
+    T d = 0, ms = 0;
     for (int i = 0; i < q; ++i) {
       d += L.M[(size_t)k * q + i] * (feq[i] - f[i]);
       ms += L.M[(size_t)k * q + i] * src[i];
@@ -255,23 +290,24 @@ void mrt_collide(const Lattice& L, const double* f, const double* feq, const dou
     r[k] = s[k] * d + (1.0 - 0.5 * s[k]) * ms;
   }
   for (int i = 0; i < q; ++i) {
-    double v = 0;
+    T v = 0;
     for (int k = 0; k < q; ++k) v += L.Minv[(size_t)i * q + k] * r[k];
     out[i] = f[i] + v;
   }
 }
 
 // v = M^-1 S M d  (the relaxed non-equilibrium part).
-void mrt_relax(const Lattice& L, const double* d, const double* s, double* out) {
+template <typename T>
+void mrt_relax(const Lattice& L, const T* d, const T* s, T* out) {
   const int q = L.q;
-  double r[27];
+  T r[27];
   for (int k = 0; k < q; ++k) {
-    double m = 0;
+    T m = 0;
     for (int i = 0; i < q; ++i) m += L.M[(size_t)k * q + i] * d[i];
     r[k] = s[k] * m;
   }
   for (int i = 0; i < q; ++i) {
-    double v = 0;
+    T v = 0;
     for (int k = 0; k < q; ++k) v += L.Minv[(size_t)i * q + k] * r[k];
     out[i] = v;
   }
@@ -279,7 +315,8 @@ void mrt_relax(const Lattice& L, const double* d, const double* s, double* out) 
 
 // Macroscopic state of one cell at the current time level: stencil, forces
 // and velocity (steps before the collision).  Needs phi of the neighbours.
-void cell_macro(const Sim& S, int x, int y, int z, const double* gcell, CellState& cs) {
+template <typename T>
+void cell_macro(const Sim<T>& S, int x, int y, int z, const T* gcell, CellState<T>& cs) {
   const Params& P = S.P;
   const Lattice& L27 = Q27();
   long c0 = cell_index(P, x, y, z);
@@ -290,7 +327,7 @@ void cell_macro(const Sim& S, int x, int y, int z, const double* gcell, CellStat
     int xs = stencil_coord(x, L27.c[3 * i], P.nx, P.bc[0], P.bc[1]);
     int ys = stencil_coord(y, L27.c[3 * i + 1], P.ny, P.bc[2], P.bc[3]);
     int zs = stencil_coord(z, L27.c[3 * i + 2], P.nz, P.bc[4], P.bc[5]);
-    double pn = S.phi[cell_index(P, xs, ys, zs)];
+    T pn = S.phi[cell_index(P, xs, ys, zs)];
     for (int a = 0; a < 3; ++a) cs.gradphi[a] += L27.w[i] * L27.c[3 * i + a] * pn;
     cs.lapphi += L27.w[i] * (pn - cs.phi);
   }
@@ -303,7 +340,7 @@ void cell_macro(const Sim& S, int x, int y, int z, const double* gcell, CellStat
   cs.tau = tauL + (cs.phi - phiL) * (tauH - tauL);
   cs.omega = 1.0 / cs.tau;
   cs.nu = CS2 * (cs.tau - 0.5);
-  double beta = 12.0 * P.sigma / P.xi, kappa = 1.5 * P.sigma * P.xi;
+  T beta = 12.0 * S.sigma / S.xi, kappa = 1.5 * S.sigma * S.xi;
   cs.mu = 4.0 * beta * (cs.phi - phiL) * (cs.phi - phiH) * (cs.phi - phi0) - kappa * cs.lapphi;
 
   cs.pstar = 0;
@@ -313,7 +350,7 @@ void cell_macro(const Sim& S, int x, int y, int z, const double* gcell, CellStat
     for (int a = 0; a < 3; ++a) cs.j[a] += L27.c[3 * i + a] * gcell[i];
   }
   double drho = P.rho_h - P.rho_l;
-  double u0[3];
+  T u0[3];
   for (int a = 0; a < 3; ++a) {
     cs.Fs[a] = cs.mu * cs.gradphi[a];
     cs.Fb[a] = cs.rho * P.g[a];
@@ -321,17 +358,17 @@ void cell_macro(const Sim& S, int x, int y, int z, const double* gcell, CellStat
     u0[a] = cs.j[a] + (cs.Fs[a] + cs.Fb[a] + cs.Fp[a]) / (2.0 * cs.rho);
   }
   // Viscous force from the non-equilibrium moments, M^-1 S M (g - g^eq(p*, u0)).
-  double geq0[27], dneq[27], relaxed[27], s[27];
+  T geq0[27], dneq[27], relaxed[27], s[27];
   geq_of(cs.pstar, u0, geq0);
   for (int k = 0; k < L27.q; ++k) s[k] = rate_g(P, L27.degree[k], cs.omega);
   for (int i = 0; i < L27.q; ++i) dneq[i] = gcell[i] - geq0[i];
   mrt_relax(L27, dneq, s, relaxed);
-  double Pi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  T Pi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
   for (int i = 0; i < L27.q; ++i)
     for (int a = 0; a < 3; ++a)
       for (int b = 0; b < 3; ++b) Pi[a][b] += L27.c[3 * i + a] * L27.c[3 * i + b] * relaxed[i];
   for (int a = 0; a < 3; ++a) {
-    double acc = 0;
+    T acc = 0;
     for (int b = 0; b < 3; ++b) acc += Pi[a][b] * cs.gradphi[b];
     // [grad u + grad u^T] ~= -(1/c_s^2) (M^-1 S M g^neq)_2
     cs.Fmu[a] = cs.nu * drho * (-acc / CS2);
@@ -342,37 +379,40 @@ void cell_macro(const Sim& S, int x, int y, int z, const double* gcell, CellStat
   }
 }
 
-void compute_phi(Sim& S) {
+template <typename T>
+void compute_phi(Sim<T>& S) {
   const Lattice& L15 = Q15();
   for (long c = 0; c < S.N; ++c) {
-    double s = 0;
+    T s = 0;
     for (int i = 0; i < L15.q; ++i) s += S.h[(size_t)i * S.N + c];
     S.phi[c] = s;
   }
 }
 
-void do_step(Sim& S) {
+template <typename T>
+void do_step(Sim<T>& S) {
+  using std::sqrt;
   const Params& P = S.P;
   const Lattice& L27 = Q27();
   const Lattice& L15 = Q15();
   const long N = S.N;
-  const double omega_phi = 1.0 / (P.mobility / CS2 + 0.5);
+  const T omega_phi = 1.0 / (S.mobility / CS2 + 0.5);
 #pragma omp parallel for collapse(2) schedule(static)
   for (int z = 0; z < P.nz; ++z) {
     for (int y = 0; y < P.ny; ++y)
       for (int x = 0; x < P.nx; ++x) {
         long c0 = cell_index(P, x, y, z);
-        double gc[27], hc[15];
+        T gc[27], hc[15];
         for (int i = 0; i < 27; ++i) gc[i] = S.g[(size_t)i * N + c0];
         for (int i = 0; i < 15; ++i) hc[i] = S.h[(size_t)i * N + c0];
-        CellState cs;
+        CellState<T> cs;
         cell_macro(S, x, y, z, gc, cs);
 
         // hydrodynamic collision
-        double geq[27], G[27], gpost[27], s27[27];
+        T geq[27], G[27], gpost[27], s27[27];
         geq_of(cs.pstar, cs.u, geq);
         for (int i = 0; i < 27; ++i) {
-          double cF = L27.c[3 * i] * cs.F[0] + L27.c[3 * i + 1] * cs.F[1] + L27.c[3 * i + 2] * cs.F[2];
+          T cF = L27.c[3 * i] * cs.F[0] + L27.c[3 * i + 1] * cs.F[1] + L27.c[3 * i + 2] * cs.F[2];
           G[i] = L27.w[i] * cF / (CS2 * cs.rho);
         }
         if (P.collision == COLL_BGK) {
@@ -384,15 +424,15 @@ void do_step(Sim& S) {
         }
 
         // phase-field collision
-        double gnorm = std::sqrt(cs.gradphi[0] * cs.gradphi[0] + cs.gradphi[1] * cs.gradphi[1] +
-                                 cs.gradphi[2] * cs.gradphi[2]);
-        double n[3];
+        T gnorm = sqrt(cs.gradphi[0] * cs.gradphi[0] + cs.gradphi[1] * cs.gradphi[1] +
+                       cs.gradphi[2] * cs.gradphi[2]);
+        T n[3];
         for (int a = 0; a < 3; ++a) n[a] = cs.gradphi[a] / (gnorm + 1e-6);
-        double theta = 4.0 * cs.phi * (1.0 - cs.phi) / P.xi;
-        double heq[15], Sh[15], hpost[15], s15[15];
+        T theta = 4.0 * cs.phi * (1.0 - cs.phi) / S.xi;
+        T heq[15], Sh[15], hpost[15], s15[15];
         for (int i = 0; i < 15; ++i) {
-          double cu = L15.c[3 * i] * cs.u[0] + L15.c[3 * i + 1] * cs.u[1] + L15.c[3 * i + 2] * cs.u[2];
-          double cn = L15.c[3 * i] * n[0] + L15.c[3 * i + 1] * n[1] + L15.c[3 * i + 2] * n[2];
+          T cu = L15.c[3 * i] * cs.u[0] + L15.c[3 * i + 1] * cs.u[1] + L15.c[3 * i + 2] * cs.u[2];
+          T cn = L15.c[3 * i] * n[0] + L15.c[3 * i + 1] * n[1] + L15.c[3 * i + 2] * n[2];
           heq[i] = L15.w[i] * cs.phi * (1.0 + cu / CS2);
           Sh[i] = L15.w[i] * theta * cn;
         }
@@ -433,17 +473,11 @@ void do_step(Sim& S) {
   S.step += 1;
 }
 
-}  // namespace
-
-extern "C" {
-
-// iparams: nx, ny, nz, bc[6], collision       (10 ints)
-// dparams: rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, gx, gy, gz (10 doubles)
-// phi0 (N), u0 (3N SoA, nullable), p0 (N, nullable): initial state; the
-// populations start at their equilibria h^eq(phi0, u0), g^eq(p0, u0).
-void* ora_new(const int* ip, const double* dp, const double* phi0, const double* u0, const double* p0) {
-  Sim* S = new Sim();
-  Params& P = S->P;
+// The initial state: parameters from (ip, dp) and populations at their
+// equilibria h^eq(phi0, u0), g^eq(p0, u0).
+template <typename T>
+void init_sim(Sim<T>& S, const int* ip, const double* dp, const double* phi0, const double* u0, const double* p0) {
+  Params& P = S.P;
   P.nx = ip[0];
   P.ny = ip[1];
   P.nz = ip[2];
@@ -459,32 +493,83 @@ void* ora_new(const int* ip, const double* dp, const double* phi0, const double*
   P.g[0] = dp[7];
   P.g[1] = dp[8];
   P.g[2] = dp[9];
-  S->N = (long)P.nx * P.ny * P.nz;
-  const long N = S->N;
-  S->h.assign((size_t)15 * N, 0.0);
-  S->hn.assign((size_t)15 * N, 0.0);
-  S->g.assign((size_t)27 * N, 0.0);
-  S->gn.assign((size_t)27 * N, 0.0);
-  S->phi.assign(N, 0.0);
+  S.sigma = P.sigma;
+  S.mobility = P.mobility;
+  S.xi = P.xi;
+  S.N = (long)P.nx * P.ny * P.nz;
+  const long N = S.N;
+  S.h.assign((size_t)15 * N, T(0.0));
+  S.hn.assign((size_t)15 * N, T(0.0));
+  S.g.assign((size_t)27 * N, T(0.0));
+  S.gn.assign((size_t)27 * N, T(0.0));
+  S.phi.assign(N, T(0.0));
   const Lattice& L15 = Q15();
   for (long c = 0; c < N; ++c) {
-    double u[3] = {0, 0, 0};
+    T u[3] = {0.0, 0.0, 0.0};
     if (u0)
       for (int a = 0; a < 3; ++a) u[a] = u0[a * N + c];
-    double ps = p0 ? p0[c] : 0.0;
-    double geq[27];
+    T ps = p0 ? p0[c] : 0.0;
+    T geq[27];
     geq_of(ps, u, geq);
-    for (int i = 0; i < 27; ++i) S->g[(size_t)i * N + c] = geq[i];
+    for (int i = 0; i < 27; ++i) S.g[(size_t)i * N + c] = geq[i];
     for (int i = 0; i < 15; ++i) {
-      double cu = L15.c[3 * i] * u[0] + L15.c[3 * i + 1] * u[1] + L15.c[3 * i + 2] * u[2];
-      S->h[(size_t)i * N + c] = L15.w[i] * phi0[c] * (1.0 + cu / CS2);
+      double cu = L15.c[3 * i] * value(u[0]) + L15.c[3 * i + 1] * value(u[1]) + L15.c[3 * i + 2] * value(u[2]);
+      S.h[(size_t)i * N + c] = L15.w[i] * phi0[c] * (1.0 + cu / CS2);
     }
   }
-  compute_phi(*S);
+  compute_phi(S);
+}
+
+typedef Sim<double> SimD;
+
+}  // namespace
+
+extern "C" {
+
+// iparams: nx, ny, nz, bc[6], collision       (10 ints)
+// dparams: rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, gx, gy, gz (10 doubles)
+// phi0 (N), u0 (3N SoA, nullable), p0 (N, nullable): initial state; the
+// populations start at their equilibria h^eq(phi0, u0), g^eq(p0, u0).
+void* ora_new(const int* ip, const double* dp, const double* phi0, const double* u0, const double* p0) {
+  SimD* S = new SimD();
+  init_sim(*S, ip, dp, phi0, u0, p0);
   return S;
 }
 
-void ora_free(void* s) { delete (Sim*)s; }
+// Exact derivative, by forward-mode differentiation of the same arithmetic, of
+// J = sum_o sum_x W_o(x) phi^{t_o}(x) after n steps from the initial state of
+// ora_new, with respect to parameter `which` (0: M, 1: xi, 2: sigma).
+// obs_steps (n_obs, each in [0, n]) and obs_w (n_obs x N, row-major).
+// Writes J and dJ / d(parameter).
+void ora_tangent(const int* ip, const double* dp, const double* phi0, const double* u0, const double* p0, int which,
+                 int n, int n_obs, const int* obs_steps, const double* obs_w, int nthreads, double* J, double* dJ) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  Sim<Dual> S;
+  init_sim(S, ip, dp, phi0, u0, p0);
+  if (which == 0) S.mobility.d = 1.0;
+  if (which == 1) S.xi.d = 1.0;
+  if (which == 2) S.sigma.d = 1.0;
+  double j = 0.0, dj = 0.0;
+  for (int k = 0; k <= n; ++k) {
+    for (int o = 0; o < n_obs; ++o)
+      if (obs_steps[o] == k) {
+        const double* W = obs_w + (size_t)o * S.N;
+        for (long c = 0; c < S.N; ++c) {
+          j += W[c] * S.phi[c].v;
+          dj += W[c] * S.phi[c].d;
+        }
+      }
+    if (k < n) do_step(S);
+  }
+  *J = j;
+  *dJ = dj;
+}
+
+void ora_free(void* s) { delete (SimD*)s; }
 
 void ora_step(void* s, int n, int nthreads) {
 #ifdef _OPENMP
@@ -492,20 +577,20 @@ void ora_step(void* s, int n, int nthreads) {
 #else
   (void)nthreads;
 #endif
-  for (int k = 0; k < n; ++k) do_step(*(Sim*)s);
+  for (int k = 0; k < n; ++k) do_step(*(SimD*)s);
 }
 
-long ora_time(void* s) { return ((Sim*)s)->step; }
+long ora_time(void* s) { return ((SimD*)s)->step; }
 
 // Populations in canonical order, SoA [i][cell].
 void ora_get_pops(void* s, double* h, double* g) {
-  Sim* S = (Sim*)s;
+  SimD* S = (SimD*)s;
   if (h) std::memcpy(h, S->h.data(), sizeof(double) * S->h.size());
   if (g) std::memcpy(g, S->g.data(), sizeof(double) * S->g.size());
 }
 
 void ora_set_pops(void* s, const double* h, const double* g) {
-  Sim* S = (Sim*)s;
+  SimD* S = (SimD*)s;
   if (h) std::memcpy(S->h.data(), h, sizeof(double) * S->h.size());
   if (g) std::memcpy(S->g.data(), g, sizeof(double) * S->g.size());
   compute_phi(*S);
@@ -514,7 +599,7 @@ void ora_set_pops(void* s, const double* h, const double* g) {
 // Macroscopic fields at the current time level (any output may be NULL):
 // phi, rho(phi), p = p* rho c_s^2, u = sum c g + F/(2 rho) (3N SoA).
 void ora_fields(void* s, double* phi, double* rho, double* p, double* u) {
-  Sim* S = (Sim*)s;
+  SimD* S = (SimD*)s;
   const Params& P = S->P;
   const long N = S->N;
 #pragma omp parallel for collapse(2) schedule(static)
@@ -524,7 +609,7 @@ void ora_fields(void* s, double* phi, double* rho, double* p, double* u) {
         long c0 = cell_index(P, x, y, z);
         double gc[27];
         for (int i = 0; i < 27; ++i) gc[i] = S->g[(size_t)i * N + c0];
-        CellState cs;
+        CellState<double> cs;
         cell_macro(*S, x, y, z, gc, cs);
         if (phi) phi[c0] = cs.phi;
         if (rho) rho[c0] = cs.rho;

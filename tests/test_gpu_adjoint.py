@@ -1,5 +1,6 @@
 """Discrete adjoint of the stream-collide step against central finite
-differences of the forward GPU path (FP64), and FP32 against FP64.
+differences of the forward GPU path (FP64), against the exact derivative of
+the CPU oracle (forward-mode dual numbers), and FP32 against FP64.
 
 J is a linear functional of phi at chosen steps (bubble rise velocity, wave
 mode amplitude); the gradient is taken with respect to M, xi and sigma.  The
@@ -80,6 +81,21 @@ def test_adjoint_matches_finite_differences(case):
     assert np.all(np.abs(gfd) > 0)
     rel = np.abs(g - gfd) / np.abs(gfd)
     assert np.all(rel < 1e-3), (g, gfd, rel)
+
+
+@pytest.mark.parametrize("case", [bubble_case, wave_case])
+def test_adjoint_matches_oracle_tangent(case):
+    """Against the exact derivative of the FP64 CPU oracle (forward-mode
+    dual numbers through the same update): both are exact up to rounding, so
+    the bar is 1e-6 relative, a thousand times tighter than the finite
+    differences above."""
+    import oracle
+    p, phi0, u0, p0, n, obs = case()
+    J, g, _ = adjoint(p, phi0, u0, p0, n, obs)
+    for k, name in enumerate(PARAMS):
+        Jo, dJo = oracle.tangent(p, phi0, u0, p0, n, obs, name)
+        assert abs(J - Jo) <= 1e-10 * max(1e-12, abs(Jo)), (J, Jo)
+        assert abs(g[k] - dJo) <= 1e-6 * abs(dJo), (name, g[k], dJo)
 
 
 def test_adjoint_same_on_both_engines():
