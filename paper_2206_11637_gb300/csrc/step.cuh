@@ -30,6 +30,16 @@
 #ifndef PFL_STEP_MINB
 #define PFL_STEP_MINB 4
 #endif
+// Resident blocks per SM the fused step is compiled for.  Three (80 registers,
+// a few bytes of spill) beat two (128 registers) by 13-20 % for FP16S: the
+// kernel is latency-bound and gains from the extra warps.  FP64, bound by the
+// FP64 units, keeps two (three would spill ~200 bytes per thread).
+#ifndef PFL_ZM_MINB
+#define PFL_ZM_MINB 3
+#endif
+#ifndef PFL_ZM_MINB_FP64
+#define PFL_ZM_MINB_FP64 2
+#endif
 
 namespace pfl {
 
@@ -658,7 +668,7 @@ __device__ __forceinline__ void frame_pos(int r, int W, int H, int& i, int& j) {
 
 // grid: (ceil(nx / ZM_TX), ceil(ny / ZM_TY), ceil(nz / zc)), block ZM_TX x ZM_TY.
 template <int PREC, int FLAT>
-__global__ void __launch_bounds__(ZM_TX * ZM_TY, 2)
+__global__ void __launch_bounds__(ZM_TX * ZM_TY, PREC == 0 ? PFL_ZM_MINB_FP64 : PFL_ZM_MINB)
     k_step_zm(Geo32 geo, Phys ph, const typename Store<PREC>::S* __restrict__ hA,
               const typename Store<PREC>::S* __restrict__ gA, typename Store<PREC>::S* __restrict__ hB,
               typename Store<PREC>::S* __restrict__ gB, const typename Store<PREC>::PhiT* __restrict__ phi_shift,

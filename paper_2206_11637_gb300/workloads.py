@@ -157,6 +157,41 @@ def hydrostatic_pstar(p, phi0, level, inclusions=()):
     return 3.0 * pres / rho
 
 
+def column_hydrostatic_pstar(p, phi0, level):
+    """p* = p / (rho(phi) c_s^2) of fluid at rest under gravity along -y, with
+    dp/dy = -rho(phi) |g| integrated up each (x, z) column by the trapezoid
+    rule between cell centres and p = 0 at height `level` (linear
+    interpolation between the two cells around it)."""
+    g = abs(p.gravity[1])
+    rho = p.rho_l + phi0 * (p.rho_h - p.rho_l)                     # (nz, ny, nx)
+    steps = 0.5 * (rho[:, 1:, :] + rho[:, :-1, :])
+    P = np.concatenate([np.zeros_like(rho[:, :1, :]), -g * np.cumsum(steps, axis=1)], axis=1)
+    j = min(max(int(math.floor(level)), 0), p.ny - 2)
+    t = level - j
+    P -= (1.0 - t) * P[:, j:j + 1, :] + t * P[:, j + 1:j + 2, :]
+    return 3.0 * P / rho
+
+
+def gravity_wave(L=100, Re=10.0, omega_h=1.99, rho_ratio=1000.0, xi=5.0, M=0.02, sigma=0.0, collision=0):
+    """Standing gravity wave (section "Gravity wave"): L x L x 1, periodic x and
+    z, no-slip walls in y, heavy phase below y = d + a0 cos(k x) with d = L / 2
+    above the bottom wall, a0 = 0.01 L, k = 2 pi / L; nu_h from omega_h and
+    nu_l = nu_h (kinematic ratio 1); g from Re = a0 omega0 L / nu and
+    omega0^2 = g k tanh(k d); surface tension off; hydrostatic start with zero
+    pressure at the mean level."""
+    nu = (1.0 / omega_h - 0.5) / 3.0
+    a0 = 0.01 * L
+    d = 0.5 * L
+    k = 2.0 * math.pi / L
+    omega0 = Re * nu / (a0 * L)
+    g = omega0 ** 2 / (k * math.tanh(k * d))
+    bc = (PERIODIC, PERIODIC, NOSLIP, NOSLIP, PERIODIC, PERIODIC)
+    p = Params(L, L, 1, bc, 1.0, 1.0 / rho_ratio, nu, nu, sigma, M, xi, (0.0, -g, 0.0), collision)
+    # the halfway wall sits half a cell below y = 0: the mean level is y = d - 1/2
+    phi0 = wave(p, d - 0.5, a0, float(L))
+    return p, phi0, None, column_hydrostatic_pstar(p, phi0, d - 0.5)
+
+
 def rising_bubble(nx=128, ny=384, nz=128, D=32.0, xi=4.0, M=0.02, rho_ratio=1000.0, mu_ratio=100.0,
                   Eo=10.0, Mo=1e-3, nu_h=1.0 / 60.0, collision=0, hydrostatic=True, level=None):
     """Gas bubble of diameter D at 1.5 D above the bottom (y up), walls on all sides.

@@ -3,6 +3,8 @@
 prosperetti  -- small-amplitude viscous capillary wave, section "Capillary
                 wave", analytical model (Prosperetti 1981): amplitude a(t) from
                 the four roots of the quartic and complementary error functions.
+gravity_omega0, gravity_damping -- standing gravity wave, section "Gravity
+                wave": omega0^2 = g k tanh(k d), decay a0 exp(-2 nu k^2 t).
 poiseuille   -- body-force driven channel with halfway walls.
 two_layer_poiseuille -- two immiscible layers with different density and
                 dynamic viscosity; continuity of velocity and shear stress.
@@ -13,6 +15,16 @@ from scipy.special import erfc, wofz
 
 def capillary_omega0(sigma, k, rho_h, rho_l):
     return np.sqrt(sigma * k ** 3 / (rho_h + rho_l))
+
+
+def gravity_omega0(g, k, d):
+    """Linear standing gravity wave over depth d (section "Gravity wave")."""
+    return np.sqrt(g * k * np.tanh(k * d))
+
+
+def gravity_damping(nu, k):
+    """Viscous amplitude decay rate of a gravity wave, a0 exp(-2 nu k^2 t)."""
+    return 2.0 * nu * k * k
 
 
 def prosperetti(t, k, nu, rho_h, rho_l, sigma, a0):

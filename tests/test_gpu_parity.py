@@ -54,6 +54,7 @@ CASES = {
     "static_drop_32": (lambda: W.static_drop(32, 10.0, u_noise=1e-3, seed=1234), 1000),
     "wave_walls_y": (lambda: W.capillary_wave(40, ny=48, a0=1.5, xi=5.0, sigma=1e-4, nu=0.01), 400),
     "bubble_all_walls": (lambda: W.rising_bubble(24, 40, 20, D=10.0, xi=4.0, M=0.05, hydrostatic=False), 200),
+    "gravity_wave_50": (lambda: W.gravity_wave(50), 1000),
 }
 
 

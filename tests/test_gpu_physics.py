@@ -10,6 +10,12 @@
   oscillation frequency from zero crossings of the interface height at x = 0
   (section "Capillary wave"), FP32 and FP16S within 1 % of FP64; FP64 against
   Prosperetti's model.
+- Gravity wave (section "Gravity wave": L x L x 1, Re 10, omega_H 1.99, rho
+  ratio 1000, xi 5, M 0.02, hydrostatic start): the fitted angular frequency
+  approaches omega0 = sqrt(g k tanh(k d)) from below as L grows (0.96 at L 50,
+  0.98 at L 100) and is within 3 % at L 100; FP32 and FP16S within 1 % of
+  FP64; the fitted amplitude decay stays below Lamb's 2 nu k^2 (the paper
+  finds the PFLBM underestimates this damping).
 - Convergence at the paper's wave parameters (L x L, Re 10, omega_H 1.99,
   xi 5, M 0.02): the period error against Prosperetti shrinks as L grows.
 """
@@ -144,3 +150,40 @@ def test_capillary_wave_converges_with_resolution():
         errs.append(abs((c_sim[1] - c_sim[0]) / (c_an[1] - c_an[0]) - 1))
     assert errs[1] < errs[0], errs
     assert errs[1] < 0.05, errs
+
+
+def damped_fit(ts, amp, T, w0, g0):
+    """(omega, decay rate) of a0 exp(-g t) cos(w t + phase) + offset fitted after t = T / 10."""
+    from scipy.optimize import curve_fit
+    f = lambda t, a, g, w, ph, c: a * np.exp(-g * t) * np.cos(w * t + ph) + c
+    m = ts > 0.1 * T
+    popt, _ = curve_fit(f, ts[m], amp[m], p0=[amp[0], g0, w0, 0.0, 0.0], maxfev=20000)
+    return popt[2], popt[1]
+
+
+def gravity_wave_fit(L, precision, periods=2.2, nsamp=180):
+    p, phi0, u0, p0 = W.gravity_wave(L)
+    k, d = 2 * math.pi / L, 0.5 * L
+    w0 = A.gravity_omega0(abs(p.gravity[1]), k, d)
+    g0 = A.gravity_damping(p.nu_h, k)
+    T = 2 * math.pi / w0
+    s = sim(p, phi0, u0, p0, precision=precision)
+    dt = max(1, int(periods * T / nsamp))
+    ts, amp = [], []
+    while s.time <= periods * T:
+        ts.append(s.time)
+        amp.append(A.interface_height(s.phi()[0, :, 0]) - (L - 1) / 2.0)
+        s.step(dt)
+    w, g = damped_fit(np.array(ts, float), np.array(amp), T, w0, g0)
+    return w / w0, g / g0
+
+
+def test_gravity_wave_dispersion():
+    w50, _ = gravity_wave_fit(50, "fp64")
+    w100, g100 = gravity_wave_fit(100, "fp64")
+    assert abs(w100 - 1) < 0.03, (w50, w100)
+    assert abs(w100 - 1) < abs(w50 - 1), (w50, w100)
+    assert 0.5 < g100 < 1.0, g100
+    for prec in ("fp32", "fp16s"):
+        w, _ = gravity_wave_fit(100, prec)
+        assert abs(w / w100 - 1) < 0.01, (prec, w, w100)
