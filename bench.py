@@ -20,6 +20,7 @@ FP64 and FP32 are timed in the same run.
 rank runs an independent replica (the path is a single domain per GPU).
 """
 import argparse
+import copy
 import hashlib
 import json
 import math
@@ -41,12 +42,13 @@ PREC_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2}
 PHI_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 4}
 
 
-def step_kernel_bytes(prec, engine=0):
+def step_kernel_bytes(prec, engine=0, qh=15):
     """Algorithmic bytes per cell of one stream-collide launch: every h and g
-    population read once and written once; the fused two-array step (engine 0)
-    also writes phi, the in-place step (engine 1) reads phi for its stencil;
-    FP16S adds the read of the h shifts (phi of the writing cells)."""
-    b = 2 * (15 + 27) * PREC_BYTES[prec] + PHI_BYTES[prec]
+    population read once and written once (qh = 15 or 27 h populations); the
+    fused two-array step (engine 0) also writes phi, the in-place step
+    (engine 1) reads phi for its stencil; FP16S adds the read of the h shifts
+    (phi of the writing cells)."""
+    b = 2 * (qh + 27) * PREC_BYTES[prec] + PHI_BYTES[prec]
     if prec == "fp16s":
         b += PHI_BYTES[prec]
     return b
@@ -90,7 +92,11 @@ def kernel_hash():
 # (dram__bytes_read.sum + dram__bytes_write.sum), keyed by workload, precision
 # and the hash of the kernel sources they were taken on.  A capture of another
 # kernel version does not apply.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # k_step_zm<2, 15, 1>, 200x400x1 wave, three captured launches: 7.08, 7.07, 7.07 MB read, 0 written
+    # (profiles/launches_capillary_wave_200x400_fp16s.md)
+    ("capillary_wave", "fp16s", "619becd42f63ed96"): 7075840.0,
+}
 
 
 def peaks():
@@ -284,7 +290,7 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def adjoint_leg(dev, barrier):
+def adjoint_leg(dev, barrier, n=400):
     """Adjoint over forward on the 128 x 384 x 128 rising bubble (FP32, walls,
     D 32, Eo 10, Mo 1e-3, xi 4, M 0.02): J = mean rise velocity over the last
     quarter of n = 400 steps, gradient with respect to (M, xi, sigma), sqrt(n)
@@ -294,7 +300,6 @@ def adjoint_leg(dev, barrier):
     from paper_2206_11637_gb300 import workloads as W
     from paper_2206_11637_gb300.pflbm import Simulation
     p, phi0, u0, p0 = W.rising_bubble()
-    n = 400
     obs = O.rise_velocity_weights(p, phi0, 3 * n // 4, n)
     fw = Simulation(p, phi0, u0, p0, precision="fp32", device=dev)
     fw.step(10)
@@ -326,7 +331,9 @@ CONFIG_LEGS = [("static_drop", "fp64", 1000),
                ("capillary_wave", "fp64", 1000), ("capillary_wave", "fp32", 2000),
                ("capillary_wave", "fp16s", 2000),
                ("rising_bubble", "fp64", 20), ("rising_bubble", "fp32", 200), ("rising_bubble", "fp16s", 200),
-               ("drop_impact", "fp32", 40), ("drop_impact", "fp16s", 40)]
+               ("drop_impact", "fp32", 40), ("drop_impact", "fp16s", 40),
+               # the paper's own phase-field lattice (D3Q27 h)
+               ("rising_bubble@d3q27", "fp32", 200), ("rising_bubble@d3q27", "fp16s", 200)]
 
 
 def config_table(dev, barrier):
@@ -340,11 +347,14 @@ def config_table(dev, barrier):
     rows = []
     cache = {}
     for name, prec, S in CONFIG_LEGS:
-        if name not in cache:
+        base, _, lat = name.partition("@")
+        if base not in cache:
             cache.clear()
-            cache[name] = workload(name)
-        wl = cache[name]
-        p = wl["p"]
+            cache[base] = workload(base)
+        wl = cache[base]
+        p = copy.copy(wl["p"])
+        qh = 27 if lat == "d3q27" else 15
+        p.h_lattice = qh
         sim = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision=prec, device=dev)
         sim.step(3)
         barrier()
@@ -357,8 +367,8 @@ def config_table(dev, barrier):
         _, nf = sim.diag(check=False)
         del sim
         r = mlups(p.cells, S, ms / 1e3)
-        bpc = step_kernel_bytes(prec, 0)
-        work = p.cells * (2 * 42 * PREC_BYTES[prec] + 2 * PHI_BYTES[prec])
+        bpc = step_kernel_bytes(prec, 0, qh)
+        work = p.cells * (2 * (qh + 27) * PREC_BYTES[prec] + 2 * PHI_BYTES[prec])
         rows.append({"workload": name, "cells": p.cells, "precision": prec, "lattice_steps": S, "mlups": r,
                      "bytes_per_cell": bpc, "hbm_frac": r * 1e6 * bpc / 1e9 / peak,
                      "l2_resident": work < L2_BYTES, "nonfinite_cells": nf})
@@ -398,11 +408,21 @@ def main():
     ap.add_argument("--lattice-steps", type=int, default=None, help="lattice steps per benchmark step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
+    ap.add_argument("--adjoint-only", type=int, default=0, metavar="N",
+                    help="run only the adjoint leg over N steps and print its JSON (profiling)")
     ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
                     help="0: fused two-array step (default), 1: in-place AA step + phi pass")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
+    if args.adjoint_only:
+        import torch
+        from paper_2206_11637_gb300 import build as B
+        B.build_library()
+        torch.cuda.set_device(0)
+        r = adjoint_leg(torch.device("cuda", 0), torch.cuda.synchronize, args.adjoint_only)
+        print(json.dumps(r), flush=True)
+        return
     if args.workload == "batched_sweep":
         return run_batched(args)
     wl = workload(args.workload)
@@ -475,10 +495,18 @@ def main():
         ms = float(t.item())
     value = mlups(N, S * K, ms / 1e3) * ws
 
-    # roofline of the stream-collide kernel (CUDA events around each launch)
+    # roofline of the stream-collide kernel.  With the fused engine the timed
+    # region launches that kernel alone, once per lattice step, so its average
+    # launch duration is the region's device time over the launch count.  The
+    # in-place engine also runs the phi pass: its share comes from CUDA events
+    # around each of the two launches of a few extra steps.
     n_rt = min(S, 400)
-    kms, pms = sim.kernel_times(n_rt)
-    avg_s = kms / n_rt / 1e3
+    if args.engine == 0:
+        kms, pms = ms, 0.0
+        avg_s = ms / (S * K) / 1e3
+    else:
+        kms, pms = sim.kernel_times(n_rt)
+        avg_s = ms / (S * K) / 1e3 * kms / (kms + pms)
     peak, peak_kind = peaks()
     achieved = N * step_kernel_bytes(prec, args.engine) / avg_s / 1e9
     traffic = NCU_TRAFFIC.get((args.workload, prec, kernel_hash()))
@@ -487,7 +515,7 @@ def main():
                 "kernel": "k_step_zm (fused two-array step)" if args.engine == 0 else "k_step_mrt (in-place step)",
                 "bytes_per_cell": step_kernel_bytes(prec, args.engine), "peak_source": peak_kind,
                 "kernel_share": kms / (kms + pms),
-                "whole_step_ideal_frac": mlups(N, n_rt, (kms + pms) / 1e3) * 1e6 * ideal_step_bytes(prec) / 1e9 / peak,
+                "whole_step_ideal_frac": mlups(N, S * K, ms / 1e3) * 1e6 * ideal_step_bytes(prec) / 1e9 / peak,
                 "working_set_bytes": work_bytes, "l2_resident": work_bytes < L2_BYTES}
     del sim
 

@@ -5,7 +5,8 @@
  * The method (section "Conservative Allen-Cahn model" of Schwarzmeier et al.,
  * "Comparison of free-surface and conservative Allen-Cahn phase-field lattice
  * Boltzmann method"):
- *   - phase-field PDFs h_i on D3Q15 with phi = sum_i h_i (Eq. zeroth_moment_phase),
+ *   - phase-field PDFs h_i on D3Q15 (or D3Q27, pfl_params.h_lattice) with
+ *     phi = sum_i h_i (Eq. zeroth_moment_phase),
  *     relaxation time tau_phi = M / c_s^2 (Eq. pflbm-tau, read as the shifted
  *     time: omega_phi = 1 / (3 M + 1/2)) and the Allen-Cahn forcing
  *     F^phi = 4 phi (1 - phi) / xi * n applied with Guo's scheme;
@@ -84,6 +85,9 @@ typedef struct {
   int precision;       /* pfl_precision                                              */
   int collision;       /* pfl_collision                                              */
   int engine;          /* pfl_engine                                                 */
+  int h_lattice;       /* phase-field lattice: 15 (D3Q15; also when 0) or 27 (D3Q27, the
+                        * paper's own 3-D choice, section "Simulation setup" of the
+                        * models).  The h collision keeps its moment form on both. */
 } pfl_params;
 
 /* How a single lattice is stepped.  PFL_ENGINE_AUTO: the fused two-array step
@@ -118,7 +122,8 @@ pfl_status pfl_step(pfl_ctx* ctx, int n_steps);
 pfl_status pfl_fields(pfl_ctx* ctx, double* phi, double* rho, double* p, double* u);
 
 /* Populations at the current time in canonical order and layout, converted to
- * FP64: h is 15N, g is 27N doubles (either may be NULL; host or device).
+ * FP64: h is QN (Q = 15 or 27, the h lattice), g is 27N doubles (either may be
+ * NULL; host or device).
  * Synchronises. */
 pfl_status pfl_populations(pfl_ctx* ctx, double* h, double* g);
 
@@ -171,12 +176,12 @@ pfl_status pfl_adjoint(pfl_ctx* ctx, int n_steps, int n_obs, const int* obs_step
  * (M, xi, sigma, densities, ...), advanced together: every lattice step is
  * one persistent grid-stride launch of the stream-collide over a work list of
  * all instances' cells (plus one of the phi pass), and pfl_batch_step replays
- * a CUDA graph of 16 steps.  All instances share the precision; MRT only;
- * 27 N < 2^32 per instance. */
+ * a CUDA graph of 16 steps.  All instances share the precision; MRT and the
+ * D3Q15 phase field only; 27 N < 2^32 per instance. */
 typedef struct pfl_batch pfl_batch;
 
 /* Device bytes of the batch workspace (0 if a parameter set is invalid,
- * precisions differ or the collision is not MRT). */
+ * precisions differ, the collision is not MRT or the h lattice is D3Q27). */
 size_t pfl_batch_workspace_bytes(const pfl_params* params, int count);
 
 /* Create the batch: params[count]; phi0[count] arrays (host or device, N_i

@@ -72,11 +72,12 @@ class Oracle:
     """
 
     def __init__(self, nx, ny, nz, bc, rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi,
-                 gravity=(0.0, 0.0, 0.0), phi0=None, u0=None, p0=None, collision=COLL_MRT):
+                 gravity=(0.0, 0.0, 0.0), phi0=None, u0=None, p0=None, collision=COLL_MRT, h_lattice=15):
         self.lib = _load()
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
-        ip = np.array([nx, ny, nz] + list(bc) + [collision], dtype=np.int32)
+        self.qh = 27 if h_lattice == 27 else 15
+        ip = np.array([nx, ny, nz] + list(bc) + [collision, self.qh], dtype=np.int32)
         dp = np.array([rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi] + list(gravity), dtype=np.float64)
         self._phi0 = _f64(phi0, self.N)
         self._u0 = _f64(u0, 3 * self.N)
@@ -97,13 +98,13 @@ class Oracle:
         return self.lib.ora_time(self.h)
 
     def populations(self):
-        h = np.empty((15,) + self.shape)
+        h = np.empty((self.qh,) + self.shape)
         g = np.empty((27,) + self.shape)
         self.lib.ora_get_pops(self.h, _ptr(h), _ptr(g))
         return h, g
 
     def set_populations(self, h, g):
-        h = _f64(h, 15 * self.N)
+        h = _f64(h, self.qh * self.N)
         g = _f64(g, 27 * self.N)
         self.lib.ora_set_pops(self.h, _ptr(h), _ptr(g))
 
@@ -143,7 +144,7 @@ def mrt_collide(q, f, feq, src, rates):
 def from_params(p, phi0, u0=None, p0=None):
     """Oracle built from a ``workloads.Params``-like object (duck-typed)."""
     return Oracle(p.nx, p.ny, p.nz, p.bc, p.rho_h, p.rho_l, p.nu_h, p.nu_l, p.sigma, p.mobility, p.xi,
-                  p.gravity, phi0, u0, p0, collision=p.collision)
+                  p.gravity, phi0, u0, p0, collision=p.collision, h_lattice=getattr(p, "h_lattice", 15))
 
 
 PARAM_INDEX = {"mobility": 0, "xi": 1, "sigma": 2}
@@ -155,7 +156,8 @@ def tangent(p, phi0, u0, p0, n, obs, param, threads=0):
     param is "mobility", "xi" or "sigma".  Returns (J, dJ)."""
     lib = _load()
     N = p.nx * p.ny * p.nz
-    ip = np.array([p.nx, p.ny, p.nz] + list(p.bc) + [p.collision], dtype=np.int32)
+    qh = 27 if getattr(p, "h_lattice", 15) == 27 else 15
+    ip = np.array([p.nx, p.ny, p.nz] + list(p.bc) + [p.collision, qh], dtype=np.int32)
     dp = np.array([p.rho_h, p.rho_l, p.nu_h, p.nu_l, p.sigma, p.mobility, p.xi] + list(p.gravity),
                   dtype=np.float64)
     steps = np.array([int(t) for t, _ in obs], dtype=np.int32)

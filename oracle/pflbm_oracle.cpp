@@ -204,6 +204,7 @@ struct Params {
   int nx, ny, nz;
   int bc[6];  // -x,+x,-y,+y,-z,+z : 0 periodic, 1 no-slip
   int collision;
+  int qh;     // phase-field lattice: 15 (D3Q15) or 27 (D3Q27)
   double rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, g[3];
 };
 
@@ -381,10 +382,10 @@ void cell_macro(const Sim<T>& S, int x, int y, int z, const T* gcell, CellState<
 
 template <typename T>
 void compute_phi(Sim<T>& S) {
-  const Lattice& L15 = Q15();
+  const Lattice& LH = S.P.qh == 27 ? Q27() : Q15();
   for (long c = 0; c < S.N; ++c) {
     T s = 0;
-    for (int i = 0; i < L15.q; ++i) s += S.h[(size_t)i * S.N + c];
+    for (int i = 0; i < LH.q; ++i) s += S.h[(size_t)i * S.N + c];
     S.phi[c] = s;
   }
 }
@@ -394,7 +395,7 @@ void do_step(Sim<T>& S) {
   using std::sqrt;
   const Params& P = S.P;
   const Lattice& L27 = Q27();
-  const Lattice& L15 = Q15();
+  const Lattice& LH = P.qh == 27 ? Q27() : Q15();  // phase-field lattice
   const long N = S.N;
   const T omega_phi = 1.0 / (S.mobility / CS2 + 0.5);
 #pragma omp parallel for collapse(2) schedule(static)
@@ -402,9 +403,9 @@ void do_step(Sim<T>& S) {
     for (int y = 0; y < P.ny; ++y)
       for (int x = 0; x < P.nx; ++x) {
         long c0 = cell_index(P, x, y, z);
-        T gc[27], hc[15];
+        T gc[27], hc[27];
         for (int i = 0; i < 27; ++i) gc[i] = S.g[(size_t)i * N + c0];
-        for (int i = 0; i < 15; ++i) hc[i] = S.h[(size_t)i * N + c0];
+        for (int i = 0; i < LH.q; ++i) hc[i] = S.h[(size_t)i * N + c0];
         CellState<T> cs;
         cell_macro(S, x, y, z, gc, cs);
 
@@ -429,19 +430,19 @@ void do_step(Sim<T>& S) {
         T n[3];
         for (int a = 0; a < 3; ++a) n[a] = cs.gradphi[a] / (gnorm + 1e-6);
         T theta = 4.0 * cs.phi * (1.0 - cs.phi) / S.xi;
-        T heq[15], Sh[15], hpost[15], s15[15];
-        for (int i = 0; i < 15; ++i) {
-          T cu = L15.c[3 * i] * cs.u[0] + L15.c[3 * i + 1] * cs.u[1] + L15.c[3 * i + 2] * cs.u[2];
-          T cn = L15.c[3 * i] * n[0] + L15.c[3 * i + 1] * n[1] + L15.c[3 * i + 2] * n[2];
-          heq[i] = L15.w[i] * cs.phi * (1.0 + cu / CS2);
-          Sh[i] = L15.w[i] * theta * cn;
+        T heq[27], Sh[27], hpost[27], sh_rates[27];
+        for (int i = 0; i < LH.q; ++i) {
+          T cu = LH.c[3 * i] * cs.u[0] + LH.c[3 * i + 1] * cs.u[1] + LH.c[3 * i + 2] * cs.u[2];
+          T cn = LH.c[3 * i] * n[0] + LH.c[3 * i + 1] * n[1] + LH.c[3 * i + 2] * n[2];
+          heq[i] = LH.w[i] * cs.phi * (1.0 + cu / CS2);
+          Sh[i] = LH.w[i] * theta * cn;
         }
         if (P.collision == COLL_BGK) {
-          for (int i = 0; i < 15; ++i)
+          for (int i = 0; i < LH.q; ++i)
             hpost[i] = hc[i] - omega_phi * (hc[i] - heq[i]) + (1.0 - 0.5 * omega_phi) * Sh[i];
         } else {
-          for (int k = 0; k < 15; ++k) s15[k] = rate_h(P, L15.degree[k], omega_phi);
-          mrt_collide(L15, hc, heq, Sh, s15, hpost);
+          for (int k = 0; k < LH.q; ++k) sh_rates[k] = rate_h(P, LH.degree[k], omega_phi);
+          mrt_collide(LH, hc, heq, Sh, sh_rates, hpost);
         }
 
         // streaming (push) with periodic wrap / halfway bounce-back
@@ -455,15 +456,15 @@ void do_step(Sim<T>& S) {
           else
             S.gn[(size_t)L27.opp[i] * N + c0] = gpost[i];
         }
-        for (int i = 0; i < 15; ++i) {
+        for (int i = 0; i < LH.q; ++i) {
           int xt, yt, zt;
-          bool ok = neighbour(x, L15.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
-                    neighbour(y, L15.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
-                    neighbour(z, L15.c[3 * i + 2], P.nz, P.bc[4], P.bc[5], zt);
+          bool ok = neighbour(x, LH.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
+                    neighbour(y, LH.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
+                    neighbour(z, LH.c[3 * i + 2], P.nz, P.bc[4], P.bc[5], zt);
           if (ok)
             S.hn[(size_t)i * N + cell_index(P, xt, yt, zt)] = hpost[i];
           else
-            S.hn[(size_t)L15.opp[i] * N + c0] = hpost[i];
+            S.hn[(size_t)LH.opp[i] * N + c0] = hpost[i];
         }
       }
   }
@@ -483,6 +484,7 @@ void init_sim(Sim<T>& S, const int* ip, const double* dp, const double* phi0, co
   P.nz = ip[2];
   for (int k = 0; k < 6; ++k) P.bc[k] = ip[3 + k];
   P.collision = ip[9];
+  P.qh = ip[10] == 27 ? 27 : 15;
   P.rho_h = dp[0];
   P.rho_l = dp[1];
   P.nu_h = dp[2];
@@ -498,12 +500,12 @@ void init_sim(Sim<T>& S, const int* ip, const double* dp, const double* phi0, co
   S.xi = P.xi;
   S.N = (long)P.nx * P.ny * P.nz;
   const long N = S.N;
-  S.h.assign((size_t)15 * N, T(0.0));
-  S.hn.assign((size_t)15 * N, T(0.0));
+  S.h.assign((size_t)P.qh * N, T(0.0));
+  S.hn.assign((size_t)P.qh * N, T(0.0));
   S.g.assign((size_t)27 * N, T(0.0));
   S.gn.assign((size_t)27 * N, T(0.0));
   S.phi.assign(N, T(0.0));
-  const Lattice& L15 = Q15();
+  const Lattice& LH = P.qh == 27 ? Q27() : Q15();
   for (long c = 0; c < N; ++c) {
     T u[3] = {0.0, 0.0, 0.0};
     if (u0)
@@ -512,9 +514,9 @@ void init_sim(Sim<T>& S, const int* ip, const double* dp, const double* phi0, co
     T geq[27];
     geq_of(ps, u, geq);
     for (int i = 0; i < 27; ++i) S.g[(size_t)i * N + c] = geq[i];
-    for (int i = 0; i < 15; ++i) {
-      double cu = L15.c[3 * i] * value(u[0]) + L15.c[3 * i + 1] * value(u[1]) + L15.c[3 * i + 2] * value(u[2]);
-      S.h[(size_t)i * N + c] = L15.w[i] * phi0[c] * (1.0 + cu / CS2);
+    for (int i = 0; i < LH.q; ++i) {
+      double cu = LH.c[3 * i] * value(u[0]) + LH.c[3 * i + 1] * value(u[1]) + LH.c[3 * i + 2] * value(u[2]);
+      S.h[(size_t)i * N + c] = LH.w[i] * phi0[c] * (1.0 + cu / CS2);
     }
   }
   compute_phi(S);
@@ -526,7 +528,7 @@ typedef Sim<double> SimD;
 
 extern "C" {
 
-// iparams: nx, ny, nz, bc[6], collision       (10 ints)
+// iparams: nx, ny, nz, bc[6], collision, h lattice (15 or 27)   (11 ints)
 // dparams: rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, gx, gy, gz (10 doubles)
 // phi0 (N), u0 (3N SoA, nullable), p0 (N, nullable): initial state; the
 // populations start at their equilibria h^eq(phi0, u0), g^eq(p0, u0).

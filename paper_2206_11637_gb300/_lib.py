@@ -27,7 +27,8 @@ class pfl_params(ctypes.Structure):
                 ("nu_h", ctypes.c_double), ("nu_l", ctypes.c_double),
                 ("sigma", ctypes.c_double), ("mobility", ctypes.c_double), ("xi", ctypes.c_double),
                 ("gravity", ctypes.c_double * 3),
-                ("precision", ctypes.c_int), ("collision", ctypes.c_int), ("engine", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("collision", ctypes.c_int), ("engine", ctypes.c_int),
+                ("h_lattice", ctypes.c_int)]
 
 
 class PFLError(RuntimeError):

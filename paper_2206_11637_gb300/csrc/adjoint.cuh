@@ -19,7 +19,7 @@
 // adjoints of x; it is kept once per cell (array `acc`) and added by the next
 // reverse step as it reads lambda, instead of being written into 15 arrays.
 //
-// Adjoint populations are kept in the canonical layout [i][cell] (h: 15 N,
+// Adjoint populations are kept in the canonical layout [i][cell] (h: QH N,
 // then g: 27 N) in the arithmetic type; lambda^t = (local part) + acc^t on the
 // h entries.
 #pragma once
@@ -57,7 +57,7 @@ __device__ __forceinline__ R block_sum3_to(R a, R b, R c, double* out3) {
   return a;
 }
 
-template <int PREC, int READ_ODD>
+template <int PREC, int QH, int READ_ODD>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, AdjPar ap,
                                                            const typename Store<PREC>::S* __restrict__ h,
                                                            const typename Store<PREC>::S* __restrict__ g,
@@ -116,13 +116,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
       if (cy && cz) pyz += (cy * cz > 0) ? S : -S;
       if (cx && cz) pxz += (cx * cz > 0) ? S : -S;
     }
-    R phl = h[7u * N + cell], hjx = 0, hjy = 0, hjz = 0, hxx = 0, hyy = 0, hzz = 0, hxy = 0, hyz = 0, hxz = 0;
+    R phl = h[(unsigned)hq_rest<QH>() * N + cell], hjx = 0, hjy = 0, hjz = 0, hxx = 0, hyy = 0, hzz = 0, hxy = 0, hyz = 0, hxz = 0;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+    for (int k = 0; k < hq_rest<QH>(); ++k) {
+      const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
       R a, b;
       unsigned fa, fb;
-      load_pair<PREC, READ_ODD>(h, N, cell, o, k, 14 - k, cx, cy, cz, a, b, fa, fb);
+      load_pair<PREC, READ_ODD>(h, N, cell, o, k, QH - 1 - k, cx, cy, cz, a, b, fa, fb);
       const R S = a + b, D = a - b;
       phl += S;
       if (cx) hjx += cx > 0 ? D : -D;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
     // ---------------- adjoints of the post-collision populations
     // g: lambda+ of population i of this cell sits where streaming put it
     R b_al = 0, b_bx = 0, b_by = 0, b_bz = 0, b_Gxx = 0, b_Gyy = 0, b_Gzz = 0, b_Gxy = 0, b_Gyz = 0, b_Gxz = 0;
-    const R* lg = lam_in + 15u * N;
+    const R* lg = lam_in + (unsigned)QH * N;
     b_al = (R)q27_w(13) * lg[13u * N + cell];
 #pragma unroll
     for (int i = 0; i < 13; ++i) {
@@ -201,19 +201,20 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
       if (cx && cz) b_Gxz += (cx * cz > 0) ? S : -S;
     }
     // h
-    R c_al = (R)q15_w(7) * (lam_in[7u * N + cell] + acc_in[cell]), c_bx = 0, c_by = 0, c_bz = 0;
+    R c_al = (R)hq_w<QH>(hq_rest<QH>()) * (lam_in[(unsigned)hq_rest<QH>() * N + cell] + acc_in[cell]), c_bx = 0,
+      c_by = 0, c_bz = 0;
     R c_Gxx = 0, c_Gyy = 0, c_Gzz = 0, c_Gxy = 0, c_Gyz = 0, c_Gxz = 0;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
-      const int ok = 14 - k;
+    for (int k = 0; k < hq_rest<QH>(); ++k) {
+      const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
+      const int ok = QH - 1 - k;
       // the slot read and the cell holding it (whose acc belongs to every h slot)
       const bool va = o.valid(cx, cy, cz), vb = o.valid(-cx, -cy, -cz);
       const unsigned ya = va ? cell + (unsigned)o.off(cx, cy, cz) : cell;
       const unsigned yb = vb ? cell + (unsigned)o.off(-cx, -cy, -cz) : cell;
       const R la = lam_in[(va ? (unsigned)k : (unsigned)ok) * N + ya] + acc_in[ya];
       const R lb = lam_in[(vb ? (unsigned)ok : (unsigned)k) * N + yb] + acc_in[yb];
-      const R w = (R)q15_w(k);
+      const R w = (R)hq_w<QH>(k);
       const R S = w * (la + lb), D = w * (la - lb);
       c_al += S;
       if (cx) c_bx += cx > 0 ? D : -D;
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
     }
 
     // ---------------- adjoints of the local pre-collision populations
-    R* og = lam_out + 15u * N;
+    R* og = lam_out + (unsigned)QH * N;
     og[13u * N + cell] = b_pst;
 #pragma unroll
     for (int i = 0; i < 13; ++i) {
@@ -421,10 +422,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
       og[(unsigned)i * N + cell] = E + L;
       og[(unsigned)(26 - i) * N + cell] = E - L;
     }
-    lam_out[7u * N + cell] = b_phl;
+    lam_out[(unsigned)hq_rest<QH>() * N + cell] = b_phl;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+    for (int k = 0; k < hq_rest<QH>(); ++k) {
+      const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
       R E = b_phl;
       if (cx) E += b_hxx;
       if (cy) E += b_hyy;
@@ -437,7 +438,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
       if (cy) L += cy > 0 ? b_hjy : -b_hjy;
       if (cz) L += cz > 0 ? b_hjz : -b_hjz;
       lam_out[(unsigned)k * N + cell] = E + L;
-      lam_out[(unsigned)(14 - k) * N + cell] = E - L;
+      lam_out[(unsigned)(QH - 1 - k) * N + cell] = E - L;
     }
     aux[0u * N + cell] = b_gx;
     aux[1u * N + cell] = b_gy;

@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 2)
     if (!I->active) continue;
     const unsigned cell = tile.c0 + threadIdx.x;
     if (cell < I->geo.N)
-      step_cell<PREC, ODD>(I->geo, I->ph, (S*)I->h, (S*)I->g, (const PhiT*)I->phi[cur], (const PhiT*)I->phi[1 - cur],
+      step_cell<PREC, 15, ODD>(I->geo, I->ph, (S*)I->h, (S*)I->g, (const PhiT*)I->phi[cur], (const PhiT*)I->phi[1 - cur],
                            cell, *tstep * 0x9E3779B9u + (unsigned)tile.inst * 0x85EBCA6Bu);
   }
 }
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(THREADS) k_batch_phi(const BInst* __restrict__
     if (!I->active) continue;
     const unsigned cell = tile.c0 + threadIdx.x;
     if (cell < I->geo.N)
-      ((PhiT*)I->phi[1 - cur])[cell] = phi_cell<PREC, READ_ODD>(I->geo, (const S*)I->h, (const PhiT*)I->phi[cur], cell);
+      ((PhiT*)I->phi[1 - cur])[cell] = phi_cell<PREC, 15, READ_ODD>(I->geo, (const S*)I->h, (const PhiT*)I->phi[cur], cell);
   }
 }
 
@@ -261,7 +261,7 @@ void launch_init_one(pfl_batch* b, int i, long long c0, long long cnt, const dou
   geo.nz = b->p[i].nz;
   for (int a = 0; a < 3; ++a) geo.wall[a] = b->p[i].bc[2 * a] == PFL_NOSLIP;
   geo.N = b->inst[i].geo.N;
-  k_init<PREC><<<blocks_for(cnt, 256), 256, 0, b->stream>>>(geo, (typename Store<PREC>::S*)b->inst[i].h,
+  k_init<PREC, 15><<<blocks_for(cnt, 256), 256, 0, b->stream>>>(geo, (typename Store<PREC>::S*)b->inst[i].h,
                                                             (typename Store<PREC>::S*)b->inst[i].g, c0, cnt, phi0, ux,
                                                             uy, uz, p0);
 }
@@ -269,7 +269,7 @@ void launch_init_one(pfl_batch* b, int i, long long c0, long long cnt, const dou
 template <int PREC>
 void launch_phi_one(pfl_batch* b, int i) {
   const BInst& I = b->inst[i];
-  k_phi32<PREC, 0><<<blocks_for(I.geo.N, 256), 256, 0, b->stream>>>(
+  k_phi32<PREC, 15, 0><<<blocks_for(I.geo.N, 256), 256, 0, b->stream>>>(
       I.geo, (const typename Store<PREC>::S*)I.h, (const typename Store<PREC>::PhiT*)I.phi[1],
       (typename Store<PREC>::PhiT*)I.phi[0]);
 }
@@ -437,6 +437,7 @@ size_t pfl_batch_workspace_bytes(const pfl_params* params, int count) {
   for (int i = 0; i < count; ++i) {
     if (!check_params(&params[i]).empty()) return 0;
     if (params[i].precision != params[0].precision || params[i].collision != PFL_MRT) return 0;
+    if (qh_of(&params[i]) != 15) return 0;
     if (27ull * params[i].nx * params[i].ny * params[i].nz >= (1ull << 32)) return 0;
   }
   return blayout(params, count).total;
@@ -454,6 +455,7 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
     if (params[i].precision != params[0].precision)
       return bfail(PFL_ERR_ARG, "all instances of a batch share one precision");
     if (params[i].collision != PFL_MRT) return bfail(PFL_ERR_ARG, "the batch runs the MRT collision");
+    if (qh_of(&params[i]) != 15) return bfail(PFL_ERR_ARG, "the batch steps D3Q15 phase fields only");
     if (27ull * params[i].nx * params[i].ny * params[i].nz >= (1ull << 32))
       return bfail(PFL_ERR_ARG, "instance " + std::to_string(i) + " too large for 32-bit indices");
     if (!phi0[i]) return bfail(PFL_ERR_ARG, "phi0 of instance " + std::to_string(i) + " is NULL");

@@ -15,6 +15,9 @@ inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 inline size_t pop_bytes(int prec) { return prec == PFL_FP64 ? 8 : prec == PFL_FP32 ? 4 : 2; }
 inline size_t phi_bytes(int prec) { return prec == PFL_FP64 ? 8 : 4; }
 
+// Velocities of the phase-field lattice: 27 for D3Q27, else 15 (D3Q15).
+inline int qh_of(const pfl_params* p) { return p->h_lattice == 27 ? 27 : 15; }
+
 // The fused two-array step applies to MRT lattices with 32-bit indices.
 inline bool uses_two_arrays(const pfl_params* p) {
   return p->engine == PFL_ENGINE_AUTO && p->collision == PFL_MRT &&
@@ -41,6 +44,7 @@ inline std::string check_params(const pfl_params* p) {
   if (p->precision < PFL_FP64 || p->precision > PFL_FP16S) return "unknown precision";
   if (p->collision != PFL_MRT && p->collision != PFL_BGK) return "unknown collision model";
   if (p->engine != PFL_ENGINE_AUTO && p->engine != PFL_ENGINE_INPLACE) return "unknown engine";
+  if (p->h_lattice != 0 && p->h_lattice != 15 && p->h_lattice != 27) return "h_lattice must be 0, 15 or 27";
   if (!std::isfinite(p->gravity[0]) || !std::isfinite(p->gravity[1]) || !std::isfinite(p->gravity[2]))
     return "gravity must be finite";
   return "";

@@ -223,20 +223,20 @@ __device__ __forceinline__ void hydro_macro(const Geo& geo, const Phys& ph, cons
 
 // h population k arriving at `cell` (FP16S: shifted by phi of the writing cell,
 // read from `shift`).
-template <int PREC, int READ_ODD>
+template <int PREC, int QH, int READ_ODD>
 __device__ __forceinline__ typename Store<PREC>::R load_h(const Geo& geo, const Nb& nb, long long cell, int k,
                                                           const typename Store<PREC>::S* __restrict__ h,
                                                           const typename Store<PREC>::PhiT* __restrict__ shift) {
   typedef typename Store<PREC>::R R;
   long long from;
-  const size_t idx = src_index<READ_ODD>(geo, nb, cell, k, q15_opp(k), q15_cx(k), q15_cy(k), q15_cz(k), from);
+  const size_t idx = src_index<READ_ODD>(geo, nb, cell, k, QH - 1 - k, hq_cx<QH>(k), hq_cy<QH>(k), hq_cz<QH>(k), from);
   R sh = 0;
   if constexpr (PREC == 2) sh = __ldg(shift + from);
-  return ld_h<PREC>(h, idx, k, sh);
+  return ld_h<PREC, QH>(h, idx, k, sh);
 }
 
 // One time step: collide both sets at every cell and stream them in place.
-template <int PREC, int ODD, int BGK>
+template <int PREC, int QH, int ODD, int BGK>
 __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<PREC>::S* __restrict__ h,
                                               typename Store<PREC>::S* __restrict__ g,
                                               const typename Store<PREC>::PhiT* __restrict__ phi,
@@ -287,12 +287,12 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
 
   // ---- h collision and streaming
   {
-    R hv[15];
+    R hv[QH];
     R phl = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
 #pragma unroll
-    for (int k = 0; k < 15; ++k) {
-      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
-      const R v = load_h<PREC, ODD>(geo, nb, cell, k, h, shift);
+    for (int k = 0; k < QH; ++k) {
+      const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
+      const R v = load_h<PREC, QH, ODD>(geo, nb, cell, k, h, shift);
       hv[k] = v;
       phl += v;
       if (cx) jx += cx > 0 ? v : -v;
@@ -320,29 +320,29 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
     // populations are written as q = h+ / w - shift; the shift is this cell's phi
     const R sh = (PREC == 2) ? m.phi : (R)0;
 #pragma unroll
-    for (int k = 0; k < 15; ++k) {
-      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+    for (int k = 0; k < QH; ++k) {
+      const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
       const R cu = (R)cx * ux + (R)cy * uy + (R)cz * uz;
       const R ct = (R)cx * tx + (R)cy * ty + (R)cz * tz;
       R q;
       if (BGK) {
-        const R w = (R)q15_w(k);
+        const R w = (R)hq_w<QH>(k);
         const R heq = w * phl * ((R)1 + (R)3 * cu);
-        q = (hv[k] - omp * (hv[k] - heq)) * (R)(1.0 / q15_w(k)) + src * ct - sh;
+        q = (hv[k] - omp * (hv[k] - heq)) * (R)(1.0 / hq_w<QH>(k)) + src * ct - sh;
       } else {
         const R cJ = (R)cx * Jx + (R)cy * Jy + (R)cz * Jz;
         const R hd = (R)(cx * cx) * dxx + (R)(cy * cy) * dyy + (R)(cz * cz) * dzz +
                      (R)2 * ((R)(cx * cy) * pxy + (R)(cy * cz) * pyz + (R)(cx * cz) * pxz) - tr3;
         q = (phl - sh) + phl * (R)3 * cu + a1 * cJ + a2 * hd + src * ct;
       }
-      st_h_q<PREC>(h, dst_index<ODD>(geo, nb, cell, k, q15_opp(k), cx, cy, cz), k, q);
+      st_h_q<PREC, QH>(h, dst_index<ODD>(geo, nb, cell, k, QH - 1 - k, cx, cy, cz), k, q);
     }
   }
 }
 
 // phi = sum_i h_i of the state left by the last step (READ_ODD after an even
 // step); `shift` holds the shifts of the stored populations.
-template <int PREC, int READ_ODD>
+template <int PREC, int QH, int READ_ODD>
 __global__ void __launch_bounds__(256) k_phi(Geo geo, const typename Store<PREC>::S* __restrict__ h,
                                              const typename Store<PREC>::PhiT* __restrict__ shift,
                                              typename Store<PREC>::PhiT* __restrict__ phi) {
@@ -355,14 +355,14 @@ __global__ void __launch_bounds__(256) k_phi(Geo geo, const typename Store<PREC>
   make_nb(geo, x, y, z, nb);
   R s = 0;
 #pragma unroll
-  for (int k = 0; k < 15; ++k) s += load_h<PREC, READ_ODD>(geo, nb, cell, k, h, shift);
+  for (int k = 0; k < QH; ++k) s += load_h<PREC, QH, READ_ODD>(geo, nb, cell, k, h, shift);
   phi[cell] = s;
 }
 
 // Equilibrium initial state (normal layout, zero shifts) for cells
 // [c0, c0 + count).  Inputs are FP64 arrays indexed from c0 (phi0, u0x, u0y,
 // u0z, p0; u and p may be NULL).
-template <int PREC>
+template <int PREC, int QH>
 __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typename Store<PREC>::S* __restrict__ g,
                        long long c0, long long count, const double* __restrict__ phi0,
                        const double* __restrict__ u0x, const double* __restrict__ u0y,
@@ -381,9 +381,9 @@ __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typenam
     st_g<PREC>(g, (size_t)i * geo.N + cell, i, (R)q27_w(i) * (ps + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu));
   }
 #pragma unroll
-  for (int k = 0; k < 15; ++k) {
-    const R cu = (R)q15_cx(k) * ux + (R)q15_cy(k) * uy + (R)q15_cz(k) * uz;
-    st_h_q<PREC>(h, (size_t)k * geo.N + cell, k, ph * ((R)1 + (R)3 * cu));
+  for (int k = 0; k < QH; ++k) {
+    const R cu = (R)hq_cx<QH>(k) * ux + (R)hq_cy<QH>(k) * uy + (R)hq_cz<QH>(k) * uz;
+    st_h_q<PREC, QH>(h, (size_t)k * geo.N + cell, k, ph * ((R)1 + (R)3 * cu));
   }
 }
 
@@ -411,10 +411,10 @@ __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename
   if (o_uz) o_uz[cell] = (double)m.uz;
 }
 
-// Population export in canonical layout (FP64): q = 15 (h) or 27 (g).
-template <int PREC, int READ_ODD>
+// Population export in canonical layout (FP64): population i of g (is_g) or h.
+template <int PREC, int QH, int READ_ODD>
 __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
-                         const typename Store<PREC>::PhiT* __restrict__ shift, int q, int i,
+                         const typename Store<PREC>::PhiT* __restrict__ shift, int is_g, int i,
                          double* __restrict__ out) {
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
@@ -422,7 +422,7 @@ __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
   cell_coords(geo, cell, x, y, z);
   Nb nb;
   make_nb(geo, x, y, z, nb);
-  if (q == 27) {
+  if (is_g) {
 #pragma unroll
     for (int j = 0; j < 27; ++j)
       if (j == i) {
@@ -432,28 +432,28 @@ __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
       }
   } else {
 #pragma unroll
-    for (int j = 0; j < 15; ++j)
-      if (j == i) out[cell] = (double)load_h<PREC, READ_ODD>(geo, nb, cell, j, f, shift);
+    for (int j = 0; j < QH; ++j)
+      if (j == i) out[cell] = (double)load_h<PREC, QH, READ_ODD>(geo, nb, cell, j, f, shift);
   }
 }
 
 // Population import (normal layout; h with zero shifts).
-template <int PREC>
-__global__ void k_import(Geo geo, typename Store<PREC>::S* __restrict__ f, int q, int i, const double* __restrict__ in) {
+template <int PREC, int QH>
+__global__ void k_import(Geo geo, typename Store<PREC>::S* __restrict__ f, int is_g, int i, const double* __restrict__ in) {
   typedef typename Store<PREC>::R R;
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
   const size_t idx = (size_t)i * geo.N + cell;
   if constexpr (PREC != 2) {
     f[idx] = (R)in[cell];
-  } else if (q == 27) {
+  } else if (is_g) {
 #pragma unroll
     for (int j = 0; j < 27; ++j)
       if (j == i) st_g<PREC>(f, idx, j, (R)in[cell]);
   } else {
 #pragma unroll
-    for (int j = 0; j < 15; ++j)
-      if (j == i) st_h_q<PREC>(f, idx, j, (R)(in[cell] / q15_w(j)));
+    for (int j = 0; j < QH; ++j)
+      if (j == i) st_h_q<PREC, QH>(f, idx, j, (R)(in[cell] / hq_w<QH>(j)));
   }
 }
 

@@ -1,6 +1,6 @@
 // Lattice constants and population storage formats of the PFLBM kernels.
 //
-// D3Q27 (hydrodynamics g) and D3Q15 (phase field h) in the canonical order of
+// D3Q27 (hydrodynamics g) and D3Q15 or D3Q27 (phase field h) in the canonical order of
 // the C interface: cz, cy, cx each over -1, 0, 1 with cx fastest.  For D3Q27
 // this gives i = (cx+1) + 3(cy+1) + 9(cz+1), so velocities, weights and
 // opposites are closed-form functions of i that fold to constants inside
@@ -34,6 +34,34 @@ __host__ __device__ constexpr int q15_opp(int k) { return 14 - k; }
 // weights 2/9, 1/9, 1/72 by |c|^2 = 0, 1, 3
 __host__ __device__ constexpr double q15_w(int k) {
   return q27_n2(q15_to27(k)) == 0 ? 2.0 / 9.0 : q27_n2(q15_to27(k)) == 1 ? 1.0 / 9.0 : 1.0 / 72.0;
+}
+
+// The phase-field lattice, QH = 15 (D3Q15) or 27 (D3Q27).  In both orders
+// member k pairs with QH - 1 - k, members k < (QH - 1) / 2 are one of each
+// opposite pair, and (QH - 1) / 2 is the rest velocity.
+template <int QH>
+__host__ __device__ constexpr int hq_to27(int k) {
+  return QH == 27 ? k : q15_to27(k);
+}
+template <int QH>
+__host__ __device__ constexpr int hq_cx(int k) {
+  return q27_cx(hq_to27<QH>(k));
+}
+template <int QH>
+__host__ __device__ constexpr int hq_cy(int k) {
+  return q27_cy(hq_to27<QH>(k));
+}
+template <int QH>
+__host__ __device__ constexpr int hq_cz(int k) {
+  return q27_cz(hq_to27<QH>(k));
+}
+template <int QH>
+__host__ __device__ constexpr double hq_w(int k) {
+  return QH == 27 ? q27_w(k) : q15_w(k);
+}
+template <int QH>
+__host__ __device__ constexpr int hq_rest() {
+  return (QH - 1) / 2;
 }
 
 // FP16S format (shifted FP16 storage, FP32 arithmetic), per population and
@@ -92,22 +120,22 @@ __device__ __forceinline__ void st_g(typename Store<PREC>::S* a, size_t idx, int
 }
 
 // h population k: load adds back the shift phi_src (FP16S only).
-template <int PREC>
+template <int PREC, int QH>
 __device__ __forceinline__ typename Store<PREC>::R ld_h(const typename Store<PREC>::S* a, size_t idx, int k,
                                                         typename Store<PREC>::R phi_src) {
   if constexpr (PREC == 2)
-    return (__half2float(a[idx]) * (float)(1.0 / KH16) + phi_src) * (float)q15_w(k);
+    return (__half2float(a[idx]) * (float)(1.0 / KH16) + phi_src) * (float)hq_w<QH>(k);
   else
     return a[idx];
 }
 // Store of h from q = h_i / w_i - shift (the shift is zero for FP64 / FP32).
-template <int PREC>
+template <int PREC, int QH>
 __device__ __forceinline__ void st_h_q(typename Store<PREC>::S* a, size_t idx, int k, typename Store<PREC>::R q) {
   typedef typename Store<PREC>::R R;
   if constexpr (PREC == 2)
     a[idx] = __float2half_rn(q * (float)KH16);
   else
-    a[idx] = (R)q15_w(k) * q;
+    a[idx] = (R)hq_w<QH>(k) * q;
 }
 
 }  // namespace pfl

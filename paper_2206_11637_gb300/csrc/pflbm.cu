@@ -58,14 +58,15 @@ Layout layout_of(const pfl_params* p) {
   Layout L;
   const size_t N = (size_t)p->nx * p->ny * p->nz;
   size_t off = 0;
+  const size_t QH = (size_t)qh_of(p);
   L.h = off;
-  off = align256(off + 15 * N * pop_bytes(p->precision));
+  off = align256(off + QH * N * pop_bytes(p->precision));
   L.g = off;
   off = align256(off + 27 * N * pop_bytes(p->precision));
   L.h2 = L.g2 = 0;
   if (uses_two_arrays(p)) {  // second array pair of the fused two-array step
     L.h2 = off;
-    off = align256(off + 15 * N * pop_bytes(p->precision));
+    off = align256(off + QH * N * pop_bytes(p->precision));
     L.g2 = off;
     off = align256(off + 27 * N * pop_bytes(p->precision));
   }
@@ -103,6 +104,7 @@ struct pfl_ctx {
   int zc;        // two-array step: z planes per block
   long long t;   // steps taken
   int swapped;   // 1 after an even step (populations await the gather read)
+  int qh;        // phase-field lattice: 15 or 27 velocities
 };
 
 namespace {
@@ -144,18 +146,18 @@ unsigned step_seed(const pfl_ctx* c) { return (unsigned)((unsigned long long)c->
 // phi of the stored state into the spare buffer, then make it current.  The
 // stored h carry the shifts of buffer `cur` (after a step) -- the spare buffer
 // is free.
-template <int PREC>
+template <int PREC, int QH>
 void launch_phi(pfl_ctx* c) {
   const unsigned nb = blocks_for(c->geo.N, 256);
   if (c->idx32) {
     if (c->swapped)
-      k_phi32<PREC, 1><<<nb, 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
+      k_phi32<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
     else
-      k_phi32<PREC, 0><<<nb, 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
+      k_phi32<PREC, QH, 0><<<nb, 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
   } else if (c->swapped)
-    k_phi<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
+    k_phi<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->geo, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
   else
-    k_phi<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
+    k_phi<PREC, QH, 0><<<nb, 256, 0, c->stream>>>(c->geo, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
   c->cur = 1 - c->cur;
 }
 
@@ -163,18 +165,18 @@ void launch_phi(pfl_ctx* c) {
 // step).  Two-array contexts run the fused kernel; MRT in place the pair-based
 // kernel; the BGK test mode, and lattices too large for 32-bit indices, the
 // generic one.
-template <int PREC, int BGK>
+template <int PREC, int QH, int BGK>
 void step_only(pfl_ctx* c) {
   const unsigned nb = blocks_for(c->geo.N, 256);
   if (c->zm) {
     const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
     const dim3 block(ZM_TX, ZM_TY);
     if (c->p.nz == 1)
-      k_step_zm<PREC, 1><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), hnext<PREC>(c),
+      k_step_zm<PREC, QH, 1><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), hnext<PREC>(c),
                                                          gnext<PREC>(c), phishift<PREC>(c), phicur<PREC>(c),
                                                          c->zc, step_seed(c));
     else
-      k_step_zm<PREC, 0><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), hnext<PREC>(c),
+      k_step_zm<PREC, QH, 0><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), hnext<PREC>(c),
                                                          gnext<PREC>(c), phishift<PREC>(c), phicur<PREC>(c),
                                                          c->zc, step_seed(c));
     // phicur now holds phi^t, the shift of the populations just written
@@ -186,18 +188,18 @@ void step_only(pfl_ctx* c) {
   }
   if (BGK || !c->idx32) {
     if (c->swapped)
-      k_step<PREC, 1, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
+      k_step<PREC, QH, 1, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
                                                        phishift<PREC>(c));
     else
-      k_step<PREC, 0, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
+      k_step<PREC, QH, 0, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
                                                        phishift<PREC>(c));
   } else {
     const unsigned nbm = blocks_for(c->geo.N, PFL_STEP_THREADS);
     if (c->swapped)
-      k_step_mrt<PREC, 1><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),
+      k_step_mrt<PREC, QH, 1><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),
                                                                     phicur<PREC>(c), phishift<PREC>(c), step_seed(c));
     else
-      k_step_mrt<PREC, 0><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),
+      k_step_mrt<PREC, QH, 0><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),
                                                                     phicur<PREC>(c), phishift<PREC>(c), step_seed(c));
   }
   c->swapped ^= 1;
@@ -206,38 +208,47 @@ void step_only(pfl_ctx* c) {
 
 // phi of the current state of a two-array context into the current buffer
 // (the same sum the next fused step forms in shared memory).
-template <int PREC>
+template <int PREC, int QH>
 void ensure_phi(pfl_ctx* c) {
   if (!c->zm || !c->stale) return;
-  k_phi32<PREC, 0><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phishift<PREC>(c),
+  k_phi32<PREC, QH, 0><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phishift<PREC>(c),
                                                                       phicur<PREC>(c));
   c->stale = false;
 }
 
 // completes a step: the phi pass in place, nothing for the fused step
-template <int PREC>
+template <int PREC, int QH>
 void after_step(pfl_ctx* c) {
-  if (!c->zm) launch_phi<PREC>(c);
+  if (!c->zm) launch_phi<PREC, QH>(c);
 }
 
-template <int PREC, int BGK>
+// one collide-stream launch in the context's collision mode
+template <int PREC, int QH>
+void step_any(pfl_ctx* c) {
+  if (c->p.collision == PFL_BGK)
+    step_only<PREC, QH, 1>(c);
+  else
+    step_only<PREC, QH, 0>(c);
+}
+
+template <int PREC, int QH>
 void launch_steps(pfl_ctx* c, int n) {
   for (int s = 0; s < n; ++s) {
-    step_only<PREC, BGK>(c);
-    after_step<PREC>(c);
+    step_any<PREC, QH>(c);
+    after_step<PREC, QH>(c);
   }
 }
 
 // Fresh populations carry zero shifts (init / import).  Zero buffer 1, make it
 // current so that launch_phi reads its shifts from it, and let launch_phi
 // write phi into buffer 0 and make that one current.
-template <int PREC>
+template <int PREC, int QH>
 pfl_status fresh_phi(pfl_ctx* c) {
   c->stale = false;
   c->cur = 1;
   CUDA_TRY(cudaMemsetAsync(phicur<PREC>(c), 0, c->geo.N * sizeof(typename Store<PREC>::PhiT), c->stream));
   c->swapped = 0;
-  launch_phi<PREC>(c);  // reads shifts from buffer 1 (zeros), writes phi into buffer 0, cur = 0
+  launch_phi<PREC, QH>(c);  // reads shifts from buffer 1 (zeros), writes phi into buffer 0, cur = 0
   CUDA_TRY(cudaGetLastError());
   return PFL_OK;
 }
@@ -253,27 +264,27 @@ void launch_fields(pfl_ctx* c, double* o[6]) {
                                                   o[1], o[2], o[3], o[4], o[5]);
 }
 
-template <int PREC>
-void launch_export(pfl_ctx* c, int q, int i, double* out) {
+template <int PREC, int QH>
+void launch_export(pfl_ctx* c, int is_g, int i, double* out) {
   const unsigned nb = blocks_for(c->geo.N, 256);
-  const typename Store<PREC>::S* f = (q == 27) ? gbuf<PREC>(c) : hbuf<PREC>(c);
+  const typename Store<PREC>::S* f = is_g ? gbuf<PREC>(c) : hbuf<PREC>(c);
   if (c->swapped)
-    k_export<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), q, i, out);
+    k_export<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), is_g, i, out);
   else
-    k_export<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), q, i, out);
+    k_export<PREC, QH, 0><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), is_g, i, out);
 }
 
-template <int PREC>
-void launch_import(pfl_ctx* c, int q, int i, const double* in) {
+template <int PREC, int QH>
+void launch_import(pfl_ctx* c, int is_g, int i, const double* in) {
   const unsigned nb = blocks_for(c->geo.N, 256);
-  typename Store<PREC>::S* f = (q == 27) ? gbuf<PREC>(c) : hbuf<PREC>(c);
-  k_import<PREC><<<nb, 256, 0, c->stream>>>(c->geo, f, q, i, in);
+  typename Store<PREC>::S* f = is_g ? gbuf<PREC>(c) : hbuf<PREC>(c);
+  k_import<PREC, QH><<<nb, 256, 0, c->stream>>>(c->geo, f, is_g, i, in);
 }
 
-template <int PREC>
+template <int PREC, int QH>
 void launch_init(pfl_ctx* c, long long c0, long long count, const double* phi0, const double* ux, const double* uy,
                  const double* uz, const double* p0) {
-  k_init<PREC><<<blocks_for(count, 256), 256, 0, c->stream>>>(c->geo, hbuf<PREC>(c), gbuf<PREC>(c), c0, count, phi0,
+  k_init<PREC, QH><<<blocks_for(count, 256), 256, 0, c->stream>>>(c->geo, hbuf<PREC>(c), gbuf<PREC>(c), c0, count, phi0,
                                                                ux, uy, uz, p0);
 }
 
@@ -290,6 +301,34 @@ void launch_diag(pfl_ctx* c, double* part, double* out) {
       case PFL_FP32: fn<1>(__VA_ARGS__); break;   \
       default: fn<2>(__VA_ARGS__); break;         \
     }                                             \
+  } while (0)
+
+// fn<PREC, QH>(...) for the context's precision and phase-field lattice
+#define DISPATCH(c, fn, ...)                                                  \
+  do {                                                                        \
+    const bool q27_ = (c)->qh == 27;                                          \
+    switch ((c)->p.precision) {                                               \
+      case PFL_FP64:                                                          \
+        if (q27_) fn<0, 27>(__VA_ARGS__); else fn<0, 15>(__VA_ARGS__);        \
+        break;                                                                \
+      case PFL_FP32:                                                          \
+        if (q27_) fn<1, 27>(__VA_ARGS__); else fn<1, 15>(__VA_ARGS__);        \
+        break;                                                                \
+      default:                                                                \
+        if (q27_) fn<2, 27>(__VA_ARGS__); else fn<2, 15>(__VA_ARGS__);        \
+        break;                                                                \
+    }                                                                         \
+  } while (0)
+
+// s = fn<PREC, QH>(...)
+#define DISPATCH_S(s, c, fn, ...)                                             \
+  do {                                                                        \
+    const bool q27_ = (c)->qh == 27;                                          \
+    switch ((c)->p.precision) {                                               \
+      case PFL_FP64: s = q27_ ? fn<0, 27>(__VA_ARGS__) : fn<0, 15>(__VA_ARGS__); break; \
+      case PFL_FP32: s = q27_ ? fn<1, 27>(__VA_ARGS__) : fn<1, 15>(__VA_ARGS__); break; \
+      default: s = q27_ ? fn<2, 27>(__VA_ARGS__) : fn<2, 15>(__VA_ARGS__); break;       \
+    }                                                                         \
   } while (0)
 
 // Copy n doubles from a host or device source into the device at dst.
@@ -340,6 +379,7 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
   c->zm = uses_two_arrays(p);
   c->ab = 0;
   c->stale = false;
+  c->qh = qh_of(p);
   {
     // z planes per block.  Every block marches zc planes and fills two more
     // (the planes below and above its first) before it starts, about half a
@@ -349,11 +389,11 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     const dim3 blk(ZM_TX, ZM_TY);
     if (p->precision == PFL_FP64)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_zm<0, 0>, (int)(blk.x * blk.y), 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_zm<0, 15, 0>, (int)(blk.x * blk.y), 0);
     else if (p->precision == PFL_FP32)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_zm<1, 0>, (int)(blk.x * blk.y), 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_zm<1, 15, 0>, (int)(blk.x * blk.y), 0);
     else
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_zm<2, 0>, (int)(blk.x * blk.y), 0);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_zm<2, 15, 0>, (int)(blk.x * blk.y), 0);
     if (per_sm < 1) per_sm = 1;
     const long long slots = (long long)sms * per_sm;
     const long long bxy = (long long)((p->nx + ZM_TX - 1) / ZM_TX) * ((p->ny + ZM_TY - 1) / ZM_TY);
@@ -428,7 +468,7 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
         return s;
       }
     }
-    DISPATCH_PREC(c, launch_init, c, c0, cnt, a_phi, u0 ? a_ux : nullptr, u0 ? a_uy : nullptr, u0 ? a_uz : nullptr,
+    DISPATCH(c, launch_init, c, c0, cnt, a_phi, u0 ? a_ux : nullptr, u0 ? a_uy : nullptr, u0 ? a_uz : nullptr,
                   p0 ? a_p : nullptr);
     // the staging area is reused by the next chunk: wait for this one
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -439,11 +479,7 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
     }
   }
   pfl_status s = PFL_OK;
-  switch (c->p.precision) {
-    case PFL_FP64: s = fresh_phi<0>(c); break;
-    case PFL_FP32: s = fresh_phi<1>(c); break;
-    default: s = fresh_phi<2>(c); break;
-  }
+  DISPATCH_S(s, c, fresh_phi, c);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (s != PFL_OK || e != cudaSuccess) {
     delete c;
@@ -458,12 +494,7 @@ pfl_status pfl_step(pfl_ctx* c, int n) {
   CUDA_TRY(cudaSetDevice(c->device));
   if (n < 0) return fail(PFL_ERR_ARG, "n_steps must be >= 0");
   if (n == 0) return PFL_OK;
-  const bool bgk = c->p.collision == PFL_BGK;
-  switch (c->p.precision) {
-    case PFL_FP64: bgk ? launch_steps<0, 1>(c, n) : launch_steps<0, 0>(c, n); break;
-    case PFL_FP32: bgk ? launch_steps<1, 1>(c, n) : launch_steps<1, 0>(c, n); break;
-    default: bgk ? launch_steps<2, 1>(c, n) : launch_steps<2, 0>(c, n); break;
-  }
+  DISPATCH(c, launch_steps, c, n);
   CUDA_TRY(cudaGetLastError());
   return PFL_OK;
 }
@@ -480,7 +511,7 @@ pfl_status pfl_fields(pfl_ctx* c, double* phi, double* rho, double* p, double* u
     if (want[k] && !host[k]) dev[k] = want[k];
   }
   // device outputs in one pass
-  DISPATCH_PREC(c, ensure_phi, c);
+  DISPATCH(c, ensure_phi, c);
   bool any_dev = false;
   for (int k = 0; k < 6; ++k) any_dev |= dev[k] != nullptr;
   if (any_dev) DISPATCH_PREC(c, launch_fields, c, dev);
@@ -502,16 +533,16 @@ pfl_status pfl_fields(pfl_ctx* c, double* phi, double* rho, double* p, double* u
 pfl_status pfl_populations(pfl_ctx* c, double* h, double* g) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
   CUDA_TRY(cudaSetDevice(c->device));
-  DISPATCH_PREC(c, ensure_phi, c);
+  DISPATCH(c, ensure_phi, c);
   const long long N = c->geo.N;
   for (int set = 0; set < 2; ++set) {
     double* dst = set == 0 ? h : g;
     if (!dst) continue;
-    const int q = set == 0 ? 15 : 27;
+    const int q = set == 0 ? c->qh : 27;
     const bool dev = is_device_ptr(dst);
     for (int i = 0; i < q; ++i) {
       double* o = dev ? dst + (size_t)i * N : stage(c);
-      DISPATCH_PREC(c, launch_export, c, q, i, o);
+      DISPATCH(c, launch_export, c, set, i, o);
       CUDA_TRY(cudaGetLastError());
       if (!dev) {
         CUDA_TRY(cudaMemcpyAsync(dst + (size_t)i * N, o, N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -532,20 +563,16 @@ pfl_status pfl_set_populations(pfl_ctx* c, const double* h, const double* g) {
   // needed, both sets are replaced; the layout becomes the normal one.
   for (int set = 0; set < 2; ++set) {
     const double* src = set == 0 ? h : g;
-    const int q = set == 0 ? 15 : 27;
+    const int q = set == 0 ? c->qh : 27;
     for (int i = 0; i < q; ++i) {
       CUDA_TRY(cudaMemcpyAsync(stage(c), src + (size_t)i * N, N * sizeof(double), cudaMemcpyDefault, c->stream));
-      DISPATCH_PREC(c, launch_import, c, q, i, stage(c));
+      DISPATCH(c, launch_import, c, set, i, stage(c));
       CUDA_TRY(cudaGetLastError());
       CUDA_TRY(cudaStreamSynchronize(c->stream));
     }
   }
   pfl_status s = PFL_OK;
-  switch (c->p.precision) {
-    case PFL_FP64: s = fresh_phi<0>(c); break;
-    case PFL_FP32: s = fresh_phi<1>(c); break;
-    default: s = fresh_phi<2>(c); break;
-  }
+  DISPATCH_S(s, c, fresh_phi, c);
   if (s != PFL_OK) return s;
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PFL_OK;
@@ -556,7 +583,7 @@ pfl_status pfl_diag(pfl_ctx* c, double out[8], long long* nonfinite) {
   CUDA_TRY(cudaSetDevice(c->device));
   double* part = (double*)(c->ws + c->L.red);
   double* res = part + DIAG_BLOCKS * 9;
-  DISPATCH_PREC(c, ensure_phi, c);
+  DISPATCH(c, ensure_phi, c);
   DISPATCH_PREC(c, launch_diag, c, part, res);
   CUDA_TRY(cudaGetLastError());
   double host[9];
@@ -577,17 +604,12 @@ pfl_status pfl_kernel_times(pfl_ctx* c, int n, double ms[2]) {
   cudaEvent_t ev[3];
   for (int k = 0; k < 3; ++k) CUDA_TRY(cudaEventCreate(&ev[k]));
   double acc[2] = {0, 0};
-  const bool bgk = c->p.collision == PFL_BGK;
   pfl_status st = PFL_OK;
   for (int s = 0; s < n && st == PFL_OK; ++s) {
     cudaEventRecord(ev[0], c->stream);
-    switch (c->p.precision) {
-      case PFL_FP64: bgk ? step_only<0, 1>(c) : step_only<0, 0>(c); break;
-      case PFL_FP32: bgk ? step_only<1, 1>(c) : step_only<1, 0>(c); break;
-      default: bgk ? step_only<2, 1>(c) : step_only<2, 0>(c); break;
-    }
+    DISPATCH(c, step_any, c);
     cudaEventRecord(ev[1], c->stream);
-    DISPATCH_PREC(c, after_step, c);
+    DISPATCH(c, after_step, c);
     cudaEventRecord(ev[2], c->stream);
     cudaError_t e = cudaEventSynchronize(ev[2]);
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -629,7 +651,8 @@ AdjLayout adj_layout(const pfl_ctx* c, int n) {
   AdjLayout A;
   const size_t N = (size_t)c->geo.N;
   const size_t S = pop_bytes(c->p.precision), P = phi_bytes(c->p.precision), R = rbytes(c->p.precision);
-  A.state = align256(15 * N * S) + align256(27 * N * S) + align256(N * P);
+  const size_t QH = (size_t)c->qh;
+  A.state = align256(QH * N * S) + align256(27 * N * S) + align256(N * P);
   A.K = 1;
   while ((long long)A.K * A.K < n) ++A.K;
   A.nck = (n + A.K - 1) / A.K;
@@ -642,9 +665,9 @@ AdjLayout adj_layout(const pfl_ctx* c, int n) {
   A.fin = off;
   if (!c->zm) off += A.state;  // the fused engine's reverse sweep leaves the live state alone
   A.lam0 = off;
-  off = align256(off + 42 * N * R);
+  off = align256(off + (QH + 27) * N * R);
   A.lam1 = off;
-  off = align256(off + 42 * N * R);
+  off = align256(off + (QH + 27) * N * R);
   A.aux = off;
   off = align256(off + 5 * N * R);
   A.acc = off;
@@ -668,7 +691,7 @@ struct Saved {
 pfl_status copy_state(pfl_ctx* c, char* slot, bool save) {
   const size_t N = (size_t)c->geo.N;
   const size_t S = pop_bytes(c->p.precision), P = phi_bytes(c->p.precision);
-  const size_t hb = 15 * N * S, gb = 27 * N * S, pb = N * P;
+  const size_t hb = (size_t)c->qh * N * S, gb = 27 * N * S, pb = N * P;
   const bool second = c->zm && c->ab;
   char* live[3] = {c->ws + (second ? c->L.h2 : c->L.h), c->ws + (second ? c->L.g2 : c->L.g),
                    c->ws + c->L.phi[c->cur]};
@@ -687,26 +710,26 @@ void launch_dot(pfl_ctx* c, const double* W, double* part, double* out) {
   k_sum_parts<<<1, 32, 0, c->stream>>>(part, DOT_BLOCKS, 1, out);
 }
 
-template <int PREC>
+template <int PREC, int QH>
 void launch_adj_step(pfl_ctx* c, const AdjLayout& A, char* aws, char* slot, int swapped, const void* lam_in,
                      void* lam_out, const double* W) {
   typedef typename Store<PREC>::R R;
   const size_t N = (size_t)c->geo.N;
   const size_t S = pop_bytes(c->p.precision);
   const typename Store<PREC>::S* h = (const typename Store<PREC>::S*)slot;
-  const typename Store<PREC>::S* g = (const typename Store<PREC>::S*)(slot + align256(15 * N * S));
+  const typename Store<PREC>::S* g = (const typename Store<PREC>::S*)(slot + align256((size_t)QH * N * S));
   const typename Store<PREC>::PhiT* phi =
-      (const typename Store<PREC>::PhiT*)(slot + align256(15 * N * S) + align256(27 * N * S));
+      (const typename Store<PREC>::PhiT*)(slot + align256((size_t)QH * N * S) + align256(27 * N * S));
   AdjPar ap{c->p.mobility, c->p.xi, c->p.sigma};
   double* part = (double*)(aws + A.part);
   R* aux = (R*)(aws + A.aux);
   R* acc = (R*)(aws + A.acc);
   const unsigned nb = blocks_for(c->geo.N, ADJ_THREADS);
   if (swapped)
-    k_adj_local<PREC, 1><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
+    k_adj_local<PREC, QH, 1><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
                                                              acc, (R*)lam_out, aux, part);
   else
-    k_adj_local<PREC, 0><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
+    k_adj_local<PREC, QH, 0><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
                                                              acc, (R*)lam_out, aux, part);
   const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
   k_adj_phi<R><<<grid, dim3(ZM_TX, ZM_TY), 0, c->stream>>>(c->g32, aux, acc, W, c->zc);
@@ -715,11 +738,10 @@ void launch_adj_step(pfl_ctx* c, const AdjLayout& A, char* aws, char* slot, int 
 // lambda at the final time: local part 0, acc = W (the objective's weight on
 // phi, which the h entries share)
 template <typename R>
-__global__ void k_lam_init(unsigned N, R* __restrict__ lam, R* __restrict__ acc, const double* __restrict__ W) {
+__global__ void k_lam_init(unsigned N, int q, R* __restrict__ lam, R* __restrict__ acc, const double* __restrict__ W) {
   const unsigned x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= N) return;
-#pragma unroll
-  for (int i = 0; i < 42; ++i) lam[(unsigned)i * N + x] = (R)0;
+  for (int i = 0; i < q; ++i) lam[(unsigned)i * N + x] = (R)0;
   acc[x] = W ? (R)W[x] : (R)0;
 }
 
@@ -732,21 +754,22 @@ struct SlotPtr {
   SlotPtr(const pfl_ctx* c, char* slot) {
     const size_t N = (size_t)c->geo.N, S = pop_bytes(c->p.precision);
     h = (typename Store<PREC>::S*)slot;
-    g = (typename Store<PREC>::S*)(slot + align256(15 * N * S));
-    phi = (typename Store<PREC>::PhiT*)(slot + align256(15 * N * S) + align256(27 * N * S));
+    const size_t hb = (size_t)c->qh * N * S;
+    g = (typename Store<PREC>::S*)(slot + align256(hb));
+    phi = (typename Store<PREC>::PhiT*)(slot + align256(hb) + align256(27 * N * S));
   }
 };
 
 // One fused step from slot a into slot b; phi of a (the sum the kernel forms
 // in shared memory) goes to a's phi.  FP64 / FP32 only: no shifts.
-template <int PREC>
+template <int PREC, int QH>
 void zm_step_slots(pfl_ctx* c, const SlotPtr<PREC>& a, const SlotPtr<PREC>& b) {
   const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
   const dim3 block(ZM_TX, ZM_TY);
   if (c->p.nz == 1)
-    k_step_zm<PREC, 1><<<grid, block, 0, c->stream>>>(c->g32, c->ph, a.h, a.g, b.h, b.g, nullptr, a.phi, c->zc, 0u);
+    k_step_zm<PREC, QH, 1><<<grid, block, 0, c->stream>>>(c->g32, c->ph, a.h, a.g, b.h, b.g, nullptr, a.phi, c->zc, 0u);
   else
-    k_step_zm<PREC, 0><<<grid, block, 0, c->stream>>>(c->g32, c->ph, a.h, a.g, b.h, b.g, nullptr, a.phi, c->zc, 0u);
+    k_step_zm<PREC, QH, 0><<<grid, block, 0, c->stream>>>(c->g32, c->ph, a.h, a.g, b.h, b.g, nullptr, a.phi, c->zc, 0u);
 }
 
 // Adjoint with the fused two-array engine.  Forward sweep: checkpoints every K
@@ -754,7 +777,7 @@ void zm_step_slots(pfl_ctx* c, const SlotPtr<PREC>& a, const SlotPtr<PREC>& b) {
 // Reverse sweep, per segment: the checkpoint is copied into slot 0 and each
 // recomputed step writes the next slot directly, so the live state (t_end) is
 // never touched and no per-step copy is made.
-template <int PREC, class ObsAt>
+template <int PREC, int QH, class ObsAt>
 pfl_status run_adjoint_zm(pfl_ctx* c, int n, const ObsAt& obs_at, char* aws, const AdjLayout& A, double* J,
                           double grad[3]) {
   typedef typename Store<PREC>::R R;
@@ -763,15 +786,15 @@ pfl_status run_adjoint_zm(pfl_ctx* c, int n, const ObsAt& obs_at, char* aws, con
   double* dot_part = part + 3 * ((c->geo.N + ADJ_THREADS - 1) / ADJ_THREADS);
   for (int k = 0; k < n; ++k) {
     const double* W = obs_at(k);
-    if (k % A.K == 0 || W) ensure_phi<PREC>(c);
+    if (k % A.K == 0 || W) ensure_phi<PREC, QH>(c);
     if (k % A.K == 0) {
       pfl_status s = copy_state(c, aws + A.ck + (size_t)(k / A.K) * A.state, true);
       if (s != PFL_OK) return s;
     }
     if (W) launch_dot<PREC>(c, W, dot_part, res);
-    step_only<PREC, 0>(c);
+    step_only<PREC, QH, 0>(c);
   }
-  ensure_phi<PREC>(c);
+  ensure_phi<PREC, QH>(c);
   if (const double* W = obs_at(n)) launch_dot<PREC>(c, W, dot_part, res);
   CUDA_TRY(cudaGetLastError());
 
@@ -779,21 +802,21 @@ pfl_status run_adjoint_zm(pfl_ctx* c, int n, const ObsAt& obs_at, char* aws, con
   void* lam2 = aws + A.lam1;
   const unsigned nbl = blocks_for(c->geo.N, ADJ_THREADS);  // per-block gradient partials, summed at the end
   CUDA_TRY(cudaMemsetAsync(part, 0, 3 * (size_t)nbl * sizeof(double), c->stream));
-  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, (R*)lam,
+  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, c->qh + 27, (R*)lam,
                                                                    (R*)(aws + A.acc), obs_at(n));
   for (int sgm = A.nck - 1; sgm >= 0; --sgm) {
     const int k0 = sgm * A.K, k1 = (k0 + A.K < n) ? k0 + A.K : n;
     char* seg = aws + A.seg;
     CUDA_TRY(cudaMemcpyAsync(seg, aws + A.ck + (size_t)sgm * A.state, A.state, cudaMemcpyDeviceToDevice, c->stream));
     for (int k = k0; k + 1 < k1; ++k)
-      zm_step_slots<PREC>(c, SlotPtr<PREC>(c, seg + (size_t)(k - k0) * A.state),
+      zm_step_slots<PREC, QH>(c, SlotPtr<PREC>(c, seg + (size_t)(k - k0) * A.state),
                           SlotPtr<PREC>(c, seg + (size_t)(k + 1 - k0) * A.state));
     if (k1 - 1 > k0) {  // phi of the last slot (the others were formed by the steps out of them)
       const SlotPtr<PREC> last(c, seg + (size_t)(k1 - 1 - k0) * A.state);
-      k_phi32<PREC, 0><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(c->g32, last.h, nullptr, last.phi);
+      k_phi32<PREC, QH, 0><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(c->g32, last.h, nullptr, last.phi);
     }
     for (int k = k1 - 1; k >= k0; --k) {
-      launch_adj_step<PREC>(c, A, aws, seg + (size_t)(k - k0) * A.state, 0, lam, lam2, obs_at(k));
+      launch_adj_step<PREC, QH>(c, A, aws, seg + (size_t)(k - k0) * A.state, 0, lam, lam2, obs_at(k));
       std::swap(lam, lam2);
     }
     CUDA_TRY(cudaGetLastError());
@@ -808,7 +831,7 @@ pfl_status run_adjoint_zm(pfl_ctx* c, int n, const ObsAt& obs_at, char* aws, con
   return PFL_OK;
 }
 
-template <int PREC>
+template <int PREC, int QH>
 pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const double* const* Wd, char* aws,
                        const AdjLayout& A, double* J, double grad[3]) {
   typedef typename Store<PREC>::R R;
@@ -820,12 +843,12 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
       if (obs_steps[o] == k) return Wd[o];
     return nullptr;
   };
-  if (c->zm) return run_adjoint_zm<PREC>(c, n, obs_at, aws, A, J, grad);
+  if (c->zm) return run_adjoint_zm<PREC, QH>(c, n, obs_at, aws, A, J, grad);
   // several weights at one step are summed into the first by the caller side; here one per step
   const long long t0 = c->t;
   std::vector<int> ck_swapped(A.nck, 0), seg_swapped(A.K, 0);
   // forward sweep with checkpoints
-  ensure_phi<PREC>(c);
+  ensure_phi<PREC, QH>(c);
   for (int k = 0; k < n; ++k) {
     if (k % A.K == 0) {
       ck_swapped[k / A.K] = c->swapped;
@@ -835,9 +858,9 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
     if (const double* W = obs_at(k)) launch_dot<PREC>(c, W, part + 3 * ((c->geo.N + ADJ_THREADS - 1) / ADJ_THREADS), res);
     const bool bgk = false;
     (void)bgk;
-    step_only<PREC, 0>(c);
-    after_step<PREC>(c);
-    ensure_phi<PREC>(c);
+    step_only<PREC, QH, 0>(c);
+    after_step<PREC, QH>(c);
+    ensure_phi<PREC, QH>(c);
   }
   if (const double* W = obs_at(n)) launch_dot<PREC>(c, W, part + 3 * ((c->geo.N + ADJ_THREADS - 1) / ADJ_THREADS), res);
   const int fin_swapped = c->swapped;
@@ -851,7 +874,7 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
   void* lam2 = aws + A.lam1;
   const unsigned nbl = blocks_for(c->geo.N, ADJ_THREADS);  // per-block gradient partials, summed at the end
   CUDA_TRY(cudaMemsetAsync(part, 0, 3 * (size_t)nbl * sizeof(double), c->stream));
-  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, (R*)lam,
+  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, c->qh + 27, (R*)lam,
                                                                    (R*)(aws + A.acc), obs_at(n));
   for (int sgm = A.nck - 1; sgm >= 0; --sgm) {
     const int k0 = sgm * A.K, k1 = (k0 + A.K < n) ? k0 + A.K : n;
@@ -863,13 +886,13 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
       st = copy_state(c, aws + A.seg + (size_t)(k - k0) * A.state, true);
       if (st != PFL_OK) return st;
       if (k + 1 < k1) {  // the last state of the segment is never stepped from here
-        step_only<PREC, 0>(c);
-        after_step<PREC>(c);
-        ensure_phi<PREC>(c);
+        step_only<PREC, QH, 0>(c);
+        after_step<PREC, QH>(c);
+        ensure_phi<PREC, QH>(c);
       }
     }
     for (int k = k1 - 1; k >= k0; --k) {
-      launch_adj_step<PREC>(c, A, aws, aws + A.seg + (size_t)(k - k0) * A.state, seg_swapped[k - k0], lam, lam2,
+      launch_adj_step<PREC, QH>(c, A, aws, aws + A.seg + (size_t)(k - k0) * A.state, seg_swapped[k - k0], lam, lam2,
                             obs_at(k));
       std::swap(lam, lam2);
     }
@@ -931,8 +954,12 @@ pfl_status pfl_adjoint(pfl_ctx* c, int n_steps, int n_obs, const int* obs_steps,
     Wd[o] = dst;
   }
   switch (c->p.precision) {
-    case PFL_FP64: return run_adjoint<0>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
-    default: return run_adjoint<1>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
+    case PFL_FP64:
+      return c->qh == 27 ? run_adjoint<0, 27>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad)
+                         : run_adjoint<0, 15>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
+    default:
+      return c->qh == 27 ? run_adjoint<1, 27>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad)
+                         : run_adjoint<1, 15>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
   }
 }
 

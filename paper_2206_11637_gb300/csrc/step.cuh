@@ -256,7 +256,7 @@ struct GlobalPhi {
 // written to (hout, gout) in the layout WRITE_ODD (the same arrays and parity
 // for the in-place AA step; a second array pair and push streaming for the
 // two-array step).  phi_at(c) returns phi^t at the stencil neighbour c.
-template <int PREC, int READ_ODD, int WRITE_ODD, class PhiAt, int HM = 0>
+template <int PREC, int QH, int READ_ODD, int WRITE_ODD, class PhiAt, int HM = 0>
 __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, const CellOff& o,
                                              const typename Store<PREC>::S* hin,
                                              const typename Store<PREC>::S* gin, typename Store<PREC>::S* hout,
@@ -394,19 +394,19 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     hyz = hmom[8 * hstride];
     hxz = hmom[9 * hstride];
   } else {
-    const R rest = raw<PREC>(hin[7u * N + cell]);
-    phl = F16 ? (rest * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7) : rest;
+    const R rest = raw<PREC>(hin[(unsigned)hq_rest<QH>() * N + cell]);
+    phl = F16 ? (rest * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)hq_w<QH>(hq_rest<QH>()) : rest;
   }
 #pragma unroll
-  for (int k = 0; k < (HM ? 0 : 7); ++k) {
-    const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+  for (int k = 0; k < (HM ? 0 : hq_rest<QH>()); ++k) {
+    const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
     R a, b;
     unsigned fa, fb;
-    load_pair<PREC, READ_ODD>(hin, N, cell, o, k, 14 - k, cx, cy, cz, a, b, fa, fb);
+    load_pair<PREC, READ_ODD>(hin, N, cell, o, k, QH - 1 - k, cx, cy, cz, a, b, fa, fb);
     R S, D;
     if (F16) {
       const R sa = (R)__ldg(shift + fa), sb = (R)__ldg(shift + fb);
-      const R w = (R)q15_w(k);
+      const R w = (R)hq_w<QH>(k);
       S = w * ((a + b) * (R)(1.0 / KH16) + (sa + sb));
       D = w * ((a - b) * (R)(1.0 / KH16) + (sa - sb));
     } else {
@@ -442,10 +442,10 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     const R bz = K * ((R)3 * phl * uz + a1 * (hjz - phl * uz) + tn * gz);
     const R Gxx = K * a2 * dxx, Gyy = K * a2 * dyy, Gzz = K * a2 * dzz;
     const R Gxy = K * (R)2 * a2 * hxy, Gyz = K * (R)2 * a2 * hyz, Gxz = K * (R)2 * a2 * hxz;
-    hout[7u * N + cell] = pack_sr<PREC>(F16 ? al : (R)q15_w(7) * al, dith);
+    hout[(unsigned)hq_rest<QH>() * N + cell] = pack_sr<PREC>(F16 ? al : (R)hq_w<QH>(hq_rest<QH>()) * al, dith);
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+    for (int k = 0; k < hq_rest<QH>(); ++k) {
+      const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
       R E = al;
       if (cx) E += Gxx;
       if (cy) E += Gyy;
@@ -459,16 +459,16 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
       if (cz) L += cz > 0 ? bz : -bz;
       R A = E + L, B = E - L;
       if (!F16) {
-        A *= (R)q15_w(k);
-        B *= (R)q15_w(k);
+        A *= (R)hq_w<QH>(k);
+        B *= (R)hq_w<QH>(k);
       }
-      store_pair<PREC, WRITE_ODD>(hout, N, cell, o, k, 14 - k, cx, cy, cz, A, B, dith);
+      store_pair<PREC, WRITE_ODD>(hout, N, cell, o, k, QH - 1 - k, cx, cy, cz, A, B, dith);
     }
   }
 }
 
 // In-place AA update of one cell with the stencil read from the phi buffer.
-template <int PREC, int ODD>
+template <int PREC, int QH, int ODD>
 __device__ __forceinline__ void step_cell(const Geo32& geo, const Phys& ph, typename Store<PREC>::S* __restrict__ h,
                                           typename Store<PREC>::S* __restrict__ g,
                                           const typename Store<PREC>::PhiT* __restrict__ phi,
@@ -477,21 +477,21 @@ __device__ __forceinline__ void step_cell(const Geo32& geo, const Phys& ph, type
   CellOff o;
   cell_off(geo, cell, o);
   GlobalPhi<PREC> at{phi, &o, cell};
-  collide_cell<PREC, ODD, ODD>(geo, ph, o, h, g, h, g, at, shift, cell, seed);
+  collide_cell<PREC, QH, ODD, ODD>(geo, ph, o, h, g, h, g, at, shift, cell, seed);
 }
 
-template <int PREC, int ODD>
+template <int PREC, int QH, int ODD>
 __global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB)
     k_step_mrt(Geo32 geo, Phys ph, typename Store<PREC>::S* __restrict__ h, typename Store<PREC>::S* __restrict__ g,
                const typename Store<PREC>::PhiT* __restrict__ phi,
                const typename Store<PREC>::PhiT* __restrict__ shift, unsigned seed) {
   const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
-  step_cell<PREC, ODD>(geo, ph, h, g, phi, shift, cell, seed);
+  step_cell<PREC, QH, ODD>(geo, ph, h, g, phi, shift, cell, seed);
 }
 
 // phi of one cell from the stored h (READ_ODD after an even step).
-template <int PREC, int READ_ODD>
+template <int PREC, int QH, int READ_ODD>
 __device__ __forceinline__ typename Store<PREC>::R phi_cell(const Geo32& geo,
                                                             const typename Store<PREC>::S* __restrict__ h,
                                                             const typename Store<PREC>::PhiT* __restrict__ shift,
@@ -500,15 +500,15 @@ __device__ __forceinline__ typename Store<PREC>::R phi_cell(const Geo32& geo,
   constexpr bool F16 = PREC == 2;
   CellOff o;
   cell_off(geo, cell, o);
-  R s = F16 ? (raw<PREC>(h[7u * geo.N + cell]) * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7)
-            : raw<PREC>(h[7u * geo.N + cell]);
+  R s = F16 ? (raw<PREC>(h[(unsigned)hq_rest<QH>() * geo.N + cell]) * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)hq_w<QH>(hq_rest<QH>())
+            : raw<PREC>(h[(unsigned)hq_rest<QH>() * geo.N + cell]);
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
+  for (int k = 0; k < hq_rest<QH>(); ++k) {
     R a, b;
     unsigned fa, fb;
-    load_pair<PREC, READ_ODD>(h, geo.N, cell, o, k, 14 - k, q15_cx(k), q15_cy(k), q15_cz(k), a, b, fa, fb);
+    load_pair<PREC, READ_ODD>(h, geo.N, cell, o, k, QH - 1 - k, hq_cx<QH>(k), hq_cy<QH>(k), hq_cz<QH>(k), a, b, fa, fb);
     if (F16)
-      s += (R)q15_w(k) * ((a + b) * (R)(1.0 / KH16) + ((R)__ldg(shift + fa) + (R)__ldg(shift + fb)));
+      s += (R)hq_w<QH>(k) * ((a + b) * (R)(1.0 / KH16) + ((R)__ldg(shift + fa) + (R)__ldg(shift + fb)));
     else
       s += a + b;
   }
@@ -517,13 +517,13 @@ __device__ __forceinline__ typename Store<PREC>::R phi_cell(const Geo32& geo,
 
 // phi = sum_i h_i of the state left by the last step (READ_ODD after an even
 // step); `shift` holds the shifts of the stored populations (FP16S).
-template <int PREC, int READ_ODD>
+template <int PREC, int QH, int READ_ODD>
 __global__ void __launch_bounds__(256) k_phi32(Geo32 geo, const typename Store<PREC>::S* __restrict__ h,
                                                const typename Store<PREC>::PhiT* __restrict__ shift,
                                                typename Store<PREC>::PhiT* __restrict__ phi) {
   const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
-  phi[cell] = phi_cell<PREC, READ_ODD>(geo, h, shift, cell);
+  phi[cell] = phi_cell<PREC, QH, READ_ODD>(geo, h, shift, cell);
 }
 
 }  // namespace pfl
@@ -564,7 +564,7 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, int wall) {
 // The 10 h moments (phi, sum c h, sum c c h) of cell (x, y, z) of the current
 // pair (normal layout), accumulated by pairs in the same order as the
 // collision does, so moms[0] equals its phi bitwise.
-template <int PREC>
+template <int PREC, int QH>
 __device__ __forceinline__ void h_moments_xyz(const Geo32& geo, const typename Store<PREC>::S* __restrict__ h,
                                               const typename Store<PREC>::PhiT* __restrict__ shift, unsigned x,
                                               unsigned y, unsigned z, typename Store<PREC>::R m[10]) {
@@ -578,19 +578,19 @@ __device__ __forceinline__ void h_moments_xyz(const Geo32& geo, const typename S
   const unsigned N = geo.N;
   R phl, hjx = 0, hjy = 0, hjz = 0, hxx = 0, hyy = 0, hzz = 0, hxy = 0, hyz = 0, hxz = 0;
   {
-    const R rest = raw<PREC>(h[7u * N + cell]);
-    phl = F16 ? (rest * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7) : rest;
+    const R rest = raw<PREC>(h[(unsigned)hq_rest<QH>() * N + cell]);
+    phl = F16 ? (rest * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)hq_w<QH>(hq_rest<QH>()) : rest;
   }
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    const int cx = q15_cx(k), cy = q15_cy(k), cz = q15_cz(k);
+  for (int k = 0; k < hq_rest<QH>(); ++k) {
+    const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
     R a, b;
     unsigned fa, fb;
-    load_pair<PREC, 0>(h, N, cell, o, k, 14 - k, cx, cy, cz, a, b, fa, fb);
+    load_pair<PREC, 0>(h, N, cell, o, k, QH - 1 - k, cx, cy, cz, a, b, fa, fb);
     R S, D;
     if (F16) {
       const R sa = (R)__ldg(shift + fa), sb = (R)__ldg(shift + fb);
-      const R w = (R)q15_w(k);
+      const R w = (R)hq_w<QH>(k);
       S = w * ((a + b) * (R)(1.0 / KH16) + (sa + sb));
       D = w * ((a - b) * (R)(1.0 / KH16) + (sa - sb));
     } else {
@@ -622,7 +622,7 @@ __device__ __forceinline__ void h_moments_xyz(const Geo32& geo, const typename S
 
 // phi at cell (x, y, z) of the current pair (normal layout), same sum as the
 // phi pass.
-template <int PREC>
+template <int PREC, int QH>
 __device__ __forceinline__ typename Store<PREC>::R phi_at_xyz(const Geo32& geo,
                                                               const typename Store<PREC>::S* __restrict__ h,
                                                               const typename Store<PREC>::PhiT* __restrict__ shift,
@@ -634,15 +634,15 @@ __device__ __forceinline__ typename Store<PREC>::R phi_at_xyz(const Geo32& geo,
   o.Y = axis_off(y, geo.ny, (int)geo.nx, geo.wall[1]);
   o.Z = axis_off(z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
   const unsigned cell = x + geo.nx * (y + geo.ny * z);
-  R s = F16 ? (raw<PREC>(h[7u * geo.N + cell]) * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)q15_w(7)
-            : raw<PREC>(h[7u * geo.N + cell]);
+  R s = F16 ? (raw<PREC>(h[(unsigned)hq_rest<QH>() * geo.N + cell]) * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)hq_w<QH>(hq_rest<QH>())
+            : raw<PREC>(h[(unsigned)hq_rest<QH>() * geo.N + cell]);
 #pragma unroll
-  for (int k = 0; k < 7; ++k) {
+  for (int k = 0; k < hq_rest<QH>(); ++k) {
     R a, b;
     unsigned fa, fb;
-    load_pair<PREC, 0>(h, geo.N, cell, o, k, 14 - k, q15_cx(k), q15_cy(k), q15_cz(k), a, b, fa, fb);
+    load_pair<PREC, 0>(h, geo.N, cell, o, k, QH - 1 - k, hq_cx<QH>(k), hq_cy<QH>(k), hq_cz<QH>(k), a, b, fa, fb);
     if (F16)
-      s += (R)q15_w(k) * ((a + b) * (R)(1.0 / KH16) + ((R)__ldg(shift + fa) + (R)__ldg(shift + fb)));
+      s += (R)hq_w<QH>(k) * ((a + b) * (R)(1.0 / KH16) + ((R)__ldg(shift + fa) + (R)__ldg(shift + fb)));
     else
       s += a + b;
   }
@@ -667,7 +667,7 @@ __device__ __forceinline__ void frame_pos(int r, int W, int H, int& i, int& j) {
 }
 
 // grid: (ceil(nx / ZM_TX), ceil(ny / ZM_TY), ceil(nz / zc)), block ZM_TX x ZM_TY.
-template <int PREC, int FLAT>
+template <int PREC, int QH, int FLAT>
 __global__ void __launch_bounds__(ZM_TX * ZM_TY, PREC == 0 ? PFL_ZM_MINB_FP64 : PFL_ZM_MINB)
     k_step_zm(Geo32 geo, Phys ph, const typename Store<PREC>::S* __restrict__ hA,
               const typename Store<PREC>::S* __restrict__ gA, typename Store<PREC>::S* __restrict__ hB,
@@ -704,11 +704,11 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, PREC == 0 ? PFL_ZM_MINB_FP64 : 
   auto fill = [&](int zp, int slot, int mslot) {
     const unsigned zq = (unsigned)wrap_or_clamp(zp, (int)geo.nz, geo.wall[2]);
     R m[10];
-    h_moments_xyz<PREC>(geo, hA, phi_shift, xq, yq, zq, m);
+    h_moments_xyz<PREC, QH>(geo, hA, phi_shift, xq, yq, zq, m);
     ring[slot][(ty + 1) * PW + tx + 1] = (PhiT)m[0];
 #pragma unroll
     for (int k = 0; k < 10; ++k) hmom[mslot][k * NT + tid] = m[k];
-    if (tid < NRING) ring[slot][rj * PW + ri] = (PhiT)phi_at_xyz<PREC>(geo, hA, phi_shift, rxq, ryq, zq);
+    if (tid < NRING) ring[slot][rj * PW + ri] = (PhiT)phi_at_xyz<PREC, QH>(geo, hA, phi_shift, rxq, ryq, zq);
   };
 
   if (FLAT) {
@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, PREC == 0 ? PFL_ZM_MINB_FP64 : 
       // with one z plane the z neighbours are the plane itself (periodic or mirrored)
       at.i0 = (ty + 1) * PW + (tx + 1);
       phi_out[cell] = (PhiT)at(0, 0, 0);
-      collide_cell<PREC, 0, 1, SmemPhi<PREC>, 1>(geo, ph, o, hA, gA, hB, gB, at, phi_shift, cell, seed,
+      collide_cell<PREC, QH, 0, 1, SmemPhi<PREC>, 1>(geo, ph, o, hA, gA, hB, gB, at, phi_shift, cell, seed,
                                                  &hmom[FLAT ? 0 : ((z - z0) & 1)][tid], NT);
     }
     if (NS == 3) __syncthreads();

@@ -24,6 +24,7 @@ def _params_struct(p, precision):
     s.precision = int(precision)
     s.collision = int(p.collision)
     s.engine = int(getattr(p, "engine", 0))
+    s.h_lattice = int(getattr(p, "h_lattice", 15))
     return s
 
 
@@ -156,8 +157,13 @@ class Simulation:
         L.check(self.lib.pfl_fields(self.ctx, _ptr(phi), None, None, None))
         return phi
 
+    @property
+    def qh(self):
+        """Velocities of the phase-field lattice (15 or 27)."""
+        return 27 if self._params.h_lattice == 27 else 15
+
     def populations(self):
-        h = np.empty((15,) + self.shape)
+        h = np.empty((self.qh,) + self.shape)
         g = np.empty((27,) + self.shape)
         L.check(self.lib.pfl_populations(self.ctx, _ptr(h), _ptr(g)))
         return h, g
@@ -165,6 +171,8 @@ class Simulation:
     def set_populations(self, h, g):
         h = np.ascontiguousarray(h, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
+        if h.size != self.qh * self.N or g.size != 27 * self.N:
+            raise ValueError("populations must hold %d h and 27 g values per cell" % self.qh)
         L.check(self.lib.pfl_set_populations(self.ctx, _ptr(h), _ptr(g)))
 
     def diag(self, check=True):

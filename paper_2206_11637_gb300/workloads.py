@@ -34,6 +34,7 @@ class Params:
     gravity: tuple = (0.0, 0.0, 0.0)
     collision: int = 0                    # 0 weighted-orthogonal MRT, 1 BGK
     engine: int = 0                       # 0 auto (fused two-array step), 1 in-place AA + phi pass
+    h_lattice: int = 15                   # phase-field lattice: 15 (D3Q15) or 27 (D3Q27)
 
     @property
     def shape(self):

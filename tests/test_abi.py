@@ -36,8 +36,21 @@ def test_workspace_size(lib):
     assert b16 < b32 < b64
 
 
+def test_workspace_grows_with_the_phase_field_lattice(lib):
+    p, _, _, _ = W.static_drop(16, 5.0)
+    n = p.cells
+    for prec, s in ((L.PFL_FP64, 8), (L.PFL_FP32, 4), (L.PFL_FP16S, 2)):
+        b15 = pflbm.workspace_bytes(p, prec)
+        p.h_lattice = 27
+        b27 = pflbm.workspace_bytes(p, prec)
+        p.h_lattice = 15
+        # two array pairs (fused engine): 2 x 12 more h populations per cell
+        assert b27 - b15 >= 2 * 12 * n * s
+        assert b27 - b15 < 2 * 12 * n * s + 4096
+
+
 @pytest.mark.parametrize("field,value", [("mobility", 0.0), ("xi", -1.0), ("rho_l", 0.0), ("nu_h", -0.2),
-                                         ("nu_l", -0.1), ("nx", 0)])
+                                         ("nu_l", -0.1), ("nx", 0), ("h_lattice", 19)])
 def test_rejects_bad_parameters(lib, field, value):
     p, phi0, _, _ = W.static_drop(8, 3.0)
     setattr(p, field, value)
@@ -61,3 +74,12 @@ def test_null_context_calls(lib):
     assert lib.pfl_fields(None, None, None, None, None) == L.PFL_ERR_ARG
     assert lib.pfl_time(None) == -1
     lib.pfl_destroy(None)
+
+
+def test_batch_takes_d3q15_instances_only(lib):
+    p, _, _, _ = W.static_drop(16, 5.0)
+    arr = (L.pfl_params * 1)(pflbm._params_struct(p, L.PFL_FP32))
+    assert lib.pfl_batch_workspace_bytes(arr, 1) > 0
+    p.h_lattice = 27
+    arr = (L.pfl_params * 1)(pflbm._params_struct(p, L.PFL_FP32))
+    assert lib.pfl_batch_workspace_bytes(arr, 1) == 0

@@ -1,0 +1,151 @@
+"""The D3Q27 phase-field lattice (the paper's own 3-D choice for h) on the GPU,
+against the FP64 oracle run on the same lattice, through the C-ABI.
+
+Same bars as the D3Q15 path: FP64 within 1e-10 (max relative error per field)
+after hundreds of steps, FP32 within 1e-5 and shifted FP16 within 1e-3 on phi;
+the population round trip; the fused and in-place engines bitwise equal; phi
+mass to 1e-12; and the FP64 adjoint equal to the oracle's exact forward-mode
+derivative within 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_11637_gb300 import objectives as O
+from paper_2206_11637_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+THREADS = 0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2206_11637_gb300 import build
+    build.build_library()
+
+
+def q27(built):
+    p, phi0, u0, p0 = built
+    p.h_lattice = 27
+    return p, phi0, u0, p0
+
+
+def sim(p, phi0, u0=None, p0=None, precision="fp64"):
+    from paper_2206_11637_gb300.pflbm import Simulation
+    return Simulation(p, phi0, u0, p0, precision=precision)
+
+
+def rel(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def ragged():
+    # 37 x 23 x 11 cells (not a multiple of any block), walls in y, gravity
+    p = W.Params(37, 23, 11, (0, 0, 1, 1, 0, 0), 1.0, 0.01, 0.02, 0.05, 2e-4, 0.03, 4.0, (1e-6, -2e-6, 0.0))
+    return p, W.sphere(p, (18.0, 11.0, 5.0), 6.0, heavy_inside=True), W.noise((3,) + p.shape, 99, 1e-3), None
+
+
+CASES = {
+    "static_drop_32": (lambda: W.static_drop(32, 10.0, u_noise=1e-3, seed=1234), 1000),
+    "wave_walls_y": (lambda: W.capillary_wave(40, ny=48, a0=1.5, xi=5.0, sigma=1e-4, nu=0.01), 400),
+    "bubble_all_walls": (lambda: W.rising_bubble(24, 40, 20, D=10.0, xi=4.0, M=0.05, hydrostatic=False), 200),
+    "ragged_gravity": (ragged, 97),
+}
+
+
+# Cases whose dynamics amplify rounding: the bar is the larger of 1e-10 and
+# four times the oracle's own spread when phi0 moves by 1e-16 (as for the
+# hydrostatic D3Q15 bubble in test_gpu_parity.py).
+AMPLIFYING = {"bubble_all_walls"}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fp64_parity_d3q27(name):
+    build, steps = CASES[name]
+    p, phi0, u0, p0 = q27(build())
+    s = sim(p, phi0, u0, p0, "fp64")
+    o = oracle.from_params(p, phi0, u0, p0)
+    s.step(steps)
+    o.step(steps, THREADS)
+    tol = 1e-10
+    if name in AMPLIFYING:
+        o2 = oracle.from_params(p, phi0 + 1e-16 * W.noise(phi0.shape, 7, 1.0), u0, p0)
+        o2.step(steps, THREADS)
+        tol = max(tol, 4 * rel(o2.fields()[0], o.fields()[0]))
+    phi, rho, pr, u = s.fields()
+    ophi, orho, opr, ou = o.fields()
+    e = {"phi": rel(phi, ophi), "u": rel(u, ou), "p": rel(pr, opr)}
+    assert max(e.values()) <= tol, (e, tol)
+    h, g = s.populations()
+    oh, og = o.populations()
+    assert h.shape[0] == 27
+    assert rel(h, oh) < tol and rel(g, og) < tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16s", 1e-3)])
+def test_reduced_precision_parity_d3q27(precision, tol):
+    p, phi0, u0, _ = q27(W.static_drop(32, 10.0, u_noise=1e-3, seed=1234))
+    s = sim(p, phi0, u0, None, precision)
+    o = oracle.from_params(p, phi0, u0, None)
+    s.step(1000)
+    o.step(1000, THREADS)
+    assert rel(s.fields()[0], o.fields()[0]) <= tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
+def test_population_roundtrip_d3q27(precision):
+    p, phi0, _, _ = q27(W.capillary_wave(48, ny=40, a0=2.0, xi=4.0, sigma=1e-3, nu=0.01))
+    o = oracle.from_params(p, phi0)
+    o.step(31, THREADS)
+    h, g = o.populations()
+    s = sim(p, phi0, None, None, precision)
+    s.set_populations(h, g)
+    h2, g2 = s.populations()
+    rt = {"fp64": 0.0, "fp32": 1e-7, "fp16s": 1e-3}[precision]
+    assert rel(h2, h) <= rt and rel(g2, g) <= rt * 10 + 1e-300
+    s.step(1)
+    o.set_populations(h2, g2)
+    o.step(1, THREADS)
+    tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16s": 1e-3}[precision]
+    assert rel(s.fields()[0], o.fields()[0]) <= tol
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
+def test_engines_agree_bitwise_d3q27(precision):
+    out = []
+    for engine in (0, 1):
+        p, phi0, u0, p0 = q27(W.rising_bubble(20, 36, 20, D=10.0, xi=4.0, M=0.05))
+        p.engine = engine
+        s = sim(p, phi0, u0, p0, precision)
+        s.step(37)
+        out.append((s.fields(), s.populations()))
+    for a, b in zip(out[0][0], out[1][0]):
+        assert np.array_equal(a, b)
+    for a, b in zip(out[0][1], out[1][1]):
+        assert np.array_equal(a, b)
+
+
+def test_mass_conservation_d3q27():
+    p, phi0, u0, _ = q27(W.static_drop(32, 10.0, u_noise=1e-3, seed=1234))
+    s = sim(p, phi0, u0, None, "fp64")
+    m0 = s.mass()
+    s.step(1000)
+    out, nf = s.diag()
+    assert nf == 0 and abs(out[0] - m0) / m0 < 1e-12
+
+
+def test_adjoint_matches_oracle_tangent_d3q27():
+    from paper_2206_11637_gb300.pflbm import Simulation
+    p, phi0, u0, p0 = q27(W.rising_bubble(20, 36, 20, D=10.0, xi=4.0, M=0.05))
+    n = 50
+    obs = O.rise_velocity_weights(p, phi0, 20, n)
+    J, g = Simulation(p, phi0, u0, p0, precision="fp64").adjoint(n, obs)
+    for k, name in enumerate(("mobility", "xi", "sigma")):
+        Jo, dJo = oracle.tangent(p, phi0, u0, p0, n, obs, name)
+        assert abs(J - Jo) <= 1e-10 * max(1e-12, abs(Jo))
+        assert abs(g[k] - dJo) <= 1e-6 * abs(dJo), (name, g[k], dJo)

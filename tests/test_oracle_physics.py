@@ -27,6 +27,9 @@ fixes, chosen so that a plausible mistake in one part fails one of them:
   symmetry        -- a centred drop stays mirror- and permutation-symmetric:
                      catches transposed components and index errors.
   BGK special case-- the full simulation with MRT rates all equal equals BGK.
+
+The phase-field pins run on both h lattices, D3Q15 and D3Q27 (the paper's
+own 3-D lattice).
 """
 import numpy as np
 import pytest
@@ -45,22 +48,27 @@ def run(p, phi0, u0=None, p0=None, n=0):
     return o
 
 
-def test_mass_conservation_3d_drop():
+@pytest.mark.parametrize("qh", [15, 27])
+def test_mass_conservation_3d_drop(qh):
     p, phi0, u0, _ = W.static_drop(24, 7.0, u_noise=1e-3, seed=1234)
+    p.h_lattice = qh
     o = run(p, phi0, u0, n=60)
     phi = o.fields()[0]
     assert abs(phi.sum() - phi0.sum()) / phi0.sum() < 1e-12
 
 
-def test_mass_conservation_walls():
+@pytest.mark.parametrize("qh", [15, 27])
+def test_mass_conservation_walls(qh):
     p, phi0, _, _ = W.capillary_wave(24, ny=24, a0=1.0, xi=4.0)
+    p.h_lattice = qh
     o = run(p, phi0, n=200)
     assert abs(o.fields()[0].sum() - phi0.sum()) / phi0.sum() < 1e-12
 
 
-def test_diffusion_rate_is_mobility():
+@pytest.mark.parametrize("qh", [15, 27])
+def test_diffusion_rate_is_mobility(qh):
     M = 0.05
-    p = W.Params(64, 1, 1, (0,) * 6, 1.0, 1.0, 1 / 6, 1 / 6, 0.0, M, 1e9)
+    p = W.Params(64, 1, 1, (0,) * 6, 1.0, 1.0, 1 / 6, 1 / 6, 0.0, M, 1e9, h_lattice=qh)
     x = np.arange(64.0)
     k = 2 * np.pi / 64
     phi0 = (0.5 + 0.1 * np.sin(k * x)).reshape(1, 1, 64)
@@ -71,8 +79,9 @@ def test_diffusion_rate_is_mobility():
     assert abs(D_measured / M - 1) < 0.01
 
 
-def test_advection_speed():
-    p = W.Params(128, 1, 1, (0,) * 6, 1.0, 1e-3, 1 / 6, 1 / 6, 1e-4, 0.02, 5.0)
+@pytest.mark.parametrize("qh", [15, 27])
+def test_advection_speed(qh):
+    p = W.Params(128, 1, 1, (0,) * 6, 1.0, 1e-3, 1 / 6, 1 / 6, 1e-4, 0.02, 5.0, h_lattice=qh)
     xx = np.arange(128.0)
     phi0 = W.tanh_profile(np.abs(xx - 40.0) - 15.0, 5.0).reshape(1, 1, 128)
     u0 = np.zeros((3, 1, 1, 128))
@@ -82,9 +91,11 @@ def test_advection_speed():
     assert abs((centre - 40.0) / 20.0 - 1) < 5e-3
 
 
-def test_flat_interface_keeps_tanh_width():
+@pytest.mark.parametrize("qh", [15, 27])
+def test_flat_interface_keeps_tanh_width(qh):
     xi = 5.0
     p, phi0, _, _ = W.flat_interface(64, xi=xi)
+    p.h_lattice = qh
     phi = run(p, phi0, n=3000).fields()[0][0, :, 0]
     f = lambda y, y0, w: 0.5 - 0.5 * np.tanh((y - y0) / (w / 2))
     (y0, w), _ = curve_fit(f, np.arange(64.0), phi, p0=[31.5, xi])
@@ -92,9 +103,11 @@ def test_flat_interface_keeps_tanh_width():
     assert abs(y0 - 31.5) < 1e-4
 
 
-def test_laplace_pressure_column():
+@pytest.mark.parametrize("qh", [15, 27])
+def test_laplace_pressure_column(qh):
     R = 16.0
     p, phi0, _, _ = W.static_cylinder(64, R, nu=1 / 6)
+    p.h_lattice = qh
     _, _, pr, u = run(p, phi0, n=2500).fields()
     dp = pr[0, 30:34, 30:34].mean() - pr[0, 0:2, 0:2].mean()
     assert abs(dp / (p.sigma / R) - 1) < 0.02
@@ -147,9 +160,11 @@ def test_capillary_wave_half_period():
     assert -a0 < amps.min() < -0.5 * a0
 
 
-def test_drop_symmetry():
+@pytest.mark.parametrize("qh", [15, 27])
+def test_drop_symmetry(qh):
     n = 16
     p, phi0, _, _ = W.static_drop(n, 5.0)
+    p.h_lattice = qh
     # break the cubic symmetry only by a symmetric velocity along x
     u0 = np.zeros((3, n, n, n))
     x = np.arange(n) - (n - 1) / 2
@@ -166,8 +181,10 @@ def test_drop_symmetry():
     assert np.abs(u[1] - u[2].transpose(1, 0, 2)).max() < 1e-13
 
 
-def test_bgk_special_case_full_step():
+@pytest.mark.parametrize("qh", [15, 27])
+def test_bgk_special_case_full_step(qh):
     p, phi0, u0, _ = W.static_drop(12, 4.0, rho_ratio=10.0, u_noise=1e-3, seed=5)
+    p.h_lattice = qh
     a = run(p, phi0, u0, n=20)
     p.collision = oracle.COLL_BGK
     b = run(p, phi0, u0, n=20)
@@ -199,3 +216,4 @@ def test_two_layer_closed_form_reduces_to_poiseuille():
     a = A.two_layer_poiseuille(y, 32, 11.0, 1e-6, 1.0, 0.2, 1.0, 0.2)
     b = A.poiseuille(y, 32, 1e-6, 0.2)
     assert np.abs(a - b).max() < 1e-15
+
