@@ -179,7 +179,28 @@ struct Dither {
     r = r * 1664525u + 1013904223u;
     return r >> 19;
   }
+  // 32 bits for a pair: the state's high half, and the low half xor-ed with
+  // the high one (the low bits of a power-of-two LCG have short periods)
+  __device__ __forceinline__ unsigned next32() {
+    r = r * 1664525u + 1013904223u;
+    return r ^ (r >> 16);
+  }
 };
+
+// Stochastic rounding of a pair in one conversion (sm_100-family
+// cvt.rs.f16x2.f32): A lands in the high half and is rounded with the high 16
+// random bits, B in the low half with the low 16; each rounds away from zero
+// with the probability of its discarded fraction (an unbiased rounding, like
+// pack_sr).  PFL_FP16S_HWSR = 0 keeps pack_sr for every store.
+#ifndef PFL_FP16S_HWSR
+#define PFL_FP16S_HWSR 1
+#endif
+__device__ __forceinline__ void pack2_sr(float A, float B, unsigned bits, __half& a, __half& b) {
+  unsigned d;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(A), "f"(B), "r"(bits));
+  a = __ushort_as_half((unsigned short)(d >> 16));
+  b = __ushort_as_half((unsigned short)(d & 0xffffu));
+}
 
 template <int PREC>
 __device__ __forceinline__ typename Store<PREC>::S pack_sr(typename Store<PREC>::R v, Dither& d) {
@@ -227,8 +248,13 @@ template <int PREC, int ODD>
 __device__ __forceinline__ void store_pair(typename Store<PREC>::S* __restrict__ f, unsigned N, unsigned cell,
                                            const CellOff& o, int i, int oi, int cx, int cy, int cz,
                                            typename Store<PREC>::R A, typename Store<PREC>::R B, Dither& d) {
-  const typename Store<PREC>::S a = pack_sr<PREC>(A, d);
-  const typename Store<PREC>::S b = pack_sr<PREC>(B, d);
+  typename Store<PREC>::S a, b;
+  if constexpr (PREC == 2 && PFL_FP16S_HWSR) {
+    pack2_sr(A, B, d.next32(), a, b);
+  } else {
+    a = pack_sr<PREC>(A, d);
+    b = pack_sr<PREC>(B, d);
+  }
   if (!ODD) {
     f[(unsigned)oi * N + cell] = a;
     f[(unsigned)i * N + cell] = b;
