@@ -42,13 +42,13 @@ PREC_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 2}
 PHI_BYTES = {"fp64": 8, "fp32": 4, "fp16s": 4}
 
 
-def step_kernel_bytes(prec, engine=0, qh=15):
+def step_kernel_bytes(prec, engine=0, qh=15, qg=27):
     """Algorithmic bytes per cell of one stream-collide launch: every h and g
-    population read once and written once (qh = 15 or 27 h populations); the
+    population read once and written once (qh h and qg g populations); the
     fused two-array step (engine 0) also writes phi, the in-place step
     (engine 1) reads phi for its stencil; FP16S adds the read of the h shifts
     (phi of the writing cells)."""
-    b = 2 * (qh + 27) * PREC_BYTES[prec] + PHI_BYTES[prec]
+    b = 2 * (qh + qg) * PREC_BYTES[prec] + PHI_BYTES[prec]
     if prec == "fp16s":
         b += PHI_BYTES[prec]
     return b
@@ -333,7 +333,10 @@ CONFIG_LEGS = [("static_drop", "fp64", 1000),
                ("rising_bubble", "fp64", 20), ("rising_bubble", "fp32", 200), ("rising_bubble", "fp16s", 200),
                ("drop_impact", "fp32", 40), ("drop_impact", "fp16s", 40),
                # the paper's own phase-field lattice (D3Q27 h)
-               ("rising_bubble@d3q27", "fp32", 200), ("rising_bubble@d3q27", "fp16s", 200)]
+               ("rising_bubble@d3q27", "fp32", 200), ("rising_bubble@d3q27", "fp16s", 200),
+               # the paper's 2-D lattices (D2Q9 h and g) on the quasi-2-D wave
+               ("capillary_wave@d2q9", "fp64", 1000), ("capillary_wave@d2q9", "fp32", 2000),
+               ("capillary_wave@d2q9", "fp16s", 2000)]
 
 
 def config_table(dev, barrier):
@@ -353,7 +356,8 @@ def config_table(dev, barrier):
             cache[base] = workload(base)
         wl = cache[base]
         p = copy.copy(wl["p"])
-        qh = 27 if lat == "d3q27" else 15
+        qh = {"d3q27": 27, "d2q9": 9}.get(lat, 15)
+        qg = 9 if qh == 9 else 27
         p.h_lattice = qh
         sim = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision=prec, device=dev)
         sim.step(3)
@@ -367,8 +371,8 @@ def config_table(dev, barrier):
         _, nf = sim.diag(check=False)
         del sim
         r = mlups(p.cells, S, ms / 1e3)
-        bpc = step_kernel_bytes(prec, 0, qh)
-        work = p.cells * (2 * (qh + 27) * PREC_BYTES[prec] + 2 * PHI_BYTES[prec])
+        bpc = step_kernel_bytes(prec, 0, qh, qg)
+        work = p.cells * (2 * (qh + qg) * PREC_BYTES[prec] + 2 * PHI_BYTES[prec])
         rows.append({"workload": name, "cells": p.cells, "precision": prec, "lattice_steps": S, "mlups": r,
                      "bytes_per_cell": bpc, "hbm_frac": r * 1e6 * bpc / 1e9 / peak,
                      "l2_resident": work < L2_BYTES, "nonfinite_cells": nf})

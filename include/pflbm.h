@@ -86,8 +86,9 @@ typedef struct {
   int collision;       /* pfl_collision                                              */
   int engine;          /* pfl_engine                                                 */
   int h_lattice;       /* phase-field lattice: 15 (D3Q15; also when 0) or 27 (D3Q27, the
-                        * paper's own 3-D choice, section "Simulation setup" of the
-                        * models).  The h collision keeps its moment form on both. */
+                        * paper's own 3-D choice); 9 selects the paper's 2-D lattices,
+                        * D2Q9 for h and g, and needs nz = 1 with periodic z faces.
+                        * The collisions keep their moment form on every lattice. */
 } pfl_params;
 
 /* How a single lattice is stepped.  PFL_ENGINE_AUTO: the fused two-array step
@@ -122,8 +123,8 @@ pfl_status pfl_step(pfl_ctx* ctx, int n_steps);
 pfl_status pfl_fields(pfl_ctx* ctx, double* phi, double* rho, double* p, double* u);
 
 /* Populations at the current time in canonical order and layout, converted to
- * FP64: h is QN (Q = 15 or 27, the h lattice), g is 27N doubles (either may be
- * NULL; host or device).
+ * FP64: h is QN (Q = 15, 27 or 9, the h lattice), g is 27N doubles (9N on the
+ * 2-D lattices; either may be NULL; host or device).
  * Synchronises. */
 pfl_status pfl_populations(pfl_ctx* ctx, double* h, double* g);
 

@@ -76,7 +76,8 @@ class Oracle:
         self.lib = _load()
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
-        self.qh = 27 if h_lattice == 27 else 15
+        self.qh = {27: 27, 9: 9}.get(h_lattice, 15)
+        self.qg = 9 if self.qh == 9 else 27
         ip = np.array([nx, ny, nz] + list(bc) + [collision, self.qh], dtype=np.int32)
         dp = np.array([rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi] + list(gravity), dtype=np.float64)
         self._phi0 = _f64(phi0, self.N)
@@ -99,13 +100,13 @@ class Oracle:
 
     def populations(self):
         h = np.empty((self.qh,) + self.shape)
-        g = np.empty((27,) + self.shape)
+        g = np.empty((self.qg,) + self.shape)
         self.lib.ora_get_pops(self.h, _ptr(h), _ptr(g))
         return h, g
 
     def set_populations(self, h, g):
         h = _f64(h, self.qh * self.N)
-        g = _f64(g, 27 * self.N)
+        g = _f64(g, self.qg * self.N)
         self.lib.ora_set_pops(self.h, _ptr(h), _ptr(g))
 
     def fields(self):
@@ -156,7 +157,7 @@ def tangent(p, phi0, u0, p0, n, obs, param, threads=0):
     param is "mobility", "xi" or "sigma".  Returns (J, dJ)."""
     lib = _load()
     N = p.nx * p.ny * p.nz
-    qh = 27 if getattr(p, "h_lattice", 15) == 27 else 15
+    qh = {27: 27, 9: 9}.get(getattr(p, "h_lattice", 15), 15)
     ip = np.array([p.nx, p.ny, p.nz] + list(p.bc) + [p.collision, qh], dtype=np.int32)
     dp = np.array([p.rho_h, p.rho_l, p.nu_h, p.nu_l, p.sigma, p.mobility, p.xi] + list(p.gravity),
                   dtype=np.float64)

@@ -94,8 +94,9 @@ struct Lattice {
 };
 
 // Canonical velocity order: loop cz, cy, cx over -1, 0, 1 (cx fastest) and
-// keep the members of the set.  D3Q27 keeps all, D3Q15 keeps |c|^2 in {0,1,3}.
-void make_velocities(Lattice& L, bool q15) {
+// keep the members of the set.  D3Q27 keeps all, D3Q15 keeps |c|^2 in {0,1,3},
+// D2Q9 keeps cz = 0 (weights 4/9, 1/9, 1/36).
+void make_velocities(Lattice& L, bool q15, bool q9 = false) {
   L.c.clear();
   L.w.clear();
   for (int cz = -1; cz <= 1; ++cz)
@@ -103,7 +104,10 @@ void make_velocities(Lattice& L, bool q15) {
       for (int cx = -1; cx <= 1; ++cx) {
         int n2 = cx * cx + cy * cy + cz * cz;
         double w;
-        if (q15) {
+        if (q9) {
+          if (cz != 0) continue;
+          w = (n2 == 0) ? 4.0 / 9.0 : (n2 == 1) ? 1.0 / 9.0 : 1.0 / 36.0;
+        } else if (q15) {
           if (n2 == 2) continue;
           w = (n2 == 0) ? 2.0 / 9.0 : (n2 == 1) ? 1.0 / 9.0 : 1.0 / 72.0;
         } else {
@@ -188,6 +192,26 @@ Lattice make_d3q15() {
   return L;
 }
 
+Lattice make_d2q9() {
+  Lattice L;
+  make_velocities(L, false, true);
+  std::vector<int> mono;  // x^a y^b, a, b <= 2, by degree
+  for (int deg = 0; deg <= 4; ++deg)
+    for (int a = 0; a <= 2; ++a)
+      for (int b = 0; b <= 2; ++b)
+        if (a + b == deg) {
+          mono.push_back(a);
+          mono.push_back(b);
+          mono.push_back(0);
+        }
+  build_moments(L, mono);
+  return L;
+}
+
+const Lattice& Q9() {
+  static Lattice L = make_d2q9();
+  return L;
+}
 const Lattice& Q27() {
   static Lattice L = make_d3q27();
   return L;
@@ -204,7 +228,7 @@ struct Params {
   int nx, ny, nz;
   int bc[6];  // -x,+x,-y,+y,-z,+z : 0 periodic, 1 no-slip
   int collision;
-  int qh;     // phase-field lattice: 15 (D3Q15) or 27 (D3Q27)
+  int qh;     // phase-field lattice: 15 (D3Q15), 27 (D3Q27) or 9 (D2Q9, with D2Q9 for g)
   double rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, g[3];
 };
 
@@ -249,9 +273,12 @@ struct CellState {
   T Fs[3], Fb[3], Fp[3], Fmu[3];
 };
 
+// The hydrodynamic lattice: D2Q9 with the 2-D phase field, else D3Q27.
+const Lattice& g_lattice(const Params& P) { return P.qh == 9 ? Q9() : Q27(); }
+const Lattice& h_lattice(const Params& P) { return P.qh == 27 ? Q27() : (P.qh == 9 ? Q9() : Q15()); }
+
 template <typename T>
-void geq_of(T pstar, const T u[3], T* out) {
-  const Lattice& L = Q27();
+void geq_of(const Lattice& L, T pstar, const T u[3], T* out) {
   T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
   for (int i = 0; i < L.q; ++i) {
     T cu = L.c[3 * i] * u[0] + L.c[3 * i + 1] * u[1] + L.c[3 * i + 2] * u[2];
@@ -319,7 +346,7 @@ void mrt_relax(const Lattice& L, const T* d, const T* s, T* out) {
 template <typename T>
 void cell_macro(const Sim<T>& S, int x, int y, int z, const T* gcell, CellState<T>& cs) {
   const Params& P = S.P;
-  const Lattice& L27 = Q27();
+  const Lattice& L27 = g_lattice(P);  // also the stencil lattice
   long c0 = cell_index(P, x, y, z);
   cs.phi = S.phi[c0];
   cs.gradphi[0] = cs.gradphi[1] = cs.gradphi[2] = 0;
@@ -360,7 +387,7 @@ void cell_macro(const Sim<T>& S, int x, int y, int z, const T* gcell, CellState<
   }
   // Viscous force from the non-equilibrium moments, M^-1 S M (g - g^eq(p*, u0)).
   T geq0[27], dneq[27], relaxed[27], s[27];
-  geq_of(cs.pstar, u0, geq0);
+  geq_of(L27, cs.pstar, u0, geq0);
   for (int k = 0; k < L27.q; ++k) s[k] = rate_g(P, L27.degree[k], cs.omega);
   for (int i = 0; i < L27.q; ++i) dneq[i] = gcell[i] - geq0[i];
   mrt_relax(L27, dneq, s, relaxed);
@@ -382,7 +409,7 @@ void cell_macro(const Sim<T>& S, int x, int y, int z, const T* gcell, CellState<
 
 template <typename T>
 void compute_phi(Sim<T>& S) {
-  const Lattice& LH = S.P.qh == 27 ? Q27() : Q15();
+  const Lattice& LH = h_lattice(S.P);
   for (long c = 0; c < S.N; ++c) {
     T s = 0;
     for (int i = 0; i < LH.q; ++i) s += S.h[(size_t)i * S.N + c];
@@ -394,8 +421,8 @@ template <typename T>
 void do_step(Sim<T>& S) {
   using std::sqrt;
   const Params& P = S.P;
-  const Lattice& L27 = Q27();
-  const Lattice& LH = P.qh == 27 ? Q27() : Q15();  // phase-field lattice
+  const Lattice& L27 = g_lattice(P);
+  const Lattice& LH = h_lattice(P);  // phase-field lattice
   const long N = S.N;
   const T omega_phi = 1.0 / (S.mobility / CS2 + 0.5);
 #pragma omp parallel for collapse(2) schedule(static)
@@ -404,23 +431,23 @@ void do_step(Sim<T>& S) {
       for (int x = 0; x < P.nx; ++x) {
         long c0 = cell_index(P, x, y, z);
         T gc[27], hc[27];
-        for (int i = 0; i < 27; ++i) gc[i] = S.g[(size_t)i * N + c0];
+        for (int i = 0; i < L27.q; ++i) gc[i] = S.g[(size_t)i * N + c0];
         for (int i = 0; i < LH.q; ++i) hc[i] = S.h[(size_t)i * N + c0];
         CellState<T> cs;
         cell_macro(S, x, y, z, gc, cs);
 
         // hydrodynamic collision
         T geq[27], G[27], gpost[27], s27[27];
-        geq_of(cs.pstar, cs.u, geq);
-        for (int i = 0; i < 27; ++i) {
+        geq_of(L27, cs.pstar, cs.u, geq);
+        for (int i = 0; i < L27.q; ++i) {
           T cF = L27.c[3 * i] * cs.F[0] + L27.c[3 * i + 1] * cs.F[1] + L27.c[3 * i + 2] * cs.F[2];
           G[i] = L27.w[i] * cF / (CS2 * cs.rho);
         }
         if (P.collision == COLL_BGK) {
-          for (int i = 0; i < 27; ++i)
+          for (int i = 0; i < L27.q; ++i)
             gpost[i] = gc[i] - cs.omega * (gc[i] - geq[i]) + (1.0 - 0.5 * cs.omega) * G[i];
         } else {
-          for (int k = 0; k < 27; ++k) s27[k] = rate_g(P, L27.degree[k], cs.omega);
+          for (int k = 0; k < L27.q; ++k) s27[k] = rate_g(P, L27.degree[k], cs.omega);
           mrt_collide(L27, gc, geq, G, s27, gpost);
         }
 
@@ -446,7 +473,7 @@ void do_step(Sim<T>& S) {
         }
 
         // streaming (push) with periodic wrap / halfway bounce-back
-        for (int i = 0; i < 27; ++i) {
+        for (int i = 0; i < L27.q; ++i) {
           int xt, yt, zt;
           bool ok = neighbour(x, L27.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
                     neighbour(y, L27.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
@@ -484,7 +511,7 @@ void init_sim(Sim<T>& S, const int* ip, const double* dp, const double* phi0, co
   P.nz = ip[2];
   for (int k = 0; k < 6; ++k) P.bc[k] = ip[3 + k];
   P.collision = ip[9];
-  P.qh = ip[10] == 27 ? 27 : 15;
+  P.qh = ip[10] == 27 ? 27 : (ip[10] == 9 ? 9 : 15);
   P.rho_h = dp[0];
   P.rho_l = dp[1];
   P.nu_h = dp[2];
@@ -502,18 +529,19 @@ void init_sim(Sim<T>& S, const int* ip, const double* dp, const double* phi0, co
   const long N = S.N;
   S.h.assign((size_t)P.qh * N, T(0.0));
   S.hn.assign((size_t)P.qh * N, T(0.0));
-  S.g.assign((size_t)27 * N, T(0.0));
-  S.gn.assign((size_t)27 * N, T(0.0));
+  const Lattice& LG = g_lattice(P);
+  S.g.assign((size_t)LG.q * N, T(0.0));
+  S.gn.assign((size_t)LG.q * N, T(0.0));
   S.phi.assign(N, T(0.0));
-  const Lattice& LH = P.qh == 27 ? Q27() : Q15();
+  const Lattice& LH = h_lattice(P);
   for (long c = 0; c < N; ++c) {
     T u[3] = {0.0, 0.0, 0.0};
     if (u0)
       for (int a = 0; a < 3; ++a) u[a] = u0[a * N + c];
     T ps = p0 ? p0[c] : 0.0;
     T geq[27];
-    geq_of(ps, u, geq);
-    for (int i = 0; i < 27; ++i) S.g[(size_t)i * N + c] = geq[i];
+    geq_of(LG, ps, u, geq);
+    for (int i = 0; i < LG.q; ++i) S.g[(size_t)i * N + c] = geq[i];
     for (int i = 0; i < LH.q; ++i) {
       double cu = LH.c[3 * i] * value(u[0]) + LH.c[3 * i + 1] * value(u[1]) + LH.c[3 * i + 2] * value(u[2]);
       S.h[(size_t)i * N + c] = LH.w[i] * phi0[c] * (1.0 + cu / CS2);
@@ -528,7 +556,7 @@ typedef Sim<double> SimD;
 
 extern "C" {
 
-// iparams: nx, ny, nz, bc[6], collision, h lattice (15 or 27)   (11 ints)
+// iparams: nx, ny, nz, bc[6], collision, h lattice (15, 27, or 9 for D2Q9 h and g)   (11 ints)
 // dparams: rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, gx, gy, gz (10 doubles)
 // phi0 (N), u0 (3N SoA, nullable), p0 (N, nullable): initial state; the
 // populations start at their equilibria h^eq(phi0, u0), g^eq(p0, u0).
@@ -610,7 +638,7 @@ void ora_fields(void* s, double* phi, double* rho, double* p, double* u) {
       for (int x = 0; x < P.nx; ++x) {
         long c0 = cell_index(P, x, y, z);
         double gc[27];
-        for (int i = 0; i < 27; ++i) gc[i] = S->g[(size_t)i * N + c0];
+        for (int i = 0; i < g_lattice(P).q; ++i) gc[i] = S->g[(size_t)i * N + c0];
         CellState<double> cs;
         cell_macro(*S, x, y, z, gc, cs);
         if (phi) phi[c0] = cs.phi;
@@ -623,7 +651,7 @@ void ora_fields(void* s, double* phi, double* rho, double* p, double* u) {
 
 // Lattice tables for the pin tests: q = 15 or 27.
 int ora_tables(int q, int* c, double* w, int* opp, int* degree, double* M, double* Minv) {
-  const Lattice* L = (q == 15) ? &Q15() : (q == 27) ? &Q27() : nullptr;
+  const Lattice* L = (q == 15) ? &Q15() : (q == 27) ? &Q27() : (q == 9) ? &Q9() : nullptr;
   if (!L) return -1;
   for (int i = 0; i < L->q; ++i) {
     for (int a = 0; a < 3; ++a) c[3 * i + a] = L->c[3 * i + a];
@@ -641,7 +669,7 @@ int ora_tables(int q, int* c, double* w, int* opp, int* degree, double* M, doubl
 // One collision of a single g cell through the MRT machinery, for pin tests:
 // f, feq, src, rates (q each) -> out.
 void ora_mrt_collide(int q, const double* f, const double* feq, const double* src, const double* s, double* out) {
-  const Lattice& L = (q == 15) ? Q15() : Q27();
+  const Lattice& L = (q == 15) ? Q15() : (q == 9) ? Q9() : Q27();
   mrt_collide(L, f, feq, src, s, out);
 }
 

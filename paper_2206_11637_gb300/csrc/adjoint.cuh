@@ -20,7 +20,7 @@
 // reverse step as it reads lambda, instead of being written into 15 arrays.
 //
 // Adjoint populations are kept in the canonical layout [i][cell] (h: QH N,
-// then g: 27 N) in the arithmetic type; lambda^t = (local part) + acc^t on the
+// then g: QG N) in the arithmetic type; lambda^t = (local part) + acc^t on the
 // h entries.
 #pragma once
 #include "step.cuh"
@@ -69,6 +69,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
                                                            double* __restrict__ part) {
   static_assert(PREC != 2, "the adjoint runs on FP64 or FP32 storage");
   typedef typename Store<PREC>::R R;
+  constexpr int QG = qg_of<QH>();   // D2Q9 with the 2-D phase field, else D3Q27
+  constexpr int GR = (QG - 1) / 2;  // rest index of g
   const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = cell < geo.N;
   R bM = 0, bXi = 0, bSig = 0;
@@ -81,11 +83,11 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
     const R pc = (R)phi[cell];
     R gx = 0, gy = 0, gz = 0, lap = 0;
 #pragma unroll
-    for (int i = 0; i < 13; ++i) {
-      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+    for (int i = 0; i < GR; ++i) {
+      const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
       const R a = (R)phi[cell + o.soff(cx, cy, cz)];
       const R b = (R)phi[cell + o.soff(-cx, -cy, -cz)];
-      const R w = (R)q27_w(i);
+      const R w = (R)lq_w<QG>(i);
       const R d = w * (a - b);
       if (cx) gx += cx > 0 ? d : -d;
       if (cy) gy += cy > 0 ? d : -d;
@@ -97,13 +99,13 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
     gz *= (R)3;
     lap *= (R)6;
 
-    R pst = g[13u * N + cell], jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
+    R pst = g[(unsigned)GR * N + cell], jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
 #pragma unroll
-    for (int i = 0; i < 13; ++i) {
-      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+    for (int i = 0; i < GR; ++i) {
+      const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
       R a, b;
       unsigned fa, fb;
-      load_pair<PREC, READ_ODD>(g, N, cell, o, i, 26 - i, cx, cy, cz, a, b, fa, fb);
+      load_pair<PREC, READ_ODD>(g, N, cell, o, i, QG - 1 - i, cx, cy, cz, a, b, fa, fb);
       const R S = a + b, D = a - b;
       pst += S;
       if (cx) jx += cx > 0 ? D : -D;
@@ -160,7 +162,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
     const R Fx = F0x + cm * NGx, Fy = F0y + cm * NGy, Fz = F0z + cm * NGz;
     const R ux = jx + Fx * inv2rho, uy = jy + Fy * inv2rho, uz = jz + Fz * inv2rho;
     const R a2 = ((R)1 - omega) * (R)4.5;
-    const R dxx = pxx - p3 - ux * ux, dyy = pyy - p3 - uy * uy, dzz = pzz - p3 - uz * uz;
+    const R dxx = pxx - p3 - ux * ux, dyy = pyy - p3 - uy * uy;
+    const R dzz = QG == 9 ? (R)0 : pzz - p3 - uz * uz;  // 2-D: the trace runs over x and y
     const R fr = (R)1.5 / rho;
     // phase field
     const R omp = (R)ph.omega_phi;
@@ -171,23 +174,23 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
     const R tn = theta / den * sfac;
     const R a1h = ((R)1 - omp) * (R)3, a2h = ((R)1 - omp) * (R)4.5;
     const R ph3 = phl * (R)(1.0 / 3.0);
-    const R dhxx = hxx - ph3, dhyy = hyy - ph3, dhzz = hzz - ph3;
+    const R dhxx = hxx - ph3, dhyy = hyy - ph3, dhzz = QG == 9 ? (R)0 : hzz - ph3;
 
     // ---------------- adjoints of the post-collision populations
     // g: lambda+ of population i of this cell sits where streaming put it
     R b_al = 0, b_bx = 0, b_by = 0, b_bz = 0, b_Gxx = 0, b_Gyy = 0, b_Gzz = 0, b_Gxy = 0, b_Gyz = 0, b_Gxz = 0;
     const R* lg = lam_in + (unsigned)QH * N;
-    b_al = (R)q27_w(13) * lg[13u * N + cell];
+    b_al = (R)lq_w<QG>(GR) * lg[(unsigned)GR * N + cell];
 #pragma unroll
-    for (int i = 0; i < 13; ++i) {
-      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
-      const int oi = 26 - i;
+    for (int i = 0; i < GR; ++i) {
+      const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
+      const int oi = QG - 1 - i;
       // direction c (index i) went to x + c (slot i) or bounced into slot oi of x
       const R la = o.valid(cx, cy, cz) ? lg[(unsigned)i * N + cell + (unsigned)o.off(cx, cy, cz)]
                                        : lg[(unsigned)oi * N + cell];
       const R lb = o.valid(-cx, -cy, -cz) ? lg[(unsigned)oi * N + cell + (unsigned)o.off(-cx, -cy, -cz)]
                                           : lg[(unsigned)i * N + cell];
-      const R w = (R)q27_w(i);
+      const R w = (R)lq_w<QG>(i);
       const R S = w * (la + lb), D = w * (la - lb);
       b_al += S;
       if (cx) b_bx += cx > 0 ? D : -D;
@@ -274,6 +277,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
       b_pxy += (R)2 * a2 * b_Gxy;
       b_pyz += (R)2 * a2 * b_Gyz;
       b_pxz += (R)2 * a2 * b_Gxz;
+      if (QG == 9) b_dzz = 0;  // 2-D: d_zz is no variable
       // d_aa = p_aa - p3 - ua^2
       b_pxx += b_dxx;
       b_pyy += b_dyy;
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
       b_hxx += bsd;
       b_hyy += bsd;
       b_hzz += bsd;
-      b_phl += -bsd;
+      b_phl += (QG == 9 ? (R)(-2.0 / 3.0) : (R)-1) * bsd;  // -1/3 from each diagonal term of the trace
       b_a2h += dhxx * c_Gxx + dhyy * c_Gyy + dhzz * c_Gzz;
       b_hxx += a2h * c_Gxx;
       b_hyy += a2h * c_Gyy;
@@ -404,10 +408,10 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
 
     // ---------------- adjoints of the local pre-collision populations
     R* og = lam_out + (unsigned)QH * N;
-    og[13u * N + cell] = b_pst;
+    og[(unsigned)GR * N + cell] = b_pst;
 #pragma unroll
-    for (int i = 0; i < 13; ++i) {
-      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+    for (int i = 0; i < GR; ++i) {
+      const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
       R E = b_pst;
       if (cx) E += b_pxx;
       if (cy) E += b_pyy;
@@ -420,7 +424,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
       if (cy) L += cy > 0 ? b_jy : -b_jy;
       if (cz) L += cz > 0 ? b_jz : -b_jz;
       og[(unsigned)i * N + cell] = E + L;
-      og[(unsigned)(26 - i) * N + cell] = E - L;
+      og[(unsigned)(QG - 1 - i) * N + cell] = E - L;
     }
     lam_out[(unsigned)hq_rest<QH>() * N + cell] = b_phl;
 #pragma unroll
@@ -467,7 +471,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, A
 //
 // Blocks of ZM_TX x ZM_TY threads march zc planes along z and keep three
 // planes of the four gathered aux fields (tile plus halo) in shared memory.
-template <typename R>
+template <typename R, int QG>
 __global__ void __launch_bounds__(ZM_TX * ZM_TY) k_adj_phi(Geo32 geo, const R* __restrict__ aux,
                                                            R* __restrict__ acc_out, const double* __restrict__ W,
                                                            int zc) {
@@ -527,17 +531,17 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY) k_adj_phi(Geo32 geo, const R* _
       const unsigned cell = (unsigned)x + geo.nx * ((unsigned)y + geo.ny * (unsigned)z);
       const int i0 = (ty + 1) * PW + (tx + 1);
       const int sl[3] = {(b + 2) % 3, b % 3, (b + 1) % 3};  // planes z - 1, z, z + 1
-      R acc = aux[4u * N + cell] - (R)(6.0 * 19.0 / 27.0) * ring[sl[1]][3][i0];
+      R acc = aux[4u * N + cell] - (R)(6.0 * (1.0 - lq_w<QG>((QG - 1) / 2))) * ring[sl[1]][3][i0];
 #pragma unroll
-      for (int q = 0; q < 27; ++q) {
-        if (q == 13) continue;
-        const int cx = q27_cx(q), cy = q27_cy(q), cz = q27_cz(q);
+      for (int q = 0; q < QG; ++q) {
+        if (q == (QG - 1) / 2) continue;
+        const int cx = q27_cx(lq_to27<QG>(q)), cy = q27_cy(lq_to27<QG>(q)), cz = q27_cz(lq_to27<QG>(q));
         const int s = sl[1 - cz], r = i0 - cx - cy * PW;   // reader y = x - c
         R v = (R)6 * ring[s][3][r];
         if (cx) v += (R)(3 * cx) * ring[s][0][r];
         if (cy) v += (R)(3 * cy) * ring[s][1][r];
         if (cz) v += (R)(3 * cz) * ring[s][2][r];
-        acc += (R)q27_w(q) * v;
+        acc += (R)lq_w<QG>(q) * v;
       }
       if (W) acc += (R)W[cell];
       acc_out[cell] = acc;

@@ -582,11 +582,11 @@ pfl_status pfl_batch_fields(pfl_batch* b, int i, double* phi, double* rho, doubl
     const unsigned nb = blocks_for(N, 256);
 #define BF(PREC)                                                                                                  \
   if (swapped)                                                                                                    \
-    k_fields<PREC, 1><<<nb, 256, 0, b->stream>>>(geo, I.ph, (const Store<PREC>::S*)I.g,                           \
+    k_fields<PREC, 15, 1><<<nb, 256, 0, b->stream>>>(geo, I.ph, (const Store<PREC>::S*)I.g,                           \
                                                  (const Store<PREC>::PhiT*)I.phi[cur], o[0], o[1],                 \
                                                  o[2], o[3], o[4], o[5]);                                         \
   else                                                                                                            \
-    k_fields<PREC, 0><<<nb, 256, 0, b->stream>>>(geo, I.ph, (const Store<PREC>::S*)I.g,                           \
+    k_fields<PREC, 15, 0><<<nb, 256, 0, b->stream>>>(geo, I.ph, (const Store<PREC>::S*)I.g,                           \
                                                  (const Store<PREC>::PhiT*)I.phi[cur], o[0], o[1],                 \
                                                  o[2], o[3], o[4], o[5]);
     switch (b->prec) {

@@ -15,8 +15,10 @@ inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 inline size_t pop_bytes(int prec) { return prec == PFL_FP64 ? 8 : prec == PFL_FP32 ? 4 : 2; }
 inline size_t phi_bytes(int prec) { return prec == PFL_FP64 ? 8 : 4; }
 
-// Velocities of the phase-field lattice: 27 for D3Q27, else 15 (D3Q15).
-inline int qh_of(const pfl_params* p) { return p->h_lattice == 27 ? 27 : 15; }
+// Velocities of the phase-field lattice: 27 (D3Q27), 9 (D2Q9, 2-D) or 15
+// (D3Q15, also for 0); the hydrodynamic lattice is D2Q9 in 2-D, else D3Q27.
+inline int qh_of(const pfl_params* p) { return p->h_lattice == 27 ? 27 : (p->h_lattice == 9 ? 9 : 15); }
+inline int qg_of(const pfl_params* p) { return qh_of(p) == 9 ? 9 : 27; }
 
 // The fused two-array step applies to MRT lattices with 32-bit indices.
 inline bool uses_two_arrays(const pfl_params* p) {
@@ -44,7 +46,10 @@ inline std::string check_params(const pfl_params* p) {
   if (p->precision < PFL_FP64 || p->precision > PFL_FP16S) return "unknown precision";
   if (p->collision != PFL_MRT && p->collision != PFL_BGK) return "unknown collision model";
   if (p->engine != PFL_ENGINE_AUTO && p->engine != PFL_ENGINE_INPLACE) return "unknown engine";
-  if (p->h_lattice != 0 && p->h_lattice != 15 && p->h_lattice != 27) return "h_lattice must be 0, 15 or 27";
+  if (p->h_lattice != 0 && p->h_lattice != 15 && p->h_lattice != 27 && p->h_lattice != 9)
+    return "h_lattice must be 0, 15, 27 or 9";
+  if (p->h_lattice == 9 && (p->nz != 1 || p->bc[4] != PFL_PERIODIC))
+    return "the 2-D lattices (h_lattice 9) need nz = 1 with periodic z faces";
   if (!std::isfinite(p->gravity[0]) || !std::isfinite(p->gravity[1]) || !std::isfinite(p->gravity[2]))
     return "gravity must be finite";
   return "";

@@ -1,4 +1,5 @@
-// PFLBM device kernels: fused stream-collide of h (D3Q15) and g (D3Q27) with
+// PFLBM device kernels: fused stream-collide of h (D3Q15 / D3Q27, or D2Q9 in
+// 2-D) and g (D3Q27, or D2Q9 in 2-D) with
 // in-place AA streaming, the phi = sum h pass, initialisation, field output
 // and FP64 reductions.
 //
@@ -130,7 +131,7 @@ struct Macro {
   R Fx, Fy, Fz, ux, uy, uz;
 };
 
-template <int PREC>
+template <int PREC, int QG>
 __device__ __forceinline__ void stencil(const Geo& geo, const Nb& nb, long long cell,
                                         const typename Store<PREC>::PhiT* __restrict__ phi,
                                         Macro<typename Store<PREC>::R>& m) {
@@ -138,11 +139,11 @@ __device__ __forceinline__ void stencil(const Geo& geo, const Nb& nb, long long 
   R pc = (R)__ldg(phi + cell);
   R gx = 0, gy = 0, gz = 0, lap = 0;
 #pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    if (i == 13) continue;
-    const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+  for (int i = 0; i < QG; ++i) {
+    if (i == (QG - 1) / 2) continue;
+    const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
     R v = (R)__ldg(phi + lin(geo, nb.sx[1 + cx], nb.sy[1 + cy], nb.sz[1 + cz]));
-    const R w = (R)q27_w(i);
+    const R w = (R)lq_w<QG>(i);
     if (cx) gx += (cx > 0 ? w : -w) * v;
     if (cy) gy += (cy > 0 ? w : -w) * v;
     if (cz) gz += (cz > 0 ? w : -w) * v;
@@ -157,18 +158,18 @@ __device__ __forceinline__ void stencil(const Geo& geo, const Nb& nb, long long 
 
 // Hydrodynamic moments, forces and velocity.  gv receives the 27 values (used
 // by the BGK mode; dead code otherwise).
-template <int PREC, int READ_ODD>
+template <int PREC, int QG, int READ_ODD>
 __device__ __forceinline__ void hydro_macro(const Geo& geo, const Phys& ph, const Nb& nb, long long cell,
                                             const typename Store<PREC>::S* __restrict__ g, Macro<typename Store<PREC>::R>& m,
-                                            typename Store<PREC>::R gv[27]) {
+                                            typename Store<PREC>::R gv[QG]) {
   typedef typename Store<PREC>::R R;
   R pst = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
 #pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+  for (int i = 0; i < QG; ++i) {
+    const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
     long long from;
-    const size_t idx = src_index<READ_ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz, from);
-    R v = ld_g<PREC>(g, idx, i);
+    const size_t idx = src_index<READ_ODD>(geo, nb, cell, i, QG - 1 - i, cx, cy, cz, from);
+    R v = ld_g<PREC, QG>(g, idx, i);
     gv[i] = v;
     pst += v;
     if (cx) jx += cx > 0 ? v : -v;
@@ -242,6 +243,7 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
                                               const typename Store<PREC>::PhiT* __restrict__ phi,
                                               const typename Store<PREC>::PhiT* __restrict__ shift) {
   typedef typename Store<PREC>::R R;
+  constexpr int QG = qg_of<QH>();
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
   int x, y, z;
@@ -249,16 +251,17 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
   Nb nb;
   make_nb(geo, x, y, z, nb);
   Macro<R> m;
-  stencil<PREC>(geo, nb, cell, phi, m);
-  R gv[27];
-  hydro_macro<PREC, ODD>(geo, ph, nb, cell, g, m, gv);
+  stencil<PREC, QG>(geo, nb, cell, phi, m);
+  R gv[QG];
+  hydro_macro<PREC, QG, ODD>(geo, ph, nb, cell, g, m, gv);
 
   // ---- g collision and streaming
   {
     const R ux = m.ux, uy = m.uy, uz = m.uz;
     const R uu = ux * ux + uy * uy + uz * uz;
     const R p3 = m.pst * (R)(1.0 / 3.0);
-    const R dxx = m.pxx - p3 - ux * ux, dyy = m.pyy - p3 - uy * uy, dzz = m.pzz - p3 - uz * uz;
+    const R dxx = m.pxx - p3 - ux * ux, dyy = m.pyy - p3 - uy * uy;
+    const R dzz = QG == 9 ? (R)0 : m.pzz - p3 - uz * uz;  // 2-D: the trace runs over x and y
     const R dxy = m.pxy - ux * uy, dyz = m.pyz - uy * uz, dxz = m.pxz - ux * uz;
     const R tr3 = (dxx + dyy + dzz) * (R)(1.0 / 3.0);
     const R a2 = ((R)1 - m.omega) * (R)4.5;
@@ -267,9 +270,9 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
     // BGK: (1 - omega/2) G_i with G_i = 2 w_i (1.5 c.F / rho)
     const R om = m.omega, fbgk = ((R)1 - (R)0.5 * om) * (R)2;
 #pragma unroll
-    for (int i = 0; i < 27; ++i) {
-      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
-      const R w = (R)q27_w(i);
+    for (int i = 0; i < QG; ++i) {
+      const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
+      const R w = (R)lq_w<QG>(i);
       const R cu = (R)cx * ux + (R)cy * uy + (R)cz * uz;
       const R geq = w * (m.pst + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu);
       const R cf = (R)cx * fx + (R)cy * fy + (R)cz * fz;  // 1.5 c.F / rho
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
                      (R)2 * ((R)(cx * cy) * dxy + (R)(cy * cz) * dyz + (R)(cx * cz) * dxz) - tr3;
         post = geq + w * (a2 * hd + cf);
       }
-      st_g<PREC>(g, dst_index<ODD>(geo, nb, cell, i, q27_opp(i), cx, cy, cz), i, post);
+      st_g<PREC, QG>(g, dst_index<ODD>(geo, nb, cell, i, QG - 1 - i, cx, cy, cz), i, post);
     }
   }
 
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
     const R a1 = ((R)1 - omp) * (R)3, a2 = ((R)1 - omp) * (R)4.5;
     const R Jx = jx - phl * ux, Jy = jy - phl * uy, Jz = jz - phl * uz;
     const R p3 = phl * (R)(1.0 / 3.0);
-    const R dxx = pxx - p3, dyy = pyy - p3, dzz = pzz - p3;
+    const R dxx = pxx - p3, dyy = pyy - p3, dzz = QG == 9 ? (R)0 : pzz - p3;
     const R tr3 = (dxx + dyy + dzz) * (R)(1.0 / 3.0);
     // populations are written as q = h+ / w - shift; the shift is this cell's phi
     const R sh = (PREC == 2) ? m.phi : (R)0;
@@ -375,10 +378,12 @@ __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typenam
   const R ux = u0x ? (R)u0x[t] : (R)0, uy = u0y ? (R)u0y[t] : (R)0, uz = u0z ? (R)u0z[t] : (R)0;
   const R ps = p0 ? (R)p0[t] : (R)0;
   const R uu = ux * ux + uy * uy + uz * uz;
+  constexpr int QG = qg_of<QH>();
 #pragma unroll
-  for (int i = 0; i < 27; ++i) {
-    const R cu = (R)q27_cx(i) * ux + (R)q27_cy(i) * uy + (R)q27_cz(i) * uz;
-    st_g<PREC>(g, (size_t)i * geo.N + cell, i, (R)q27_w(i) * (ps + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu));
+  for (int i = 0; i < QG; ++i) {
+    const int j = lq_to27<QG>(i);
+    const R cu = (R)q27_cx(j) * ux + (R)q27_cy(j) * uy + (R)q27_cz(j) * uz;
+    st_g<PREC, QG>(g, (size_t)i * geo.N + cell, i, (R)lq_w<QG>(i) * (ps + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu));
   }
 #pragma unroll
   for (int k = 0; k < QH; ++k) {
@@ -388,11 +393,12 @@ __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typenam
 }
 
 // Macroscopic output: any of phi, rho, p, ux, uy, uz (device FP64, may be NULL).
-template <int PREC, int READ_ODD>
+template <int PREC, int QH, int READ_ODD>
 __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename Store<PREC>::S* __restrict__ g,
                                                 const typename Store<PREC>::PhiT* __restrict__ phi, double* o_phi, double* o_rho,
                                                 double* o_p, double* o_ux, double* o_uy, double* o_uz) {
   typedef typename Store<PREC>::R R;
+  constexpr int QG = qg_of<QH>();
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
   int x, y, z;
@@ -400,9 +406,9 @@ __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename
   Nb nb;
   make_nb(geo, x, y, z, nb);
   Macro<R> m;
-  stencil<PREC>(geo, nb, cell, phi, m);
-  R gv[27];
-  hydro_macro<PREC, READ_ODD>(geo, ph, nb, cell, g, m, gv);
+  stencil<PREC, QG>(geo, nb, cell, phi, m);
+  R gv[QG];
+  hydro_macro<PREC, QG, READ_ODD>(geo, ph, nb, cell, g, m, gv);
   if (o_phi) o_phi[cell] = (double)m.phi;
   if (o_rho) o_rho[cell] = (double)m.rho;
   if (o_p) o_p[cell] = (double)m.pst * (double)m.rho / 3.0;
@@ -424,11 +430,13 @@ __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
   make_nb(geo, x, y, z, nb);
   if (is_g) {
 #pragma unroll
-    for (int j = 0; j < 27; ++j)
+    constexpr int QG = qg_of<QH>();
+    for (int j = 0; j < QG; ++j)
       if (j == i) {
         long long from;
-        const size_t idx = src_index<READ_ODD>(geo, nb, cell, j, q27_opp(j), q27_cx(j), q27_cy(j), q27_cz(j), from);
-        out[cell] = (double)ld_g<PREC>(f, idx, j);
+        const int k = lq_to27<QG>(j);
+        const size_t idx = src_index<READ_ODD>(geo, nb, cell, j, QG - 1 - j, q27_cx(k), q27_cy(k), q27_cz(k), from);
+        out[cell] = (double)ld_g<PREC, QG>(f, idx, j);
       }
   } else {
 #pragma unroll
@@ -448,8 +456,8 @@ __global__ void k_import(Geo geo, typename Store<PREC>::S* __restrict__ f, int i
     f[idx] = (R)in[cell];
   } else if (is_g) {
 #pragma unroll
-    for (int j = 0; j < 27; ++j)
-      if (j == i) st_g<PREC>(f, idx, j, (R)in[cell]);
+    for (int j = 0; j < qg_of<QH>(); ++j)
+      if (j == i) st_g<PREC, qg_of<QH>()>(f, idx, j, (R)in[cell]);
   } else {
 #pragma unroll
     for (int j = 0; j < QH; ++j)

@@ -1,6 +1,7 @@
 // Lattice constants and population storage formats of the PFLBM kernels.
 //
-// D3Q27 (hydrodynamics g) and D3Q15 or D3Q27 (phase field h) in the canonical order of
+// D3Q27 (hydrodynamics g) and D3Q15 or D3Q27 (phase field h), or D2Q9 for both in
+// 2-D, in the canonical order of
 // the C interface: cz, cy, cx each over -1, 0, 1 with cx fastest.  For D3Q27
 // this gives i = (cx+1) + 3(cy+1) + 9(cz+1), so velocities, weights and
 // opposites are closed-form functions of i that fold to constants inside
@@ -36,12 +37,34 @@ __host__ __device__ constexpr double q15_w(int k) {
   return q27_n2(q15_to27(k)) == 0 ? 2.0 / 9.0 : q27_n2(q15_to27(k)) == 1 ? 1.0 / 9.0 : 1.0 / 72.0;
 }
 
-// The phase-field lattice, QH = 15 (D3Q15) or 27 (D3Q27).  In both orders
-// member k pairs with QH - 1 - k, members k < (QH - 1) / 2 are one of each
-// opposite pair, and (QH - 1) / 2 is the rest velocity.
+// D2Q9 (the 2-D lattice of both sets) is the cz = 0 slice of D3Q27: member j
+// sits at D3Q27 index 9 + j, its opposite is 8 - j; weights 4/9, 1/9, 1/36 by
+// |c|^2 = 0, 1, 2.
+__host__ __device__ constexpr double q9_w(int j) {
+  return q27_n2(9 + j) == 0 ? 4.0 / 9.0 : q27_n2(9 + j) == 1 ? 1.0 / 9.0 : 1.0 / 36.0;
+}
+
+// A lattice by its size Q = 27 (D3Q27), 15 (D3Q15) or 9 (D2Q9).  In each
+// order member k pairs with Q - 1 - k, members k < (Q - 1) / 2 are one of each
+// opposite pair, and (Q - 1) / 2 is the rest velocity.
+template <int Q>
+__host__ __device__ constexpr int lq_to27(int k) {
+  return Q == 27 ? k : (Q == 15 ? q15_to27(k) : 9 + k);
+}
+template <int Q>
+__host__ __device__ constexpr double lq_w(int k) {
+  return Q == 27 ? q27_w(k) : (Q == 15 ? q15_w(k) : q9_w(k));
+}
+
+// The phase-field lattice QH = 15 (D3Q15), 27 (D3Q27) or 9 (D2Q9); the
+// hydrodynamic lattice that goes with it is D2Q9 for QH = 9, else D3Q27.
+template <int QH>
+__host__ __device__ constexpr int qg_of() {
+  return QH == 9 ? 9 : 27;
+}
 template <int QH>
 __host__ __device__ constexpr int hq_to27(int k) {
-  return QH == 27 ? k : q15_to27(k);
+  return lq_to27<QH>(k);
 }
 template <int QH>
 __host__ __device__ constexpr int hq_cx(int k) {
@@ -57,7 +80,7 @@ __host__ __device__ constexpr int hq_cz(int k) {
 }
 template <int QH>
 __host__ __device__ constexpr double hq_w(int k) {
-  return QH == 27 ? q27_w(k) : q15_w(k);
+  return lq_w<QH>(k);
 }
 template <int QH>
 __host__ __device__ constexpr int hq_rest() {
@@ -104,17 +127,17 @@ struct Store<2> {  // shifted FP16 storage, FP32 arithmetic
 };
 
 // g population i: load / store in the arithmetic type.
-template <int PREC>
+template <int PREC, int QG = 27>
 __device__ __forceinline__ typename Store<PREC>::R ld_g(const typename Store<PREC>::S* a, size_t idx, int i) {
   if constexpr (PREC == 2)
-    return __half2float(a[idx]) * (float)(q27_w(i) / KG16);
+    return __half2float(a[idx]) * (float)(lq_w<QG>(i) / KG16);
   else
     return a[idx];
 }
-template <int PREC>
+template <int PREC, int QG = 27>
 __device__ __forceinline__ void st_g(typename Store<PREC>::S* a, size_t idx, int i, typename Store<PREC>::R v) {
   if constexpr (PREC == 2)
-    a[idx] = __float2half_rn(v * (float)(KG16 / q27_w(i)));
+    a[idx] = __float2half_rn(v * (float)(KG16 / lq_w<QG>(i)));
   else
     a[idx] = v;
 }

@@ -62,13 +62,13 @@ Layout layout_of(const pfl_params* p) {
   L.h = off;
   off = align256(off + QH * N * pop_bytes(p->precision));
   L.g = off;
-  off = align256(off + 27 * N * pop_bytes(p->precision));
+  off = align256(off + (size_t)qg_of(p) * N * pop_bytes(p->precision));
   L.h2 = L.g2 = 0;
   if (uses_two_arrays(p)) {  // second array pair of the fused two-array step
     L.h2 = off;
     off = align256(off + QH * N * pop_bytes(p->precision));
     L.g2 = off;
-    off = align256(off + 27 * N * pop_bytes(p->precision));
+    off = align256(off + (size_t)qg_of(p) * N * pop_bytes(p->precision));
   }
   for (int b = 0; b < 2; ++b) {
     L.phi[b] = off;
@@ -104,7 +104,8 @@ struct pfl_ctx {
   int zc;        // two-array step: z planes per block
   long long t;   // steps taken
   int swapped;   // 1 after an even step (populations await the gather read)
-  int qh;        // phase-field lattice: 15 or 27 velocities
+  int qh;        // phase-field lattice: 15, 27 or 9 velocities
+  int qg;        // hydrodynamic lattice: 27, or 9 in 2-D
 };
 
 namespace {
@@ -253,14 +254,14 @@ pfl_status fresh_phi(pfl_ctx* c) {
   return PFL_OK;
 }
 
-template <int PREC>
+template <int PREC, int QH>
 void launch_fields(pfl_ctx* c, double* o[6]) {
   const unsigned nb = blocks_for(c->geo.N, 256);
   if (c->swapped)
-    k_fields<PREC, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0],
+    k_fields<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0],
                                                   o[1], o[2], o[3], o[4], o[5]);
   else
-    k_fields<PREC, 0><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0],
+    k_fields<PREC, QH, 0><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0],
                                                   o[1], o[2], o[3], o[4], o[5]);
 }
 
@@ -306,16 +307,22 @@ void launch_diag(pfl_ctx* c, double* part, double* out) {
 // fn<PREC, QH>(...) for the context's precision and phase-field lattice
 #define DISPATCH(c, fn, ...)                                                  \
   do {                                                                        \
-    const bool q27_ = (c)->qh == 27;                                          \
+    const int qh_ = (c)->qh;                                                  \
     switch ((c)->p.precision) {                                               \
       case PFL_FP64:                                                          \
-        if (q27_) fn<0, 27>(__VA_ARGS__); else fn<0, 15>(__VA_ARGS__);        \
+        if (qh_ == 27) fn<0, 27>(__VA_ARGS__);                                \
+        else if (qh_ == 9) fn<0, 9>(__VA_ARGS__);                             \
+        else fn<0, 15>(__VA_ARGS__);                                          \
         break;                                                                \
       case PFL_FP32:                                                          \
-        if (q27_) fn<1, 27>(__VA_ARGS__); else fn<1, 15>(__VA_ARGS__);        \
+        if (qh_ == 27) fn<1, 27>(__VA_ARGS__);                                \
+        else if (qh_ == 9) fn<1, 9>(__VA_ARGS__);                             \
+        else fn<1, 15>(__VA_ARGS__);                                          \
         break;                                                                \
       default:                                                                \
-        if (q27_) fn<2, 27>(__VA_ARGS__); else fn<2, 15>(__VA_ARGS__);        \
+        if (qh_ == 27) fn<2, 27>(__VA_ARGS__);                                \
+        else if (qh_ == 9) fn<2, 9>(__VA_ARGS__);                             \
+        else fn<2, 15>(__VA_ARGS__);                                          \
         break;                                                                \
     }                                                                         \
   } while (0)
@@ -323,11 +330,11 @@ void launch_diag(pfl_ctx* c, double* part, double* out) {
 // s = fn<PREC, QH>(...)
 #define DISPATCH_S(s, c, fn, ...)                                             \
   do {                                                                        \
-    const bool q27_ = (c)->qh == 27;                                          \
+    const int qh_ = (c)->qh;                                                  \
     switch ((c)->p.precision) {                                               \
-      case PFL_FP64: s = q27_ ? fn<0, 27>(__VA_ARGS__) : fn<0, 15>(__VA_ARGS__); break; \
-      case PFL_FP32: s = q27_ ? fn<1, 27>(__VA_ARGS__) : fn<1, 15>(__VA_ARGS__); break; \
-      default: s = q27_ ? fn<2, 27>(__VA_ARGS__) : fn<2, 15>(__VA_ARGS__); break;       \
+      case PFL_FP64: s = qh_ == 27 ? fn<0, 27>(__VA_ARGS__) : qh_ == 9 ? fn<0, 9>(__VA_ARGS__) : fn<0, 15>(__VA_ARGS__); break; \
+      case PFL_FP32: s = qh_ == 27 ? fn<1, 27>(__VA_ARGS__) : qh_ == 9 ? fn<1, 9>(__VA_ARGS__) : fn<1, 15>(__VA_ARGS__); break; \
+      default: s = qh_ == 27 ? fn<2, 27>(__VA_ARGS__) : qh_ == 9 ? fn<2, 9>(__VA_ARGS__) : fn<2, 15>(__VA_ARGS__); break;       \
     }                                                                         \
   } while (0)
 
@@ -380,6 +387,7 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
   c->ab = 0;
   c->stale = false;
   c->qh = qh_of(p);
+  c->qg = qg_of(p);
   {
     // z planes per block.  Every block marches zc planes and fills two more
     // (the planes below and above its first) before it starts, about half a
@@ -514,13 +522,13 @@ pfl_status pfl_fields(pfl_ctx* c, double* phi, double* rho, double* p, double* u
   DISPATCH(c, ensure_phi, c);
   bool any_dev = false;
   for (int k = 0; k < 6; ++k) any_dev |= dev[k] != nullptr;
-  if (any_dev) DISPATCH_PREC(c, launch_fields, c, dev);
+  if (any_dev) DISPATCH(c, launch_fields, c, dev);
   // host outputs one at a time through the staging area
   for (int k = 0; k < 6; ++k) {
     if (!host[k]) continue;
     double* o[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     o[k] = stage(c);
-    DISPATCH_PREC(c, launch_fields, c, o);
+    DISPATCH(c, launch_fields, c, o);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(want[k], stage(c), N * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -538,7 +546,7 @@ pfl_status pfl_populations(pfl_ctx* c, double* h, double* g) {
   for (int set = 0; set < 2; ++set) {
     double* dst = set == 0 ? h : g;
     if (!dst) continue;
-    const int q = set == 0 ? c->qh : 27;
+    const int q = set == 0 ? c->qh : c->qg;
     const bool dev = is_device_ptr(dst);
     for (int i = 0; i < q; ++i) {
       double* o = dev ? dst + (size_t)i * N : stage(c);
@@ -563,7 +571,7 @@ pfl_status pfl_set_populations(pfl_ctx* c, const double* h, const double* g) {
   // needed, both sets are replaced; the layout becomes the normal one.
   for (int set = 0; set < 2; ++set) {
     const double* src = set == 0 ? h : g;
-    const int q = set == 0 ? c->qh : 27;
+    const int q = set == 0 ? c->qh : c->qg;
     for (int i = 0; i < q; ++i) {
       CUDA_TRY(cudaMemcpyAsync(stage(c), src + (size_t)i * N, N * sizeof(double), cudaMemcpyDefault, c->stream));
       DISPATCH(c, launch_import, c, set, i, stage(c));
@@ -652,7 +660,8 @@ AdjLayout adj_layout(const pfl_ctx* c, int n) {
   const size_t N = (size_t)c->geo.N;
   const size_t S = pop_bytes(c->p.precision), P = phi_bytes(c->p.precision), R = rbytes(c->p.precision);
   const size_t QH = (size_t)c->qh;
-  A.state = align256(QH * N * S) + align256(27 * N * S) + align256(N * P);
+  const size_t QG = (size_t)c->qg;
+  A.state = align256(QH * N * S) + align256(QG * N * S) + align256(N * P);
   A.K = 1;
   while ((long long)A.K * A.K < n) ++A.K;
   A.nck = (n + A.K - 1) / A.K;
@@ -665,9 +674,9 @@ AdjLayout adj_layout(const pfl_ctx* c, int n) {
   A.fin = off;
   if (!c->zm) off += A.state;  // the fused engine's reverse sweep leaves the live state alone
   A.lam0 = off;
-  off = align256(off + (QH + 27) * N * R);
+  off = align256(off + (QH + QG) * N * R);
   A.lam1 = off;
-  off = align256(off + (QH + 27) * N * R);
+  off = align256(off + (QH + QG) * N * R);
   A.aux = off;
   off = align256(off + 5 * N * R);
   A.acc = off;
@@ -691,7 +700,7 @@ struct Saved {
 pfl_status copy_state(pfl_ctx* c, char* slot, bool save) {
   const size_t N = (size_t)c->geo.N;
   const size_t S = pop_bytes(c->p.precision), P = phi_bytes(c->p.precision);
-  const size_t hb = (size_t)c->qh * N * S, gb = 27 * N * S, pb = N * P;
+  const size_t hb = (size_t)c->qh * N * S, gb = (size_t)c->qg * N * S, pb = N * P;
   const bool second = c->zm && c->ab;
   char* live[3] = {c->ws + (second ? c->L.h2 : c->L.h), c->ws + (second ? c->L.g2 : c->L.g),
                    c->ws + c->L.phi[c->cur]};
@@ -719,7 +728,7 @@ void launch_adj_step(pfl_ctx* c, const AdjLayout& A, char* aws, char* slot, int 
   const typename Store<PREC>::S* h = (const typename Store<PREC>::S*)slot;
   const typename Store<PREC>::S* g = (const typename Store<PREC>::S*)(slot + align256((size_t)QH * N * S));
   const typename Store<PREC>::PhiT* phi =
-      (const typename Store<PREC>::PhiT*)(slot + align256((size_t)QH * N * S) + align256(27 * N * S));
+      (const typename Store<PREC>::PhiT*)(slot + align256((size_t)QH * N * S) + align256((size_t)qg_of<QH>() * N * S));
   AdjPar ap{c->p.mobility, c->p.xi, c->p.sigma};
   double* part = (double*)(aws + A.part);
   R* aux = (R*)(aws + A.aux);
@@ -732,7 +741,7 @@ void launch_adj_step(pfl_ctx* c, const AdjLayout& A, char* aws, char* slot, int 
     k_adj_local<PREC, QH, 0><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
                                                              acc, (R*)lam_out, aux, part);
   const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
-  k_adj_phi<R><<<grid, dim3(ZM_TX, ZM_TY), 0, c->stream>>>(c->g32, aux, acc, W, c->zc);
+  k_adj_phi<R, qg_of<QH>()><<<grid, dim3(ZM_TX, ZM_TY), 0, c->stream>>>(c->g32, aux, acc, W, c->zc);
 }
 
 // lambda at the final time: local part 0, acc = W (the objective's weight on
@@ -756,7 +765,7 @@ struct SlotPtr {
     h = (typename Store<PREC>::S*)slot;
     const size_t hb = (size_t)c->qh * N * S;
     g = (typename Store<PREC>::S*)(slot + align256(hb));
-    phi = (typename Store<PREC>::PhiT*)(slot + align256(hb) + align256(27 * N * S));
+    phi = (typename Store<PREC>::PhiT*)(slot + align256(hb) + align256((size_t)c->qg * N * S));
   }
 };
 
@@ -802,7 +811,7 @@ pfl_status run_adjoint_zm(pfl_ctx* c, int n, const ObsAt& obs_at, char* aws, con
   void* lam2 = aws + A.lam1;
   const unsigned nbl = blocks_for(c->geo.N, ADJ_THREADS);  // per-block gradient partials, summed at the end
   CUDA_TRY(cudaMemsetAsync(part, 0, 3 * (size_t)nbl * sizeof(double), c->stream));
-  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, c->qh + 27, (R*)lam,
+  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, c->qh + c->qg, (R*)lam,
                                                                    (R*)(aws + A.acc), obs_at(n));
   for (int sgm = A.nck - 1; sgm >= 0; --sgm) {
     const int k0 = sgm * A.K, k1 = (k0 + A.K < n) ? k0 + A.K : n;
@@ -874,7 +883,7 @@ pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const 
   void* lam2 = aws + A.lam1;
   const unsigned nbl = blocks_for(c->geo.N, ADJ_THREADS);  // per-block gradient partials, summed at the end
   CUDA_TRY(cudaMemsetAsync(part, 0, 3 * (size_t)nbl * sizeof(double), c->stream));
-  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, c->qh + 27, (R*)lam,
+  k_lam_init<R><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>((unsigned)c->geo.N, c->qh + c->qg, (R*)lam,
                                                                    (R*)(aws + A.acc), obs_at(n));
   for (int sgm = A.nck - 1; sgm >= 0; --sgm) {
     const int k0 = sgm * A.K, k1 = (k0 + A.K < n) ? k0 + A.K : n;
@@ -955,11 +964,13 @@ pfl_status pfl_adjoint(pfl_ctx* c, int n_steps, int n_obs, const int* obs_steps,
   }
   switch (c->p.precision) {
     case PFL_FP64:
-      return c->qh == 27 ? run_adjoint<0, 27>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad)
-                         : run_adjoint<0, 15>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
+      if (c->qh == 27) return run_adjoint<0, 27>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
+      if (c->qh == 9) return run_adjoint<0, 9>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
+      return run_adjoint<0, 15>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
     default:
-      return c->qh == 27 ? run_adjoint<1, 27>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad)
-                         : run_adjoint<1, 15>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
+      if (c->qh == 27) return run_adjoint<1, 27>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
+      if (c->qh == 9) return run_adjoint<1, 9>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
+      return run_adjoint<1, 15>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
   }
 }
 

@@ -292,6 +292,8 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
                                              const typename Store<PREC>::R* hmom = nullptr, int hstride = 0) {
   typedef typename Store<PREC>::R R;
   constexpr bool F16 = PREC == 2;
+  constexpr int QG = qg_of<QH>();  // D2Q9 with the 2-D phase field, else D3Q27
+  constexpr int GR = (QG - 1) / 2;  // rest index of g
   const unsigned N = geo.N;
   Dither dith{F16 ? hash32(cell * 0x9E3779B1u + seed) : 0u};
 
@@ -299,11 +301,11 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
   const R pc = phi_at(0, 0, 0);
   R gx = 0, gy = 0, gz = 0, lap = 0;
 #pragma unroll
-  for (int i = 0; i < 13; ++i) {
-    const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+  for (int i = 0; i < GR; ++i) {
+    const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
     const R a = phi_at(cx, cy, cz);
     const R b = phi_at(-cx, -cy, -cz);
-    const R w = (R)q27_w(i);
+    const R w = (R)lq_w<QG>(i);
     const R d = w * (a - b);
     if (cx) gx += cx > 0 ? d : -d;
     if (cy) gy += cy > 0 ? d : -d;
@@ -318,19 +320,19 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
   // ---- g moments (FP16: g_i = w_i s / KG)
   R pst, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
   {
-    const R rest = raw<PREC>(gin[13u * N + cell]);
-    pst = F16 ? rest * (R)(q27_w(13) / KG16) : rest;
+    const R rest = raw<PREC>(gin[(unsigned)GR * N + cell]);
+    pst = F16 ? rest * (R)(lq_w<QG>(GR) / KG16) : rest;
   }
 #pragma unroll
-  for (int i = 0; i < 13; ++i) {
-    const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+  for (int i = 0; i < GR; ++i) {
+    const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
     R a, b;
     unsigned fa, fb;
-    load_pair<PREC, READ_ODD>(gin, N, cell, o, i, 26 - i, cx, cy, cz, a, b, fa, fb);
+    load_pair<PREC, READ_ODD>(gin, N, cell, o, i, QG - 1 - i, cx, cy, cz, a, b, fa, fb);
     R S = a + b, D = a - b;
     if (F16) {
-      S *= (R)(q27_w(i) / KG16);
-      D *= (R)(q27_w(i) / KG16);
+      S *= (R)(lq_w<QG>(i) / KG16);
+      D *= (R)(lq_w<QG>(i) / KG16);
     }
     pst += S;
     if (cx) jx += cx > 0 ? D : -D;
@@ -372,7 +374,8 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
   {
     const R uu = ux * ux + uy * uy + uz * uz;
     const R a2 = ((R)1 - omega) * (R)4.5;
-    const R dxx = pxx - p3 - ux * ux, dyy = pyy - p3 - uy * uy, dzz = pzz - p3 - uz * uz;
+    const R dxx = pxx - p3 - ux * ux, dyy = pyy - p3 - uy * uy;
+    const R dzz = QG == 9 ? (R)0 : pzz - p3 - uz * uz;  // 2-D: the trace runs over x and y
     const R K = F16 ? (R)KG16 : (R)1;
     const R al = K * (pst - (R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
     const R fr = (R)1.5 / rho;
@@ -382,10 +385,10 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     const R Gxy = K * (R)2 * ((R)4.5 * ux * uy + a2 * (pxy - ux * uy));
     const R Gyz = K * (R)2 * ((R)4.5 * uy * uz + a2 * (pyz - uy * uz));
     const R Gxz = K * (R)2 * ((R)4.5 * ux * uz + a2 * (pxz - ux * uz));
-    gout[13u * N + cell] = pack_sr<PREC>(F16 ? al : (R)q27_w(13) * al, dith);
+    gout[(unsigned)GR * N + cell] = pack_sr<PREC>(F16 ? al : (R)lq_w<QG>(GR) * al, dith);
 #pragma unroll
-    for (int i = 0; i < 13; ++i) {
-      const int cx = q27_cx(i), cy = q27_cy(i), cz = q27_cz(i);
+    for (int i = 0; i < GR; ++i) {
+      const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
       R E = al;
       if (cx) E += Gxx;
       if (cy) E += Gyy;
@@ -399,10 +402,10 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
       if (cz) L += cz > 0 ? bz : -bz;
       R A = E + L, B = E - L;
       if (!F16) {
-        A *= (R)q27_w(i);
-        B *= (R)q27_w(i);
+        A *= (R)lq_w<QG>(i);
+        B *= (R)lq_w<QG>(i);
       }
-      store_pair<PREC, WRITE_ODD>(gout, N, cell, o, i, 26 - i, cx, cy, cz, A, B, dith);
+      store_pair<PREC, WRITE_ODD>(gout, N, cell, o, i, QG - 1 - i, cx, cy, cz, A, B, dith);
     }
   }
 
@@ -459,7 +462,7 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     const R tn = theta / (gn + (R)1e-6) * ((R)1 - (R)0.5 * omp);  // (1 - omega_phi/2) theta / |grad phi|
     const R a1 = ((R)1 - omp) * (R)3, a2 = ((R)1 - omp) * (R)4.5;
     const R ph3 = phl * (R)(1.0 / 3.0);
-    const R dxx = hxx - ph3, dyy = hyy - ph3, dzz = hzz - ph3;
+    const R dxx = hxx - ph3, dyy = hyy - ph3, dzz = QG == 9 ? (R)0 : hzz - ph3;
     const R K = F16 ? (R)KH16 : (R)1;
     const R sh = F16 ? pc : (R)0;   // this cell's phi: the shift of everything it writes
     const R al = K * ((phl - sh) - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));

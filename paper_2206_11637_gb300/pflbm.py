@@ -159,20 +159,25 @@ class Simulation:
 
     @property
     def qh(self):
-        """Velocities of the phase-field lattice (15 or 27)."""
-        return 27 if self._params.h_lattice == 27 else 15
+        """Velocities of the phase-field lattice (15, 27, or 9 in 2-D)."""
+        return {27: 27, 9: 9}.get(self._params.h_lattice, 15)
+
+    @property
+    def qg(self):
+        """Velocities of the hydrodynamic lattice (27, or 9 in 2-D)."""
+        return 9 if self.qh == 9 else 27
 
     def populations(self):
         h = np.empty((self.qh,) + self.shape)
-        g = np.empty((27,) + self.shape)
+        g = np.empty((self.qg,) + self.shape)
         L.check(self.lib.pfl_populations(self.ctx, _ptr(h), _ptr(g)))
         return h, g
 
     def set_populations(self, h, g):
         h = np.ascontiguousarray(h, dtype=np.float64)
         g = np.ascontiguousarray(g, dtype=np.float64)
-        if h.size != self.qh * self.N or g.size != 27 * self.N:
-            raise ValueError("populations must hold %d h and 27 g values per cell" % self.qh)
+        if h.size != self.qh * self.N or g.size != self.qg * self.N:
+            raise ValueError("populations must hold %d h and %d g values per cell" % (self.qh, self.qg))
         L.check(self.lib.pfl_set_populations(self.ctx, _ptr(h), _ptr(g)))
 
     def diag(self, check=True):

@@ -50,7 +50,8 @@ def test_workspace_grows_with_the_phase_field_lattice(lib):
 
 
 @pytest.mark.parametrize("field,value", [("mobility", 0.0), ("xi", -1.0), ("rho_l", 0.0), ("nu_h", -0.2),
-                                         ("nu_l", -0.1), ("nx", 0), ("h_lattice", 19)])
+                                         ("nu_l", -0.1), ("nx", 0), ("h_lattice", 19),
+                                         ("h_lattice", 9)])   # 9 (D2Q9) needs nz = 1
 def test_rejects_bad_parameters(lib, field, value):
     p, phi0, _, _ = W.static_drop(8, 3.0)
     setattr(p, field, value)
@@ -83,3 +84,13 @@ def test_batch_takes_d3q15_instances_only(lib):
     p.h_lattice = 27
     arr = (L.pfl_params * 1)(pflbm._params_struct(p, L.PFL_FP32))
     assert lib.pfl_batch_workspace_bytes(arr, 1) == 0
+
+
+def test_two_d_lattice_workspace(lib):
+    p, _, _, _ = W.capillary_wave(32, ny=32)
+    n = p.cells
+    b3 = pflbm.workspace_bytes(p, L.PFL_FP32)
+    p.h_lattice = 9
+    b2 = pflbm.workspace_bytes(p, L.PFL_FP32)
+    # two array pairs of (9 + 9) instead of (15 + 27) populations per cell
+    assert b3 - b2 >= 2 * 24 * n * 4

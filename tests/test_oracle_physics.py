@@ -28,8 +28,10 @@ fixes, chosen so that a plausible mistake in one part fails one of them:
                      catches transposed components and index errors.
   BGK special case-- the full simulation with MRT rates all equal equals BGK.
 
-The phase-field pins run on both h lattices, D3Q15 and D3Q27 (the paper's
-own 3-D lattice).
+The phase-field pins run on both 3-D h lattices, D3Q15 and D3Q27 (the
+paper's own 3-D lattice); those on quasi-2-D set-ups also on D2Q9 for both
+sets (h_lattice 9, the paper's 2-D lattice), and so do Poiseuille and the
+two-layer flow.
 """
 import numpy as np
 import pytest
@@ -57,7 +59,7 @@ def test_mass_conservation_3d_drop(qh):
     assert abs(phi.sum() - phi0.sum()) / phi0.sum() < 1e-12
 
 
-@pytest.mark.parametrize("qh", [15, 27])
+@pytest.mark.parametrize("qh", [15, 27, 9])
 def test_mass_conservation_walls(qh):
     p, phi0, _, _ = W.capillary_wave(24, ny=24, a0=1.0, xi=4.0)
     p.h_lattice = qh
@@ -65,7 +67,7 @@ def test_mass_conservation_walls(qh):
     assert abs(o.fields()[0].sum() - phi0.sum()) / phi0.sum() < 1e-12
 
 
-@pytest.mark.parametrize("qh", [15, 27])
+@pytest.mark.parametrize("qh", [15, 27, 9])
 def test_diffusion_rate_is_mobility(qh):
     M = 0.05
     p = W.Params(64, 1, 1, (0,) * 6, 1.0, 1.0, 1 / 6, 1 / 6, 0.0, M, 1e9, h_lattice=qh)
@@ -79,7 +81,7 @@ def test_diffusion_rate_is_mobility(qh):
     assert abs(D_measured / M - 1) < 0.01
 
 
-@pytest.mark.parametrize("qh", [15, 27])
+@pytest.mark.parametrize("qh", [15, 27, 9])
 def test_advection_speed(qh):
     p = W.Params(128, 1, 1, (0,) * 6, 1.0, 1e-3, 1 / 6, 1 / 6, 1e-4, 0.02, 5.0, h_lattice=qh)
     xx = np.arange(128.0)
@@ -91,7 +93,7 @@ def test_advection_speed(qh):
     assert abs((centre - 40.0) / 20.0 - 1) < 5e-3
 
 
-@pytest.mark.parametrize("qh", [15, 27])
+@pytest.mark.parametrize("qh", [15, 27, 9])
 def test_flat_interface_keeps_tanh_width(qh):
     xi = 5.0
     p, phi0, _, _ = W.flat_interface(64, xi=xi)
@@ -103,7 +105,7 @@ def test_flat_interface_keeps_tanh_width(qh):
     assert abs(y0 - 31.5) < 1e-4
 
 
-@pytest.mark.parametrize("qh", [15, 27])
+@pytest.mark.parametrize("qh", [15, 27, 9])
 def test_laplace_pressure_column(qh):
     R = 16.0
     p, phi0, _, _ = W.static_cylinder(64, R, nu=1 / 6)
@@ -114,18 +116,21 @@ def test_laplace_pressure_column(qh):
     assert np.abs(u).max() < 1e-5
 
 
+@pytest.mark.parametrize("qh", [15, 9])
 @pytest.mark.parametrize("H", [8, 16])
-def test_poiseuille_exact(H):
+def test_poiseuille_exact(H, qh):
     g, nu = 1e-6, 1 / 8
     p, phi0, _, _ = W.poiseuille(H, g=g, nu=nu)
+    p.h_lattice = qh          # 9: D2Q9 for g as well
     u = run(p, phi0, n=int(6 * H * H / nu)).fields()[3][0, 0, :, 0]
     ua = A.poiseuille(np.arange(H), H, g, nu)
     assert np.linalg.norm(u - ua) / np.linalg.norm(ua) < 1e-10
 
 
-def test_two_layer_flow_needs_dynamic_stress_continuity():
+@pytest.mark.parametrize("qh", [15, 9])
+def test_two_layer_flow_needs_dynamic_stress_continuity(qh):
     H, g = 32, 1e-6
-    p = W.Params(1, H, 1, (0, 0, 1, 1, 0, 0), 1.0, 0.1, 1 / 6, 1 / 6, 1e-4, 0.02, 4.0, (g, 0.0, 0.0))
+    p = W.Params(1, H, 1, (0, 0, 1, 1, 0, 0), 1.0, 0.1, 1 / 6, 1 / 6, 1e-4, 0.02, 4.0, (g, 0.0, 0.0), h_lattice=qh)
     u = run(p, W.flat(p, 15.5), n=30000).fields()[3][0, 0, :, 0]
     right = A.two_layer_poiseuille(np.arange(H), H, 16.0, g, 1.0, 1 / 6, 0.1, 0.1 / 6)
     wrong = A.two_layer_poiseuille(np.arange(H), H, 16.0, g, 1.0, 1 / 6, 0.1, 1 / 6)

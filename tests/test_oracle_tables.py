@@ -68,7 +68,7 @@ def test_moment_matrices(q):
     assert [int(np.sum(deg == d)) for d in range(3)] == [1, 3, 6]
 
 
-@pytest.mark.parametrize("q", [15, 27])
+@pytest.mark.parametrize("q", [15, 27, 9])
 def test_mrt_equal_rates_is_bgk(q):
     rng = np.random.Generator(np.random.PCG64(7))
     f, feq, src = rng.random(q), rng.random(q), rng.standard_normal(q) * 1e-3
@@ -78,7 +78,7 @@ def test_mrt_equal_rates_is_bgk(q):
     assert np.abs(out - bgk).max() < 1e-13
 
 
-@pytest.mark.parametrize("q", [15, 27])
+@pytest.mark.parametrize("q", [15, 27, 9])
 def test_collision_conserves_zeroth_moment(q):
     t = oracle.tables(q)
     rng = np.random.Generator(np.random.PCG64(11))
@@ -96,3 +96,27 @@ def test_collision_conserves_zeroth_moment(q):
     assert np.abs(mo[hi] - meq[hi]).max() < 1e-13
     two = t["degree"] == 2
     assert np.abs(mo[two] - (m[two] - 1.6 * (m[two] - meq[two]))).max() < 1e-13
+
+
+def test_d2q9_lattice():
+    """D2Q9, the 2-D lattice of both sets: the cz = 0 slice of D3Q27 in the
+    canonical order, weights 4/9, 1/9, 1/36, isotropic to 4th order in the
+    plane, and a weighted-orthogonal moment basis graded 1, 2, 3 over degrees
+    0, 1, 2."""
+    t = oracle.tables(9)
+    c, w = t["c"].astype(float), t["w"]
+    expect = [(cx, cy, 0) for cy in (-1, 0, 1) for cx in (-1, 0, 1)]
+    assert [tuple(r) for r in t["c"]] == expect
+    assert list(t["opp"]) == [8 - i for i in range(9)]
+    assert np.allclose(w, [1 / 36, 1 / 9, 1 / 36, 1 / 9, 4 / 9, 1 / 9, 1 / 36, 1 / 9, 1 / 36], atol=1e-16)
+    c2 = c[:, :2]
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, c2, c2), CS2 * np.eye(2), atol=1e-15)
+    d = np.eye(2)
+    iso = CS2 ** 2 * (np.einsum("ab,cd->abcd", d, d) + np.einsum("ac,bd->abcd", d, d)
+                      + np.einsum("ad,bc->abcd", d, d))
+    assert np.allclose(np.einsum("i,ia,ib,ic,id->abcd", w, c2, c2, c2, c2), iso, atol=1e-15)
+    M, Minv, deg = t["M"], t["Minv"], t["degree"]
+    assert np.abs(M @ Minv - np.eye(9)).max() < 1e-13
+    G = M @ np.diag(w) @ M.T
+    assert np.abs(G - np.diag(np.diag(G))).max() < 1e-14
+    assert [int(np.sum(deg == k)) for k in range(5)] == [1, 2, 3, 2, 1]

@@ -43,10 +43,12 @@ def wave():
     return p, phi0, u0, p0, n, [(n, w), (n // 2, 0.5 * w)]
 
 
-@pytest.mark.parametrize("qh", [15, 27])
+@pytest.mark.parametrize("qh", [15, 27, 9])
 @pytest.mark.parametrize("case", [bubble, wave])
 @pytest.mark.parametrize("param", ["mobility", "xi", "sigma"])
 def test_tangent_matches_central_differences(case, param, qh):
+    if qh == 9 and case is bubble:
+        pytest.skip("D2Q9 is the 2-D lattice; the bubble is 3-D")
     p, phi0, u0, p0, n, obs = case()
     p.h_lattice = qh
     J, dJ = oracle.tangent(p, phi0, u0, p0, n, obs, param)
