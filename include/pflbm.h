@@ -89,6 +89,8 @@ typedef struct {
                         * paper's own 3-D choice); 9 selects the paper's 2-D lattices,
                         * D2Q9 for h and g, and needs nz = 1 with periodic z faces.
                         * The collisions keep their moment form on every lattice. */
+  int solids;          /* 1: the lattice may hold solid cells (pfl_set_solid; 4 bytes
+                        * per cell of workspace; fused engine only), 0: none */
 } pfl_params;
 
 /* How a single lattice is stepped.  PFL_ENGINE_AUTO: the fused two-array step
@@ -131,6 +133,17 @@ pfl_status pfl_populations(pfl_ctx* ctx, double* h, double* g);
 /* Overwrite the populations (canonical order, FP64, host or device; rounded
  * to the storage precision) and recompute phi.  Synchronises. */
 pfl_status pfl_set_populations(pfl_ctx* ctx, const double* h, const double* g);
+
+/* Solid cells inside the lattice, voxelised obstacles and channel walls (the
+ * Taylor bubble's pipe, section "Taylor bubble": no-slip walls on a Cartesian
+ * grid).  mask: N bytes (host or device), nonzero = solid.  A link from a
+ * fluid cell into a solid one is bounced back half-way, as at a no-slip face;
+ * a phi stencil read of a solid neighbour returns the cell's own phi (neutral
+ * wetting); solid cells are not updated, hold zero populations, and every
+ * pfl_fields output is zero there.  Needs pfl_params.solids = 1 at init and
+ * comes before the first step (PFL_ERR_STATE otherwise).  The adjoint and the
+ * batch engine do not take solid cells.  Synchronises. */
+pfl_status pfl_set_solid(pfl_ctx* ctx, const unsigned char* mask);
 
 /* FP64 reductions over the domain (section "Rising bubble": centre of mass):
  *   out[0] = sum phi, out[1..3] = sum phi * (x, y, z),

@@ -44,6 +44,7 @@ def _load():
         lib.ora_tables.restype = ctypes.c_int
         lib.ora_tables.argtypes = [ctypes.c_int, P, P, P, P, P, P]
         lib.ora_mrt_collide.argtypes = [ctypes.c_int, P, P, P, P, P]
+        lib.ora_set_solid.argtypes = [P, P]
         lib.ora_tangent.argtypes = [P, P, P, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int,
                                     P, P]
         _lib = lib
@@ -90,6 +91,13 @@ class Oracle:
         if h:
             self.lib.ora_free(h)
             self.h = None
+
+    def set_solid(self, mask):
+        """Solid cells (nonzero entries of a (nz, ny, nx) mask)."""
+        m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, dtype=np.uint8)
+        if m.size != self.N:
+            raise ValueError("solid mask must hold one byte per cell")
+        self.lib.ora_set_solid(self.h, _ptr(m))
 
     def step(self, n=1, threads=0):
         self.lib.ora_step(self.h, int(n), int(threads))
@@ -144,8 +152,11 @@ def mrt_collide(q, f, feq, src, rates):
 
 def from_params(p, phi0, u0=None, p0=None):
     """Oracle built from a ``workloads.Params``-like object (duck-typed)."""
-    return Oracle(p.nx, p.ny, p.nz, p.bc, p.rho_h, p.rho_l, p.nu_h, p.nu_l, p.sigma, p.mobility, p.xi,
-                  p.gravity, phi0, u0, p0, collision=p.collision, h_lattice=getattr(p, "h_lattice", 15))
+    o = Oracle(p.nx, p.ny, p.nz, p.bc, p.rho_h, p.rho_l, p.nu_h, p.nu_l, p.sigma, p.mobility, p.xi,
+               p.gravity, phi0, u0, p0, collision=p.collision, h_lattice=getattr(p, "h_lattice", 15))
+    if getattr(p, "solid", None) is not None:
+        o.set_solid(p.solid)
+    return o
 
 
 PARAM_INDEX = {"mobility": 0, "xi": 1, "sigma": 2}

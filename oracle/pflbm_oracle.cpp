@@ -238,6 +238,7 @@ struct Sim {
   T sigma, mobility, xi;  // P's values, as T (seeded for a derivative)
   long N;
   std::vector<T> h, g, hn, gn, phi;  // populations SoA [i][cell]
+  std::vector<unsigned char> solid;  // solid cells (empty: none)
   long step = 0;
 };
 
@@ -355,7 +356,9 @@ void cell_macro(const Sim<T>& S, int x, int y, int z, const T* gcell, CellState<
     int xs = stencil_coord(x, L27.c[3 * i], P.nx, P.bc[0], P.bc[1]);
     int ys = stencil_coord(y, L27.c[3 * i + 1], P.ny, P.bc[2], P.bc[3]);
     int zs = stencil_coord(z, L27.c[3 * i + 2], P.nz, P.bc[4], P.bc[5]);
-    T pn = S.phi[cell_index(P, xs, ys, zs)];
+    const long cn = cell_index(P, xs, ys, zs);
+    // a solid neighbour reads as this cell (neutral wetting)
+    T pn = (!S.solid.empty() && S.solid[cn]) ? cs.phi : S.phi[cn];
     for (int a = 0; a < 3; ++a) cs.gradphi[a] += L27.w[i] * L27.c[3 * i + a] * pn;
     cs.lapphi += L27.w[i] * (pn - cs.phi);
   }
@@ -430,6 +433,7 @@ void do_step(Sim<T>& S) {
     for (int y = 0; y < P.ny; ++y)
       for (int x = 0; x < P.nx; ++x) {
         long c0 = cell_index(P, x, y, z);
+        if (!S.solid.empty() && S.solid[c0]) continue;  // solid cells are not updated
         T gc[27], hc[27];
         for (int i = 0; i < L27.q; ++i) gc[i] = S.g[(size_t)i * N + c0];
         for (int i = 0; i < LH.q; ++i) hc[i] = S.h[(size_t)i * N + c0];
@@ -478,6 +482,7 @@ void do_step(Sim<T>& S) {
           bool ok = neighbour(x, L27.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
                     neighbour(y, L27.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
                     neighbour(z, L27.c[3 * i + 2], P.nz, P.bc[4], P.bc[5], zt);
+          if (ok && !S.solid.empty() && S.solid[cell_index(P, xt, yt, zt)]) ok = false;  // bounce at a solid cell
           if (ok)
             S.gn[(size_t)i * N + cell_index(P, xt, yt, zt)] = gpost[i];
           else
@@ -488,6 +493,7 @@ void do_step(Sim<T>& S) {
           bool ok = neighbour(x, LH.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
                     neighbour(y, LH.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
                     neighbour(z, LH.c[3 * i + 2], P.nz, P.bc[4], P.bc[5], zt);
+          if (ok && !S.solid.empty() && S.solid[cell_index(P, xt, yt, zt)]) ok = false;
           if (ok)
             S.hn[(size_t)i * N + cell_index(P, xt, yt, zt)] = hpost[i];
           else
@@ -601,6 +607,20 @@ void ora_tangent(const int* ip, const double* dp, const double* phi0, const doub
 
 void ora_free(void* s) { delete (SimD*)s; }
 
+// Solid cells (mask of N bytes, nonzero = solid): links into them bounce
+// back half-way, stencil reads of them return the reading cell's phi, they are
+// not updated and hold zero populations.
+void ora_set_solid(void* s, const unsigned char* mask) {
+  SimD* S = (SimD*)s;
+  S->solid.assign(mask, mask + S->N);
+  for (long c = 0; c < S->N; ++c)
+    if (S->solid[c]) {
+      for (size_t i = 0; i < S->h.size() / S->N; ++i) S->h[i * S->N + c] = 0.0;
+      for (size_t i = 0; i < S->g.size() / S->N; ++i) S->g[i * S->N + c] = 0.0;
+    }
+  compute_phi(*S);
+}
+
 void ora_step(void* s, int n, int nthreads) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -637,6 +657,14 @@ void ora_fields(void* s, double* phi, double* rho, double* p, double* u) {
     for (int y = 0; y < P.ny; ++y)
       for (int x = 0; x < P.nx; ++x) {
         long c0 = cell_index(P, x, y, z);
+        if (!S->solid.empty() && S->solid[c0]) {  // every output is zero in a solid cell
+          if (phi) phi[c0] = 0;
+          if (rho) rho[c0] = 0;
+          if (p) p[c0] = 0;
+          if (u)
+            for (int a = 0; a < 3; ++a) u[a * N + c0] = 0;
+          continue;
+        }
         double gc[27];
         for (int i = 0; i < g_lattice(P).q; ++i) gc[i] = S->g[(size_t)i * N + c0];
         CellState<double> cs;

@@ -28,7 +28,7 @@ class pfl_params(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("mobility", ctypes.c_double), ("xi", ctypes.c_double),
                 ("gravity", ctypes.c_double * 3),
                 ("precision", ctypes.c_int), ("collision", ctypes.c_int), ("engine", ctypes.c_int),
-                ("h_lattice", ctypes.c_int)]
+                ("h_lattice", ctypes.c_int), ("solids", ctypes.c_int)]
 
 
 class PFLError(RuntimeError):
@@ -62,6 +62,8 @@ def load():
     lib.pfl_populations.argtypes = [P, P, P]
     lib.pfl_set_populations.restype = I
     lib.pfl_set_populations.argtypes = [P, P, P]
+    lib.pfl_set_solid.restype = I
+    lib.pfl_set_solid.argtypes = [P, P]
     lib.pfl_diag.restype = I
     lib.pfl_diag.argtypes = [P, P, ctypes.POINTER(ctypes.c_longlong)]
     lib.pfl_adjoint_workspace_bytes.restype = S

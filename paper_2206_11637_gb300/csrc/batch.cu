@@ -437,7 +437,7 @@ size_t pfl_batch_workspace_bytes(const pfl_params* params, int count) {
   for (int i = 0; i < count; ++i) {
     if (!check_params(&params[i]).empty()) return 0;
     if (params[i].precision != params[0].precision || params[i].collision != PFL_MRT) return 0;
-    if (qh_of(&params[i]) != 15) return 0;
+    if (qh_of(&params[i]) != 15 || params[i].solids) return 0;
     if (27ull * params[i].nx * params[i].ny * params[i].nz >= (1ull << 32)) return 0;
   }
   return blayout(params, count).total;
@@ -456,6 +456,7 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
       return bfail(PFL_ERR_ARG, "all instances of a batch share one precision");
     if (params[i].collision != PFL_MRT) return bfail(PFL_ERR_ARG, "the batch runs the MRT collision");
     if (qh_of(&params[i]) != 15) return bfail(PFL_ERR_ARG, "the batch steps D3Q15 phase fields only");
+    if (params[i].solids) return bfail(PFL_ERR_ARG, "the batch takes no solid cells");
     if (27ull * params[i].nx * params[i].ny * params[i].nz >= (1ull << 32))
       return bfail(PFL_ERR_ARG, "instance " + std::to_string(i) + " too large for 32-bit indices");
     if (!phi0[i]) return bfail(PFL_ERR_ARG, "phi0 of instance " + std::to_string(i) + " is NULL");

@@ -48,6 +48,8 @@ inline std::string check_params(const pfl_params* p) {
   if (p->engine != PFL_ENGINE_AUTO && p->engine != PFL_ENGINE_INPLACE) return "unknown engine";
   if (p->h_lattice != 0 && p->h_lattice != 15 && p->h_lattice != 27 && p->h_lattice != 9)
     return "h_lattice must be 0, 15, 27 or 9";
+  if (p->solids != 0 && p->solids != 1) return "solids must be 0 or 1";
+  if (p->solids && !uses_two_arrays(p)) return "solid cells need the fused engine (MRT, engine AUTO)";
   if (p->h_lattice == 9 && (p->nz != 1 || p->bc[4] != PFL_PERIODIC))
     return "the 2-D lattices (h_lattice 9) need nz = 1 with periodic z faces";
   if (!std::isfinite(p->gravity[0]) || !std::isfinite(p->gravity[1]) || !std::isfinite(p->gravity[2]))

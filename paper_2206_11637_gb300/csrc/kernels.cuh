@@ -134,7 +134,7 @@ struct Macro {
 template <int PREC, int QG>
 __device__ __forceinline__ void stencil(const Geo& geo, const Nb& nb, long long cell,
                                         const typename Store<PREC>::PhiT* __restrict__ phi,
-                                        Macro<typename Store<PREC>::R>& m) {
+                                        Macro<typename Store<PREC>::R>& m, unsigned blk = 0) {
   typedef typename Store<PREC>::R R;
   R pc = (R)__ldg(phi + cell);
   R gx = 0, gy = 0, gz = 0, lap = 0;
@@ -142,7 +142,10 @@ __device__ __forceinline__ void stencil(const Geo& geo, const Nb& nb, long long 
   for (int i = 0; i < QG; ++i) {
     if (i == (QG - 1) / 2) continue;
     const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
-    R v = (R)__ldg(phi + lin(geo, nb.sx[1 + cx], nb.sy[1 + cy], nb.sz[1 + cz]));
+    // a solid neighbour (bit (cx+1) + 3(cy+1) + 9(cz+1) of blk) reads as this cell
+    R v = (blk >> ((cx + 1) + 3 * (cy + 1) + 9 * (cz + 1))) & 1u
+              ? pc
+              : (R)__ldg(phi + lin(geo, nb.sx[1 + cx], nb.sy[1 + cy], nb.sz[1 + cz]));
     const R w = (R)lq_w<QG>(i);
     if (cx) gx += (cx > 0 ? w : -w) * v;
     if (cy) gy += (cy > 0 ? w : -w) * v;
@@ -393,10 +396,12 @@ __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typenam
 }
 
 // Macroscopic output: any of phi, rho, p, ux, uy, uz (device FP64, may be NULL).
+// With solid cells (links non-NULL) every output is zero in a solid cell.
 template <int PREC, int QH, int READ_ODD>
 __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename Store<PREC>::S* __restrict__ g,
                                                 const typename Store<PREC>::PhiT* __restrict__ phi, double* o_phi, double* o_rho,
-                                                double* o_p, double* o_ux, double* o_uy, double* o_uz) {
+                                                double* o_p, double* o_ux, double* o_uy, double* o_uz,
+                                                const unsigned* __restrict__ links = nullptr) {
   typedef typename Store<PREC>::R R;
   constexpr int QG = qg_of<QH>();
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -405,8 +410,15 @@ __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename
   cell_coords(geo, cell, x, y, z);
   Nb nb;
   make_nb(geo, x, y, z, nb);
+  const unsigned blk = links ? links[cell] : 0u;
+  if (blk & (1u << 13)) {
+    double* outs[6] = {o_phi, o_rho, o_p, o_ux, o_uy, o_uz};
+    for (int k = 0; k < 6; ++k)
+      if (outs[k]) outs[k][cell] = 0.0;
+    return;
+  }
   Macro<R> m;
-  stencil<PREC, QG>(geo, nb, cell, phi, m);
+  stencil<PREC, QG>(geo, nb, cell, phi, m, blk);
   R gv[QG];
   hydro_macro<PREC, QG, READ_ODD>(geo, ph, nb, cell, g, m, gv);
   if (o_phi) o_phi[cell] = (double)m.phi;
@@ -429,8 +441,8 @@ __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
   Nb nb;
   make_nb(geo, x, y, z, nb);
   if (is_g) {
-#pragma unroll
     constexpr int QG = qg_of<QH>();
+#pragma unroll
     for (int j = 0; j < QG; ++j)
       if (j == i) {
         long long from;
@@ -521,6 +533,46 @@ static __global__ void k_diag_final(const double* __restrict__ part, int nblocks
   for (int b = threadIdx.x; b < nblocks; b += 32) s += part[(size_t)b * 9 + k];
   s = warp_sum(s);
   if (threadIdx.x == 0) out[k] = s;
+}
+
+}  // namespace pfl
+
+namespace pfl {
+
+// Link words from a solid mask (N bytes, nonzero = solid): for each cell, bit
+// (cx+1) + 3(cy+1) + 9(cz+1) for each D3Q27 neighbour that is solid (periodic
+// wrap; no neighbour beyond a no-slip face) and bit 13 for the cell itself.
+static __global__ void k_links(Geo geo, const unsigned char* __restrict__ mask, unsigned* __restrict__ links) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= geo.N) return;
+  int x, y, z;
+  cell_coords(geo, cell, x, y, z);
+  const int n[3] = {geo.nx, geo.ny, geo.nz};
+  const int xc[3] = {x, y, z};
+  unsigned w = 0;
+  for (int i = 0; i < 27; ++i) {
+    const int c[3] = {q27_cx(i), q27_cy(i), q27_cz(i)};
+    // the neighbour, wrapped on periodic axes and clamped onto the face cell
+    // beyond a no-slip face (where the phi stencil reads); a link through a
+    // face already bounces, and a clamped solid face cell reads as this cell
+    int t[3];
+    for (int a = 0; a < 3; ++a) {
+      t[a] = xc[a] + c[a];
+      if (t[a] < 0 || t[a] >= n[a]) t[a] = geo.wall[a] ? (t[a] < 0 ? 0 : n[a] - 1) : (t[a] + n[a]) % n[a];
+    }
+    if (mask[t[0] + (long long)n[0] * (t[1] + (long long)n[1] * t[2])]) w |= 1u << i;
+  }
+  links[cell] = w;
+}
+
+// Zero the populations of solid cells (q arrays of N) so that they stay zero:
+// no fluid cell writes into a solid one, and solid cells are not updated.
+template <int PREC>
+__global__ void k_zero_solid(long long N, int q, const unsigned* __restrict__ links,
+                             typename Store<PREC>::S* __restrict__ f) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= N || !(links[cell] & (1u << 13))) return;
+  for (int i = 0; i < q; ++i) f[(size_t)i * N + cell] = (typename Store<PREC>::S)0.0f;
 }
 
 }  // namespace pfl

@@ -51,7 +51,7 @@ pfl_status cuda_fail(cudaError_t e, const char* what) {
 
 
 struct Layout {
-  size_t h, g, h2, g2, phi[2], stage, red, total;
+  size_t h, g, h2, g2, phi[2], links, stage, red, total;
 };
 
 Layout layout_of(const pfl_params* p) {
@@ -74,6 +74,8 @@ Layout layout_of(const pfl_params* p) {
     L.phi[b] = off;
     off = align256(off + N * phi_bytes(p->precision));
   }
+  L.links = off;  // blocked-link words of solid lattices
+  if (p->solids) off = align256(off + N * sizeof(unsigned));
   L.stage = off;
   off = align256(off + (N + 16) * sizeof(double));
   L.red = off;
@@ -106,6 +108,7 @@ struct pfl_ctx {
   int swapped;   // 1 after an even step (populations await the gather read)
   int qh;        // phase-field lattice: 15, 27 or 9 velocities
   int qg;        // hydrodynamic lattice: 27, or 9 in 2-D
+  bool solid;    // solid cells set (pfl_set_solid): the fused step reads the link words
 };
 
 namespace {
@@ -151,10 +154,11 @@ template <int PREC, int QH>
 void launch_phi(pfl_ctx* c) {
   const unsigned nb = blocks_for(c->geo.N, 256);
   if (c->idx32) {
+    const unsigned* links = c->solid ? (const unsigned*)(c->ws + c->L.links) : nullptr;
     if (c->swapped)
-      k_phi32<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
+      k_phi32<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c), links);
     else
-      k_phi32<PREC, QH, 0><<<nb, 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
+      k_phi32<PREC, QH, 0><<<nb, 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c), links);
   } else if (c->swapped)
     k_phi<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->geo, hbuf<PREC>(c), phicur<PREC>(c), phishift<PREC>(c));
   else
@@ -172,14 +176,24 @@ void step_only(pfl_ctx* c) {
   if (c->zm) {
     const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
     const dim3 block(ZM_TX, ZM_TY);
-    if (c->p.nz == 1)
-      k_step_zm<PREC, QH, 1><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), hnext<PREC>(c),
-                                                         gnext<PREC>(c), phishift<PREC>(c), phicur<PREC>(c),
-                                                         c->zc, step_seed(c));
-    else
-      k_step_zm<PREC, QH, 0><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), hnext<PREC>(c),
-                                                         gnext<PREC>(c), phishift<PREC>(c), phicur<PREC>(c),
-                                                         c->zc, step_seed(c));
+    const unsigned* links = (const unsigned*)(c->ws + c->L.links);
+#define PFL_ZM(FLAT, SOLID)                                                                                      \
+  k_step_zm<PREC, QH, FLAT, SOLID><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),   \
+                                                                  hnext<PREC>(c), gnext<PREC>(c),                 \
+                                                                  phishift<PREC>(c), phicur<PREC>(c), c->zc,      \
+                                                                  step_seed(c), links)
+    if (c->p.nz == 1) {
+      if (c->solid)
+        PFL_ZM(1, 1);
+      else
+        PFL_ZM(1, 0);
+    } else {
+      if (c->solid)
+        PFL_ZM(0, 1);
+      else
+        PFL_ZM(0, 0);
+    }
+#undef PFL_ZM
     // phicur now holds phi^t, the shift of the populations just written
     c->ab ^= 1;
     c->cur = 1 - c->cur;
@@ -212,8 +226,9 @@ void step_only(pfl_ctx* c) {
 template <int PREC, int QH>
 void ensure_phi(pfl_ctx* c) {
   if (!c->zm || !c->stale) return;
-  k_phi32<PREC, QH, 0><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(c->g32, hbuf<PREC>(c), phishift<PREC>(c),
-                                                                      phicur<PREC>(c));
+  k_phi32<PREC, QH, 0><<<blocks_for(c->geo.N, 256), 256, 0, c->stream>>>(
+      c->g32, hbuf<PREC>(c), phishift<PREC>(c), phicur<PREC>(c),
+      c->solid ? (const unsigned*)(c->ws + c->L.links) : nullptr);
   c->stale = false;
 }
 
@@ -257,12 +272,13 @@ pfl_status fresh_phi(pfl_ctx* c) {
 template <int PREC, int QH>
 void launch_fields(pfl_ctx* c, double* o[6]) {
   const unsigned nb = blocks_for(c->geo.N, 256);
+  const unsigned* links = (const unsigned*)(c->ws + c->L.links);
   if (c->swapped)
     k_fields<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0],
-                                                  o[1], o[2], o[3], o[4], o[5]);
+                                                  o[1], o[2], o[3], o[4], o[5], c->solid ? links : nullptr);
   else
     k_fields<PREC, QH, 0><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0],
-                                                  o[1], o[2], o[3], o[4], o[5]);
+                                                  o[1], o[2], o[3], o[4], o[5], c->solid ? links : nullptr);
 }
 
 template <int PREC, int QH>
@@ -344,6 +360,22 @@ pfl_status to_device(pfl_ctx* c, double* dst, const double* src, size_t n) {
   return PFL_OK;
 }
 
+// Link words from the device mask, zero populations in solid cells, fresh phi.
+template <int PREC, int QH>
+pfl_status apply_solid(pfl_ctx* c, const unsigned char* mask_dev) {
+  const long long N = c->geo.N;
+  unsigned* links = (unsigned*)(c->ws + c->L.links);
+  k_links<<<blocks_for(N, 256), 256, 0, c->stream>>>(c->geo, mask_dev, links);
+  const size_t offs[4] = {c->L.h, c->L.g, c->L.h2, c->L.g2};
+  const int qs[4] = {c->qh, c->qg, c->qh, c->qg};
+  for (int k = 0; k < 4; ++k)
+    k_zero_solid<PREC><<<blocks_for(N, 256), 256, 0, c->stream>>>(N, qs[k], links,
+                                                                  (typename Store<PREC>::S*)(c->ws + offs[k]));
+  CUDA_TRY(cudaGetLastError());
+  c->solid = true;
+  return fresh_phi<PREC, QH>(c);  // phi = 0 in solid cells; shifts of fresh populations
+}
+
 }  // namespace
 
 extern "C" {
@@ -388,6 +420,7 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
   c->stale = false;
   c->qh = qh_of(p);
   c->qg = qg_of(p);
+  c->solid = false;
   {
     // z planes per block.  Every block marches zc planes and fills two more
     // (the planes below and above its first) before it starts, about half a
@@ -581,6 +614,22 @@ pfl_status pfl_set_populations(pfl_ctx* c, const double* h, const double* g) {
   }
   pfl_status s = PFL_OK;
   DISPATCH_S(s, c, fresh_phi, c);
+  if (s != PFL_OK) return s;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return PFL_OK;
+}
+
+pfl_status pfl_set_solid(pfl_ctx* c, const unsigned char* mask) {
+  if (!c) return fail(PFL_ERR_ARG, "context is NULL");
+  if (!mask) return fail(PFL_ERR_ARG, "mask is NULL");
+  if (!c->p.solids) return fail(PFL_ERR_STATE, "the context was created without solids (pfl_params.solids = 0)");
+  if (c->t != 0) return fail(PFL_ERR_STATE, "solid cells are set before the first step");
+  CUDA_TRY(cudaSetDevice(c->device));
+  const long long N = c->geo.N;
+  unsigned char* st = (unsigned char*)stage(c);  // N bytes fit the N + 16 doubles of the staging area
+  CUDA_TRY(cudaMemcpyAsync(st, mask, (size_t)N, cudaMemcpyDefault, c->stream));
+  pfl_status s = PFL_OK;
+  DISPATCH_S(s, c, apply_solid, c, st);
   if (s != PFL_OK) return s;
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PFL_OK;
@@ -937,6 +986,7 @@ pfl_status pfl_adjoint(pfl_ctx* c, int n_steps, int n_obs, const int* obs_steps,
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
   if (n_steps < 1) return fail(PFL_ERR_ARG, "n_steps must be >= 1");
   if (c->p.precision == PFL_FP16S) return fail(PFL_ERR_STATE, "the adjoint runs on FP64 or FP32 storage");
+  if (c->solid) return fail(PFL_ERR_STATE, "the adjoint covers lattices without solid cells");
   if (c->p.collision != PFL_MRT) return fail(PFL_ERR_STATE, "the adjoint covers the MRT collision");
   if (!c->idx32) return fail(PFL_ERR_STATE, "lattice too large for the adjoint kernels (27 N >= 2^32)");
   if (n_obs < 1 || n_obs > ADJ_MAX_OBS || !obs_steps || !obs_weights)

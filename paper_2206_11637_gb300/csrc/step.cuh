@@ -123,16 +123,27 @@ __device__ __forceinline__ AxisOff axis_off(unsigned x, unsigned n, int stride, 
 }
 
 
+// Blocked links of a cell next to solid cells: bit (cx+1) + 3(cy+1) + 9(cz+1)
+// is set when the neighbour in direction c is solid; bit 13 (the rest
+// direction) marks the cell itself solid.  Zero away from solids, and a
+// compile-time zero in kernels built without solids.
+__host__ __device__ constexpr unsigned link_bit(int cx, int cy, int cz) {
+  return 1u << ((cx + 1) + 3 * (cy + 1) + 9 * (cz + 1));
+}
+constexpr unsigned SOLID_SELF = 1u << 13;
+
 struct CellOff {
   AxisOff X, Y, Z;
-  // population offset and validity of direction (cx, cy, cz)
+  unsigned blk = 0;  // blocked links (solid neighbours)
+  // population offset and validity of direction (cx, cy, cz): a link leaving
+  // through a no-slip face or into a solid cell is bounced back half-way
   __device__ __forceinline__ int off(int cx, int cy, int cz) const {
     return (cx < 0 ? X.om : cx > 0 ? X.op : 0) + (cy < 0 ? Y.om : cy > 0 ? Y.op : 0) +
            (cz < 0 ? Z.om : cz > 0 ? Z.op : 0);
   }
   __device__ __forceinline__ bool valid(int cx, int cy, int cz) const {
     return (cx < 0 ? X.vm : cx > 0 ? X.vp : true) && (cy < 0 ? Y.vm : cy > 0 ? Y.vp : true) &&
-           (cz < 0 ? Z.vm : cz > 0 ? Z.vp : true);
+           (cz < 0 ? Z.vm : cz > 0 ? Z.vp : true) && !(blk & link_bit(cx, cy, cz));
   }
   __device__ __forceinline__ int soff(int cx, int cy, int cz) const {
     return (cx < 0 ? X.sm : cx > 0 ? X.sp : 0) + (cy < 0 ? Y.sm : cy > 0 ? Y.sp : 0) +
@@ -524,11 +535,12 @@ template <int PREC, int QH, int READ_ODD>
 __device__ __forceinline__ typename Store<PREC>::R phi_cell(const Geo32& geo,
                                                             const typename Store<PREC>::S* __restrict__ h,
                                                             const typename Store<PREC>::PhiT* __restrict__ shift,
-                                                            unsigned cell) {
+                                                            unsigned cell, unsigned blk = 0) {
   typedef typename Store<PREC>::R R;
   constexpr bool F16 = PREC == 2;
   CellOff o;
   cell_off(geo, cell, o);
+  o.blk = blk;  // a bounced population was written by this cell
   R s = F16 ? (raw<PREC>(h[(unsigned)hq_rest<QH>() * geo.N + cell]) * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)hq_w<QH>(hq_rest<QH>())
             : raw<PREC>(h[(unsigned)hq_rest<QH>() * geo.N + cell]);
 #pragma unroll
@@ -545,14 +557,18 @@ __device__ __forceinline__ typename Store<PREC>::R phi_cell(const Geo32& geo,
 }
 
 // phi = sum_i h_i of the state left by the last step (READ_ODD after an even
-// step); `shift` holds the shifts of the stored populations (FP16S).
+// step); `shift` holds the shifts of the stored populations (FP16S).  With
+// `links` (a lattice with solid cells) blocked links bounce and solid cells
+// hold phi = 0.
 template <int PREC, int QH, int READ_ODD>
 __global__ void __launch_bounds__(256) k_phi32(Geo32 geo, const typename Store<PREC>::S* __restrict__ h,
                                                const typename Store<PREC>::PhiT* __restrict__ shift,
-                                               typename Store<PREC>::PhiT* __restrict__ phi) {
+                                               typename Store<PREC>::PhiT* __restrict__ phi,
+                                               const unsigned* __restrict__ links = nullptr) {
   const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
-  phi[cell] = phi_cell<PREC, QH, READ_ODD>(geo, h, shift, cell);
+  const unsigned blk = links ? __ldg(links + cell) : 0u;
+  phi[cell] = (blk & SOLID_SELF) ? (typename Store<PREC>::PhiT)0 : phi_cell<PREC, QH, READ_ODD>(geo, h, shift, cell, blk);
 }
 
 }  // namespace pfl
@@ -580,7 +596,9 @@ template <int PREC>
 struct SmemPhi {
   const typename Store<PREC>::PhiT* plane[3];  // planes z - 1, z, z + 1 of (ZM_TY + 2) x (ZM_TX + 2) values
   int i0;                 // index of this thread's column in a plane
+  unsigned blk = 0;       // blocked links: a solid neighbour reads as this cell (neutral wetting)
   __device__ __forceinline__ typename Store<PREC>::R operator()(int cx, int cy, int cz) const {
+    if (blk & link_bit(cx, cy, cz)) return (typename Store<PREC>::R)plane[1][i0];
     return (typename Store<PREC>::R)plane[1 + cz][i0 + cy * (ZM_TX + 2) + cx];
   }
 };
@@ -596,13 +614,15 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, int wall) {
 template <int PREC, int QH>
 __device__ __forceinline__ void h_moments_xyz(const Geo32& geo, const typename Store<PREC>::S* __restrict__ h,
                                               const typename Store<PREC>::PhiT* __restrict__ shift, unsigned x,
-                                              unsigned y, unsigned z, typename Store<PREC>::R m[10]) {
+                                              unsigned y, unsigned z, typename Store<PREC>::R m[10],
+                                              unsigned blk = 0) {
   typedef typename Store<PREC>::R R;
   constexpr bool F16 = PREC == 2;
   CellOff o;
   o.X = axis_off(x, geo.nx, 1, geo.wall[0]);
   o.Y = axis_off(y, geo.ny, (int)geo.nx, geo.wall[1]);
   o.Z = axis_off(z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
+  o.blk = blk;  // a bounced population was written by this cell
   const unsigned cell = x + geo.nx * (y + geo.ny * z);
   const unsigned N = geo.N;
   R phl, hjx = 0, hjy = 0, hjz = 0, hxx = 0, hyy = 0, hzz = 0, hxy = 0, hyz = 0, hxz = 0;
@@ -655,13 +675,15 @@ template <int PREC, int QH>
 __device__ __forceinline__ typename Store<PREC>::R phi_at_xyz(const Geo32& geo,
                                                               const typename Store<PREC>::S* __restrict__ h,
                                                               const typename Store<PREC>::PhiT* __restrict__ shift,
-                                                              unsigned x, unsigned y, unsigned z) {
+                                                              unsigned x, unsigned y, unsigned z,
+                                                              unsigned blk = 0) {
   typedef typename Store<PREC>::R R;
   constexpr bool F16 = PREC == 2;
   CellOff o;
   o.X = axis_off(x, geo.nx, 1, geo.wall[0]);
   o.Y = axis_off(y, geo.ny, (int)geo.nx, geo.wall[1]);
   o.Z = axis_off(z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
+  o.blk = blk;  // a bounced population was written by this cell
   const unsigned cell = x + geo.nx * (y + geo.ny * z);
   R s = F16 ? (raw<PREC>(h[(unsigned)hq_rest<QH>() * geo.N + cell]) * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)hq_w<QH>(hq_rest<QH>())
             : raw<PREC>(h[(unsigned)hq_rest<QH>() * geo.N + cell]);
@@ -696,12 +718,14 @@ __device__ __forceinline__ void frame_pos(int r, int W, int H, int& i, int& j) {
 }
 
 // grid: (ceil(nx / ZM_TX), ceil(ny / ZM_TY), ceil(nz / zc)), block ZM_TX x ZM_TY.
-template <int PREC, int QH, int FLAT>
+// SOLID: the lattice holds solid cells, given by `links` (one word per cell).
+template <int PREC, int QH, int FLAT, int SOLID = 0>
 __global__ void __launch_bounds__(ZM_TX * ZM_TY, PREC == 0 ? PFL_ZM_MINB_FP64 : PFL_ZM_MINB)
     k_step_zm(Geo32 geo, Phys ph, const typename Store<PREC>::S* __restrict__ hA,
               const typename Store<PREC>::S* __restrict__ gA, typename Store<PREC>::S* __restrict__ hB,
               typename Store<PREC>::S* __restrict__ gB, const typename Store<PREC>::PhiT* __restrict__ phi_shift,
-              typename Store<PREC>::PhiT* __restrict__ phi_out, int zc, unsigned seed) {
+              typename Store<PREC>::PhiT* __restrict__ phi_out, int zc, unsigned seed,
+              const unsigned* __restrict__ links = nullptr) {
   typedef typename Store<PREC>::PhiT PhiT;
   typedef typename Store<PREC>::R R;
   constexpr int NT = ZM_TX * ZM_TY;
@@ -733,11 +757,15 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, PREC == 0 ? PFL_ZM_MINB_FP64 : 
   auto fill = [&](int zp, int slot, int mslot) {
     const unsigned zq = (unsigned)wrap_or_clamp(zp, (int)geo.nz, geo.wall[2]);
     R m[10];
-    h_moments_xyz<PREC, QH>(geo, hA, phi_shift, xq, yq, zq, m);
+    const unsigned bt = SOLID ? __ldg(links + xq + geo.nx * (yq + geo.ny * zq)) : 0u;
+    h_moments_xyz<PREC, QH>(geo, hA, phi_shift, xq, yq, zq, m, bt);
     ring[slot][(ty + 1) * PW + tx + 1] = (PhiT)m[0];
 #pragma unroll
     for (int k = 0; k < 10; ++k) hmom[mslot][k * NT + tid] = m[k];
-    if (tid < NRING) ring[slot][rj * PW + ri] = (PhiT)phi_at_xyz<PREC, QH>(geo, hA, phi_shift, rxq, ryq, zq);
+    if (tid < NRING) {
+      const unsigned br = SOLID ? __ldg(links + rxq + geo.nx * (ryq + geo.ny * zq)) : 0u;
+      ring[slot][rj * PW + ri] = (PhiT)phi_at_xyz<PREC, QH>(geo, hA, phi_shift, rxq, ryq, zq, br);
+    }
   };
 
   if (FLAT) {
@@ -750,9 +778,13 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, PREC == 0 ? PFL_ZM_MINB_FP64 : 
     const int b = z - (z0 - 1);
     if (!FLAT) fill(z + 1, (b + 1) % NS, (z + 1 - z0) & 1);
     __syncthreads();
-    if (active) {
-      const unsigned cell = (unsigned)x + geo.nx * ((unsigned)y + geo.ny * (unsigned)z);
+    const unsigned cell = (unsigned)x + geo.nx * ((unsigned)y + geo.ny * (unsigned)z);
+    const unsigned blk = (SOLID && active) ? __ldg(links + cell) : 0u;
+    if (SOLID && active && (blk & SOLID_SELF)) {
+      phi_out[cell] = (PhiT)0;  // solid cells are not updated; their populations stay zero
+    } else if (active) {
       CellOff o;
+      o.blk = blk;
       o.X = axis_off((unsigned)x, geo.nx, 1, geo.wall[0]);
       o.Y = axis_off((unsigned)y, geo.ny, (int)geo.nx, geo.wall[1]);
       o.Z = axis_off((unsigned)z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
@@ -766,6 +798,7 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, PREC == 0 ? PFL_ZM_MINB_FP64 : 
       }
       // with one z plane the z neighbours are the plane itself (periodic or mirrored)
       at.i0 = (ty + 1) * PW + (tx + 1);
+      at.blk = blk;
       phi_out[cell] = (PhiT)at(0, 0, 0);
       collide_cell<PREC, QH, 0, 1, SmemPhi<PREC>, 1>(geo, ph, o, hA, gA, hB, gB, at, phi_shift, cell, seed,
                                                  &hmom[FLAT ? 0 : ((z - z0) & 1)][tid], NT);

@@ -25,6 +25,7 @@ def _params_struct(p, precision):
     s.collision = int(p.collision)
     s.engine = int(getattr(p, "engine", 0))
     s.h_lattice = int(getattr(p, "h_lattice", 15))
+    s.solids = 1 if getattr(p, "solid", None) is not None else 0
     return s
 
 
@@ -74,6 +75,12 @@ class Simulation:
                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(ctx)))
         self.ctx = ctx
         self._keep = None
+        solid = getattr(p, "solid", None)
+        if solid is not None:   # solid cells (nonzero), (nz, ny, nx)
+            mask = np.ascontiguousarray(np.asarray(solid).reshape(-1) != 0, dtype=np.uint8)
+            if mask.size != self.N:
+                raise ValueError("solid mask must hold one byte per cell")
+            L.check(self.lib.pfl_set_solid(self.ctx, _ptr(mask)))
 
     def _as_f64(self, a, n):
         if a is None:

@@ -34,7 +34,8 @@ class Params:
     gravity: tuple = (0.0, 0.0, 0.0)
     collision: int = 0                    # 0 weighted-orthogonal MRT, 1 BGK
     engine: int = 0                       # 0 auto (fused two-array step), 1 in-place AA + phi pass
-    h_lattice: int = 15                   # phase-field lattice: 15 (D3Q15) or 27 (D3Q27)
+    h_lattice: int = 15                   # phase-field lattice: 15 (D3Q15), 27 (D3Q27) or 9 (D2Q9 h and g, 2-D)
+    solid: object = None                  # optional solid-cell mask (nz, ny, nx), nonzero = solid
 
     @property
     def shape(self):
@@ -248,6 +249,61 @@ def drop_impact(nx=512, ny=384, nz=512, D=64.0, depth=128.0, gap=8.0, We=200.0, 
         rho = p.rho_l + phi0 * (p.rho_h - p.rho_l)
         p0 = 3.0 * pres / rho
     return p, phi0, u0, p0
+
+
+def pipe_mask(p, diameter):
+    """Solid cells outside a tube of the given diameter along y, centred in x and z."""
+    x, y, z = coords(p)
+    r = np.sqrt((x - (p.nx - 1) / 2.0) ** 2 + (z - (p.nz - 1) / 2.0) ** 2)
+    return (r > diameter / 2.0).astype(np.uint8)
+
+
+def hagen_poiseuille(D=16, L=4, g=1e-6, nu=1.0 / 6.0):
+    """Single-phase flow driven by a body force along y in a voxelised tube of
+    diameter D (solid cells outside), periodic along y."""
+    n = D + 2
+    p = Params(n, L, n, (PERIODIC,) * 6, 1.0, 1e-3, nu, nu, 1e-4, 0.02, 5.0, (0.0, g, 0.0))
+    p.solid = pipe_mask(p, D)
+    return p, np.ones(p.shape), None, None
+
+
+def taylor_bubble(D=64, Bo=100.0, Mo=0.015, rho_ratio=744.0, mu_ratio=4236.0, omega_h=1.76, xi=3.0, M=0.08,
+                  collision=0, p_level=None):
+    """Taylor bubble (section "Taylor bubble"): a vertical tube of diameter D
+    along y (solid cells outside it, one solid ring at least: the lattice is
+    (D + 2) x 10D x (D + 2)), no-slip top and bottom; a gas cylinder of
+    diameter 0.75 D and length 3 D with its bottom at D; nu_H from omega_H,
+    nu_L = nu_H rho_ratio / mu_ratio; with rho_H = 1 the Bond number
+    Bo = g D^2 / sigma and the Morton number Mo = g mu_H^4 (1 - rho_L) / sigma^3
+    give sigma = mu_H^2 sqrt(Bo (1 - rho_L) / Mo) / D and g.  Hydrostatic start
+    with zero pressure at height p_level: by default the bubble's top, so that
+    the gas starts near zero pressure (the pressure force -p* c_s^2 grad rho
+    makes the model sensitive to the gas pressure level); the paper's
+    reference height is 5 D."""
+    nu_h = (1.0 / omega_h - 0.5) / 3.0
+    rho_l = 1.0 / rho_ratio
+    sigma = nu_h ** 2 * math.sqrt(Bo * (1.0 - rho_l) / Mo) / D
+    g = Bo * sigma / (D * D)
+    bc = (PERIODIC, PERIODIC, NOSLIP, NOSLIP, PERIODIC, PERIODIC)
+    n = D + 2
+    p = Params(n, 10 * D, n, bc, 1.0, rho_l, nu_h, nu_h * rho_ratio / mu_ratio, sigma, M, xi, (0.0, -g, 0.0),
+               collision)
+    p.solid = pipe_mask(p, D)
+    x, y, z = coords(p)
+    r = np.sqrt((x - (n - 1) / 2.0) ** 2 + (z - (n - 1) / 2.0) ** 2)
+    yb, yt = D - 0.5, 4 * D - 0.5            # the bottom wall sits half a cell below y = 0
+    d = np.maximum(r - 0.375 * D, np.maximum(yb - y, y - yt))   # < 0 inside the gas cylinder
+    phi0 = tanh_profile(-d, xi)
+    level = yt if p_level is None else p_level
+    return p, phi0, None, column_hydrostatic_pstar(p, phi0, level)
+
+
+def gas_centroid_y(phi, solid):
+    """Height of the gas centroid, sum (1 - phi) y / sum (1 - phi) over fluid cells."""
+    fluid = np.asarray(solid).reshape(phi.shape) == 0
+    gas = np.where(fluid, 1.0 - phi, 0.0)
+    y = np.arange(phi.shape[1], dtype=np.float64)[None, :, None]
+    return float((gas * y).sum() / gas.sum())
 
 
 def batched_sweep(count=512, seed=20240601, small=False):
