@@ -54,6 +54,20 @@ def step_kernel_bytes(prec, engine=0, qh=15, qg=27):
     return b
 
 
+GRAPH_STEPS = 32   # the library's default steps per replayed graph (fused engine)
+
+
+def step_launches(S, engine):
+    """Kernel launches of one pfl_step(S): the fused engine runs S // 32 graph
+    replays of 32 step kernels and one step-count kernel each, the remaining
+    steps one by one and, after those, one kernel that sets the device step
+    count before the next replay; the in-place engine launches the step and
+    its phi pass per step."""
+    if engine != 0:
+        return 2 * S
+    return S + S // GRAPH_STEPS + (1 if S % GRAPH_STEPS else 0)
+
+
 def ideal_step_bytes(prec):
     """Algorithmic bytes per cell update of the whole step: 2 (15 + 27) S + phi read + phi write."""
     return 2 * (15 + 27) * PREC_BYTES[prec] + 2 * PHI_BYTES[prec]
@@ -587,7 +601,7 @@ def main():
                 "config": {"workload": args.workload, "description": wl["desc"], "precision": prec,
                            "cells": N, "lattice_steps_per_step": S, "parallelism": "replicas" if ws > 1 else "1 GPU",
                            "l2": "flushed between timed steps" if flush else "working set larger than L2"},
-                "e2e": e2e, "gpu_launches": (1 if args.engine == 0 else 2) * S * K, "clocks": clocks, "roofline": roofline,
+                "e2e": e2e, "gpu_launches": step_launches(S, args.engine) * K, "clocks": clocks, "roofline": roofline,
                 "cpu_baseline": cpu, "nonfinite_cells": nf, "wall_s": wall, "adjoint": adj,
                 "configs": configs}
         line.update(compare)

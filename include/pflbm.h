@@ -115,8 +115,17 @@ size_t pfl_workspace_bytes(const pfl_params* p);
 pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, const double* p0,
                     void* workspace, size_t workspace_bytes, void* stream, pfl_ctx** out);
 
-/* Advance n_steps >= 0 time steps.  Asynchronous: only queues kernels. */
+/* Advance n_steps >= 0 time steps.  Asynchronous: only queues kernels.
+ * The fused engine advances whole runs of graph_k steps (default 32) by
+ * replaying a CUDA graph of them, captured on first use on a stream of the
+ * context's own; the rest, and every step while the caller's stream is being
+ * captured, launch one by one.  Both give bitwise the same states. */
 pfl_status pfl_step(pfl_ctx* ctx, int n_steps);
+
+/* Steps per CUDA graph of the fused engine: 0 (launch every step on its own)
+ * or even in [2, 4096].  Drops the graphs captured so far.  Synchronises the
+ * stream.  PFL_ERR_ARG for other values. */
+pfl_status pfl_set_graph_steps(pfl_ctx* ctx, int graph_steps);
 
 /* Macroscopic fields at the current time: phi, rho(phi), p = p* rho c_s^2
  * (Eq. zeroth_moment_hydro and the definition of p*) and u = sum_i c_i g_i +

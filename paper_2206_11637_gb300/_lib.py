@@ -56,6 +56,8 @@ def load():
     lib.pfl_init.argtypes = [PP, P, P, P, P, S, P, ctypes.POINTER(P)]
     lib.pfl_step.restype = I
     lib.pfl_step.argtypes = [P, I]
+    lib.pfl_set_graph_steps.restype = I
+    lib.pfl_set_graph_steps.argtypes = [P, I]
     lib.pfl_fields.restype = I
     lib.pfl_fields.argtypes = [P, P, P, P, P]
     lib.pfl_populations.restype = I

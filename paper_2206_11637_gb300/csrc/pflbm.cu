@@ -51,7 +51,7 @@ pfl_status cuda_fail(cudaError_t e, const char* what) {
 
 
 struct Layout {
-  size_t h, g, h2, g2, phi[2], links, stage, red, total;
+  size_t h, g, h2, g2, phi[2], links, stage, red, clock, total;
 };
 
 Layout layout_of(const pfl_params* p) {
@@ -80,6 +80,8 @@ Layout layout_of(const pfl_params* p) {
   off = align256(off + (N + 16) * sizeof(double));
   L.red = off;
   off = align256(off + (DIAG_BLOCKS * 9 + 16) * sizeof(double));
+  L.clock = off;  // step count read by graph-replayed steps
+  off = align256(off + sizeof(unsigned long long));
   L.total = off;
   return L;
 }
@@ -109,6 +111,14 @@ struct pfl_ctx {
   int qh;        // phase-field lattice: 15, 27 or 9 velocities
   int qg;        // hydrodynamic lattice: 27, or 9 in 2-D
   bool solid;    // solid cells set (pfl_set_solid): the fused step reads the link words
+  // CUDA graphs of graph_k fused steps, one per (ab, cur) state at capture;
+  // replays read the step count from the workspace clock
+  int graph_k;
+  cudaGraphExec_t gx[4];
+  cudaStream_t cap;         // capture stream (created on first use)
+  bool capturing;           // launches are being captured: pass the clock
+  long long cap_t0;         // step count when the capture began
+  long long clock_t;        // step count the device clock holds (-1: unknown)
 };
 
 namespace {
@@ -145,7 +155,16 @@ typename Store<PREC>::PhiT* phishift(pfl_ctx* c) {
 double* stage(pfl_ctx* c) { return (double*)(c->ws + c->L.stage); }
 
 // seed of the FP16 stochastic rounding of one step
-unsigned step_seed(const pfl_ctx* c) { return (unsigned)((unsigned long long)c->t * 0x9E3779B97F4A7C15ull >> 32); }
+unsigned step_seed(const pfl_ctx* c) { return step_seed_of((unsigned long long)c->t); }
+unsigned long long* clock_of(pfl_ctx* c) { return (unsigned long long*)(c->ws + c->L.clock); }
+
+// the device step count: set (add = 0) or advance (add = 1)
+__global__ void k_clock(unsigned long long* t, long long v, int add) {
+  if (add)
+    *t += (unsigned long long)v;
+  else
+    *t = (unsigned long long)v;
+}
 
 // phi of the stored state into the spare buffer, then make it current.  The
 // stored h carry the shifts of buffer `cur` (after a step) -- the spare buffer
@@ -174,14 +193,17 @@ template <int PREC, int QH, int BGK>
 void step_only(pfl_ctx* c) {
   const unsigned nb = blocks_for(c->geo.N, 256);
   if (c->zm) {
-    const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
-    const dim3 block(ZM_TX, ZM_TY);
+    const int ty = zm_ty(c->p.nz == 1);
+    const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ty - 1) / ty, (c->p.nz + c->zc - 1) / c->zc);
+    const dim3 block(ZM_TX, ty);
     const unsigned* links = (const unsigned*)(c->ws + c->L.links);
 #define PFL_ZM(FLAT, SOLID)                                                                                      \
   k_step_zm<PREC, QH, FLAT, SOLID><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),   \
                                                                   hnext<PREC>(c), gnext<PREC>(c),                 \
                                                                   phishift<PREC>(c), phicur<PREC>(c), c->zc,      \
-                                                                  step_seed(c), links)
+                                                                  step_seed(c), links,                            \
+                                                                  c->capturing ? clock_of(c) : nullptr,           \
+                                                                  (int)(c->t - c->cap_t0))
     if (c->p.nz == 1) {
       if (c->solid)
         PFL_ZM(1, 1);
@@ -376,6 +398,63 @@ pfl_status apply_solid(pfl_ctx* c, const unsigned char* mask_dev) {
   return fresh_phi<PREC, QH>(c);  // phi = 0 in solid cells; shifts of fresh populations
 }
 
+void drop_graphs(pfl_ctx* c) {
+  for (int k = 0; k < 4; ++k)
+    if (c->gx[k]) {
+      cudaGraphExecDestroy(c->gx[k]);
+      c->gx[k] = nullptr;
+    }
+}
+
+// One replay of graph_k fused steps (captured on first use for the current
+// (ab, cur) state; graph_k is even, so a replay returns the context to it).
+// Every launch of the graph reads the step count from the device clock, which
+// the graph advances by graph_k at its end: FP16S runs draw the same rounding
+// bits as step-by-step launches.
+pfl_status graph_steps(pfl_ctx* c) {
+  const int slot = c->ab * 2 + c->cur;
+  if (!c->gx[slot]) {
+    if (!c->cap) CUDA_TRY(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+    const long long t = c->t;
+    const int ab = c->ab, cur = c->cur;
+    const bool stale = c->stale;
+    cudaStream_t user = c->stream;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      c->stream = c->cap;
+      c->capturing = true;
+      c->cap_t0 = t;
+      DISPATCH(c, launch_steps, c, c->graph_k);
+      k_clock<<<1, 1, 0, c->cap>>>(clock_of(c), c->graph_k, 1);
+      const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+      e = cudaGetLastError();
+      if (e == cudaSuccess) e = e2;
+    }
+    c->stream = user;
+    c->capturing = false;
+    c->t = t;
+    c->ab = ab;
+    c->cur = cur;
+    c->stale = stale;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gx[slot], g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      c->gx[slot] = nullptr;
+      return cuda_fail(e, "capturing the step graph");
+    }
+  }
+  if (c->clock_t != c->t) {
+    k_clock<<<1, 1, 0, c->stream>>>(clock_of(c), c->t, 0);
+    c->clock_t = c->t;
+  }
+  CUDA_TRY(cudaGraphLaunch(c->gx[slot], c->stream));
+  c->t += c->graph_k;
+  c->clock_t += c->graph_k;
+  c->stale = true;
+  return PFL_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -421,6 +500,12 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
   c->qh = qh_of(p);
   c->qg = qg_of(p);
   c->solid = false;
+  c->graph_k = 32;
+  for (int k = 0; k < 4; ++k) c->gx[k] = nullptr;
+  c->cap = nullptr;
+  c->capturing = false;
+  c->cap_t0 = 0;
+  c->clock_t = -1;
   {
     // z planes per block.  Every block marches zc planes and fills two more
     // (the planes below and above its first) before it starts, about half a
@@ -535,8 +620,29 @@ pfl_status pfl_step(pfl_ctx* c, int n) {
   CUDA_TRY(cudaSetDevice(c->device));
   if (n < 0) return fail(PFL_ERR_ARG, "n_steps must be >= 0");
   if (n == 0) return PFL_OK;
-  DISPATCH(c, launch_steps, c, n);
+  if (c->zm && c->graph_k > 0 && n >= c->graph_k) {
+    // whole graphs of graph_k steps, unless the caller is capturing the stream
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(c->stream, &cs));
+    if (cs == cudaStreamCaptureStatusNone) {
+      for (; n >= c->graph_k; n -= c->graph_k) {
+        const pfl_status s = graph_steps(c);
+        if (s != PFL_OK) return s;
+      }
+    }
+  }
+  if (n > 0) DISPATCH(c, launch_steps, c, n);
   CUDA_TRY(cudaGetLastError());
+  return PFL_OK;
+}
+
+pfl_status pfl_set_graph_steps(pfl_ctx* c, int k) {
+  if (!c) return fail(PFL_ERR_ARG, "context is NULL");
+  if (k < 0 || k % 2 != 0 || k > 4096) return fail(PFL_ERR_ARG, "graph steps must be 0 or even in [2, 4096]");
+  CUDA_TRY(cudaSetDevice(c->device));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  c->graph_k = k;
   return PFL_OK;
 }
 
@@ -822,8 +928,9 @@ struct SlotPtr {
 // in shared memory) goes to a's phi.  FP64 / FP32 only: no shifts.
 template <int PREC, int QH>
 void zm_step_slots(pfl_ctx* c, const SlotPtr<PREC>& a, const SlotPtr<PREC>& b) {
-  const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
-  const dim3 block(ZM_TX, ZM_TY);
+  const int ty = zm_ty(c->p.nz == 1);
+  const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ty - 1) / ty, (c->p.nz + c->zc - 1) / c->zc);
+  const dim3 block(ZM_TX, ty);
   if (c->p.nz == 1)
     k_step_zm<PREC, QH, 1><<<grid, block, 0, c->stream>>>(c->g32, c->ph, a.h, a.g, b.h, b.g, nullptr, a.phi, c->zc, 0u);
   else
@@ -1027,6 +1134,8 @@ pfl_status pfl_adjoint(pfl_ctx* c, int n_steps, int n_obs, const int* obs_steps,
 void pfl_destroy(pfl_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
+  drop_graphs(c);
+  if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
 }
 

@@ -132,6 +132,11 @@ __host__ __device__ constexpr unsigned link_bit(int cx, int cy, int cz) {
 }
 constexpr unsigned SOLID_SELF = 1u << 13;
 
+// seed of the FP16 stochastic rounding of step t (Fibonacci hashing of t)
+__host__ __device__ __forceinline__ unsigned step_seed_of(unsigned long long t) {
+  return (unsigned)(t * 0x9E3779B97F4A7C15ull >> 32);
+}
+
 struct CellOff {
   AxisOff X, Y, Z;
   unsigned blk = 0;  // blocked links (solid neighbours)
@@ -589,8 +594,13 @@ namespace pfl {
 // FP16S shift of the populations written this step and the phi output), so
 // the separate phi pass and its re-read of h disappear.  Ring and z-halo
 // planes repeat the phi sum of neighbouring tiles (from L2).
+// A single-plane lattice (FLAT) has no z march to hide latency behind; its
+// tiles are 32 x 4, so that a small lattice spreads over more blocks (and the
+// SMs' loads even out) for a slightly larger share of ring cells.
 constexpr int ZM_TX = 32;
 constexpr int ZM_TY = 8;
+constexpr int ZM_TY_FLAT = 4;
+__host__ __device__ constexpr int zm_ty(int flat) { return flat ? ZM_TY_FLAT : ZM_TY; }
 
 template <int PREC>
 struct SmemPhi {
@@ -717,19 +727,26 @@ __device__ __forceinline__ void frame_pos(int r, int W, int H, int& i, int& j) {
   }
 }
 
-// grid: (ceil(nx / ZM_TX), ceil(ny / ZM_TY), ceil(nz / zc)), block ZM_TX x ZM_TY.
+// grid: (ceil(nx / ZM_TX), ceil(ny / TY), ceil(nz / zc)), block ZM_TX x TY with
+// TY = zm_ty(FLAT).
 // SOLID: the lattice holds solid cells, given by `links` (one word per cell).
+// tclock (launches replayed from a CUDA graph): the FP16 rounding seed comes
+// from the step count *tclock + tofs in device memory instead of `seed`, the
+// same function of the step count as the host's.
 template <int PREC, int QH, int FLAT, int SOLID = 0>
-__global__ void __launch_bounds__(ZM_TX * ZM_TY, PREC == 0 ? PFL_ZM_MINB_FP64 : PFL_ZM_MINB)
+__global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_FP64 : PFL_ZM_MINB) * ZM_TY / zm_ty(FLAT))
     k_step_zm(Geo32 geo, Phys ph, const typename Store<PREC>::S* __restrict__ hA,
               const typename Store<PREC>::S* __restrict__ gA, typename Store<PREC>::S* __restrict__ hB,
               typename Store<PREC>::S* __restrict__ gB, const typename Store<PREC>::PhiT* __restrict__ phi_shift,
               typename Store<PREC>::PhiT* __restrict__ phi_out, int zc, unsigned seed,
-              const unsigned* __restrict__ links = nullptr) {
+              const unsigned* __restrict__ links = nullptr, const unsigned long long* tclock = nullptr,
+              int tofs = 0) {
   typedef typename Store<PREC>::PhiT PhiT;
   typedef typename Store<PREC>::R R;
-  constexpr int NT = ZM_TX * ZM_TY;
-  constexpr int PW = ZM_TX + 2, PH = ZM_TY + 2, PS = PW * PH;
+  if (PREC == 2 && tclock) seed = step_seed_of(*tclock + (unsigned long long)tofs);
+  constexpr int TY = zm_ty(FLAT);
+  constexpr int NT = ZM_TX * TY;
+  constexpr int PW = ZM_TX + 2, PH = TY + 2, PS = PW * PH;
   constexpr int NRING = 2 * (PW + PH) - 4;
   static_assert(NRING <= NT, "one thread per ring position");
   // phi planes z - 1, z, z + 1 and the one being filled: with four slots the
@@ -741,7 +758,7 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY, PREC == 0 ? PFL_ZM_MINB_FP64 : 
   __shared__ PhiT ring[NS][PS];
   __shared__ R hmom[FLAT ? 1 : 2][10 * NT];  // h moments of the tile's own cells
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZM_TX + tx;
-  const int x0 = blockIdx.x * ZM_TX, y0 = blockIdx.y * ZM_TY;
+  const int x0 = blockIdx.x * ZM_TX, y0 = blockIdx.y * TY;
   const int z0 = blockIdx.z * zc;
   const int z1 = min(z0 + zc, (int)geo.nz);
   const int x = x0 + tx, y = y0 + ty;

@@ -113,6 +113,10 @@ class Simulation:
     def step(self, n=1):
         L.check(self.lib.pfl_step(self.ctx, int(n)))
 
+    def set_graph_steps(self, k):
+        """Steps per replayed CUDA graph of the fused engine (0: none)."""
+        L.check(self.lib.pfl_set_graph_steps(self.ctx, int(k)))
+
     def adjoint(self, n_steps, observations):
         """Discrete adjoint over the next n_steps steps.
 
