@@ -107,9 +107,12 @@ def kernel_hash():
 # and the hash of the kernel sources they were taken on.  A capture of another
 # kernel version does not apply.
 NCU_TRAFFIC = {
-    # k_step_zm<2, 15, 1>, 200x400x1 wave, three captured launches: 7.08, 7.07, 7.07 MB read, 0 written
-    # (profiles/launches_capillary_wave_200x400_fp16s.md)
-    ("capillary_wave", "fp16s", "619becd42f63ed96"): 7075840.0,
+    # k_step_zm<2, 15, 1, 0>, 200x400x1 wave, three captured launches: 7.07 MB read, 0 written
+    # (profiles/k_step_zm_capillary_wave_200x400_fp16s.md)
+    ("capillary_wave", "fp16s", "294c3b9824cb842a"): 7073536.0,
+    # k_step_zm<2, 15, 0, 0>, rising bubble 128x384x128: 578.7 MB read + 519.9 MB written
+    # (profiles/k_step_zm_rising_bubble_128x384x128.md)
+    ("rising_bubble", "fp16s", "294c3b9824cb842a"): 1098625536.0,
 }
 
 
