@@ -28,6 +28,12 @@
 namespace pfl {
 
 constexpr int ADJ_THREADS = 128;
+// Resident blocks of k_adj_local per SM the compiler is asked for (0: no bound,
+// 158 registers, 3 blocks).  On the 128x384x128 FP32 bubble (400 steps) the
+// adjoint took 832 ms unbounded, 880 / 856 / 871 ms at 4 / 5 / 6 blocks.
+#ifndef PFL_ADJ_MINB
+#define PFL_ADJ_MINB 0
+#endif
 
 // Parameters of the reverse sweep that the forward step folds into Phys.
 struct AdjPar {
@@ -58,7 +64,7 @@ __device__ __forceinline__ R block_sum3_to(R a, R b, R c, double* out3) {
 }
 
 template <int PREC, int QH, int READ_ODD>
-__global__ void __launch_bounds__(ADJ_THREADS) k_adj_local(Geo32 geo, Phys ph, AdjPar ap,
+__global__ void __launch_bounds__(ADJ_THREADS, PFL_ADJ_MINB) k_adj_local(Geo32 geo, Phys ph, AdjPar ap,
                                                            const typename Store<PREC>::S* __restrict__ h,
                                                            const typename Store<PREC>::S* __restrict__ g,
                                                            const typename Store<PREC>::PhiT* __restrict__ phi,
