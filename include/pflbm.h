@@ -154,6 +154,25 @@ pfl_status pfl_set_populations(pfl_ctx* ctx, const double* h, const double* g);
  * batch engine do not take solid cells.  Synchronises. */
 pfl_status pfl_set_solid(pfl_ctx* ctx, const unsigned char* mask);
 
+/* Saved states (checkpoint and resume).  A state is the stored arrays of the
+ * context as they are (the current h and g in the storage precision, both phi
+ * buffers, the link words of solid cells) after a small header with the
+ * lattice, the engine, the step count and the layout flags.  Loading it into a
+ * context of the same lattice, boundaries, precision, phase-field lattice and
+ * engine resumes the run bitwise: the step count (and with it the FP16
+ * rounding seeds) continues.  The physical parameters of the loading context
+ * apply from then on.
+ *   pfl_state_bytes: bytes of a saved state of this context (0 if ctx is NULL).
+ *   pfl_save: writes the state to buf (host or device, >= pfl_state_bytes).
+ *   pfl_load: reads it back; PFL_ERR_ARG for a buffer that is short, not a
+ *     state, or of another lattice, boundaries, precision or engine;
+ *     PFL_ERR_STATE for a state with solid cells loaded into a context created
+ *     without solids (or the reverse).
+ * Both synchronise the stream. */
+size_t pfl_state_bytes(const pfl_ctx* ctx);
+pfl_status pfl_save(pfl_ctx* ctx, void* buf, size_t bytes);
+pfl_status pfl_load(pfl_ctx* ctx, const void* buf, size_t bytes);
+
 /* FP64 reductions over the domain (section "Rising bubble": centre of mass):
  *   out[0] = sum phi, out[1..3] = sum phi * (x, y, z),
  *   out[4] = sum (1 - phi), out[5..7] = sum (1 - phi) * (x, y, z).

@@ -66,6 +66,12 @@ def load():
     lib.pfl_set_populations.argtypes = [P, P, P]
     lib.pfl_set_solid.restype = I
     lib.pfl_set_solid.argtypes = [P, P]
+    lib.pfl_state_bytes.restype = ctypes.c_size_t
+    lib.pfl_state_bytes.argtypes = [P]
+    lib.pfl_save.restype = I
+    lib.pfl_save.argtypes = [P, P, ctypes.c_size_t]
+    lib.pfl_load.restype = I
+    lib.pfl_load.argtypes = [P, P, ctypes.c_size_t]
     lib.pfl_diag.restype = I
     lib.pfl_diag.argtypes = [P, P, ctypes.POINTER(ctypes.c_longlong)]
     lib.pfl_adjoint_workspace_bytes.restype = S

@@ -725,6 +725,128 @@ pfl_status pfl_set_populations(pfl_ctx* c, const double* h, const double* g) {
   return PFL_OK;
 }
 
+// ---- saved states: a header, then the stored arrays as they sit in the
+// workspace (current h, current g, both phi buffers, the link words)
+struct SavedHeader {
+  char magic[8];          // "PFLSTATE"
+  int version;            // 1
+  int precision, qh, qg;  // storage and lattices
+  int nx, ny, nz, bc[6];  // lattice
+  int zm, solid;          // engine (fused two-array step or in-place), solid cells present
+  int cur, swapped, stale;
+  long long t;
+  unsigned long long bytes[5];  // h, g, phi buffer 0, phi buffer 1, links
+};
+
+// workspace offsets of the saved sections: the current h and g, the phi buffers, the links
+static void saved_offsets(const pfl_ctx* c, size_t o[5]) {
+  const bool second = c->zm && c->ab;
+  o[0] = second ? c->L.h2 : c->L.h;
+  o[1] = second ? c->L.g2 : c->L.g;
+  o[2] = c->L.phi[0];
+  o[3] = c->L.phi[1];
+  o[4] = c->L.links;
+}
+
+static void saved_sections(const pfl_ctx* c, unsigned long long b[5]) {
+  const unsigned long long N = (unsigned long long)c->geo.N;
+  b[0] = (unsigned long long)c->qh * N * pop_bytes(c->p.precision);
+  b[1] = (unsigned long long)c->qg * N * pop_bytes(c->p.precision);
+  b[2] = b[3] = N * phi_bytes(c->p.precision);
+  b[4] = c->solid ? N * sizeof(unsigned) : 0;
+}
+
+size_t pfl_state_bytes(const pfl_ctx* c) {
+  if (!c) return 0;
+  unsigned long long b[5];
+  saved_sections(c, b);
+  return sizeof(SavedHeader) + (size_t)(b[0] + b[1] + b[2] + b[3] + b[4]);
+}
+
+pfl_status pfl_save(pfl_ctx* c, void* buf, size_t bytes) {
+  if (!c) return fail(PFL_ERR_ARG, "context is NULL");
+  if (!buf) return fail(PFL_ERR_ARG, "buffer is NULL");
+  if (bytes < pfl_state_bytes(c))
+    return fail(PFL_ERR_ARG, "buffer holds " + std::to_string(bytes) + " bytes, a state needs " +
+                                 std::to_string(pfl_state_bytes(c)));
+  CUDA_TRY(cudaSetDevice(c->device));
+  SavedHeader hd;
+  std::memset(&hd, 0, sizeof hd);
+  std::memcpy(hd.magic, "PFLSTATE", 8);
+  hd.version = 1;
+  hd.precision = c->p.precision;
+  hd.qh = c->qh;
+  hd.qg = c->qg;
+  hd.nx = c->p.nx;
+  hd.ny = c->p.ny;
+  hd.nz = c->p.nz;
+  for (int k = 0; k < 6; ++k) hd.bc[k] = c->p.bc[k];
+  hd.zm = c->zm;
+  hd.solid = c->solid;
+  hd.cur = c->cur;
+  hd.swapped = c->swapped;
+  hd.stale = c->stale;
+  hd.t = c->t;
+  saved_sections(c, hd.bytes);
+  char* dst = (char*)buf;
+  CUDA_TRY(cudaMemcpyAsync(dst, &hd, sizeof hd, cudaMemcpyDefault, c->stream));
+  size_t off = sizeof hd;
+  size_t so[5];
+  saved_offsets(c, so);
+  for (int k = 0; k < 5; ++k) {
+    if (hd.bytes[k]) CUDA_TRY(cudaMemcpyAsync(dst + off, c->ws + so[k], hd.bytes[k], cudaMemcpyDefault, c->stream));
+    off += hd.bytes[k];
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));  // the header lives on this stack
+  return PFL_OK;
+}
+
+pfl_status pfl_load(pfl_ctx* c, const void* buf, size_t bytes) {
+  if (!c) return fail(PFL_ERR_ARG, "context is NULL");
+  if (!buf) return fail(PFL_ERR_ARG, "buffer is NULL");
+  if (bytes < sizeof(SavedHeader)) return fail(PFL_ERR_ARG, "buffer is shorter than a state header");
+  CUDA_TRY(cudaSetDevice(c->device));
+  SavedHeader hd;
+  CUDA_TRY(cudaMemcpy(&hd, buf, sizeof hd, cudaMemcpyDefault));
+  if (std::memcmp(hd.magic, "PFLSTATE", 8) != 0 || hd.version != 1)
+    return fail(PFL_ERR_ARG, "not a saved state (magic or version)");
+  bool same = hd.precision == c->p.precision && hd.qh == c->qh && hd.qg == c->qg && hd.nx == c->p.nx &&
+              hd.ny == c->p.ny && hd.nz == c->p.nz && hd.zm == (int)c->zm;
+  for (int k = 0; k < 6; ++k) same = same && hd.bc[k] == c->p.bc[k];
+  if (!same)
+    return fail(PFL_ERR_ARG, "the saved state's lattice, boundaries, precision or engine differ from the context's");
+  if (hd.solid && !c->p.solids) return fail(PFL_ERR_STATE, "the saved state has solid cells; create the context with solids = 1");
+  if (!hd.solid && c->solid) return fail(PFL_ERR_STATE, "the context has solid cells and the saved state none");
+  unsigned long long want[5];
+  const bool was_solid = c->solid;
+  c->solid = hd.solid != 0;
+  saved_sections(c, want);
+  c->solid = was_solid;
+  size_t total = sizeof hd;
+  for (int k = 0; k < 5; ++k) {
+    if (hd.bytes[k] != want[k]) return fail(PFL_ERR_ARG, "the saved state's section sizes do not match");
+    total += (size_t)want[k];
+  }
+  if (bytes < total) return fail(PFL_ERR_ARG, "buffer is shorter than the saved state");
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  // the saved phi buffers keep their roles: buffer `cur` holds phi^t
+  const char* from = (const char*)buf + sizeof hd;
+  size_t so[5];
+  saved_offsets(c, so);
+  for (int k = 0; k < 5; ++k) {
+    if (want[k]) CUDA_TRY(cudaMemcpyAsync(c->ws + so[k], from, want[k], cudaMemcpyDefault, c->stream));
+    from += want[k];
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->solid = hd.solid != 0;
+  c->cur = hd.cur;
+  c->swapped = hd.swapped;
+  c->stale = hd.stale != 0;
+  c->t = hd.t;
+  c->clock_t = -1;  // the device step count of graph replays is set again before the next replay
+  return PFL_OK;
+}
+
 pfl_status pfl_set_solid(pfl_ctx* c, const unsigned char* mask) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
   if (!mask) return fail(PFL_ERR_ARG, "mask is NULL");

@@ -113,6 +113,26 @@ class Simulation:
     def step(self, n=1):
         L.check(self.lib.pfl_step(self.ctx, int(n)))
 
+    def save(self, out=None):
+        """The saved state (pfl_save) as a uint8 array, or into `out` (a host
+        uint8 numpy array or a CUDA uint8 tensor of at least state_bytes)."""
+        n = int(self.lib.pfl_state_bytes(self.ctx))
+        if out is None:
+            out = np.empty(n, dtype=np.uint8)
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        size = out.numel() if hasattr(out, "numel") else out.nbytes
+        L.check(self.lib.pfl_save(self.ctx, ctypes.c_void_p(ptr), ctypes.c_size_t(size)))
+        return out
+
+    def load(self, state):
+        """Resume from a saved state (pfl_load): host array or CUDA tensor."""
+        if hasattr(state, "data_ptr"):
+            ptr, size = state.data_ptr(), state.numel() * state.element_size()
+        else:
+            state = np.ascontiguousarray(state, dtype=np.uint8)
+            ptr, size = state.ctypes.data, state.nbytes
+        L.check(self.lib.pfl_load(self.ctx, ctypes.c_void_p(ptr), ctypes.c_size_t(size)))
+
     def set_graph_steps(self, k):
         """Steps per replayed CUDA graph of the fused engine (0: none)."""
         L.check(self.lib.pfl_set_graph_steps(self.ctx, int(k)))
