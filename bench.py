@@ -109,10 +109,21 @@ def kernel_hash():
 NCU_TRAFFIC = {
     # k_step_zm<2, 15, 1, 0>, 200x400x1 wave, three captured launches: 7.07 MB read, 0 written
     # (profiles/k_step_zm_capillary_wave_200x400_fp16s.md)
-    ("capillary_wave", "fp16s", "294c3b9824cb842a"): 7073536.0,
-    # k_step_zm<2, 15, 0, 0>, rising bubble 128x384x128: 578.7 MB read + 519.9 MB written
+    ("capillary_wave", "fp16s", "fb6ff709ae5c6039"): 7073536.0,
+    # k_step_zm<2, 15, 0, 0>, rising bubble 128x384x128: 580.1 MB read + 519.4 MB written
     # (profiles/k_step_zm_rising_bubble_128x384x128.md)
-    ("rising_bubble", "fp16s", "294c3b9824cb842a"): 1098625536.0,
+    ("rising_bubble", "fp16s", "fb6ff709ae5c6039"): 1099430656.0,
+    # k_step_zm<1, 15, 0, 0>: 1.1457 GB read + 1.0444 GB written
+    ("rising_bubble", "fp32", "fb6ff709ae5c6039"): 2190027000.0,
+}
+
+# Warp instructions per launch of the same kernels (smsp__inst_executed.sum),
+# for the instruction-issue side of the roofline: launches that stay in L2
+# (the 80 K-cell wave) or issue more than they move (FP16S) are bound there.
+NCU_INST = {
+    ("capillary_wave", "fp16s", "fb6ff709ae5c6039"): 4613165.0,
+    ("rising_bubble", "fp16s", "fb6ff709ae5c6039"): 307476646.0,
+    ("rising_bubble", "fp32", "fb6ff709ae5c6039"): 248540103.0,
 }
 
 
@@ -538,6 +549,15 @@ def main():
                 "kernel_share": kms / (kms + pms),
                 "whole_step_ideal_frac": mlups(N, S * K, ms / 1e3) * 1e6 * ideal_step_bytes(prec) / 1e9 / peak,
                 "working_set_bytes": work_bytes, "l2_resident": work_bytes < L2_BYTES}
+    inst = NCU_INST.get((args.workload, prec, kernel_hash()))
+    if inst is not None and args.engine == 0:
+        # issue side: 4 warp instructions per SM per clock at the maximum SM clock
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        ipeak = sms * 4 * mhz * 1e6
+        roofline["issue"] = {"achieved": inst / avg_s, "peak": ipeak, "unit": "warp instructions/s",
+                             "frac": inst / avg_s / ipeak, "inst_per_launch": inst, "sms": sms, "sm_mhz": mhz,
+                             "source": "smsp__inst_executed.sum of one ncu capture of this kernel version"}
     del sim
 
     # e2e through the public API with host buffers

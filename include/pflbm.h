@@ -180,6 +180,14 @@ pfl_status pfl_load(pfl_ctx* ctx, const void* buf, size_t bytes);
  * Returns PFL_ERR_UNSTABLE when that number is non-zero.  Synchronises. */
 pfl_status pfl_diag(pfl_ctx* ctx, double out[8], long long* nonfinite);
 
+/* Interface height of the column (x, z) (the amplitude measure of the wave
+ * cases, section "Gravity wave", "Capillary wave"): the first j, going up
+ * along y, with phi_j >= 1/2 > phi_{j+1}, interpolated linearly:
+ * y = j + (phi_j - 1/2) / (phi_j - phi_{j+1}), in FP64 from the stored phi.
+ * NaN when the column has no such crossing.  y: one double, host or device.
+ * PFL_ERR_ARG for a column outside the lattice.  Synchronises. */
+pfl_status pfl_interface_height(pfl_ctx* ctx, int x, int z, double* y);
+
 /* Advance n_steps > 0 steps like pfl_step, recording a CUDA event pair on the
  * context's stream around every kernel launch; ms[0] receives the summed
  * device time of the stream-collide kernel, ms[1] that of the phi pass

@@ -66,6 +66,8 @@ def load():
     lib.pfl_set_populations.argtypes = [P, P, P]
     lib.pfl_set_solid.restype = I
     lib.pfl_set_solid.argtypes = [P, P]
+    lib.pfl_interface_height.restype = I
+    lib.pfl_interface_height.argtypes = [P, I, I, P]
     lib.pfl_state_bytes.restype = ctypes.c_size_t
     lib.pfl_state_bytes.argtypes = [P]
     lib.pfl_save.restype = I

@@ -398,6 +398,37 @@ pfl_status apply_solid(pfl_ctx* c, const unsigned char* mask_dev) {
   return fresh_phi<PREC, QH>(c);  // phi = 0 in solid cells; shifts of fresh populations
 }
 
+// Height of the phi = 1/2 crossing along y in the column (x, z): the first j
+// with phi_j >= 1/2 > phi_{j+1} (going up from the heavy side), interpolated
+// linearly, j + (phi_j - 1/2) / (phi_j - phi_{j+1}); NaN if there is none.
+// One block; the lowest crossing wins.
+template <typename PhiT>
+__global__ void k_iface(const PhiT* __restrict__ phi, int nx, int ny, int x, int z, double* out) {
+  __shared__ int first;
+  if (threadIdx.x == 0) first = ny;
+  __syncthreads();
+  const long long col = (long long)x + (long long)nx * (long long)ny * z;
+  for (int j = threadIdx.x; j + 1 < ny; j += blockDim.x) {
+    const double a = (double)phi[col + (long long)nx * j], b = (double)phi[col + (long long)nx * (j + 1)];
+    if (a >= 0.5 && 0.5 > b) atomicMin(&first, j);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int j = first;
+    if (j >= ny) {
+      out[0] = __longlong_as_double(0x7ff8000000000000ll);
+    } else {
+      const double a = (double)phi[col + (long long)nx * j], b = (double)phi[col + (long long)nx * (j + 1)];
+      out[0] = (double)j + (a - 0.5) / (a - b);
+    }
+  }
+}
+
+template <int PREC>
+void launch_iface(pfl_ctx* c, int x, int z, double* out) {
+  k_iface<<<1, 256, 0, c->stream>>>(phicur<PREC>(c), c->p.nx, c->p.ny, x, z, out);
+}
+
 void drop_graphs(pfl_ctx* c) {
   for (int k = 0; k < 4; ++k)
     if (c->gx[k]) {
@@ -879,6 +910,20 @@ pfl_status pfl_diag(pfl_ctx* c, double out[8], long long* nonfinite) {
   long long nf = (long long)host[8];
   if (nonfinite) *nonfinite = nf;
   if (nf > 0) return fail(PFL_ERR_UNSTABLE, std::to_string(nf) + " cells hold a non-finite phi");
+  return PFL_OK;
+}
+
+pfl_status pfl_interface_height(pfl_ctx* c, int x, int z, double* y) {
+  if (!c) return fail(PFL_ERR_ARG, "context is NULL");
+  if (!y) return fail(PFL_ERR_ARG, "y is NULL");
+  if (x < 0 || x >= c->p.nx || z < 0 || z >= c->p.nz) return fail(PFL_ERR_ARG, "column (x, z) outside the lattice");
+  CUDA_TRY(cudaSetDevice(c->device));
+  DISPATCH(c, ensure_phi, c);
+  double* res = (double*)(c->ws + c->L.red) + DIAG_BLOCKS * 9 + 9;  // a spare word after the diag results
+  DISPATCH_PREC(c, launch_iface, c, x, z, res);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(y, res, sizeof(double), cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PFL_OK;
 }
 

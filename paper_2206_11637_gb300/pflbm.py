@@ -113,6 +113,13 @@ class Simulation:
     def step(self, n=1):
         L.check(self.lib.pfl_step(self.ctx, int(n)))
 
+    def interface_height(self, x=0, z=0):
+        """First phi = 1/2 crossing along y of the column (x, z), from the
+        heavy side, interpolated linearly (pfl_interface_height); NaN if none."""
+        y = ctypes.c_double()
+        L.check(self.lib.pfl_interface_height(self.ctx, int(x), int(z), ctypes.byref(y)))
+        return y.value
+
     def save(self, out=None):
         """The saved state (pfl_save) as a uint8 array, or into `out` (a host
         uint8 numpy array or a CUDA uint8 tensor of at least state_bytes)."""

@@ -65,3 +65,23 @@ def test_graph_steps_argument_checks():
     s.set_graph_steps(0)
     s.step(5)
     assert s.time == 10
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
+def test_interface_height_matches_the_fields(precision):
+    """pfl_interface_height equals the host's first-crossing interpolation on
+    the same phi, in every column tried; a column without a crossing is NaN."""
+    import analytic as A
+    p, phi0, u0, p0 = W.capillary_wave(48, ny=40, a0=2.0, xi=4.0, sigma=1e-3, nu=0.01)
+    s = sim(p, phi0, u0, p0, precision)
+    s.step(50)
+    phi = s.phi()
+    for x in (0, 7, 47):
+        want = A.interface_height(phi[0, :, x])
+        assert s.interface_height(x, 0) == want
+    q, _, _, _ = W.static_drop(16, 5.0)
+    d = sim(q, np.ones(q.shape), None, None, precision)
+    assert np.isnan(d.interface_height(3, 3))
+    from paper_2206_11637_gb300 import _lib as L
+    y = np.zeros(1)
+    assert d.lib.pfl_interface_height(d.ctx, 16, 0, y.ctypes.data) == L.PFL_ERR_ARG
