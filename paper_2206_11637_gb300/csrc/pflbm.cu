@@ -197,13 +197,23 @@ void step_only(pfl_ctx* c) {
     const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ty - 1) / ty, (c->p.nz + c->zc - 1) / c->zc);
     const dim3 block(ZM_TX, ty);
     const unsigned* links = (const unsigned*)(c->ws + c->L.links);
-#define PFL_ZM(FLAT, SOLID)                                                                                      \
-  k_step_zm<PREC, QH, FLAT, SOLID><<<grid, block, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),   \
-                                                                  hnext<PREC>(c), gnext<PREC>(c),                 \
-                                                                  phishift<PREC>(c), phicur<PREC>(c), c->zc,      \
-                                                                  step_seed(c), links,                            \
-                                                                  c->capturing ? clock_of(c) : nullptr,           \
-                                                                  (int)(c->t - c->cap_t0))
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = c->stream;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = PFL_ZM_PDL ? 1 : 0;
+    const typename Store<PREC>::S* ha = hbuf<PREC>(c);
+    const typename Store<PREC>::S* ga = gbuf<PREC>(c);
+    const typename Store<PREC>::PhiT* shift = phishift<PREC>(c);
+    const unsigned long long* tclock = c->capturing ? clock_of(c) : nullptr;
+    const int tofs = (int)(c->t - c->cap_t0);
+#define PFL_ZM(FLAT, SOLID)                                                                                   \
+  cudaLaunchKernelEx(&cfg, k_step_zm<PREC, QH, FLAT, SOLID>, c->g32, c->ph, ha, ga, hnext<PREC>(c),           \
+                     gnext<PREC>(c), shift, phicur<PREC>(c), c->zc, step_seed(c), links, tclock, tofs)
     if (c->p.nz == 1) {
       if (c->solid)
         PFL_ZM(1, 1);

@@ -48,6 +48,17 @@
 #ifndef PFL_ZM_PREFETCH
 #define PFL_ZM_PREFETCH 1
 #endif
+// Programmatic dependent launch of the fused step (1; 0 = plain launches):
+// the host launches each step with programmatic stream serialisation, so the
+// next step's blocks are scheduled while the last blocks of the previous one
+// finish; every block waits (griddepcontrol.wait, a no-op without the launch
+// attribute) for the previous grid's completion before its first global access.
+// 200x400 wave: FP16S 11.3 -> 12.0 GLUPS, FP32 11.6 -> 12.3; the 3-D bubble is
+// unchanged.  Releasing the dependents early (launch_dependents right after
+// the wait) lost 6-13 %: waiting blocks then hold the SMs' block slots.
+#ifndef PFL_ZM_PDL
+#define PFL_ZM_PDL 1
+#endif
 
 namespace pfl {
 
@@ -755,7 +766,6 @@ __global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_
               int tofs = 0) {
   typedef typename Store<PREC>::PhiT PhiT;
   typedef typename Store<PREC>::R R;
-  if (PREC == 2 && tclock) seed = step_seed_of(*tclock + (unsigned long long)tofs);
   constexpr int TY = zm_ty(FLAT);
   constexpr int NT = ZM_TX * TY;
   constexpr int PW = ZM_TX + 2, PH = TY + 2, PS = PW * PH;
@@ -781,6 +791,9 @@ __global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_
   if (tid < NRING) frame_pos(tid, PW, PH, ri, rj);
   const unsigned rxq = (unsigned)wrap_or_clamp(x0 - 1 + ri, (int)geo.nx, geo.wall[0]);
   const unsigned ryq = (unsigned)wrap_or_clamp(y0 - 1 + rj, (int)geo.ny, geo.wall[1]);
+  // everything above is index arithmetic; global memory only from here on
+  if (PFL_ZM_PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (PREC == 2 && tclock) seed = step_seed_of(*tclock + (unsigned long long)tofs);
 
   // L1 prefetch of the g populations plane zp's collision will read
   auto prefetch_plane = [&](int zp) {
