@@ -17,6 +17,7 @@ import math
 import numpy as np
 import pytest
 
+import golden
 import oracle
 from paper_2206_11637_gb300 import workloads as W
 
@@ -152,4 +153,5 @@ def test_taylor_bubble_reynolds_number():
     assert nf == 0
     U = (ys[1] - ys[0]) / (5.0 * t_unit)
     Re = U * D / p.nu_h
-    assert abs(Re / 26.83 - 1) < 0.05, Re
+    paper, _ = golden.taylor_bubble_re()
+    assert abs(Re / paper[D] - 1) < 0.05, Re
