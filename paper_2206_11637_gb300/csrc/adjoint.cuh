@@ -34,6 +34,9 @@ constexpr int ADJ_THREADS = 128;
 #ifndef PFL_ADJ_MINB
 #define PFL_ADJ_MINB 0
 #endif
+// (An L1 prefetch of the lambda gathers on entry, to overlap them with the
+// forward recomputation, doubled the adjoint's time on the same bubble: 831 ->
+// 1691 ms.  It is not used.)
 
 // Parameters of the reverse sweep that the forward step folds into Phys.
 struct AdjPar {
@@ -84,7 +87,6 @@ __global__ void __launch_bounds__(ADJ_THREADS, PFL_ADJ_MINB) k_adj_local(Geo32 g
     const unsigned N = geo.N;
     CellOff o;
     cell_off(geo, cell, o);
-
     // ---------------- forward recomputation (as in k_step_mrt)
     const R pc = (R)phi[cell];
     R gx = 0, gy = 0, gz = 0, lap = 0;

@@ -621,14 +621,16 @@ constexpr int ZM_TY = 8;
 constexpr int ZM_TY_FLAT = 4;
 __host__ __device__ constexpr int zm_ty(int flat) { return flat ? ZM_TY_FLAT : ZM_TY; }
 
-template <int PREC>
+// FLAT: a single plane, its own z neighbour (periodic) -- every cz reads the
+// plane itself, so the compiler loads each in-plane value once.
+template <int PREC, int FLAT = 0>
 struct SmemPhi {
   const typename Store<PREC>::PhiT* plane[3];  // planes z - 1, z, z + 1 of (ZM_TY + 2) x (ZM_TX + 2) values
   int i0;                 // index of this thread's column in a plane
   unsigned blk = 0;       // blocked links: a solid neighbour reads as this cell (neutral wetting)
   __device__ __forceinline__ typename Store<PREC>::R operator()(int cx, int cy, int cz) const {
     if (blk & link_bit(cx, cy, cz)) return (typename Store<PREC>::R)plane[1][i0];
-    return (typename Store<PREC>::R)plane[1 + cz][i0 + cy * (ZM_TX + 2) + cx];
+    return (typename Store<PREC>::R)plane[FLAT ? 1 : 1 + cz][i0 + cy * (ZM_TX + 2) + cx];
   }
 };
 
@@ -841,7 +843,7 @@ __global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_
       o.X = axis_off((unsigned)x, geo.nx, 1, geo.wall[0]);
       o.Y = axis_off((unsigned)y, geo.ny, (int)geo.nx, geo.wall[1]);
       o.Z = axis_off((unsigned)z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
-      SmemPhi<PREC> at;
+      SmemPhi<PREC, FLAT> at;
       if (FLAT) {
         at.plane[0] = at.plane[1] = at.plane[2] = ring[0];
       } else {
@@ -853,7 +855,7 @@ __global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_
       at.i0 = (ty + 1) * PW + (tx + 1);
       at.blk = blk;
       phi_out[cell] = (PhiT)at(0, 0, 0);
-      collide_cell<PREC, QH, 0, 1, SmemPhi<PREC>, 1>(geo, ph, o, hA, gA, hB, gB, at, phi_shift, cell, seed,
+      collide_cell<PREC, QH, 0, 1, SmemPhi<PREC, FLAT>, 1>(geo, ph, o, hA, gA, hB, gB, at, phi_shift, cell, seed,
                                                  &hmom[FLAT ? 0 : ((z - z0) & 1)][tid], NT);
     }
     if (NS == 3) __syncthreads();
