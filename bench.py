@@ -109,21 +109,21 @@ def kernel_hash():
 NCU_TRAFFIC = {
     # k_step_zm<2, 15, 1, 0>, 200x400x1 wave, three captured launches: 7.07 MB read, 0 written
     # (profiles/k_step_zm_capillary_wave_200x400_fp16s.md)
-    ("capillary_wave", "fp16s", "fb6ff709ae5c6039"): 7073536.0,
-    # k_step_zm<2, 15, 0, 0>, rising bubble 128x384x128: 580.1 MB read + 519.4 MB written
+    ("capillary_wave", "fp16s", "5ed1f6cb0b3def0e"): 7073792.0,
+    # k_step_zm<2, 15, 0, 0>, rising bubble 128x384x128: 580.0 MB read + 519.4 MB written
     # (profiles/k_step_zm_rising_bubble_128x384x128.md)
-    ("rising_bubble", "fp16s", "fb6ff709ae5c6039"): 1099430656.0,
-    # k_step_zm<1, 15, 0, 0>: 1.1457 GB read + 1.0444 GB written
-    ("rising_bubble", "fp32", "fb6ff709ae5c6039"): 2190027000.0,
+    ("rising_bubble", "fp16s", "5ed1f6cb0b3def0e"): 1099392512.0,
+    # k_step_zm<1, 15, 0, 0>: 1.1475 GB read + 1.0450 GB written
+    ("rising_bubble", "fp32", "5ed1f6cb0b3def0e"): 2192553000.0,
 }
 
 # Warp instructions per launch of the same kernels (smsp__inst_executed.sum),
 # for the instruction-issue side of the roofline: launches that stay in L2
 # (the 80 K-cell wave) or issue more than they move (FP16S) are bound there.
 NCU_INST = {
-    ("capillary_wave", "fp16s", "fb6ff709ae5c6039"): 4613165.0,
-    ("rising_bubble", "fp16s", "fb6ff709ae5c6039"): 307476646.0,
-    ("rising_bubble", "fp32", "fb6ff709ae5c6039"): 248540103.0,
+    ("capillary_wave", "fp16s", "5ed1f6cb0b3def0e"): 4615965.0,
+    ("rising_bubble", "fp16s", "5ed1f6cb0b3def0e"): 307487398.0,
+    ("rising_bubble", "fp32", "5ed1f6cb0b3def0e"): 248550855.0,
 }
 
 
