@@ -196,6 +196,22 @@ def dist_env():
     return ws, rank, local
 
 
+def ranks_max(dist, x, device=None):
+    """Max of x over all ranks of the process group (x itself without one)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard(n, rank, world):
+    """The units rank takes of n independent units: rank, rank + world, ...
+    (the ranks' shards partition range(n); no unit is shared)."""
+    return list(range(rank, n, world))
+
+
 def mlups(cells, steps, seconds):
     return cells * steps / seconds / 1e6
 
@@ -259,19 +275,31 @@ def run_batched(args):
     64..256) with their own M, xi, sigma, advanced together in FP32 by the
     batched persistent launches (CUDA graph, tuned shapes).  value = aggregate
     MLUPS; error_vs_fp64 compares 16 instances with the FP64 single-lattice
-    path (itself checked against the oracle to 1e-10)."""
+    path (itself checked against the oracle to 1e-10).  Under torchrun the
+    instances are sharded over the ranks (rank r takes r, r + N, ...), with
+    no collective on the data path: value = all instances' cell updates over
+    the slowest rank's time, "scaling" strong (the total work is fixed)."""
     import numpy as np
     import torch
     from paper_2206_11637_gb300 import workloads as W
     from paper_2206_11637_gb300 import build as B
-    ws, rank, _ = dist_env()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    B.build_library()
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0:
+        B.build_library()
+    if dist:
+        dist.barrier()
     from paper_2206_11637_gb300.batch import Batch
     from paper_2206_11637_gb300.pflbm import Simulation
-    inst = W.batched_sweep(512)
-    cells = sum(p.cells for p, _, _, _ in inst)
+    every = W.batched_sweep(512)
+    mine = shard(len(every), rank, ws)
+    inst = [every[i] for i in mine]
+    cells = sum(p.cells for p, _, _, _ in every)
     t0 = time.perf_counter()
     b = Batch(inst, precision="fp32", tune=True, device=dev)
     t_init = time.perf_counter() - t0
@@ -287,16 +315,18 @@ def run_batched(args):
         b.step(S)
     e1.record()
     torch.cuda.synchronize()
-    clocks = clk.stop(0)
-    ms = e0.elapsed_time(e1)
+    clocks = clk.stop(local)
+    ms = ranks_max(dist, e0.elapsed_time(e1), dev)
     out, nf, _ = b.diag(check=False)
     threads, grid, ntiles = b.shapes()
     # error of 16 instances against FP64 after the same number of steps
     n_done = b.time
     errs = []
-    for i in range(0, 32, 2):                      # 8 drops and 8 waves
-        p, phi0, u0, p0 = inst[i + (i // 2) % 2]
-        j = i + (i // 2) % 2
+    for i in range(0, 32, 2):                      # 8 drops and 8 waves (of this rank's shard)
+        if i + (i // 2) % 2 not in mine:
+            continue
+        j = mine.index(i + (i // 2) % 2)
+        p, phi0, u0, p0 = inst[j]
         ref = Simulation(p, phi0, u0, p0, precision="fp64", device=dev)
         ref.step(n_done)
         phi = b.fields(j)[0]
@@ -304,10 +334,17 @@ def run_batched(args):
             errs.append(float(np.abs(phi - ref.phi()).max()))
         del ref
     v = mlups(cells, S * args.steps, ms / 1e3)
-    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak",
+            "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batched_sweep", "instances": len(inst), "cells": cells,
+            "config": {"workload": "batched_sweep", "instances": len(every), "cells": cells,
+                       "parallelism": "instances sharded over %d ranks" % ws if ws > 1 else "1 GPU",
                        "lattice_steps_per_step": S, "precision": "fp32",
                        "l2": "working set larger than L2"},
             "gpu_launches": 4 * S * args.steps, "clocks": clocks,
@@ -521,10 +558,7 @@ def main():
 
     K, Wm = args.steps, args.warmup
     sim, ms, wall, clocks, nf = timed_device(prec, K, Wm)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = ranks_max(dist, ms, dev)
     value = mlups(N, S * K, ms / 1e3) * ws
 
     # roofline of the stream-collide kernel.  With the fused engine the timed
