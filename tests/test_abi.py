@@ -74,6 +74,11 @@ def test_null_context_calls(lib):
     assert lib.pfl_step(None, 1) == L.PFL_ERR_ARG
     assert lib.pfl_fields(None, None, None, None, None) == L.PFL_ERR_ARG
     assert lib.pfl_time(None) == -1
+    assert lib.pfl_set_graph_steps(None, 2) == L.PFL_ERR_ARG
+    assert lib.pfl_state_bytes(None) == 0
+    assert lib.pfl_save(None, None, 0) == L.PFL_ERR_ARG
+    assert lib.pfl_load(None, None, 0) == L.PFL_ERR_ARG
+    assert lib.pfl_interface_height(None, 0, 0, None) == L.PFL_ERR_ARG
     lib.pfl_destroy(None)
 
 
