@@ -54,3 +54,24 @@ def test_rising_bubble_full_size_properties(precision):
     assert nf == 0
     tol = 1e-5 if precision == "fp32" else 2e-3
     assert abs(out[0] - m0) / m0 < tol
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("fp16s", 2e-3)])
+def test_rising_bubble_128x384x128_one_step(precision, tol):
+    """The full 6.29 M-cell bubble (walls everywhere, gravity, hydrostatic
+    start): one GPU step against one oracle step from the same populations."""
+    from paper_2206_11637_gb300.pflbm import Simulation
+    p, phi0, u0, p0 = W.rising_bubble()
+    s = Simulation(p, phi0, u0, p0, precision=precision)
+    s.step(11)
+    h, g = s.populations()
+    o = oracle.from_params(p, phi0, u0, p0)
+    o.set_populations(h, g)
+    del h, g
+    s.step(1)
+    o.step(1, 0)
+    phi, _, _, u = s.fields()
+    ophi, _, _, ou = o.fields()
+    assert np.all(np.isfinite(phi))
+    assert rel(phi, ophi) < tol
+    assert rel(u, ou) < tol * 50
