@@ -16,7 +16,6 @@
 // kernels overlap on that GPU (different streams, or threads racing) corrupt
 // each other's partial sums, so callers must order them.
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "../../include/pflbm.h"
@@ -32,10 +31,6 @@ constexpr long long PFL_STATIC_MAX_CELLS = 2147483647LL;  // coordinates are 32-
 
 static __device__ __align__(256) double g_static_scratch[PFL_STATIC_PARTIALS * 9 + 16];
 
-constexpr int MAX_DEVICES = 64;
-std::mutex g_mu;
-double* g_scratch_ptr[MAX_DEVICES] = {nullptr};
-
 pfl_status sfail(pfl_status s, const std::string& m) {
   pfl_internal::set_error(m);
   return s;
@@ -44,20 +39,37 @@ pfl_status sfail(pfl_status s, const std::string& m) {
 // Device address of the static scratch on the current device.  Host code only
 // sees a host-side stand-in for g_static_scratch; handing that to a kernel
 // would fault or address the wrong memory, so the address is looked up with
-// cudaGetSymbolAddress once per device, with that device current.
-pfl_status scratch_for(int device, double** out) {
-  if (device < 0 || device >= MAX_DEVICES) return sfail(PFL_ERR_ARG, "device index out of range");
-  std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess)
-      return sfail(PFL_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_ptr[device] = (double*)p;
-  }
-  *out = g_scratch_ptr[device];
+// cudaGetSymbolAddress, with the device that holds phi current.  The lookup is
+// repeated on every call (it is a table lookup once the library's module is
+// loaded on the device): an address kept from an earlier call would be stale
+// after the device's primary context was destroyed and created again
+// (cudaDeviceReset).  The first call on a device loads the module there, so
+// it belongs before any stream capture.
+pfl_status scratch_address(double** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+  if (e != cudaSuccess) return sfail(PFL_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = (double*)p;
   return PFL_OK;
 }
+
+// Makes `device` current for the lifetime of the guard and gives the caller's
+// current device back on every return path.
+struct DeviceGuard {
+  int saved = -1;
+  cudaError_t set(int device) {
+    cudaError_t e = cudaGetDevice(&saved);
+    if (e != cudaSuccess) {
+      saved = -1;
+      return e;
+    }
+    return saved == device ? cudaSuccess : cudaSetDevice(device);
+  }
+  ~DeviceGuard() {
+    int now = -1;
+    if (saved >= 0 && cudaGetDevice(&now) == cudaSuccess && now != saved) cudaSetDevice(saved);
+  }
+};
 
 }  // namespace
 
@@ -78,10 +90,11 @@ pfl_status pfl_phi_moments_static(const void* phi, int phi_fp64, int nx, int ny,
     cudaGetLastError();
     return sfail(PFL_ERR_ARG, "phi must be device memory");
   }
-  cudaError_t e = cudaSetDevice(a.device);
+  DeviceGuard dg;  // the kernels run on phi's device; the caller's current device is restored
+  cudaError_t e = dg.set(a.device);
   if (e != cudaSuccess) return sfail(PFL_ERR_CUDA, std::string("cudaSetDevice: ") + cudaGetErrorString(e));
   double* scratch = nullptr;
-  pfl_status st = scratch_for(a.device, &scratch);
+  pfl_status st = scratch_address(&scratch);
   if (st != PFL_OK) return st;
 
   Geo geo;

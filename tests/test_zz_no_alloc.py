@@ -29,10 +29,10 @@ def _entry():
     return lib, fn
 
 
-def _static_sums(fn, phi_dev, p, fp64):
+def _static_sums(fn, phi_dev, p, fp64, stream=None):
     out = np.full(8, np.nan)
     nf = ctypes.c_longlong(-1)
-    stream = torch.cuda.current_stream().cuda_stream
+    stream = (torch.cuda.current_stream() if stream is None else stream).cuda_stream
     st = fn(ctypes.c_void_p(phi_dev.data_ptr()), 1 if fp64 else 0, p.nx, p.ny, p.nz,
             out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nf), ctypes.c_void_p(stream))
     return st, out, nf.value
@@ -69,3 +69,47 @@ def test_static_scratch_rejects_oversized_lattice():
     st = fn(ctypes.c_void_p(phi.data_ptr()), 1, 2048, 2048, 1024, out.ctypes.data_as(ctypes.c_void_p), None, None)
     assert st == L.PFL_ERR_ARG
     assert "at most" in lib.pfl_last_error().decode()
+
+
+def test_static_scratch_keeps_current_device_and_runs_on_a_second_stream():
+    """The call leaves the caller's current device as it was, and a call on a
+    second stream, ordered after the first by synchronisation, gives the same
+    sums as pfl_diag."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    lib, fn = _entry()
+    from paper_2206_11637_gb300.pflbm import Simulation
+    p, phi0, u0, p0 = W.rising_bubble(24, 40, 20, D=10.0, xi=4.0, M=0.05)
+    s = Simulation(p, phi0, u0, p0, precision="fp64")
+    s.step(11)
+    ref, _ = s.diag()
+    phi_dev = torch.empty(p.cells, dtype=torch.float64, device="cuda")
+    s.fields(out={"phi": phi_dev})
+    before = torch.cuda.current_device()
+    st, out, nf = _static_sums(fn, phi_dev, p, True)
+    assert st == L.PFL_OK, lib.pfl_last_error()
+    assert torch.cuda.current_device() == before
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream()
+    st, out2, nf2 = _static_sums(fn, phi_dev, p, True, stream=side)
+    assert st == L.PFL_OK, lib.pfl_last_error()
+    assert torch.cuda.current_device() == before
+    assert np.allclose(out2, ref, rtol=1e-12, atol=1e-9)
+    assert np.array_equal(out, out2)
+
+
+def test_static_scratch_on_a_device_that_is_not_current():
+    """phi held by another GPU: the sums come from that GPU's scratch and the
+    caller's current device stays current."""
+    if not torch.cuda.is_available() or torch.cuda.device_count() < 2:
+        pytest.skip("needs two CUDA devices")
+    lib, fn = _entry()
+    p, phi0, _, _ = W.static_drop(20, 6.0)
+    torch.cuda.set_device(0)
+    phi_other = torch.from_numpy(phi0.reshape(-1).copy()).to("cuda:1")
+    with torch.cuda.device(1):
+        other_stream = torch.cuda.current_stream()
+    st, out, nf = _static_sums(fn, phi_other, p, True, stream=other_stream)
+    assert st == L.PFL_OK, lib.pfl_last_error()
+    assert torch.cuda.current_device() == 0
+    assert abs(out[0] - phi0.sum()) <= 1e-9 * phi0.sum()
