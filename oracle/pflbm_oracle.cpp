@@ -21,7 +21,7 @@
 //   * conservative Allen-Cahn forcing F^phi = 4 phi (1 - phi) / xi * n;
 //   * streaming with periodic wrap or halfway bounce-back at no-slip faces.
 //
-// Readings where the paper is silent or garbled (each is listed in the design doc):
+// Readings where the paper is silent or garbled:
 //   tau_phi = M / c_s^2 is the shifted relaxation time, omega_phi = 1/(3M + 1/2);
 //   mu_phi = 4 beta phi (phi - 1)(phi - 1/2) - kappa lap(phi), beta = 12 sigma / xi,
 //     kappa = 3 sigma xi / 2;

@@ -14,7 +14,9 @@ fixes, chosen so that a plausible mistake in one part fails one of them:
                      xi (initialisation formula of the PFLBM): pins F^phi and
                      its normalisation together with omega_phi.
   Laplace         -- static column: p_in - p_out = sigma / R: pins beta, kappa
-                     of the chemical potential and F_s, F_p.
+                     of the chemical potential and F_s, F_p; static 3-D drop:
+                     2 sigma / R, twice the column's jump at the same R, xi
+                     (pins the 3-D mean curvature of the stencil).
   Poiseuille      -- single phase, body force, halfway bounce-back walls: with
                      degree-2 rate omega and degree >= 3 rate 1 the wall sits
                      exactly half-way at nu = 1/8 (Lambda = 3/16): pins nu(tau),
@@ -23,7 +25,8 @@ fixes, chosen so that a plausible mistake in one part fails one of them:
                      shear stress needs F_mu; pins F_mu, rho(phi), tau(phi).
   capillary wave  -- half-period against Prosperetti's model (section
                      "Capillary wave"); loose at this small L (diffuse
-                     interface of Cn = xi/L = 0.125).
+                     interface of Cn = xi/L = 0.125); in the paper's L x L
+                     set-up the period error falls as xi / L (L = 24, 32, 48).
   symmetry        -- a centred drop stays mirror- and permutation-symmetric:
                      catches transposed components and index errors.
   BGK special case-- the full simulation with MRT rates all equal equals BGK.
@@ -222,3 +225,65 @@ def test_two_layer_closed_form_reduces_to_poiseuille():
     b = A.poiseuille(y, 32, 1e-6, 0.2)
     assert np.abs(a - b).max() < 1e-15
 
+
+
+@pytest.mark.parametrize("qh", [15, 27])
+def test_laplace_pressure_3d_drop_is_twice_the_column(qh):
+    """Laplace law in 3-D (section "Capillary wave" set-up, Laplace pressure
+    p_in - p_out = 2 sigma / R of a static drop): the jump of a drop is 2 sigma
+    / R within 5 %, and twice that of a 2-D column of the same radius and
+    interface width (sigma / R, one curvature) within 3 %, so the 3-D mean
+    curvature (two principal curvatures) is pinned separately from the
+    diffuse-interface deficit both share."""
+    n, R, xi = 24, 6.0, 3.0
+    p, phi0, _, _ = W.static_drop(n, R, xi=xi, nu=1 / 6)
+    p.h_lattice = qh
+    q, phc, _, _ = W.static_cylinder(n, R, xi=xi, nu=1 / 6)
+    q.h_lattice = qh
+    c = n // 2
+    _, _, pr, u = run(p, phi0, n=600).fields()
+    d3 = pr[c - 2:c + 2, c - 2:c + 2, c - 2:c + 2].mean() - pr[0:3, 0:3, 0:3].mean()
+    _, _, pr2, _ = run(q, phc, n=600).fields()
+    d2 = pr2[0, c - 2:c + 2, c - 2:c + 2].mean() - pr2[0, 0:3, 0:3].mean()
+    assert abs(d3 / (2 * p.sigma / R) - 1) < 0.05, d3 / (2 * p.sigma / R)
+    assert abs(d3 / d2 / 2 - 1) < 0.03, d3 / d2
+    assert np.abs(u).max() < 1e-4
+
+
+def test_capillary_wave_period_converges_in_L():
+    """The paper's capillary-wave set-up (section "Capillary wave": an L x L
+    box, walls top and bottom, the interface at half height, compared with
+    Prosperetti's solution) at fixed interface width xi = 4: the diffuse
+    interface lengthens the oscillation period by an amount that falls with
+    the Cahn number xi / L.  On the oracle the first full period between two
+    zero crossings of the interface height at x = 0, against the same
+    crossings of Prosperetti's a(t), is 16.5 %, 12.4 % and 8.1 % long at
+    L = 24, 32 and 48: first order in xi / L.  The test asks for a monotone
+    fall, an error below 10 % at L = 48 and a ratio err(24) / err(48) in
+    [1.6, 2.6] (2 for first order)."""
+    sigma, nu, xi = 1e-3, 0.002, 4.0
+    errs = []
+    for L in (24, 32, 48):
+        k = 2 * np.pi / L
+        a0 = 0.02 * L
+        p, phi0, _, _ = W.capillary_wave(L, ny=L, a0=a0, xi=xi, M=0.02, sigma=sigma, nu=nu)
+        o = oracle.from_params(p, phi0)
+        T = 2 * np.pi / A.capillary_omega0(sigma, k, 1.0, 1e-3)
+        dt = max(1, int(T / 80))
+        ts, amps = [], []
+        while o.time < 1.3 * T:
+            ts.append(o.time)
+            amps.append(A.interface_height(o.fields()[0][0, :, 0]) - (L - 1) / 2)
+            o.step(dt, THREADS)
+        ts, amps = np.array(ts, float), np.array(amps)
+        an = A.prosperetti(ts, k, nu, 1.0, 1e-3, sigma, a0)
+
+        def crossings(a):
+            return np.array([ts[i] + a[i] / (a[i] - a[i + 1]) * (ts[i + 1] - ts[i])
+                             for i in range(len(a) - 1) if (a[i] > 0) != (a[i + 1] > 0)])
+
+        cs, ca = crossings(amps), crossings(an)
+        errs.append((cs[1] - cs[0]) / (ca[1] - ca[0]) - 1)
+    assert errs[0] > errs[1] > errs[2] > 0, errs
+    assert errs[2] < 0.10, errs
+    assert 1.6 < errs[0] / errs[2] < 2.6, errs
