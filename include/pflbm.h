@@ -49,21 +49,29 @@ extern "C" {
 
 typedef struct pfl_ctx pfl_ctx;
 
+/* Largest flow speed |u| (lattice units) that pfl_diag accepts.  The LBM
+ * equilibria are expansions in u / c_s (Eq. feq); beyond |u| = 0.3
+ * (u / c_s = 0.52) a run is taken as unstable, like one with NaN/Inf. */
+#define PFL_SPEED_LIMIT 0.3
+
 typedef enum {
   PFL_OK = 0,
   PFL_ERR_ARG = 1,      /* invalid argument or parameter set                  */
   PFL_ERR_CUDA = 2,     /* a CUDA runtime call failed                          */
   PFL_ERR_OOM = 3,      /* workspace too small                                 */
-  PFL_ERR_UNSTABLE = 4, /* the last diagnostic found NaN/Inf in phi            */
+  PFL_ERR_UNSTABLE = 4, /* the last diagnostic found NaN/Inf in phi or a flow
+                         * speed above PFL_SPEED_LIMIT                          */
   PFL_ERR_STATE = 5     /* call not valid in the context's current state       */
 } pfl_status;
 
 /* Storage precision of the populations.  PFL_FP64: FP64 storage and arithmetic
  * (reference mode).  PFL_FP32: FP32 storage and arithmetic.  PFL_FP16S
  * (shifted FP16 storage): each population is stored in FP16 as its deviation
- * from a rest equilibrium -- h_i from w_i phi of the cell that wrote it, g_i
- * from zero (the rest equilibrium of p* = 0) -- divided by its lattice weight
- * and scaled by a power of two; arithmetic in FP32; phi kept in FP32. */
+ * from the rest equilibrium of the cell that wrote it -- h_i from w_i phi,
+ * g_i from w_i P with P = fp16(p*) kept per cell -- divided by its lattice
+ * weight and scaled by a power of two; arithmetic in FP32; phi kept in FP32.
+ * The initial state is stored against its own phi0 and p0, exactly for a
+ * fluid at rest. */
 typedef enum { PFL_FP64 = 0, PFL_FP32 = 1, PFL_FP16S = 2 } pfl_precision;
 
 typedef enum { PFL_PERIODIC = 0, PFL_NOSLIP = 1 } pfl_bc;
@@ -91,6 +99,13 @@ typedef struct {
                         * The collisions keep their moment form on every lattice. */
   int solids;          /* 1: the lattice may hold solid cells (pfl_set_solid; 4 bytes
                         * per cell of workspace; fused engine only), 0: none */
+  int hydrostatic;     /* 1: pfl_init called with p0 == NULL starts from the pressure of
+                        * the fluid at rest under gravity (the paper's start in its
+                        * gravity cases, sections "Gravity wave", "Rising bubble",
+                        * "Drop impact"); gravity must then act along one axis.
+                        * 0: p* starts at zero unless p0 is given. */
+  double p_level;      /* hydrostatic start: cell-centre coordinate along the gravity
+                        * axis where the pressure is zero */
 } pfl_params;
 
 /* How a single lattice is stepped.  PFL_ENGINE_AUTO: the fused two-array step
@@ -105,8 +120,13 @@ size_t pfl_workspace_bytes(const pfl_params* p);
 
 /* Create a context and write the initial state.
  *   phi0: N doubles, required.  u0: 3N doubles SoA or NULL (zero).  p0: N
- *   doubles of initial normalised pressure p* or NULL (zero).  Each may be a
- *   host or a device pointer.  The populations start at their equilibria
+ *   doubles of initial normalised pressure p* or NULL: zero, or with
+ *   pfl_params.hydrostatic = 1 the hydrostatic p* = p / (rho(phi0) c_s^2) with
+ *   dp/ds = rho(phi0) g_s integrated along each line of cells parallel to the
+ *   gravity axis s (trapezoid rule between cell centres, FP64 on the host) and
+ *   p = 0 at s = p_level (linear interpolation between the two cells around
+ *   it).  A given p0 overrides the hydrostatic start.  Each may be a host or a
+ *   device pointer.  The populations start at their equilibria
  *   h^eq(phi0, u0) and g^eq(p0, u0); phi is then recomputed as sum_i h_i.
  *   workspace: device pointer, >= pfl_workspace_bytes(p) bytes, 256-byte aligned.
  *   stream: a cudaStream_t (NULL = legacy default stream).
@@ -156,7 +176,7 @@ pfl_status pfl_set_solid(pfl_ctx* ctx, const unsigned char* mask);
 
 /* Saved states (checkpoint and resume).  A state is the stored arrays of the
  * context as they are (the current h and g in the storage precision, both phi
- * buffers, the link words of solid cells) after a small header with the
+ * buffers, the link words of solid cells, the FP16S p* shifts) after a small header with the
  * lattice, the engine, the step count and the layout flags.  Loading it into a
  * context of the same lattice, boundaries, precision, phase-field lattice and
  * engine resumes the run bitwise: the step count (and with it the FP16
@@ -177,8 +197,16 @@ pfl_status pfl_load(pfl_ctx* ctx, const void* buf, size_t bytes);
  *   out[0] = sum phi, out[1..3] = sum phi * (x, y, z),
  *   out[4] = sum (1 - phi), out[5..7] = sum (1 - phi) * (x, y, z).
  * nonfinite (may be NULL) receives the number of cells whose phi is NaN/Inf.
- * Returns PFL_ERR_UNSTABLE when that number is non-zero.  Synchronises. */
+ * Returns PFL_ERR_UNSTABLE when that number is non-zero or when the largest
+ * flow speed |u| over the fluid cells (pfl_max_speed) exceeds
+ * PFL_SPEED_LIMIT; out and nonfinite are filled in either case.
+ * Synchronises. */
 pfl_status pfl_diag(pfl_ctx* ctx, double out[8], long long* nonfinite);
+
+/* Largest flow speed max |u| over the fluid cells of the current state, with
+ * u = sum_i c_i g_i + F / (2 rho) as in pfl_fields; a NaN/Inf velocity gives
+ * +inf.  umax: one double, host or device.  Synchronises. */
+pfl_status pfl_max_speed(pfl_ctx* ctx, double* umax);
 
 /* Interface height of the column (x, z) (the amplitude measure of the wave
  * cases, section "Gravity wave", "Capillary wave"): the first j, going up
@@ -209,7 +237,12 @@ size_t pfl_adjoint_workspace_bytes(const pfl_ctx* ctx, int n_steps);
  * phi because sum(1 - phi) is conserved) and the amplitude of a wave mode are
  * such functionals.
  *   obs_steps: n_obs distinct steps in [0, n_steps], relative to the current
- *   time; obs_weights: n_obs arrays of N doubles (host or device).
+ *   time; obs_weights: n_obs arrays of N doubles (host or device; device
+ *   arrays are read in place, host arrays copied in when their step comes).
+ *   A nonlinear J of phi at those steps is differentiated by passing the
+ *   weights W_o = dJ / dphi(t_o) evaluated on a forward run (chain rule):
+ *   the gradient returned is then dJ / d(M, xi, sigma), while *J holds the
+ *   linear functional sum_o W_o . phi(t_o) of those weights.
  *   The forward run keeps a checkpoint every K = ceil(sqrt(n_steps)) steps,
  *   and the reverse sweep recomputes one K-step segment at a time.
  *   On return the context holds the state after n_steps steps (as pfl_step);
@@ -217,29 +250,35 @@ size_t pfl_adjoint_workspace_bytes(const pfl_ctx* ctx, int n_steps);
  *   adj_workspace: device memory of pfl_adjoint_workspace_bytes() bytes,
  *   256-byte aligned, caller-owned.
  * PFL_ERR_STATE for FP16S storage, the BGK mode or lattices with 27 N >= 2^32;
- * PFL_ERR_ARG for bad observations (at most 8).  Synchronises. */
+ * PFL_ERR_ARG for bad observations (NULL weights, steps outside [0, n_steps]
+ * or repeated).  Synchronises. */
 pfl_status pfl_adjoint(pfl_ctx* ctx, int n_steps, int n_obs, const int* obs_steps, const double* const* obs_weights,
                        void* adj_workspace, size_t adj_bytes, double* J, double grad[3]);
 
 /* ------------------------------------------------------------------ batch --
  * Many independent lattices of uneven size, each with its own parameters
  * (M, xi, sigma, densities, ...), advanced together: every lattice step is
- * one persistent grid-stride launch of the stream-collide over a work list of
- * all instances' cells (plus one of the phi pass), and pfl_batch_step replays
- * a CUDA graph of 16 steps.  All instances share the precision; MRT and the
- * D3Q15 phase field only; 27 N < 2^32 per instance. */
+ * one persistent grid-stride launch of the fused two-array step per class of
+ * instances (one z plane, and 3-D) over a work list of (instance, xy tile,
+ * z chunk) tiles -- the single-lattice step's tile code, phi formed in the
+ * step -- and pfl_batch_step replays a CUDA graph of 16 steps.  Each instance
+ * evolves bitwise as the same lattice run alone with the fused engine.  All instances share the precision (FP64 or
+ * FP32); MRT and the D3Q15 phase field only; 27 N < 2^32 per instance. */
 typedef struct pfl_batch pfl_batch;
 
 /* Device bytes of the batch workspace (0 if a parameter set is invalid,
- * precisions differ, the collision is not MRT or the h lattice is D3Q27). */
+ * precisions differ or are FP16S, the collision is not MRT or the h lattice
+ * is D3Q27). */
 size_t pfl_batch_workspace_bytes(const pfl_params* params, int count);
 
 /* Create the batch: params[count]; phi0[count] arrays (host or device, N_i
  * doubles each, required); u0, p0: NULL or arrays of count pointers (entries
  * may be NULL).  tune_shapes != 0 times the candidate launch shapes of each
- * size class (below / above 65536 cells) on the initial state and keeps the
- * fastest -- threads per block 128 or 256, grid 1, 2 or 4 x SMs x resident
- * blocks -- then rebuilds the initial state.  Synchronises. */
+ * class on the initial state and keeps the fastest -- tile height 4 or 8
+ * (128 or 256 threads per block) for one z plane, the z chunk (a cost
+ * model's, 8, 16, 32, whole) in 3-D, grid 1, 2 or 4 x SMs x resident blocks
+ * -- then rebuilds the initial state.  Without tuning: tile height 4 / 8, the
+ * cost model's z chunk, grid SMs x resident blocks.  Synchronises. */
 pfl_status pfl_batch_init(const pfl_params* params, int count, const double* const* phi0, const double* const* u0,
                           const double* const* p0, void* workspace, size_t workspace_bytes, void* stream,
                           int tune_shapes, pfl_batch** out);
@@ -251,12 +290,14 @@ pfl_status pfl_batch_step(pfl_batch* b, int n_steps);
 pfl_status pfl_batch_fields(pfl_batch* b, int i, double* phi, double* rho, double* p, double* u);
 
 /* pfl_diag of every instance: out[8 * count] (may be NULL), nonfinite[count]
- * (may be NULL).  Instances whose phi holds NaN/Inf are stopped (skipped by
- * later steps) and the call returns PFL_ERR_UNSTABLE.  Synchronises. */
+ * (may be NULL).  Instances whose phi holds NaN/Inf or whose flow speed
+ * exceeds PFL_SPEED_LIMIT are stopped (skipped by later steps, their state
+ * kept) and the call returns PFL_ERR_UNSTABLE.  Synchronises. */
 pfl_status pfl_batch_diag(pfl_batch* b, double* out, long long* nonfinite);
 
-/* Launch shape chosen for each of the two size classes: threads per block,
- * grid blocks and work-list tiles (each array of 2, may be NULL). */
+/* Launch shape chosen for each of the two classes (0: one z plane, 1: 3-D):
+ * threads per block, grid blocks and work-list tiles (each array of 2, may be
+ * NULL). */
 pfl_status pfl_batch_shapes(const pfl_batch* b, int* threads, int* grid, int* ntiles);
 
 /* Steps taken by the batch (-1 for NULL). */
@@ -277,10 +318,14 @@ void pfl_batch_destroy(pfl_batch* b);
  *   out: host array of 8 doubles, the same sums as pfl_diag; nonfinite (host,
  *        may be NULL) the number of NaN/Inf values.  stream: a cudaStream_t.
  * Scratch: a fixed array inside the library image (about 88 KB per device,
- * held until the process exits); no cudaMalloc/cudaFree is called.  The first
- * call on a device looks up that array's device address, so make it before
- * any stream capture.  All calls on one device share the array: calls that
- * overlap on the GPU race and must be ordered by the caller.
+ * held until the process exits); no cudaMalloc/cudaFree is called.  Every
+ * call looks up that array's device address on phi's device, so a device
+ * whose context was reset is picked up by the next call; the first call on a
+ * device also loads the library's kernels there, so make it before any stream
+ * capture.  The kernels run on phi's device; the caller's current device is
+ * the same after the call as before it.  All calls on one device share the
+ * array: calls that overlap on the GPU race and must be ordered by the
+ * caller.
  * Errors: PFL_ERR_ARG for NULL pointers, non-device phi, dims < 1 or more than
  * 2^31 - 1 cells; PFL_ERR_UNSTABLE when NaN/Inf are present; PFL_ERR_CUDA.
  * Synchronises the stream. */
@@ -296,7 +341,7 @@ void pfl_destroy(pfl_ctx* ctx);
 /* Message of the last failed call on this thread ("" if none). */
 const char* pfl_last_error(void);
 
-/* Library interface version (1). */
+/* Library interface version (2: pfl_params carries hydrostatic and p_level). */
 int pfl_version(void);
 
 #ifdef __cplusplus

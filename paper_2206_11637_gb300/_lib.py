@@ -12,6 +12,7 @@ LIB_PATH = os.path.join(HERE, "libpflbm.so")
 HEADER = os.path.join(os.path.dirname(HERE), "include", "pflbm.h")
 
 PFL_OK, PFL_ERR_ARG, PFL_ERR_CUDA, PFL_ERR_OOM, PFL_ERR_UNSTABLE, PFL_ERR_STATE = range(6)
+PFL_SPEED_LIMIT = 0.3
 PFL_FP64, PFL_FP32, PFL_FP16S = 0, 1, 2
 PFL_PERIODIC, PFL_NOSLIP = 0, 1
 PFL_MRT, PFL_BGK = 0, 1
@@ -28,7 +29,8 @@ class pfl_params(ctypes.Structure):
                 ("sigma", ctypes.c_double), ("mobility", ctypes.c_double), ("xi", ctypes.c_double),
                 ("gravity", ctypes.c_double * 3),
                 ("precision", ctypes.c_int), ("collision", ctypes.c_int), ("engine", ctypes.c_int),
-                ("h_lattice", ctypes.c_int), ("solids", ctypes.c_int)]
+                ("h_lattice", ctypes.c_int), ("solids", ctypes.c_int),
+                ("hydrostatic", ctypes.c_int), ("p_level", ctypes.c_double)]
 
 
 class PFLError(RuntimeError):
@@ -76,6 +78,8 @@ def load():
     lib.pfl_load.argtypes = [P, P, ctypes.c_size_t]
     lib.pfl_diag.restype = I
     lib.pfl_diag.argtypes = [P, P, ctypes.POINTER(ctypes.c_longlong)]
+    lib.pfl_max_speed.restype = I
+    lib.pfl_max_speed.argtypes = [P, P]
     lib.pfl_adjoint_workspace_bytes.restype = S
     lib.pfl_adjoint_workspace_bytes.argtypes = [P, I]
     lib.pfl_adjoint.restype = I

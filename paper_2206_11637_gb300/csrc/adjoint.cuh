@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(ADJ_THREADS, PFL_ADJ_MINB) k_adj_local(Geo32 g
       if (cx) gx += cx > 0 ? d : -d;
       if (cy) gy += cy > 0 ? d : -d;
       if (cz) gz += cz > 0 ? d : -d;
-      lap += w * ((a + b) - (R)2 * pc);
+      lap += w * ((a - pc) + (b - pc));  // differences first: exact for nearby values
     }
     gx *= (R)3;
     gy *= (R)3;

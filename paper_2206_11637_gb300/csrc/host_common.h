@@ -3,6 +3,7 @@
 #pragma once
 #include <cmath>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -54,6 +55,12 @@ inline std::string check_params(const pfl_params* p) {
     return "the 2-D lattices (h_lattice 9) need nz = 1 with periodic z faces";
   if (!std::isfinite(p->gravity[0]) || !std::isfinite(p->gravity[1]) || !std::isfinite(p->gravity[2]))
     return "gravity must be finite";
+  if (p->hydrostatic != 0 && p->hydrostatic != 1) return "hydrostatic must be 0 or 1";
+  if (p->hydrostatic) {
+    const int axes = (p->gravity[0] != 0) + (p->gravity[1] != 0) + (p->gravity[2] != 0);
+    if (axes != 1) return "the hydrostatic start needs gravity along exactly one axis";
+    if (!std::isfinite(p->p_level)) return "p_level must be finite";
+  }
   return "";
 }
 
@@ -67,6 +74,46 @@ inline bool is_device_ptr(const void* ptr, int* device = nullptr) {
   }
   if (device) *device = a.device;
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Normalised pressure p* = p / (rho(phi) c_s^2) of the fluid at rest under
+// gravity (the hydrostatic start of the paper's gravity cases): along every
+// line of cells parallel to the gravity axis a, dp/ds = rho(phi) g_a is
+// integrated by the trapezoid rule between cell centres,
+//   P_0 = 0,  P_j = g_a * sum_{k < j} (rho_k + rho_{k+1}) / 2,
+// then shifted so that p = 0 at s = level (linear interpolation between the
+// cells j and j + 1 around it, j clamped to [0, n_a - 2]).  phi0 and out are
+// N host doubles, x-fastest.
+inline void hydrostatic_pstar(const pfl_params* p, const double* phi0, std::vector<double>& out) {
+  const long long n[3] = {p->nx, p->ny, p->nz};
+  const long long N = n[0] * n[1] * n[2];
+  out.assign((size_t)N, 0.0);
+  int a = 0;
+  while (a < 2 && p->gravity[a] == 0) ++a;
+  const double ga = p->gravity[a];
+  const long long stride[3] = {1, n[0], n[0] * n[1]};
+  const long long na = n[a];
+  // the two axes across the lines
+  const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+  std::vector<double> rho((size_t)na), P((size_t)na);
+  long long j0 = (long long)std::floor(p->p_level);
+  if (j0 > na - 2) j0 = na - 2;
+  if (j0 < 0) j0 = 0;
+  const double t = p->p_level - (double)j0;
+  for (long long ic = 0; ic < n[c]; ++ic)
+    for (long long ib = 0; ib < n[b]; ++ib) {
+      const long long base = ib * stride[b] + ic * stride[c];
+      for (long long j = 0; j < na; ++j)
+        rho[(size_t)j] = p->rho_l + phi0[base + j * stride[a]] * (p->rho_h - p->rho_l);
+      double acc = 0.0;
+      P[0] = 0.0;
+      for (long long j = 1; j < na; ++j) {
+        acc += 0.5 * (rho[(size_t)j] + rho[(size_t)(j - 1)]);
+        P[(size_t)j] = ga * acc;
+      }
+      const double ref = na > 1 ? (1.0 - t) * P[(size_t)j0] + t * P[(size_t)(j0 + 1)] : 0.0;
+      for (long long j = 0; j < na; ++j) out[(size_t)(base + j * stride[a])] = 3.0 * (P[(size_t)j] - ref) / rho[(size_t)j];
+    }
 }
 
 inline unsigned blocks_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }

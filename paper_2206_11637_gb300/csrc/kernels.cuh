@@ -164,7 +164,7 @@ __device__ __forceinline__ void stencil(const Geo& geo, const Nb& nb, long long 
 template <int PREC, int QG, int READ_ODD>
 __device__ __forceinline__ void hydro_macro(const Geo& geo, const Phys& ph, const Nb& nb, long long cell,
                                             const typename Store<PREC>::S* __restrict__ g, Macro<typename Store<PREC>::R>& m,
-                                            typename Store<PREC>::R gv[QG]) {
+                                            typename Store<PREC>::R gv[QG], const __half* __restrict__ pg = nullptr) {
   typedef typename Store<PREC>::R R;
   R pst = 0, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
 #pragma unroll
@@ -172,7 +172,9 @@ __device__ __forceinline__ void hydro_macro(const Geo& geo, const Phys& ph, cons
     const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
     long long from;
     const size_t idx = src_index<READ_ODD>(geo, nb, cell, i, QG - 1 - i, cx, cy, cz, from);
-    R v = ld_g<PREC, QG>(g, idx, i);
+    R psh = 0;
+    if constexpr (PREC == 2) psh = ld_pshift(pg, from);
+    R v = ld_g<PREC, QG>(g, idx, i, psh);
     gv[i] = v;
     pst += v;
     if (cx) jx += cx > 0 ? v : -v;
@@ -244,7 +246,9 @@ template <int PREC, int QH, int ODD, int BGK>
 __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<PREC>::S* __restrict__ h,
                                               typename Store<PREC>::S* __restrict__ g,
                                               const typename Store<PREC>::PhiT* __restrict__ phi,
-                                              const typename Store<PREC>::PhiT* __restrict__ shift) {
+                                              const typename Store<PREC>::PhiT* __restrict__ shift,
+                                              const __half* __restrict__ pg_in = nullptr,
+                                              __half* __restrict__ pg_out = nullptr) {
   typedef typename Store<PREC>::R R;
   constexpr int QG = qg_of<QH>();
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -256,7 +260,14 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
   Macro<R> m;
   stencil<PREC, QG>(geo, nb, cell, phi, m);
   R gv[QG];
-  hydro_macro<PREC, QG, ODD>(geo, ph, nb, cell, g, m, gv);
+  hydro_macro<PREC, QG, ODD>(geo, ph, nb, cell, g, m, gv, pg_in);
+  // FP16S: the p* shift of everything this cell writes
+  R pw = 0;
+  if constexpr (PREC == 2) {
+    const __half ps = __float2half_rn(m.pst);
+    pg_out[cell] = ps;
+    pw = __half2float(ps);
+  }
 
   // ---- g collision and streaming
   {
@@ -287,7 +298,7 @@ __global__ void __launch_bounds__(256) k_step(Geo geo, Phys ph, typename Store<P
                      (R)2 * ((R)(cx * cy) * dxy + (R)(cy * cz) * dyz + (R)(cx * cz) * dxz) - tr3;
         post = geq + w * (a2 * hd + cf);
       }
-      st_g<PREC, QG>(g, dst_index<ODD>(geo, nb, cell, i, QG - 1 - i, cx, cy, cz), i, post);
+      st_g<PREC, QG>(g, dst_index<ODD>(geo, nb, cell, i, QG - 1 - i, cx, cy, cz), i, post, pw);
     }
   }
 
@@ -365,14 +376,30 @@ __global__ void __launch_bounds__(256) k_phi(Geo geo, const typename Store<PREC>
   phi[cell] = s;
 }
 
-// Equilibrium initial state (normal layout, zero shifts) for cells
-// [c0, c0 + count).  Inputs are FP64 arrays indexed from c0 (phi0, u0x, u0y,
-// u0z, p0; u and p may be NULL).
+// FP16S fresh state, first pass: the shifts of cells [c0, c0 + count) --
+// their own initial phi (FP32) and fp16(p*) -- into hshift and pshift (inputs
+// indexed from c0; p0 may be NULL).
+static __global__ void k_init_shift(long long c0, long long count, const double* __restrict__ phi0,
+                             const double* __restrict__ p0, float* __restrict__ hshift, __half* __restrict__ pshift) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  hshift[c0 + t] = (float)phi0[t];
+  pshift[c0 + t] = __float2half_rn(p0 ? (float)p0[t] : 0.0f);
+}
+
+// Equilibrium initial state (normal layout) for cells [c0, c0 + count).
+// Inputs are FP64 arrays indexed from c0 (phi0, u0x, u0y, u0z, p0; u and p may
+// be NULL).  FP16S (after k_init_shift has written every cell's shifts):
+// population c of cell x is stored the way a step would have pushed it, against
+// the shifts of its writer x - c (of x itself where x - c lies behind a wall),
+// so that the readers' convention holds from the first step on and a cell at
+// rest in a uniform region is stored exactly.
 template <int PREC, int QH>
 __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typename Store<PREC>::S* __restrict__ g,
                        long long c0, long long count, const double* __restrict__ phi0,
                        const double* __restrict__ u0x, const double* __restrict__ u0y,
-                       const double* __restrict__ u0z, const double* __restrict__ p0) {
+                       const double* __restrict__ u0z, const double* __restrict__ p0,
+                       const float* __restrict__ hshift = nullptr, const __half* __restrict__ pshift = nullptr) {
   typedef typename Store<PREC>::R R;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= count) return;
@@ -382,16 +409,77 @@ __global__ void k_init(Geo geo, typename Store<PREC>::S* __restrict__ h, typenam
   const R ps = p0 ? (R)p0[t] : (R)0;
   const R uu = ux * ux + uy * uy + uz * uz;
   constexpr int QG = qg_of<QH>();
+  Nb nb;
+  if constexpr (PREC == 2) {
+    int x, y, z;
+    cell_coords(geo, cell, x, y, z);
+    make_nb(geo, x, y, z, nb);
+  }
 #pragma unroll
   for (int i = 0; i < QG; ++i) {
     const int j = lq_to27<QG>(i);
-    const R cu = (R)q27_cx(j) * ux + (R)q27_cy(j) * uy + (R)q27_cz(j) * uz;
-    st_g<PREC, QG>(g, (size_t)i * geo.N + cell, i, (R)lq_w<QG>(i) * (ps + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu));
+    const int cx = q27_cx(j), cy = q27_cy(j), cz = q27_cz(j);
+    const R cu = (R)cx * ux + (R)cy * uy + (R)cz * uz;
+    if constexpr (PREC == 2) {  // stored directly as g / w - P_writer
+      long long from;
+      src_index<0>(geo, nb, cell, i, QG - 1 - i, cx, cy, cz, from);
+      const R pw = __half2float(pshift[from]);
+      g[(size_t)i * geo.N + cell] = __float2half_rn(((ps - pw) + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu) * (R)KG16);
+    } else {
+      st_g<PREC, QG>(g, (size_t)i * geo.N + cell, i, (R)lq_w<QG>(i) * (ps + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * uu));
+    }
   }
 #pragma unroll
   for (int k = 0; k < QH; ++k) {
-    const R cu = (R)hq_cx<QH>(k) * ux + (R)hq_cy<QH>(k) * uy + (R)hq_cz<QH>(k) * uz;
-    st_h_q<PREC, QH>(h, (size_t)k * geo.N + cell, k, ph * ((R)1 + (R)3 * cu));
+    const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
+    const R cu = (R)cx * ux + (R)cy * uy + (R)cz * uz;
+    R q = ph * ((R)1 + (R)3 * cu);  // h / w
+    if constexpr (PREC == 2) {       // less the writer's phi
+      long long from;
+      src_index<0>(geo, nb, cell, k, QH - 1 - k, cx, cy, cz, from);
+      q = (ph - (R)hshift[from]) + ph * (R)3 * cu;
+    }
+    st_h_q<PREC, QH>(h, (size_t)k * geo.N + cell, k, q);
+  }
+}
+
+// FP16S fresh state with solid cells: a population of a fluid cell whose
+// incoming link now starts in a solid cell counts as bounced back, written by
+// the cell itself; re-store it against the cell's own shifts instead of the
+// solid neighbour's (fresh states, before the first step).
+template <int QH>
+__global__ void k_reshift_blocked(Geo geo, __half* __restrict__ h, __half* __restrict__ g,
+                                  const float* __restrict__ hshift, const __half* __restrict__ pshift,
+                                  const unsigned* __restrict__ links) {
+  const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= geo.N) return;
+  const unsigned blk = links[cell];
+  if (!blk || (blk & (1u << 13))) return;
+  int x, y, z;
+  cell_coords(geo, cell, x, y, z);
+  Nb nb;
+  make_nb(geo, x, y, z, nb);
+  constexpr int QG = qg_of<QH>();
+#pragma unroll
+  for (int i = 0; i < QG; ++i) {
+    const int j = lq_to27<QG>(i);
+    const int cx = q27_cx(j), cy = q27_cy(j), cz = q27_cz(j);
+    if (!(blk & (1u << ((1 - cx) + 3 * (1 - cy) + 9 * (1 - cz))))) continue;  // neighbour at x - c is solid
+    long long from;
+    src_index<0>(geo, nb, cell, i, QG - 1 - i, cx, cy, cz, from);
+    const size_t idx = (size_t)i * geo.N + cell;
+    const float v = __half2float(g[idx]) + (float)KG16 * (__half2float(pshift[from]) - __half2float(pshift[cell]));
+    g[idx] = __float2half_rn(v);
+  }
+#pragma unroll
+  for (int k = 0; k < QH; ++k) {
+    const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
+    if (!(blk & (1u << ((1 - cx) + 3 * (1 - cy) + 9 * (1 - cz))))) continue;
+    long long from;
+    src_index<0>(geo, nb, cell, k, QH - 1 - k, cx, cy, cz, from);
+    const size_t idx = (size_t)k * geo.N + cell;
+    const float v = __half2float(h[idx]) + (float)KH16 * (hshift[from] - hshift[cell]);
+    h[idx] = __float2half_rn(v);
   }
 }
 
@@ -401,7 +489,8 @@ template <int PREC, int QH, int READ_ODD>
 __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename Store<PREC>::S* __restrict__ g,
                                                 const typename Store<PREC>::PhiT* __restrict__ phi, double* o_phi, double* o_rho,
                                                 double* o_p, double* o_ux, double* o_uy, double* o_uz,
-                                                const unsigned* __restrict__ links = nullptr) {
+                                                const unsigned* __restrict__ links = nullptr,
+                                                const __half* __restrict__ pg = nullptr) {
   typedef typename Store<PREC>::R R;
   constexpr int QG = qg_of<QH>();
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -420,7 +509,7 @@ __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename
   Macro<R> m;
   stencil<PREC, QG>(geo, nb, cell, phi, m, blk);
   R gv[QG];
-  hydro_macro<PREC, QG, READ_ODD>(geo, ph, nb, cell, g, m, gv);
+  hydro_macro<PREC, QG, READ_ODD>(geo, ph, nb, cell, g, m, gv, pg);
   if (o_phi) o_phi[cell] = (double)m.phi;
   if (o_rho) o_rho[cell] = (double)m.rho;
   if (o_p) o_p[cell] = (double)m.pst * (double)m.rho / 3.0;
@@ -433,7 +522,7 @@ __global__ void __launch_bounds__(256) k_fields(Geo geo, Phys ph, const typename
 template <int PREC, int QH, int READ_ODD>
 __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
                          const typename Store<PREC>::PhiT* __restrict__ shift, int is_g, int i,
-                         double* __restrict__ out) {
+                         double* __restrict__ out, const __half* __restrict__ pg = nullptr) {
   const long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
   int x, y, z;
@@ -448,7 +537,9 @@ __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
         long long from;
         const int k = lq_to27<QG>(j);
         const size_t idx = src_index<READ_ODD>(geo, nb, cell, j, QG - 1 - j, q27_cx(k), q27_cy(k), q27_cz(k), from);
-        out[cell] = (double)ld_g<PREC, QG>(f, idx, j);
+        float psh = 0.0f;
+        if constexpr (PREC == 2) psh = ld_pshift(pg, from);
+        out[cell] = (double)ld_g<PREC, QG>(f, idx, j, psh);
       }
   } else {
 #pragma unroll
@@ -457,7 +548,7 @@ __global__ void k_export(Geo geo, const typename Store<PREC>::S* __restrict__ f,
   }
 }
 
-// Population import (normal layout; h with zero shifts).
+// Population import (normal layout; h and g with zero shifts).
 template <int PREC, int QH>
 __global__ void k_import(Geo geo, typename Store<PREC>::S* __restrict__ f, int is_g, int i, const double* __restrict__ in) {
   typedef typename Store<PREC>::R R;
@@ -533,6 +624,57 @@ static __global__ void k_diag_final(const double* __restrict__ part, int nblocks
   for (int b = threadIdx.x; b < nblocks; b += 32) s += part[(size_t)b * 9 + k];
   s = warp_sum(s);
   if (threadIdx.x == 0) out[k] = s;
+}
+
+// Largest flow speed |u| (u = sum c g + F / (2 rho), as pfl_fields) over the
+// fluid cells: each block writes the largest |u|^2 of its cells to
+// part[block] (grid-stride over the lattice; a non-finite u counts as +inf);
+// k_max_final takes the largest of the partials.  Solid cells (links non-NULL,
+// bit 13) are skipped.
+template <int PREC, int QH, int READ_ODD>
+__global__ void __launch_bounds__(DIAG_THREADS) k_umax(Geo geo, Phys ph, const typename Store<PREC>::S* __restrict__ g,
+                                                       const typename Store<PREC>::PhiT* __restrict__ phi,
+                                                       double* __restrict__ part,
+                                                       const unsigned* __restrict__ links = nullptr,
+                                                       const __half* __restrict__ pg = nullptr) {
+  typedef typename Store<PREC>::R R;
+  constexpr int QG = qg_of<QH>();
+  double best = 0.0;
+  for (long long cell = (long long)blockIdx.x * blockDim.x + threadIdx.x; cell < geo.N;
+       cell += (long long)gridDim.x * blockDim.x) {
+    const unsigned blk = links ? links[cell] : 0u;
+    if (blk & (1u << 13)) continue;
+    int x, y, z;
+    cell_coords(geo, cell, x, y, z);
+    Nb nb;
+    make_nb(geo, x, y, z, nb);
+    Macro<R> m;
+    stencil<PREC, QG>(geo, nb, cell, phi, m, blk);
+    R gv[QG];
+    hydro_macro<PREC, QG, READ_ODD>(geo, ph, nb, cell, g, m, gv, pg);
+    const double u2 = (double)m.ux * (double)m.ux + (double)m.uy * (double)m.uy + (double)m.uz * (double)m.uz;
+    best = isfinite(u2) ? fmax(best, u2) : INFINITY;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  __shared__ double sm[DIAG_THREADS / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sm[wid] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = sm[0];
+    for (int w = 1; w < DIAG_THREADS / 32; ++w) b = fmax(b, sm[w]);
+    part[blockIdx.x] = b;
+  }
+}
+
+// out[0] = sqrt of the largest of part[0 .. nblocks) (one warp)
+static __global__ void k_max_final(const double* __restrict__ part, int nblocks, double* __restrict__ out) {
+  double b = 0.0;
+  for (int k = threadIdx.x; k < nblocks; k += 32) b = fmax(b, part[k]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  if (threadIdx.x == 0) out[0] = sqrt(b);
 }
 
 }  // namespace pfl

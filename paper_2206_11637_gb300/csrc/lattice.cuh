@@ -91,14 +91,18 @@ __host__ __device__ constexpr int hq_rest() {
 // divided by its weight:
 //   h: stored = fp16(KH16 * (h_i / w_i - phi_x)), x the writing cell and phi_x
 //      its phase field at the step of writing (a double-buffered per-cell
-//      array), so that only the non-equilibrium and velocity parts are stored;
-//   g: stored = fp16(KG16 * g_i / w_i).  g_i / w_i is p* + O(u) and p* stays
-//      O(1) in both phases, so no shift is needed; a p*-shifted g format was
-//      measured to give the same wave period, mass drift and phi error at 15 %
-//      more memory traffic per step.
-// The power-of-two scales lift small values out of the FP16 subnormal range
-// while keeping |h_i / w_i - phi| up to 64 and |g_i / w_i| up to 256
-// representable.
+//      FP32 array), so that only the non-equilibrium and velocity parts are
+//      stored;
+//   g: stored = fp16(KG16 * (g_i / w_i - P_x)), P_x = fp16(p*_x) the
+//      normalised pressure of the writing cell at the step of writing, itself
+//      kept in a double-buffered per-cell FP16 array (reader and writer use
+//      the same rounded value).  g_i / w_i = p* + O(u): without the shift, the
+//      FP16 rounding of p* alone (5e-4 p*) swamps u where p* >> |u|, as in the
+//      gas of a bubble (p* = 3 p / rho_L).
+// Fresh states (initialisation) are stored against their own initial phi and
+// p*, so that a state at rest is stored exactly.  The power-of-two scales lift
+// small values out of the FP16 subnormal range while keeping
+// |h_i / w_i - phi| up to 64 and |g_i / w_i - P| up to 256 representable.
 constexpr double KH16 = 1024.0;
 constexpr double KG16 = 256.0;
 
@@ -126,21 +130,27 @@ struct Store<2> {  // shifted FP16 storage, FP32 arithmetic
   typedef float PhiT;
 };
 
-// g population i: load / store in the arithmetic type.
+// g population i: load / store in the arithmetic type; pshift is the p*
+// shift of the writing cell (FP16S only, zero otherwise).
 template <int PREC, int QG = 27>
-__device__ __forceinline__ typename Store<PREC>::R ld_g(const typename Store<PREC>::S* a, size_t idx, int i) {
+__device__ __forceinline__ typename Store<PREC>::R ld_g(const typename Store<PREC>::S* a, size_t idx, int i,
+                                                        typename Store<PREC>::R pshift = 0) {
   if constexpr (PREC == 2)
-    return __half2float(a[idx]) * (float)(lq_w<QG>(i) / KG16);
+    return (__half2float(a[idx]) * (float)(1.0 / KG16) + pshift) * (float)lq_w<QG>(i);
   else
     return a[idx];
 }
 template <int PREC, int QG = 27>
-__device__ __forceinline__ void st_g(typename Store<PREC>::S* a, size_t idx, int i, typename Store<PREC>::R v) {
+__device__ __forceinline__ void st_g(typename Store<PREC>::S* a, size_t idx, int i, typename Store<PREC>::R v,
+                                     typename Store<PREC>::R pshift = 0) {
   if constexpr (PREC == 2)
-    a[idx] = __float2half_rn(v * (float)(KG16 / lq_w<QG>(i)));
+    a[idx] = __float2half_rn((v * (float)(1.0 / lq_w<QG>(i)) - pshift) * (float)KG16);
   else
     a[idx] = v;
 }
+
+// p* shift of the cells that wrote the stored g (FP16S), as the arithmetic type.
+__device__ __forceinline__ float ld_pshift(const __half* p, size_t cell) { return __half2float(__ldg(p + cell)); }
 
 // h population k: load adds back the shift phi_src (FP16S only).
 template <int PREC, int QH>

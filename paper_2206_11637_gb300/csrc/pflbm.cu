@@ -51,7 +51,7 @@ pfl_status cuda_fail(cudaError_t e, const char* what) {
 
 
 struct Layout {
-  size_t h, g, h2, g2, phi[2], links, stage, red, clock, total;
+  size_t h, g, h2, g2, phi[2], pg[2], links, stage, red, clock, total;
 };
 
 Layout layout_of(const pfl_params* p) {
@@ -74,12 +74,18 @@ Layout layout_of(const pfl_params* p) {
     L.phi[b] = off;
     off = align256(off + N * phi_bytes(p->precision));
   }
+  // FP16S: the p* shifts of the stored g (one FP16 per cell, double-buffered
+  // like phi)
+  for (int b = 0; b < 2; ++b) {
+    L.pg[b] = off;
+    if (p->precision == PFL_FP16S) off = align256(off + N * sizeof(__half));
+  }
   L.links = off;  // blocked-link words of solid lattices
   if (p->solids) off = align256(off + N * sizeof(unsigned));
   L.stage = off;
   off = align256(off + (N + 16) * sizeof(double));
-  L.red = off;
-  off = align256(off + (DIAG_BLOCKS * 9 + 16) * sizeof(double));
+  L.red = off;  // phi partials (9 per block), results, flow-speed partials (1 per block), result
+  off = align256(off + (DIAG_BLOCKS * 10 + 32) * sizeof(double));
   L.clock = off;  // step count read by graph-replayed steps
   off = align256(off + sizeof(unsigned long long));
   L.total = off;
@@ -152,6 +158,12 @@ template <int PREC>
 typename Store<PREC>::PhiT* phishift(pfl_ctx* c) {
   return phibuf<PREC>(c, 1 - c->cur);
 }
+// FP16S p* shifts: pgshift holds those of the stored g (read by a step),
+// pgcur receives those of the g a step writes (same parity as phi); NULL for
+// the other precisions.
+__half* pgbuf(pfl_ctx* c, int b) { return c->p.precision == PFL_FP16S ? (__half*)(c->ws + c->L.pg[b]) : nullptr; }
+__half* pgcur(pfl_ctx* c) { return pgbuf(c, c->cur); }
+__half* pgshift(pfl_ctx* c) { return pgbuf(c, 1 - c->cur); }
 double* stage(pfl_ctx* c) { return (double*)(c->ws + c->L.stage); }
 
 // seed of the FP16 stochastic rounding of one step
@@ -213,7 +225,8 @@ void step_only(pfl_ctx* c) {
     const int tofs = (int)(c->t - c->cap_t0);
 #define PFL_ZM(FLAT, SOLID)                                                                                   \
   cudaLaunchKernelEx(&cfg, k_step_zm<PREC, QH, FLAT, SOLID>, c->g32, c->ph, ha, ga, hnext<PREC>(c),           \
-                     gnext<PREC>(c), shift, phicur<PREC>(c), c->zc, step_seed(c), links, tclock, tofs)
+                     gnext<PREC>(c), shift, phicur<PREC>(c), c->zc, step_seed(c), links, tclock, tofs,       \
+                     (const __half*)pgshift(c), pgcur(c))
     if (c->p.nz == 1) {
       if (c->solid)
         PFL_ZM(1, 1);
@@ -236,18 +249,20 @@ void step_only(pfl_ctx* c) {
   if (BGK || !c->idx32) {
     if (c->swapped)
       k_step<PREC, QH, 1, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
-                                                       phishift<PREC>(c));
+                                                       phishift<PREC>(c), pgshift(c), pgcur(c));
     else
       k_step<PREC, QH, 0, BGK><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, hbuf<PREC>(c), gbuf<PREC>(c), phicur<PREC>(c),
-                                                       phishift<PREC>(c));
+                                                       phishift<PREC>(c), pgshift(c), pgcur(c));
   } else {
     const unsigned nbm = blocks_for(c->geo.N, PFL_STEP_THREADS);
     if (c->swapped)
       k_step_mrt<PREC, QH, 1><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),
-                                                                    phicur<PREC>(c), phishift<PREC>(c), step_seed(c));
+                                                                    phicur<PREC>(c), phishift<PREC>(c), step_seed(c),
+                                                                    pgshift(c), pgcur(c));
     else
       k_step_mrt<PREC, QH, 0><<<nbm, PFL_STEP_THREADS, 0, c->stream>>>(c->g32, c->ph, hbuf<PREC>(c), gbuf<PREC>(c),
-                                                                    phicur<PREC>(c), phishift<PREC>(c), step_seed(c));
+                                                                    phicur<PREC>(c), phishift<PREC>(c), step_seed(c),
+                                                                    pgshift(c), pgcur(c));
   }
   c->swapped ^= 1;
   c->t += 1;
@@ -287,14 +302,18 @@ void launch_steps(pfl_ctx* c, int n) {
   }
 }
 
-// Fresh populations carry zero shifts (init / import).  Zero buffer 1, make it
-// current so that launch_phi reads its shifts from it, and let launch_phi
-// write phi into buffer 0 and make that one current.
+// Fresh populations (init, import) carry the shifts of buffer 1: the
+// initial phi and p* written by k_init, or zeros (zero_shifts, for imported
+// populations).  Make buffer 1 current so that launch_phi reads its shifts from
+// it, and let launch_phi write phi into buffer 0 and make that one current.
 template <int PREC, int QH>
-pfl_status fresh_phi(pfl_ctx* c) {
+pfl_status fresh_phi(pfl_ctx* c, bool zero_shifts) {
   c->stale = false;
   c->cur = 1;
-  CUDA_TRY(cudaMemsetAsync(phicur<PREC>(c), 0, c->geo.N * sizeof(typename Store<PREC>::PhiT), c->stream));
+  if (zero_shifts) {
+    CUDA_TRY(cudaMemsetAsync(phicur<PREC>(c), 0, c->geo.N * sizeof(typename Store<PREC>::PhiT), c->stream));
+    if (pgbuf(c, 1)) CUDA_TRY(cudaMemsetAsync(pgbuf(c, 1), 0, c->geo.N * sizeof(__half), c->stream));
+  }
   c->swapped = 0;
   launch_phi<PREC, QH>(c);  // reads shifts from buffer 1 (zeros), writes phi into buffer 0, cur = 0
   CUDA_TRY(cudaGetLastError());
@@ -307,10 +326,12 @@ void launch_fields(pfl_ctx* c, double* o[6]) {
   const unsigned* links = (const unsigned*)(c->ws + c->L.links);
   if (c->swapped)
     k_fields<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0],
-                                                  o[1], o[2], o[3], o[4], o[5], c->solid ? links : nullptr);
+                                                  o[1], o[2], o[3], o[4], o[5], c->solid ? links : nullptr,
+                                                  pgshift(c));
   else
     k_fields<PREC, QH, 0><<<nb, 256, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c), o[0],
-                                                  o[1], o[2], o[3], o[4], o[5], c->solid ? links : nullptr);
+                                                  o[1], o[2], o[3], o[4], o[5], c->solid ? links : nullptr,
+                                                  pgshift(c));
 }
 
 template <int PREC, int QH>
@@ -318,9 +339,9 @@ void launch_export(pfl_ctx* c, int is_g, int i, double* out) {
   const unsigned nb = blocks_for(c->geo.N, 256);
   const typename Store<PREC>::S* f = is_g ? gbuf<PREC>(c) : hbuf<PREC>(c);
   if (c->swapped)
-    k_export<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), is_g, i, out);
+    k_export<PREC, QH, 1><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), is_g, i, out, pgshift(c));
   else
-    k_export<PREC, QH, 0><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), is_g, i, out);
+    k_export<PREC, QH, 0><<<nb, 256, 0, c->stream>>>(c->geo, f, phishift<PREC>(c), is_g, i, out, pgshift(c));
 }
 
 template <int PREC, int QH>
@@ -333,14 +354,30 @@ void launch_import(pfl_ctx* c, int is_g, int i, const double* in) {
 template <int PREC, int QH>
 void launch_init(pfl_ctx* c, long long c0, long long count, const double* phi0, const double* ux, const double* uy,
                  const double* uz, const double* p0) {
+  // FP16S: stored against the writers' shifts, which k_init_shift has put into
+  // buffer 1 (fresh_phi reads them there)
+  const float* hs = PREC == 2 ? (const float*)phibuf<PREC>(c, 1) : nullptr;
   k_init<PREC, QH><<<blocks_for(count, 256), 256, 0, c->stream>>>(c->geo, hbuf<PREC>(c), gbuf<PREC>(c), c0, count, phi0,
-                                                               ux, uy, uz, p0);
+                                                               ux, uy, uz, p0, hs, pgbuf(c, 1));
 }
 
 template <int PREC>
 void launch_diag(pfl_ctx* c, double* part, double* out) {
   k_diag<typename Store<PREC>::PhiT><<<DIAG_BLOCKS, DIAG_THREADS, 0, c->stream>>>(c->geo, phicur<PREC>(c), part);
   k_diag_final<<<9, 32, 0, c->stream>>>(part, DIAG_BLOCKS, out);
+}
+
+// Largest |u| of the current state into out[0] (partials in part[0 .. DIAG_BLOCKS)).
+template <int PREC, int QH>
+void launch_umax(pfl_ctx* c, double* part, double* out) {
+  const unsigned* links = c->solid ? (const unsigned*)(c->ws + c->L.links) : nullptr;
+  if (c->swapped)
+    k_umax<PREC, QH, 1><<<DIAG_BLOCKS, DIAG_THREADS, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c),
+                                                                     part, links, pgshift(c));
+  else
+    k_umax<PREC, QH, 0><<<DIAG_BLOCKS, DIAG_THREADS, 0, c->stream>>>(c->geo, c->ph, gbuf<PREC>(c), phicur<PREC>(c),
+                                                                     part, links, pgshift(c));
+  k_max_final<<<1, 32, 0, c->stream>>>(part, DIAG_BLOCKS, out);
 }
 
 #define DISPATCH_PREC(c, fn, ...)                 \
@@ -403,9 +440,12 @@ pfl_status apply_solid(pfl_ctx* c, const unsigned char* mask_dev) {
   for (int k = 0; k < 4; ++k)
     k_zero_solid<PREC><<<blocks_for(N, 256), 256, 0, c->stream>>>(N, qs[k], links,
                                                                   (typename Store<PREC>::S*)(c->ws + offs[k]));
+  if constexpr (PREC == 2)
+    k_reshift_blocked<QH><<<blocks_for(N, 256), 256, 0, c->stream>>>(
+        c->geo, (__half*)hbuf<PREC>(c), (__half*)gbuf<PREC>(c), (const float*)phibuf<PREC>(c, 1), pgbuf(c, 1), links);
   CUDA_TRY(cudaGetLastError());
   c->solid = true;
-  return fresh_phi<PREC, QH>(c);  // phi = 0 in solid cells; shifts of fresh populations
+  return fresh_phi<PREC, QH>(c, false);  // phi = 0 in solid cells; the initial shifts stay
 }
 
 // Height of the phi = 1/2 crossing along y in the column (x, z): the first j
@@ -500,7 +540,7 @@ pfl_status graph_steps(pfl_ctx* c) {
 
 extern "C" {
 
-int pfl_version(void) { return 1; }
+int pfl_version(void) { return 2; }
 
 const char* pfl_last_error(void) { return g_err.c_str(); }
 
@@ -606,47 +646,73 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
   c->ph.gy = p->gravity[1];
   c->ph.gz = p->gravity[2];
 
-  // Initial state, in chunks through the FP64 staging area (5 arrays per chunk).
+  // Hydrostatic start (p0 == NULL, params.hydrostatic): p* from phi0 on the host.
   const long long N = c->geo.N;
+  std::vector<double> p_hydro;
+  if (!p0 && p->hydrostatic) {
+    std::vector<double> phi_host;
+    const double* ph0 = phi0;
+    if (is_device_ptr(phi0)) {
+      phi_host.resize((size_t)N);
+      cudaError_t e = cudaMemcpy(phi_host.data(), phi0, (size_t)N * sizeof(double), cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "phi0 to the host for the hydrostatic start");
+      }
+      ph0 = phi_host.data();
+    }
+    hydrostatic_pstar(p, ph0, p_hydro);
+    p0 = p_hydro.data();
+  }
+
+  // Initial state, in chunks through the FP64 staging area (5 arrays per
+  // chunk).  FP16S takes two passes: every cell's shifts first, then the
+  // populations stored against their writers' shifts.
   const long long chunk = N / 5 > 0 ? N / 5 : 1;  // 5 * chunk <= N + 16 staging doubles
   double* st = stage(c);
-  for (long long c0 = 0; c0 < N; c0 += chunk) {
-    const long long cnt = (N - c0 < chunk) ? N - c0 : chunk;
-    double* a_phi = st;
-    double* a_ux = st + cnt;
-    double* a_uy = st + 2 * cnt;
-    double* a_uz = st + 3 * cnt;
-    double* a_p = st + 4 * cnt;
-    pfl_status s;
-    if ((s = to_device(c, a_phi, phi0 + c0, cnt)) != PFL_OK) {
-      delete c;
-      return s;
-    }
-    if (u0) {
-      if ((s = to_device(c, a_ux, u0 + c0, cnt)) != PFL_OK || (s = to_device(c, a_uy, u0 + N + c0, cnt)) != PFL_OK ||
-          (s = to_device(c, a_uz, u0 + 2 * N + c0, cnt)) != PFL_OK) {
+  const int passes = p->precision == PFL_FP16S ? 2 : 1;
+  for (int pass = passes == 2 ? 0 : 1; pass < 2; ++pass)
+    for (long long c0 = 0; c0 < N; c0 += chunk) {
+      const long long cnt = (N - c0 < chunk) ? N - c0 : chunk;
+      double* a_phi = st;
+      double* a_ux = st + cnt;
+      double* a_uy = st + 2 * cnt;
+      double* a_uz = st + 3 * cnt;
+      double* a_p = st + 4 * cnt;
+      pfl_status s;
+      if ((s = to_device(c, a_phi, phi0 + c0, cnt)) != PFL_OK) {
         delete c;
         return s;
       }
-    }
-    if (p0) {
-      if ((s = to_device(c, a_p, p0 + c0, cnt)) != PFL_OK) {
+      if (u0 && pass == 1) {
+        if ((s = to_device(c, a_ux, u0 + c0, cnt)) != PFL_OK || (s = to_device(c, a_uy, u0 + N + c0, cnt)) != PFL_OK ||
+            (s = to_device(c, a_uz, u0 + 2 * N + c0, cnt)) != PFL_OK) {
+          delete c;
+          return s;
+        }
+      }
+      if (p0) {
+        if ((s = to_device(c, a_p, p0 + c0, cnt)) != PFL_OK) {
+          delete c;
+          return s;
+        }
+      }
+      if (pass == 0)
+        k_init_shift<<<blocks_for(cnt, 256), 256, 0, c->stream>>>(c0, cnt, a_phi, p0 ? a_p : nullptr,
+                                                                   (float*)(c->ws + c->L.phi[1]), pgbuf(c, 1));
+      else
+        DISPATCH(c, launch_init, c, c0, cnt, a_phi, u0 ? a_ux : nullptr, u0 ? a_uy : nullptr, u0 ? a_uz : nullptr,
+                      p0 ? a_p : nullptr);
+      // the staging area is reused by the next chunk: wait for this one
+      cudaError_t e = cudaStreamSynchronize(c->stream);
+      if (e == cudaSuccess) e = cudaGetLastError();
+      if (e != cudaSuccess) {
         delete c;
-        return s;
+        return cuda_fail(e, "initialisation");
       }
     }
-    DISPATCH(c, launch_init, c, c0, cnt, a_phi, u0 ? a_ux : nullptr, u0 ? a_uy : nullptr, u0 ? a_uz : nullptr,
-                  p0 ? a_p : nullptr);
-    // the staging area is reused by the next chunk: wait for this one
-    cudaError_t e = cudaStreamSynchronize(c->stream);
-    if (e == cudaSuccess) e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      delete c;
-      return cuda_fail(e, "initialisation");
-    }
-  }
   pfl_status s = PFL_OK;
-  DISPATCH_S(s, c, fresh_phi, c);
+  DISPATCH_S(s, c, fresh_phi, c, false);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (s != PFL_OK || e != cudaSuccess) {
     delete c;
@@ -760,7 +826,7 @@ pfl_status pfl_set_populations(pfl_ctx* c, const double* h, const double* g) {
     }
   }
   pfl_status s = PFL_OK;
-  DISPATCH_S(s, c, fresh_phi, c);
+  DISPATCH_S(s, c, fresh_phi, c, true);
   if (s != PFL_OK) return s;
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PFL_OK;
@@ -768,40 +834,47 @@ pfl_status pfl_set_populations(pfl_ctx* c, const double* h, const double* g) {
 
 // ---- saved states: a header, then the stored arrays as they sit in the
 // workspace (current h, current g, both phi buffers, the link words)
+constexpr int NSAVED = 7;
 struct SavedHeader {
   char magic[8];          // "PFLSTATE"
-  int version;            // 1
+  int version;            // 2 (7 sections)
   int precision, qh, qg;  // storage and lattices
   int nx, ny, nz, bc[6];  // lattice
   int zm, solid;          // engine (fused two-array step or in-place), solid cells present
   int cur, swapped, stale;
   long long t;
-  unsigned long long bytes[5];  // h, g, phi buffer 0, phi buffer 1, links
+  unsigned long long bytes[NSAVED];  // h, g, phi buffers 0 and 1, links, p* shift buffers 0 and 1
 };
 
-// workspace offsets of the saved sections: the current h and g, the phi buffers, the links
-static void saved_offsets(const pfl_ctx* c, size_t o[5]) {
+// workspace offsets of the saved sections: the current h and g, the phi
+// buffers, the links, the FP16S p* shift buffers
+static void saved_offsets(const pfl_ctx* c, size_t o[NSAVED]) {
   const bool second = c->zm && c->ab;
   o[0] = second ? c->L.h2 : c->L.h;
   o[1] = second ? c->L.g2 : c->L.g;
   o[2] = c->L.phi[0];
   o[3] = c->L.phi[1];
   o[4] = c->L.links;
+  o[5] = c->L.pg[0];
+  o[6] = c->L.pg[1];
 }
 
-static void saved_sections(const pfl_ctx* c, unsigned long long b[5]) {
+static void saved_sections(const pfl_ctx* c, unsigned long long b[NSAVED]) {
   const unsigned long long N = (unsigned long long)c->geo.N;
   b[0] = (unsigned long long)c->qh * N * pop_bytes(c->p.precision);
   b[1] = (unsigned long long)c->qg * N * pop_bytes(c->p.precision);
   b[2] = b[3] = N * phi_bytes(c->p.precision);
   b[4] = c->solid ? N * sizeof(unsigned) : 0;
+  b[5] = b[6] = c->p.precision == PFL_FP16S ? N * sizeof(__half) : 0;
 }
 
 size_t pfl_state_bytes(const pfl_ctx* c) {
   if (!c) return 0;
-  unsigned long long b[5];
+  unsigned long long b[NSAVED];
   saved_sections(c, b);
-  return sizeof(SavedHeader) + (size_t)(b[0] + b[1] + b[2] + b[3] + b[4]);
+  size_t total = sizeof(SavedHeader);
+  for (int k = 0; k < NSAVED; ++k) total += (size_t)b[k];
+  return total;
 }
 
 pfl_status pfl_save(pfl_ctx* c, void* buf, size_t bytes) {
@@ -814,7 +887,7 @@ pfl_status pfl_save(pfl_ctx* c, void* buf, size_t bytes) {
   SavedHeader hd;
   std::memset(&hd, 0, sizeof hd);
   std::memcpy(hd.magic, "PFLSTATE", 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.precision = c->p.precision;
   hd.qh = c->qh;
   hd.qg = c->qg;
@@ -832,9 +905,9 @@ pfl_status pfl_save(pfl_ctx* c, void* buf, size_t bytes) {
   char* dst = (char*)buf;
   CUDA_TRY(cudaMemcpyAsync(dst, &hd, sizeof hd, cudaMemcpyDefault, c->stream));
   size_t off = sizeof hd;
-  size_t so[5];
+  size_t so[NSAVED];
   saved_offsets(c, so);
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < NSAVED; ++k) {
     if (hd.bytes[k]) CUDA_TRY(cudaMemcpyAsync(dst + off, c->ws + so[k], hd.bytes[k], cudaMemcpyDefault, c->stream));
     off += hd.bytes[k];
   }
@@ -849,7 +922,7 @@ pfl_status pfl_load(pfl_ctx* c, const void* buf, size_t bytes) {
   CUDA_TRY(cudaSetDevice(c->device));
   SavedHeader hd;
   CUDA_TRY(cudaMemcpy(&hd, buf, sizeof hd, cudaMemcpyDefault));
-  if (std::memcmp(hd.magic, "PFLSTATE", 8) != 0 || hd.version != 1)
+  if (std::memcmp(hd.magic, "PFLSTATE", 8) != 0 || hd.version != 2)
     return fail(PFL_ERR_ARG, "not a saved state (magic or version)");
   bool same = hd.precision == c->p.precision && hd.qh == c->qh && hd.qg == c->qg && hd.nx == c->p.nx &&
               hd.ny == c->p.ny && hd.nz == c->p.nz && hd.zm == (int)c->zm;
@@ -858,13 +931,13 @@ pfl_status pfl_load(pfl_ctx* c, const void* buf, size_t bytes) {
     return fail(PFL_ERR_ARG, "the saved state's lattice, boundaries, precision or engine differ from the context's");
   if (hd.solid && !c->p.solids) return fail(PFL_ERR_STATE, "the saved state has solid cells; create the context with solids = 1");
   if (!hd.solid && c->solid) return fail(PFL_ERR_STATE, "the context has solid cells and the saved state none");
-  unsigned long long want[5];
+  unsigned long long want[NSAVED];
   const bool was_solid = c->solid;
   c->solid = hd.solid != 0;
   saved_sections(c, want);
   c->solid = was_solid;
   size_t total = sizeof hd;
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < NSAVED; ++k) {
     if (hd.bytes[k] != want[k]) return fail(PFL_ERR_ARG, "the saved state's section sizes do not match");
     total += (size_t)want[k];
   }
@@ -872,9 +945,9 @@ pfl_status pfl_load(pfl_ctx* c, const void* buf, size_t bytes) {
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   // the saved phi buffers keep their roles: buffer `cur` holds phi^t
   const char* from = (const char*)buf + sizeof hd;
-  size_t so[5];
+  size_t so[NSAVED];
   saved_offsets(c, so);
-  for (int k = 0; k < 5; ++k) {
+  for (int k = 0; k < NSAVED; ++k) {
     if (want[k]) CUDA_TRY(cudaMemcpyAsync(c->ws + so[k], from, want[k], cudaMemcpyDefault, c->stream));
     from += want[k];
   }
@@ -904,22 +977,50 @@ pfl_status pfl_set_solid(pfl_ctx* c, const unsigned char* mask) {
   return PFL_OK;
 }
 
+// Largest flow speed of the current state (FP64, on the device into *res).
+static pfl_status queue_speed(pfl_ctx* c, double* res) {
+  double* part = (double*)(c->ws + c->L.red) + DIAG_BLOCKS * 9 + 16;
+  DISPATCH(c, ensure_phi, c);
+  DISPATCH(c, launch_umax, c, part, res);
+  CUDA_TRY(cudaGetLastError());
+  return PFL_OK;
+}
+
 pfl_status pfl_diag(pfl_ctx* c, double out[8], long long* nonfinite) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
   CUDA_TRY(cudaSetDevice(c->device));
   double* part = (double*)(c->ws + c->L.red);
   double* res = part + DIAG_BLOCKS * 9;
+  double* ures = part + DIAG_BLOCKS * 10 + 16;
   DISPATCH(c, ensure_phi, c);
   DISPATCH_PREC(c, launch_diag, c, part, res);
   CUDA_TRY(cudaGetLastError());
-  double host[9];
+  pfl_status st = queue_speed(c, ures);
+  if (st != PFL_OK) return st;
+  double host[9], umax = 0.0;
   CUDA_TRY(cudaMemcpyAsync(host, res, sizeof(host), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaMemcpyAsync(&umax, ures, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (out)
     for (int k = 0; k < 8; ++k) out[k] = host[k];
   long long nf = (long long)host[8];
   if (nonfinite) *nonfinite = nf;
   if (nf > 0) return fail(PFL_ERR_UNSTABLE, std::to_string(nf) + " cells hold a non-finite phi");
+  if (!(umax <= PFL_SPEED_LIMIT))
+    return fail(PFL_ERR_UNSTABLE, "flow speed |u| = " + std::to_string(umax) + " exceeds " +
+                                      std::to_string(PFL_SPEED_LIMIT) + " (lattice units)");
+  return PFL_OK;
+}
+
+pfl_status pfl_max_speed(pfl_ctx* c, double* umax) {
+  if (!c) return fail(PFL_ERR_ARG, "context is NULL");
+  if (!umax) return fail(PFL_ERR_ARG, "umax is NULL");
+  CUDA_TRY(cudaSetDevice(c->device));
+  double* ures = (double*)(c->ws + c->L.red) + DIAG_BLOCKS * 10 + 16;
+  pfl_status st = queue_speed(c, ures);
+  if (st != PFL_OK) return st;
+  CUDA_TRY(cudaMemcpyAsync(umax, ures, sizeof(double), cudaMemcpyDefault, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
   return PFL_OK;
 }
 
@@ -976,7 +1077,8 @@ long long pfl_time(const pfl_ctx* c) { return c ? c->t : -1; }
 // ----------------------------------------------------------------- adjoint --
 namespace {
 
-constexpr int ADJ_MAX_OBS = 8;
+constexpr int ADJ_MAX_OBS = 1 << 20;  // observations per call (distinct steps in [0, n_steps])
+constexpr int ADJ_STAGE = 8;          // device slots through which host weight fields are staged
 constexpr int DOT_BLOCKS = 1024;
 
 struct AdjLayout {
@@ -1014,7 +1116,7 @@ AdjLayout adj_layout(const pfl_ctx* c, int n) {
   A.acc = off;
   off = align256(off + N * R);
   A.W = off;
-  off = align256(off + (size_t)ADJ_MAX_OBS * N * sizeof(double));
+  off = align256(off + (size_t)ADJ_STAGE * N * sizeof(double));
   A.part = off;
   const size_t nb = (N + ADJ_THREADS - 1) / ADJ_THREADS;
   off = align256(off + (3 * nb + DOT_BLOCKS) * sizeof(double));
@@ -1173,18 +1275,38 @@ pfl_status run_adjoint_zm(pfl_ctx* c, int n, const ObsAt& obs_at, char* aws, con
   return PFL_OK;
 }
 
+// The weight field of the observation at step k (relative to the adjoint's
+// first step), as device memory, or NULL: a device field as given; a host
+// field copied, when asked for, into the next of ADJ_STAGE staging slots of
+// the adjoint workspace (the copy is ordered on the stream before the kernel
+// that reads the slot, and after the kernels that read its previous content).
+struct ObsTable {
+  std::vector<int> at;                 // step -> observation index, or -1
+  const double* const* w;
+  std::vector<char> dev;               // the field is device memory
+  double* stage;                       // ADJ_STAGE slots of N doubles
+  size_t N;
+  cudaStream_t stream;
+  mutable int next = 0;
+  mutable cudaError_t err = cudaSuccess;
+  const double* operator()(int k) const {
+    if (k < 0 || k >= (int)at.size() || at[(size_t)k] < 0) return nullptr;
+    const int o = at[(size_t)k];
+    if (dev[(size_t)o]) return w[o];
+    double* slot = stage + (size_t)(next++ % ADJ_STAGE) * N;
+    cudaError_t e = cudaMemcpyAsync(slot, w[o], N * sizeof(double), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) err = e;
+    return slot;
+  }
+};
+
 template <int PREC, int QH>
-pfl_status run_adjoint(pfl_ctx* c, int n, int nobs, const int* obs_steps, const double* const* Wd, char* aws,
-                       const AdjLayout& A, double* J, double grad[3]) {
+pfl_status run_adjoint(pfl_ctx* c, int n, const ObsTable& obs_at, char* aws, const AdjLayout& A, double* J,
+                       double grad[3]) {
   typedef typename Store<PREC>::R R;
   double* res = (double*)(aws + A.res);  // [0] J, [1..3] dJ/d(M, xi, sigma)
   double* part = (double*)(aws + A.part);
   CUDA_TRY(cudaMemsetAsync(res, 0, 8 * sizeof(double), c->stream));
-  auto obs_at = [&](int k) -> const double* {
-    for (int o = 0; o < nobs; ++o)
-      if (obs_steps[o] == k) return Wd[o];
-    return nullptr;
-  };
   if (c->zm) return run_adjoint_zm<PREC, QH>(c, n, obs_at, aws, A, J, grad);
   // several weights at one step are summed into the first by the caller side; here one per step
   const long long t0 = c->t;
@@ -1290,22 +1412,28 @@ pfl_status pfl_adjoint(pfl_ctx* c, int n_steps, int n_obs, const int* obs_steps,
   CUDA_TRY(cudaSetDevice(c->device));
   char* aws = (char*)adj_workspace;
   const size_t N = (size_t)c->geo.N;
-  const double* Wd[ADJ_MAX_OBS];
+  ObsTable obs;
+  obs.at.assign((size_t)n_steps + 1, -1);
+  obs.dev.resize((size_t)n_obs);
   for (int o = 0; o < n_obs; ++o) {
-    double* dst = (double*)(aws + A.W) + (size_t)o * N;
-    CUDA_TRY(cudaMemcpyAsync(dst, obs_weights[o], N * sizeof(double), cudaMemcpyDefault, c->stream));
-    Wd[o] = dst;
+    obs.at[(size_t)obs_steps[o]] = o;
+    obs.dev[(size_t)o] = is_device_ptr(obs_weights[o]) ? 1 : 0;
   }
-  switch (c->p.precision) {
-    case PFL_FP64:
-      if (c->qh == 27) return run_adjoint<0, 27>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
-      if (c->qh == 9) return run_adjoint<0, 9>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
-      return run_adjoint<0, 15>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
-    default:
-      if (c->qh == 27) return run_adjoint<1, 27>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
-      if (c->qh == 9) return run_adjoint<1, 9>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
-      return run_adjoint<1, 15>(c, n_steps, n_obs, obs_steps, Wd, aws, A, J, grad);
-  }
+  obs.w = obs_weights;
+  obs.stage = (double*)(aws + A.W);
+  obs.N = N;
+  obs.stream = c->stream;
+  pfl_status st;
+  if (c->p.precision == PFL_FP64)
+    st = c->qh == 27 ? run_adjoint<0, 27>(c, n_steps, obs, aws, A, J, grad)
+         : c->qh == 9 ? run_adjoint<0, 9>(c, n_steps, obs, aws, A, J, grad)
+                      : run_adjoint<0, 15>(c, n_steps, obs, aws, A, J, grad);
+  else
+    st = c->qh == 27 ? run_adjoint<1, 27>(c, n_steps, obs, aws, A, J, grad)
+         : c->qh == 9 ? run_adjoint<1, 9>(c, n_steps, obs, aws, A, J, grad)
+                      : run_adjoint<1, 15>(c, n_steps, obs, aws, A, J, grad);
+  if (st == PFL_OK && obs.err != cudaSuccess) return cuda_fail(obs.err, "observation weights to the device");
+  return st;
 }
 
 void pfl_destroy(pfl_ctx* c) {

@@ -22,6 +22,8 @@
 // crosses a no-slip face; offsets of a direction are sums of these, fixed at
 // compile time inside the unrolled loops.
 #pragma once
+#include <type_traits>
+
 #include "kernels.cuh"
 
 #ifndef PFL_STEP_THREADS
@@ -58,6 +60,12 @@
 // the wait) lost 6-13 %: waiting blocks then hold the SMs' block slots.
 #ifndef PFL_ZM_PDL
 #define PFL_ZM_PDL 1
+#endif
+// Interior form of the fused step (1; 0 = the general form everywhere): blocks
+// clear of the lattice's faces by two cells take neighbour offsets without
+// wall, wrap or solid tests.
+#ifndef PFL_ZM_INTERIOR
+#define PFL_ZM_INTERIOR 1
 #endif
 
 namespace pfl {
@@ -175,6 +183,18 @@ struct CellOff {
   }
 };
 
+// Offsets of a cell whose neighbours two cells deep all lie inside the lattice
+// (no face, no wrap, no solid): every link is valid and the offset of
+// direction c is cx + cy sy + cz sz.  The fused step takes this form for blocks
+// whose tile, ring and z range stay clear of the lattice's faces.
+struct CellOffI {
+  int sy, sz;
+  static constexpr unsigned blk = 0;
+  __device__ __forceinline__ int off(int cx, int cy, int cz) const { return cx + cy * sy + cz * sz; }
+  __device__ __forceinline__ constexpr bool valid(int, int, int) const { return true; }
+  __device__ __forceinline__ int soff(int cx, int cy, int cz) const { return off(cx, cy, cz); }
+};
+
 // Raw stored value as the arithmetic type (FP16: the stored number, unscaled).
 template <int PREC>
 __device__ __forceinline__ typename Store<PREC>::R raw(typename Store<PREC>::S v) {
@@ -260,9 +280,9 @@ __device__ __forceinline__ void cell_off(const Geo32& geo, unsigned c, CellOff& 
 // Load the pair (i: direction c, oi: direction -c) arriving at `cell`.
 // a, b: raw stored values; fa, fb: the cells that wrote them.  Indices are
 // 32-bit (unsigned wrap-around arithmetic; the final index is in range).
-template <int PREC, int READ_ODD>
+template <int PREC, int READ_ODD, class Off>
 __device__ __forceinline__ void load_pair(const typename Store<PREC>::S* __restrict__ f, unsigned N, unsigned cell,
-                                          const CellOff& o, int i, int oi, int cx, int cy, int cz,
+                                          const Off& o, int i, int oi, int cx, int cy, int cz,
                                           typename Store<PREC>::R& a, typename Store<PREC>::R& b, unsigned& fa,
                                           unsigned& fb) {
   const bool vmc = o.valid(-cx, -cy, -cz), vc = o.valid(cx, cy, cz);
@@ -279,9 +299,9 @@ __device__ __forceinline__ void load_pair(const typename Store<PREC>::S* __restr
 }
 
 // Store the post-collision pair (A: direction c, B: direction -c) of `cell`.
-template <int PREC, int ODD>
+template <int PREC, int ODD, class Off>
 __device__ __forceinline__ void store_pair(typename Store<PREC>::S* __restrict__ f, unsigned N, unsigned cell,
-                                           const CellOff& o, int i, int oi, int cx, int cy, int cz,
+                                           const Off& o, int i, int oi, int cx, int cy, int cz,
                                            typename Store<PREC>::R A, typename Store<PREC>::R B, Dither& d) {
   typename Store<PREC>::S a, b;
   if constexpr (PREC == 2 && PFL_FP16S_HWSR) {
@@ -312,19 +332,36 @@ struct GlobalPhi {
   }
 };
 
+// p* shift of the cell that wrote a g population (FP16S): the population
+// arriving from offset (dx, dy, dz) -- the opposite of its velocity -- was
+// written by `writer` (the neighbour, or the cell itself after a bounce-back,
+// valid = false).  GlobalShift reads the writer's shift from the per-cell
+// array; the fused step reads it from a shared-memory ring (SmemShift).
+struct GlobalShift {
+  const __half* __restrict__ p;
+  __device__ __forceinline__ float operator()(unsigned writer, int dx, int dy, int dz, bool valid) const {
+    return __half2float(__ldg(p + writer));
+  }
+};
+struct NoShift {
+  __device__ __forceinline__ float operator()(unsigned, int, int, int, bool) const { return 0.0f; }
+};
+
 // The collide-stream update of one cell, shared by every stream-collide
 // kernel: populations are read from (hin, gin) in the layout READ_ODD and
 // written to (hout, gout) in the layout WRITE_ODD (the same arrays and parity
 // for the in-place AA step; a second array pair and push streaming for the
 // two-array step).  phi_at(c) returns phi^t at the stencil neighbour c.
-template <int PREC, int QH, int READ_ODD, int WRITE_ODD, class PhiAt, int HM = 0>
-__device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, const CellOff& o,
+template <int PREC, int QH, int READ_ODD, int WRITE_ODD, class PhiAt, int HM = 0, class PShift = NoShift,
+          class Off = CellOff>
+__device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, const Off& o,
                                              const typename Store<PREC>::S* hin,
                                              const typename Store<PREC>::S* gin, typename Store<PREC>::S* hout,
                                              typename Store<PREC>::S* gout, const PhiAt& phi_at,
                                              const typename Store<PREC>::PhiT* __restrict__ shift,
                                              unsigned cell, unsigned seed,
-                                             const typename Store<PREC>::R* hmom = nullptr, int hstride = 0) {
+                                             const typename Store<PREC>::R* hmom = nullptr, int hstride = 0,
+                                             const PShift& pshift = PShift(), __half* __restrict__ pg_out = nullptr) {
   typedef typename Store<PREC>::R R;
   constexpr bool F16 = PREC == 2;
   constexpr int QG = qg_of<QH>();  // D2Q9 with the 2-D phase field, else D3Q27
@@ -345,18 +382,18 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     if (cx) gx += cx > 0 ? d : -d;
     if (cy) gy += cy > 0 ? d : -d;
     if (cz) gz += cz > 0 ? d : -d;
-    lap += w * ((a + b) - (R)2 * pc);
+    lap += w * ((a - pc) + (b - pc));  // differences first: exact for nearby values
   }
   gx *= (R)3;
   gy *= (R)3;
   gz *= (R)3;
   lap *= (R)6;
 
-  // ---- g moments (FP16: g_i = w_i s / KG)
+  // ---- g moments (FP16: g_i = w_i (s / KG + P_writer))
   R pst, jx = 0, jy = 0, jz = 0, pxx = 0, pyy = 0, pzz = 0, pxy = 0, pyz = 0, pxz = 0;
   {
     const R rest = raw<PREC>(gin[(unsigned)GR * N + cell]);
-    pst = F16 ? rest * (R)(lq_w<QG>(GR) / KG16) : rest;
+    pst = F16 ? (rest * (R)(1.0 / KG16) + (R)pshift(cell, 0, 0, 0, false)) * (R)lq_w<QG>(GR) : rest;
   }
 #pragma unroll
   for (int i = 0; i < GR; ++i) {
@@ -366,8 +403,12 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     load_pair<PREC, READ_ODD>(gin, N, cell, o, i, QG - 1 - i, cx, cy, cz, a, b, fa, fb);
     R S = a + b, D = a - b;
     if (F16) {
-      S *= (R)(lq_w<QG>(i) / KG16);
-      D *= (R)(lq_w<QG>(i) / KG16);
+      // a arrives from x - c, b from x + c
+      const R pa = (R)pshift(fa, -cx, -cy, -cz, o.valid(-cx, -cy, -cz));
+      const R pb = (R)pshift(fb, cx, cy, cz, o.valid(cx, cy, cz));
+      const R w = (R)lq_w<QG>(i);
+      S = w * (S * (R)(1.0 / KG16) + (pa + pb));
+      D = w * (D * (R)(1.0 / KG16) + (pa - pb));
     }
     pst += S;
     if (cx) jx += cx > 0 ? D : -D;
@@ -404,6 +445,13 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     Fz += cm * (nxz * gx + nyz * gy + nzz * gz);
   }
   const R ux = jx + Fx * inv2rho, uy = jy + Fy * inv2rho, uz = jz + Fz * inv2rho;
+  // FP16S: every g this cell writes is stored against P = fp16(p*) of the cell
+  R pw = 0;
+  if constexpr (F16) {
+    const __half q = __float2half_rn(pst);
+    pg_out[cell] = q;
+    pw = __half2float(q);
+  }
 
   // ---- g post-collision coefficients and pair stores
   {
@@ -412,7 +460,7 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     const R dxx = pxx - p3 - ux * ux, dyy = pyy - p3 - uy * uy;
     const R dzz = QG == 9 ? (R)0 : pzz - p3 - uz * uz;  // 2-D: the trace runs over x and y
     const R K = F16 ? (R)KG16 : (R)1;
-    const R al = K * (pst - (R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
+    const R al = K * ((pst - pw) - (R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
     const R fr = (R)1.5 / rho;
     const R bx = K * ((R)3 * ux + fr * Fx), by = K * ((R)3 * uy + fr * Fy), bz = K * ((R)3 * uz + fr * Fz);
     const R Gxx = K * ((R)4.5 * ux * ux + a2 * dxx), Gyy = K * ((R)4.5 * uy * uy + a2 * dyy),
@@ -532,26 +580,31 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
 }
 
 // In-place AA update of one cell with the stencil read from the phi buffer.
+// pg_in / pg_out: the p* shifts of the stored g (FP16S; NULL otherwise),
+// read for the populations loaded and written for those stored.
 template <int PREC, int QH, int ODD>
 __device__ __forceinline__ void step_cell(const Geo32& geo, const Phys& ph, typename Store<PREC>::S* __restrict__ h,
                                           typename Store<PREC>::S* __restrict__ g,
                                           const typename Store<PREC>::PhiT* __restrict__ phi,
                                           const typename Store<PREC>::PhiT* __restrict__ shift, unsigned cell,
-                                          unsigned seed) {
+                                          unsigned seed, const __half* __restrict__ pg_in = nullptr,
+                                          __half* __restrict__ pg_out = nullptr) {
   CellOff o;
   cell_off(geo, cell, o);
   GlobalPhi<PREC> at{phi, &o, cell};
-  collide_cell<PREC, QH, ODD, ODD>(geo, ph, o, h, g, h, g, at, shift, cell, seed);
+  collide_cell<PREC, QH, ODD, ODD, GlobalPhi<PREC>, 0, GlobalShift>(geo, ph, o, h, g, h, g, at, shift, cell, seed,
+                                                                    nullptr, 0, GlobalShift{pg_in}, pg_out);
 }
 
 template <int PREC, int QH, int ODD>
 __global__ void __launch_bounds__(PFL_STEP_THREADS, PFL_STEP_MINB)
     k_step_mrt(Geo32 geo, Phys ph, typename Store<PREC>::S* __restrict__ h, typename Store<PREC>::S* __restrict__ g,
                const typename Store<PREC>::PhiT* __restrict__ phi,
-               const typename Store<PREC>::PhiT* __restrict__ shift, unsigned seed) {
+               const typename Store<PREC>::PhiT* __restrict__ shift, unsigned seed,
+               const __half* __restrict__ pg_in = nullptr, __half* __restrict__ pg_out = nullptr) {
   const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= geo.N) return;
-  step_cell<PREC, QH, ODD>(geo, ph, h, g, phi, shift, cell, seed);
+  step_cell<PREC, QH, ODD>(geo, ph, h, g, phi, shift, cell, seed, pg_in, pg_out);
 }
 
 // phi of one cell from the stored h (READ_ODD after an even step).
@@ -634,6 +687,18 @@ struct SmemPhi {
   }
 };
 
+// p* shift of the writer of a g population from the ring of P planes z - 1,
+// z, z + 1 of the fused step (tile plus a one-cell ring, like SmemPhi): the
+// neighbour at (dx, dy, dz), or the cell itself after a bounce-back.
+template <int FLAT = 0>
+struct SmemShift {
+  const float* plane[3];
+  int i0;
+  __device__ __forceinline__ float operator()(unsigned, int dx, int dy, int dz, bool valid) const {
+    return valid ? plane[FLAT ? 1 : 1 + dz][i0 + dy * (ZM_TX + 2) + dx] : plane[1][i0];
+  }
+};
+
 __device__ __forceinline__ void prefetch_l1(const void* p) {
   asm volatile("{\n\t.reg .u64 ga;\n\tcvta.to.global.u64 ga, %0;\n\tprefetch.global.L1 [ga];\n\t}" ::"l"(p));
 }
@@ -643,22 +708,15 @@ __device__ __forceinline__ int wrap_or_clamp(int v, int n, int wall) {
   return v < 0 ? v + n : (v >= n ? v - n : v);
 }
 
-// The 10 h moments (phi, sum c h, sum c c h) of cell (x, y, z) of the current
-// pair (normal layout), accumulated by pairs in the same order as the
-// collision does, so moms[0] equals its phi bitwise.
-template <int PREC, int QH>
-__device__ __forceinline__ void h_moments_xyz(const Geo32& geo, const typename Store<PREC>::S* __restrict__ h,
-                                              const typename Store<PREC>::PhiT* __restrict__ shift, unsigned x,
-                                              unsigned y, unsigned z, typename Store<PREC>::R m[10],
-                                              unsigned blk = 0) {
+// The 10 h moments (phi, sum c h, sum c c h) of `cell` of the current pair
+// (normal layout, neighbour offsets o), accumulated by pairs in the same order
+// as the collision does, so moms[0] equals its phi bitwise.
+template <int PREC, int QH, class Off>
+__device__ __forceinline__ void h_moments_at(const Geo32& geo, const typename Store<PREC>::S* __restrict__ h,
+                                             const typename Store<PREC>::PhiT* __restrict__ shift, unsigned cell,
+                                             const Off& o, typename Store<PREC>::R m[10]) {
   typedef typename Store<PREC>::R R;
   constexpr bool F16 = PREC == 2;
-  CellOff o;
-  o.X = axis_off(x, geo.nx, 1, geo.wall[0]);
-  o.Y = axis_off(y, geo.ny, (int)geo.nx, geo.wall[1]);
-  o.Z = axis_off(z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
-  o.blk = blk;  // a bounced population was written by this cell
-  const unsigned cell = x + geo.nx * (y + geo.ny * z);
   const unsigned N = geo.N;
   R phl, hjx = 0, hjy = 0, hjz = 0, hxx = 0, hyy = 0, hzz = 0, hxy = 0, hyz = 0, hxz = 0;
   {
@@ -704,22 +762,13 @@ __device__ __forceinline__ void h_moments_xyz(const Geo32& geo, const typename S
   m[9] = hxz;
 }
 
-// phi at cell (x, y, z) of the current pair (normal layout), same sum as the
-// phi pass.
-template <int PREC, int QH>
-__device__ __forceinline__ typename Store<PREC>::R phi_at_xyz(const Geo32& geo,
-                                                              const typename Store<PREC>::S* __restrict__ h,
-                                                              const typename Store<PREC>::PhiT* __restrict__ shift,
-                                                              unsigned x, unsigned y, unsigned z,
-                                                              unsigned blk = 0) {
+// phi of `cell` of the current pair (normal layout), same sum as the phi pass.
+template <int PREC, int QH, class Off>
+__device__ __forceinline__ typename Store<PREC>::R phi_at(const Geo32& geo, const typename Store<PREC>::S* __restrict__ h,
+                                                          const typename Store<PREC>::PhiT* __restrict__ shift,
+                                                          unsigned cell, const Off& o) {
   typedef typename Store<PREC>::R R;
   constexpr bool F16 = PREC == 2;
-  CellOff o;
-  o.X = axis_off(x, geo.nx, 1, geo.wall[0]);
-  o.Y = axis_off(y, geo.ny, (int)geo.nx, geo.wall[1]);
-  o.Z = axis_off(z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
-  o.blk = blk;  // a bounced population was written by this cell
-  const unsigned cell = x + geo.nx * (y + geo.ny * z);
   R s = F16 ? (raw<PREC>(h[(unsigned)hq_rest<QH>() * geo.N + cell]) * (R)(1.0 / KH16) + (R)__ldg(shift + cell)) * (R)hq_w<QH>(hq_rest<QH>())
             : raw<PREC>(h[(unsigned)hq_rest<QH>() * geo.N + cell]);
 #pragma unroll
@@ -733,6 +782,48 @@ __device__ __forceinline__ typename Store<PREC>::R phi_at_xyz(const Geo32& geo,
       s += a + b;
   }
   return s;
+}
+
+// Offsets of cell (x, y, z): the general form, or (INT) the interior one.
+template <int INT>
+struct OffOf;
+template <>
+struct OffOf<0> {
+  typedef CellOff T;
+  static __device__ __forceinline__ CellOff at(const Geo32& geo, unsigned x, unsigned y, unsigned z, unsigned blk) {
+    CellOff o;
+    o.X = axis_off(x, geo.nx, 1, geo.wall[0]);
+    o.Y = axis_off(y, geo.ny, (int)geo.nx, geo.wall[1]);
+    o.Z = axis_off(z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
+    o.blk = blk;  // a bounced population was written by this cell
+    return o;
+  }
+};
+template <>
+struct OffOf<1> {
+  typedef CellOffI T;
+  static __device__ __forceinline__ CellOffI at(const Geo32& geo, unsigned, unsigned, unsigned, unsigned) {
+    return CellOffI{(int)geo.nx, geo.nz == 1 ? 0 : (int)(geo.nx * geo.ny)};
+  }
+};
+
+template <int PREC, int QH, int INT = 0>
+__device__ __forceinline__ void h_moments_xyz(const Geo32& geo, const typename Store<PREC>::S* __restrict__ h,
+                                              const typename Store<PREC>::PhiT* __restrict__ shift, unsigned x,
+                                              unsigned y, unsigned z, typename Store<PREC>::R m[10],
+                                              unsigned blk = 0) {
+  const unsigned cell = x + geo.nx * (y + geo.ny * z);
+  h_moments_at<PREC, QH>(geo, h, shift, cell, OffOf<INT>::at(geo, x, y, z, blk), m);
+}
+
+template <int PREC, int QH, int INT = 0>
+__device__ __forceinline__ typename Store<PREC>::R phi_at_xyz(const Geo32& geo,
+                                                              const typename Store<PREC>::S* __restrict__ h,
+                                                              const typename Store<PREC>::PhiT* __restrict__ shift,
+                                                              unsigned x, unsigned y, unsigned z,
+                                                              unsigned blk = 0) {
+  const unsigned cell = x + geo.nx * (y + geo.ny * z);
+  return phi_at<PREC, QH>(geo, h, shift, cell, OffOf<INT>::at(geo, x, y, z, blk));
 }
 
 // position r in [0, 2 (W + H) - 4) of the frame of a W x H plane -> (i, j)
@@ -758,17 +849,19 @@ __device__ __forceinline__ void frame_pos(int r, int W, int H, int& i, int& j) {
 // tclock (launches replayed from a CUDA graph): the FP16 rounding seed comes
 // from the step count *tclock + tofs in device memory instead of `seed`, the
 // same function of the step count as the host's.
-template <int PREC, int QH, int FLAT, int SOLID = 0>
-__global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_FP64 : PFL_ZM_MINB) * ZM_TY / zm_ty(FLAT))
-    k_step_zm(Geo32 geo, Phys ph, const typename Store<PREC>::S* __restrict__ hA,
-              const typename Store<PREC>::S* __restrict__ gA, typename Store<PREC>::S* __restrict__ hB,
-              typename Store<PREC>::S* __restrict__ gB, const typename Store<PREC>::PhiT* __restrict__ phi_shift,
-              typename Store<PREC>::PhiT* __restrict__ phi_out, int zc, unsigned seed,
-              const unsigned* __restrict__ links = nullptr, const unsigned long long* tclock = nullptr,
-              int tofs = 0) {
+// One tile of the fused step: the xy tile (bx, by) of ZM_TX x TY columns and
+// the z chunk bz of zc planes (the grid of k_step_zm, or an entry of the
+// batched engine's work list).  The caller has waited for the previous step.
+template <int PREC, int QH, int TY, int FLAT, int SOLID>
+__device__ __forceinline__ void zm_tile(const Geo32& geo, const Phys& ph, const typename Store<PREC>::S* __restrict__ hA,
+                                        const typename Store<PREC>::S* __restrict__ gA,
+                                        typename Store<PREC>::S* __restrict__ hB, typename Store<PREC>::S* __restrict__ gB,
+                                        const typename Store<PREC>::PhiT* __restrict__ phi_shift,
+                                        typename Store<PREC>::PhiT* __restrict__ phi_out, int zc, unsigned seed,
+                                        const unsigned* __restrict__ links, const __half* __restrict__ pg_in,
+                                        __half* __restrict__ pg_out, int bx, int by, int bz) {
   typedef typename Store<PREC>::PhiT PhiT;
   typedef typename Store<PREC>::R R;
-  constexpr int TY = zm_ty(FLAT);
   constexpr int NT = ZM_TX * TY;
   constexpr int PW = ZM_TX + 2, PH = TY + 2, PS = PW * PH;
   constexpr int NRING = 2 * (PW + PH) - 4;
@@ -781,9 +874,11 @@ __global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_
   constexpr int NS = FLAT ? 1 : (sizeof(R) == 8 ? 3 : 4);
   __shared__ PhiT ring[NS][PS];
   __shared__ R hmom[FLAT ? 1 : 2][10 * NT];  // h moments of the tile's own cells
+  constexpr bool F16 = PREC == 2;
+  __shared__ float pring[F16 ? NS : 1][F16 ? PS : 1];  // FP16S: p* shifts of the stored g, ring like phi
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZM_TX + tx;
-  const int x0 = blockIdx.x * ZM_TX, y0 = blockIdx.y * TY;
-  const int z0 = blockIdx.z * zc;
+  const int x0 = bx * ZM_TX, y0 = by * TY;
+  const int z0 = bz * zc;
   const int z1 = min(z0 + zc, (int)geo.nz);
   const int x = x0 + tx, y = y0 + ty;
   const bool active = x < (int)geo.nx && y < (int)geo.ny;
@@ -793,9 +888,6 @@ __global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_
   if (tid < NRING) frame_pos(tid, PW, PH, ri, rj);
   const unsigned rxq = (unsigned)wrap_or_clamp(x0 - 1 + ri, (int)geo.nx, geo.wall[0]);
   const unsigned ryq = (unsigned)wrap_or_clamp(y0 - 1 + rj, (int)geo.ny, geo.wall[1]);
-  // everything above is index arithmetic; global memory only from here on
-  if (PFL_ZM_PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
-  if (PREC == 2 && tclock) seed = step_seed_of(*tclock + (unsigned long long)tofs);
 
   // L1 prefetch of the g populations plane zp's collision will read
   auto prefetch_plane = [&](int zp) {
@@ -806,18 +898,26 @@ __global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_
     for (int i = 0; i < QG; ++i) prefetch_l1(gA + (unsigned)i * geo.N + c);
   };
 
+  // The march over the block's z planes, in the general form (INT = 0) or, for
+  // blocks whose tile, ring and planes z0 - 2 .. z1 + 1 lie clear of the
+  // lattice's faces, the interior one (INT = 1: every link valid, neighbour
+  // offsets without wall or wrap tests).
+  auto march = [&](auto int_tag) {
+  constexpr int INT = decltype(int_tag)::value;
   // phi of plane zp over the tile (with the h moments of the own cells) and its ring
   auto fill = [&](int zp, int slot, int mslot) {
     const unsigned zq = (unsigned)wrap_or_clamp(zp, (int)geo.nz, geo.wall[2]);
     R m[10];
     const unsigned bt = SOLID ? __ldg(links + xq + geo.nx * (yq + geo.ny * zq)) : 0u;
-    h_moments_xyz<PREC, QH>(geo, hA, phi_shift, xq, yq, zq, m, bt);
+    h_moments_xyz<PREC, QH, INT>(geo, hA, phi_shift, xq, yq, zq, m, bt);
     ring[slot][(ty + 1) * PW + tx + 1] = (PhiT)m[0];
+    if constexpr (F16) pring[slot][(ty + 1) * PW + tx + 1] = ld_pshift(pg_in, xq + geo.nx * (yq + geo.ny * zq));
 #pragma unroll
     for (int k = 0; k < 10; ++k) hmom[mslot][k * NT + tid] = m[k];
     if (tid < NRING) {
       const unsigned br = SOLID ? __ldg(links + rxq + geo.nx * (ryq + geo.ny * zq)) : 0u;
-      ring[slot][rj * PW + ri] = (PhiT)phi_at_xyz<PREC, QH>(geo, hA, phi_shift, rxq, ryq, zq, br);
+      ring[slot][rj * PW + ri] = (PhiT)phi_at_xyz<PREC, QH, INT>(geo, hA, phi_shift, rxq, ryq, zq, br);
+      if constexpr (F16) pring[slot][rj * PW + ri] = ld_pshift(pg_in, rxq + geo.nx * (ryq + geo.ny * zq));
     }
   };
 
@@ -838,11 +938,7 @@ __global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_
     if (SOLID && active && (blk & SOLID_SELF)) {
       phi_out[cell] = (PhiT)0;  // solid cells are not updated; their populations stay zero
     } else if (active) {
-      CellOff o;
-      o.blk = blk;
-      o.X = axis_off((unsigned)x, geo.nx, 1, geo.wall[0]);
-      o.Y = axis_off((unsigned)y, geo.ny, (int)geo.nx, geo.wall[1]);
-      o.Z = axis_off((unsigned)z, geo.nz, (int)(geo.nx * geo.ny), geo.wall[2]);
+      const typename OffOf<INT>::T o = OffOf<INT>::at(geo, (unsigned)x, (unsigned)y, (unsigned)z, blk);
       SmemPhi<PREC, FLAT> at;
       if (FLAT) {
         at.plane[0] = at.plane[1] = at.plane[2] = ring[0];
@@ -854,12 +950,46 @@ __global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_
       // with one z plane the z neighbours are the plane itself (periodic or mirrored)
       at.i0 = (ty + 1) * PW + (tx + 1);
       at.blk = blk;
+      SmemShift<FLAT> psh;
+      if constexpr (F16) {
+        if (FLAT) {
+          psh.plane[0] = psh.plane[1] = psh.plane[2] = pring[0];
+        } else {
+          psh.plane[0] = pring[(b - 1) % NS];
+          psh.plane[1] = pring[b % NS];
+          psh.plane[2] = pring[(b + 1) % NS];
+        }
+        psh.i0 = at.i0;
+      }
       phi_out[cell] = (PhiT)at(0, 0, 0);
-      collide_cell<PREC, QH, 0, 1, SmemPhi<PREC, FLAT>, 1>(geo, ph, o, hA, gA, hB, gB, at, phi_shift, cell, seed,
-                                                 &hmom[FLAT ? 0 : ((z - z0) & 1)][tid], NT);
+      collide_cell<PREC, QH, 0, 1, SmemPhi<PREC, FLAT>, 1, SmemShift<FLAT>, typename OffOf<INT>::T>(
+          geo, ph, o, hA, gA, hB, gB, at, phi_shift, cell, seed, &hmom[FLAT ? 0 : ((z - z0) & 1)][tid], NT, psh,
+          pg_out);
     }
     if (NS == 3) __syncthreads();
   }
+  };
+  const bool interior = !SOLID && PFL_ZM_INTERIOR && x0 >= 2 && x0 + ZM_TX + 1 < (int)geo.nx && y0 >= 2 &&
+                        y0 + TY + 1 < (int)geo.ny && (FLAT || (z0 >= 2 && z1 + 1 < (int)geo.nz));
+  if (interior)
+    march(std::integral_constant<int, 1>());
+  else
+    march(std::integral_constant<int, 0>());
+}
+
+template <int PREC, int QH, int FLAT, int SOLID = 0>
+__global__ void __launch_bounds__(ZM_TX * zm_ty(FLAT), (PREC == 0 ? PFL_ZM_MINB_FP64 : PFL_ZM_MINB) * ZM_TY / zm_ty(FLAT))
+    k_step_zm(Geo32 geo, Phys ph, const typename Store<PREC>::S* __restrict__ hA,
+              const typename Store<PREC>::S* __restrict__ gA, typename Store<PREC>::S* __restrict__ hB,
+              typename Store<PREC>::S* __restrict__ gB, const typename Store<PREC>::PhiT* __restrict__ phi_shift,
+              typename Store<PREC>::PhiT* __restrict__ phi_out, int zc, unsigned seed,
+              const unsigned* __restrict__ links = nullptr, const unsigned long long* tclock = nullptr,
+              int tofs = 0, const __half* __restrict__ pg_in = nullptr, __half* __restrict__ pg_out = nullptr) {
+  // global memory only after the previous step has completed
+  if (PFL_ZM_PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
+  if (PREC == 2 && tclock) seed = step_seed_of(*tclock + (unsigned long long)tofs);
+  zm_tile<PREC, QH, zm_ty(FLAT), FLAT, SOLID>(geo, ph, hA, gA, hB, gB, phi_shift, phi_out, zc, seed, links, pg_in,
+                                              pg_out, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace pfl

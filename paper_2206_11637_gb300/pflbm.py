@@ -26,6 +26,8 @@ def _params_struct(p, precision):
     s.engine = int(getattr(p, "engine", 0))
     s.h_lattice = int(getattr(p, "h_lattice", 15))
     s.solids = 1 if getattr(p, "solid", None) is not None else 0
+    s.hydrostatic = int(getattr(p, "hydrostatic", 0))
+    s.p_level = float(getattr(p, "p_level", 0.0))
     return s
 
 
@@ -226,6 +228,12 @@ class Simulation:
         if check:
             L.check(st)
         return out, int(nf.value)
+
+    def max_speed(self):
+        """Largest flow speed |u| over the fluid cells (pfl_max_speed)."""
+        v = ctypes.c_double(0.0)
+        L.check(self.lib.pfl_max_speed(self.ctx, ctypes.byref(v)))
+        return v.value
 
     def mass(self):
         return self.diag()[0][0]

@@ -36,6 +36,8 @@ class Params:
     engine: int = 0                       # 0 auto (fused two-array step), 1 in-place AA + phi pass
     h_lattice: int = 15                   # phase-field lattice: 15 (D3Q15), 27 (D3Q27) or 9 (D2Q9 h and g, 2-D)
     solid: object = None                  # optional solid-cell mask (nz, ny, nx), nonzero = solid
+    hydrostatic: int = 0                  # 1: with p0 None the library starts from the hydrostatic p*
+    p_level: float = 0.0                  # ... with zero pressure at this coordinate along the gravity axis
 
     @property
     def shape(self):

@@ -21,7 +21,7 @@ def test_exports_every_declared_symbol(lib):
     assert {"pfl_init", "pfl_step", "pfl_fields", "pfl_diag"} <= set(names)
     for n in names:
         assert hasattr(lib, n), n
-    assert lib.pfl_version() == 1
+    assert lib.pfl_version() == 2
 
 
 def test_workspace_size(lib):
@@ -99,3 +99,21 @@ def test_two_d_lattice_workspace(lib):
     b2 = pflbm.workspace_bytes(p, L.PFL_FP32)
     # two array pairs of (9 + 9) instead of (15 + 27) populations per cell
     assert b3 - b2 >= 2 * 24 * n * 4
+
+
+def test_hydrostatic_start_needs_gravity_along_one_axis(lib):
+    p, _, _, _ = W.rising_bubble(16, 24, 16, D=8.0)
+    p.hydrostatic, p.p_level = 1, 12.0
+    assert pflbm.workspace_bytes(p, L.PFL_FP32) > 0
+    p.gravity = (1e-6, -1e-6, 0.0)
+    assert pflbm.workspace_bytes(p, L.PFL_FP32) == 0
+    p.gravity = (0.0, 0.0, 0.0)
+    assert pflbm.workspace_bytes(p, L.PFL_FP32) == 0
+    p.gravity, p.p_level = (0.0, -1e-6, 0.0), float("nan")
+    assert pflbm.workspace_bytes(p, L.PFL_FP32) == 0
+    p.hydrostatic = 2
+    assert pflbm.workspace_bytes(p, L.PFL_FP32) == 0
+
+
+def test_null_context_speed(lib):
+    assert lib.pfl_max_speed(None, None) == L.PFL_ERR_ARG
