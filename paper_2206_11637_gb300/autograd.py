@@ -6,6 +6,12 @@ tension (0-d float64 tensors) and returns J = sum_o sum_x W_o(x) phi(x, t_o)
 as a 0-d tensor.  The forward call runs the library's adjoint directly (its
 forward sweep computes J and its reverse sweep the gradient in the same call,
 with sqrt(n) checkpointing); backward scales that gradient by the incoming one.
+
+``ObjectiveRollout.apply(M, xi, sigma, setup, objective)`` does the same for a
+nonlinear objective of phi at chosen steps (``objectives.WaveFrequency``: the
+fitted capillary-wave frequency): a forward run records phi at the
+objective's steps, the objective gives J and its seed fields dJ / dphi(t_o),
+and the library's adjoint of those seeds gives dJ / d(M, xi, sigma).
 """
 import copy
 
@@ -47,3 +53,32 @@ class PFLRollout(torch.autograd.Function):
 
 def rollout(M, xi, sigma, setup):
     return PFLRollout.apply(M, xi, sigma, setup)
+
+
+class ObjectiveRollout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, M, xi, sigma, setup, objective):
+        p = copy.copy(setup.params)
+        p.mobility, p.xi, p.sigma = float(M), float(xi), float(sigma)
+        sim = Simulation(p, setup.phi0, setup.u0, setup.p0, precision=setup.precision, device=setup.device)
+        for s in sorted(set(objective.steps)):
+            sim.step(s - sim.time)
+            objective.record(s, sim.phi())
+        sim.close()
+        J = objective.value()
+        seeds = objective.seeds((p.nz, p.ny, p.nx))
+        sim = Simulation(p, setup.phi0, setup.u0, setup.p0, precision=setup.precision, device=setup.device)
+        _, grad = sim.adjoint(max(objective.steps), seeds)
+        sim.close()
+        ctx.save_for_backward(torch.tensor(grad, dtype=torch.float64))
+        return torch.tensor(J, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, gout):
+        (g,) = ctx.saved_tensors
+        gout = gout.to(torch.float64)
+        return gout * g[0], gout * g[1], gout * g[2], None, None
+
+
+def objective_rollout(M, xi, sigma, setup, objective):
+    return ObjectiveRollout.apply(M, xi, sigma, setup, objective)

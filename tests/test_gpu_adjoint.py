@@ -159,3 +159,78 @@ def test_autograd_function():
     assert abs(J.item() - forward_J(p, phi0, u0, p0, n, obs)) < 1e-12
     got = np.array([M.grad.item(), xi.grad.item(), sg.grad.item()])
     assert np.allclose(got, 3.0 * g, rtol=1e-12, atol=0)
+
+
+def wave_frequency_case():
+    """Capillary wave L x L (depth L / 2, the paper's set-up), sigma 1e-3,
+    nu 0.002, rho ratio 1000, xi 4, M 0.02: the interface height of column
+    x = 0 every 40 steps from a quarter period to 1.5 periods; J = the
+    fitted angular frequency."""
+    import analytic as A
+    L = 32
+    p, phi0, u0, p0 = W.capillary_wave(L, ny=L, a0=1.0, xi=4.0, M=0.02, sigma=1e-3, nu=0.002)
+    k = 2 * np.pi / L
+    w0 = A.capillary_omega0(p.sigma, k, p.rho_h, p.rho_l)
+    T = 2 * np.pi / w0
+    steps = list(range(int(T / 4) // 40 * 40, int(1.5 * T), 40))
+    return p, phi0, u0, p0, steps, w0
+
+
+def frequency_forward(p, phi0, u0, p0, steps, w0, precision="fp64"):
+    from paper_2206_11637_gb300.pflbm import Simulation
+    obj = O.WaveFrequency(steps, w0)
+    s = Simulation(p, phi0, u0, p0, precision=precision)
+    for t in steps:
+        s.step(t - s.time)
+        obj.record(t, s.phi())
+    return obj
+
+
+def test_wave_frequency_gradient():
+    """Gradient of the capillary-wave frequency with respect to (M, xi,
+    sigma), the wave objective the adjoint is built for: seed fields from a
+    forward pass (the fit's implicit derivative times the derivative of the
+    interpolated interface height), one adjoint of those seeds.  Checked
+    against central differences of the whole pipeline (forward run, height,
+    fit) at 1e-3, against the oracle's exact derivative of the same seeded
+    functional at 1e-6, and d omega / d sigma against the dispersion relation
+    omega^2 proportional to sigma (within 10 %)."""
+    import oracle
+    p, phi0, u0, p0, steps, w0 = wave_frequency_case()
+    obj = frequency_forward(p, phi0, u0, p0, steps, w0)
+    omega = obj.value()
+    assert abs(omega / w0 - 1) < 0.15
+    seeds = obj.seeds(p.shape)
+    n = steps[-1]
+    _, g, _ = adjoint(p, phi0, u0, p0, n, seeds)
+    fd = []
+    for name in PARAMS:
+        v = getattr(p, name)
+        d = 1e-4 * v
+        pp, pm = copy.copy(p), copy.copy(p)
+        setattr(pp, name, v + d)
+        setattr(pm, name, v - d)
+        fd.append((frequency_forward(pp, phi0, u0, p0, steps, w0).value()
+                   - frequency_forward(pm, phi0, u0, p0, steps, w0).value()) / (2 * d))
+    fd = np.array(fd)
+    assert np.all(np.abs(g - fd) <= 1e-3 * np.abs(fd)), (g, fd)
+    for k, name in enumerate(PARAMS):
+        _, dJo = oracle.tangent(p, phi0, u0, p0, n, seeds, name)
+        assert abs(g[k] - dJo) <= 1e-6 * abs(dJo), (name, g[k], dJo)
+    assert abs(g[2] / (omega / (2 * p.sigma)) - 1) < 0.10, (g[2], omega / (2 * p.sigma))
+
+
+def test_objective_rollout_autograd():
+    from paper_2206_11637_gb300.autograd import RolloutSetup, objective_rollout
+    p, phi0, u0, p0, steps, w0 = wave_frequency_case()
+    setup = RolloutSetup(p, phi0, steps[-1], None, u0, p0, precision="fp64")
+    M = torch.tensor(p.mobility, dtype=torch.float64, requires_grad=True)
+    xi = torch.tensor(p.xi, dtype=torch.float64, requires_grad=True)
+    sg = torch.tensor(p.sigma, dtype=torch.float64, requires_grad=True)
+    J = objective_rollout(M, xi, sg, setup, O.WaveFrequency(steps, w0))
+    J.backward()
+    obj = frequency_forward(p, phi0, u0, p0, steps, w0)
+    assert abs(J.item() - obj.value()) <= 1e-12 * obj.value()
+    _, g, _ = adjoint(p, phi0, u0, p0, steps[-1], obj.seeds(p.shape))
+    got = np.array([M.grad.item(), xi.grad.item(), sg.grad.item()])
+    assert np.allclose(got, g, rtol=1e-12, atol=0)
