@@ -93,3 +93,60 @@ def test_drop_impact_512x384x512_properties(precision):
     assert abs(out[0] - m0) / m0 < tol
     del s
     torch.cuda.empty_cache()
+
+
+def _device_populations(s):
+    """(h, g) of a Simulation exported as FP64 CUDA tensors (qh N and qg N)."""
+    import ctypes
+    from paper_2206_11637_gb300 import _lib as L
+    h = torch.empty((s.qh,) + s.shape, dtype=torch.float64, device="cuda")
+    g = torch.empty((s.qg,) + s.shape, dtype=torch.float64, device="cuda")
+    L.check(s.lib.pfl_populations(s.ctx, ctypes.c_void_p(h.data_ptr()), ctypes.c_void_p(g.data_ptr())))
+    return h, g
+
+
+@pytest.mark.parametrize("precision,tol_phi,tol_u", [("fp64", 1e-12, 1e-12), ("fp32", 2e-6, 1e-5),
+                                                     ("fp16s", 2e-3, 1e-3)])
+def test_drop_impact_512x384x512_crop_one_step(precision, tol_phi, tol_u):
+    """The benchmark's workload (100.7 M cells) in its timed launch
+    configuration: after 150 steps (the drop has reached the pool), a 64^3
+    sub-box around the impact point of the GPU state goes to the oracle; one
+    step on each side.  The oracle's walls at the sub-box faces change the
+    face cells' collisions (mirrored stencil) and the populations they push:
+    phi and p two or more cells away from the faces, and u (whose force term
+    reads the new phi of the neighbours) three or more away, are unaffected.
+    Those are compared: u against max |u| of the sub-box, the bar u / u_max."""
+    from paper_2206_11637_gb300.pflbm import Simulation
+    p, phi0, u0, p0 = W.drop_impact()
+    s = Simulation(p, phi0, u0, p0, precision=precision)
+    del phi0, u0, p0
+    s.step(150)
+    x0, y0, z0, n = 224, 100, 224, 64
+    sl = (slice(z0, z0 + n), slice(y0, y0 + n), slice(x0, x0 + n))
+    h, g = _device_populations(s)
+    hc = h[(slice(None),) + sl].cpu().numpy()
+    gc = g[(slice(None),) + sl].cpu().numpy()
+    del h, g
+    torch.cuda.empty_cache()
+    s.step(1)
+    out = {k: torch.empty(s.N * (3 if k == "u" else 1), dtype=torch.float64, device="cuda")
+           for k in ("phi", "p", "u")}
+    s.fields(out)
+    phi = out["phi"].view(s.shape)[sl].cpu().numpy()
+    pr = out["p"].view(s.shape)[sl].cpu().numpy()
+    u = out["u"].view((3,) + s.shape)[(slice(None),) + sl].cpu().numpy()
+    del s, out
+    torch.cuda.empty_cache()
+    q = W.Params(n, n, n, (1,) * 6, p.rho_h, p.rho_l, p.nu_h, p.nu_l, p.sigma, p.mobility, p.xi, p.gravity)
+    o = oracle.from_params(q, np.ones((n, n, n)))
+    o.set_populations(hc, gc)
+    o.step(1, 0)
+    ophi, _, opr, ou = o.fields()
+    inner = (slice(2, n - 2),) * 3
+    inner3 = (slice(None),) + (slice(3, n - 3),) * 3
+    assert ophi[inner].min() < 0.1 and ophi[inner].max() > 0.9   # the sub-box holds both phases
+    umax = np.abs(ou[inner3]).max()
+    assert umax > 1e-3                                 # and moving fluid
+    assert np.abs(phi[inner] - ophi[inner]).max() <= tol_phi
+    assert np.abs(pr[inner] - opr[inner]).max() <= max(tol_phi, 1e-12) * np.abs(opr[inner]).max() * 10
+    assert np.abs(u[inner3] - ou[inner3]).max() <= tol_u * umax
