@@ -1,21 +1,23 @@
 // Batched PFLBM: many independent lattices of uneven size and their own
 // parameters (M, xi, sigma, ...) advanced together.
 //
-// Every lattice time step is one persistent launch of the stream-collide over
-// all instances and one of the phi pass: a grid of (SMs x resident blocks)
-// blocks walks a device work list of tiles (instance, first cell), each tile
-// one cell per thread, and reads the instance's geometry, parameters and
-// buffers from a device table.  Instances fall into two size classes (below
-// and above 64 K cells); each class has its own work list and launch shape.
-// The shapes -- threads per block and grid size -- are chosen at init by
-// timing the candidates on the initial state (which is then rebuilt).  The
-// step loop is captured once into a CUDA graph of 2 G lattice steps (an even
-// count, so parity and phi buffers return to their starting roles) and
-// replayed.
+// Every lattice time step is one persistent launch of the fused two-array
+// step per class of instances (quasi-2-D lattices with one z plane, and 3-D
+// lattices): a grid of (SMs x resident blocks x m) blocks walks a device work
+// list of tiles (instance, xy tile, z chunk), and each block runs the same
+// tile code as the single-lattice step (zm_tile: the phi stencil from a
+// shared-memory ring marched along z, both collisions, push streaming into the
+// instance's other array pair) with the instance's geometry and parameters,
+// read from a device table into shared memory.  phi of the stored state is
+// formed in the step itself, so there is no separate phi pass.  The launch
+// shapes -- the tile height of the quasi-2-D class, the z chunk of the 3-D
+// class, the grid size of both -- are chosen at init by timing the candidates
+// on the initial state (which is then rebuilt).  The step loop is captured
+// once into a CUDA graph of 2 G lattice steps (an even count, so the array
+// pairs return to their starting roles) and replayed.
 //
-// The per-cell arithmetic is step_cell / phi_cell, the same code as the
-// single-lattice kernels, so an instance of the batch evolves exactly like the
-// same lattice run alone.
+// An instance of the batch evolves exactly like the same lattice run alone by
+// the fused single-lattice step: the per-cell arithmetic is the same code.
 #include <algorithm>
 #include <cstring>
 #include <string>
@@ -45,66 +47,69 @@ pfl_status bfail(pfl_status s, const std::string& m) {
 struct BInst {
   Geo32 geo;
   Phys ph;
-  void* h;
-  void* g;
-  void* phi[2];
+  void* h[2];   // the two array pairs of the fused step
+  void* g[2];
+  void* phi;    // phi written by the steps (phi of the state each step started from)
+  void* phic;   // phi of the current state, formed on demand (fields, diagnostics)
+  int zc;       // z planes per tile of the work list
   int active;
-  int frozen_cur, frozen_swapped;  // host bookkeeping: roles of the buffers when the instance stopped
+  int frozen_ab;  // host bookkeeping: the pair holding the state when the instance stopped
 };
 
 struct BTile {
   int inst;
-  unsigned c0;
+  unsigned short bx, by, bz, pad;
 };
 
-constexpr int NCLASS = 2;
-constexpr unsigned SMALL_CELLS = 65536;
+constexpr int NCLASS = 2;     // class 0: one z plane (quasi-2-D), class 1: 3-D
 constexpr int GRAPH_PAIRS = 8;  // a graph holds 2 * GRAPH_PAIRS lattice steps
 
-template <int PREC, int ODD, int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == 128 ? 4 : 2)
-    k_batch_step(const BInst* __restrict__ inst, const BTile* __restrict__ tiles, int ntiles, int cur,
-                 const unsigned* __restrict__ tstep) {
+// One lattice step of the instances of one class: a persistent walk over the
+// class's work list (ab: the array pair holding the current state).
+template <int PREC, int TY, int FLAT>
+__global__ void __launch_bounds__(ZM_TX * TY, (PREC == 0 ? PFL_ZM_MINB_FP64 : PFL_ZM_MINB) * ZM_TY / TY)
+    k_batch_zm(const BInst* __restrict__ inst, const BTile* __restrict__ tiles, int ntiles, int ab) {
   typedef typename Store<PREC>::S S;
   typedef typename Store<PREC>::PhiT PhiT;
+  __shared__ Geo32 sgeo;
+  __shared__ Phys sph;
+  __shared__ int sact;
+  __shared__ void* sptr[5];
+  __shared__ int szc;
+  if (PFL_ZM_PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const BTile tile = tiles[t];
-    const BInst* I = inst + tile.inst;
-    if (!I->active) continue;
-    const unsigned cell = tile.c0 + threadIdx.x;
-    if (cell < I->geo.N)
-      step_cell<PREC, 15, ODD>(I->geo, I->ph, (S*)I->h, (S*)I->g, (const PhiT*)I->phi[cur], (const PhiT*)I->phi[1 - cur],
-                           cell, *tstep * 0x9E3779B9u + (unsigned)tile.inst * 0x85EBCA6Bu);
-  }
-}
-
-// The phi pass of the last class also advances the device step counter that
-// seeds the stochastic rounding (the graph replays fixed kernel arguments).
-template <int PREC, int READ_ODD, int THREADS>
-__global__ void __launch_bounds__(THREADS) k_batch_phi(const BInst* __restrict__ inst, const BTile* __restrict__ tiles,
-                                                       int ntiles, int cur, unsigned* __restrict__ tick) {
-  typedef typename Store<PREC>::S S;
-  typedef typename Store<PREC>::PhiT PhiT;
-  if (tick && blockIdx.x == 0 && threadIdx.x == 0) *tick += 1u;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const BTile tile = tiles[t];
-    const BInst* I = inst + tile.inst;
-    if (!I->active) continue;
-    const unsigned cell = tile.c0 + threadIdx.x;
-    if (cell < I->geo.N)
-      ((PhiT*)I->phi[1 - cur])[cell] = phi_cell<PREC, 15, READ_ODD>(I->geo, (const S*)I->h, (const PhiT*)I->phi[cur], cell);
+    if (tid == 0) {
+      const BInst* I = inst + tile.inst;
+      sgeo = I->geo;
+      sph = I->ph;
+      sact = I->active;
+      sptr[0] = I->h[ab];
+      sptr[1] = I->g[ab];
+      sptr[2] = I->h[1 - ab];
+      sptr[3] = I->g[1 - ab];
+      sptr[4] = I->phi;
+      szc = I->zc;
+    }
+    __syncthreads();
+    if (sact)
+      zm_tile<PREC, 15, TY, FLAT, 0>(sgeo, sph, (const S*)sptr[0], (const S*)sptr[1], (S*)sptr[2], (S*)sptr[3], nullptr,
+                                     (PhiT*)sptr[4], szc, 0u, nullptr, nullptr, nullptr, tile.bx, tile.by, tile.bz);
+    __syncthreads();  // the next tile refills the shared rings and the instance slot
   }
 }
 
 struct Shape {
-  int threads;  // 128 or 256 (one cell per thread per tile)
-  int grid;     // blocks of the persistent launch
+  int ty;    // tile height (threads per block = ZM_TX * ty); 4 or 8 for one z plane, 8 in 3-D
+  int zc;    // z planes per tile (3-D class; 0 = the whole lattice)
+  int grid;  // blocks of the persistent launch
 };
 
 struct ClassPlan {
   std::vector<int> members;
-  Shape shape{128, 0};
-  BTile* tiles = nullptr;  // device, for shape.threads
+  Shape shape{8, 0, 0};
+  BTile* tiles = nullptr;  // device
   int ntiles = 0;
 };
 
@@ -137,9 +142,8 @@ struct pfl_batch {
   std::vector<size_t> off;     // workspace offset of each instance's buffers
   size_t table_off, tiles_off, stage_off, red_off;
   BInst* d_inst;
-  unsigned* d_tick;  // device step counter (seed of the FP16 stochastic rounding)
   ClassPlan cls[NCLASS];
-  int cur, swapped;
+  int ab;                      // the array pair holding the current state
   long long t;
   cudaGraphExec_t graph;
   int sms, tuned;
@@ -154,8 +158,14 @@ struct BLayout {
 
 size_t inst_bytes(const pfl_params& p) {
   const size_t N = (size_t)p.nx * p.ny * p.nz;
-  return align256(15 * N * pop_bytes(p.precision)) + align256(27 * N * pop_bytes(p.precision)) +
+  return 2 * (align256(15 * N * pop_bytes(p.precision)) + align256(27 * N * pop_bytes(p.precision))) +
          2 * align256(N * phi_bytes(p.precision));
+}
+
+// tiles of one instance for a tile height and z chunk
+size_t tiles_of(const pfl_params& p, int ty, int zc) {
+  const size_t zc_ = zc > 0 && zc < p.nz ? (size_t)zc : (size_t)p.nz;
+  return (size_t)((p.nx + ZM_TX - 1) / ZM_TX) * ((p.ny + ty - 1) / ty) * ((p.nz + zc_ - 1) / zc_);
 }
 
 BLayout blayout(const pfl_params* p, int count) {
@@ -166,7 +176,7 @@ BLayout blayout(const pfl_params* p, int count) {
     off += inst_bytes(p[i]);
     const size_t N = (size_t)p[i].nx * p[i].ny * p[i].nz;
     maxN = std::max(maxN, N);
-    tiles += (N + 127) / 128;  // the largest tile count over the shapes (128 threads)
+    tiles += tiles_of(p[i], 4, 1);  // the most tiles any shape takes
   }
   L.table = off;
   off = align256(off + (size_t)count * sizeof(BInst) + 256);
@@ -175,79 +185,61 @@ BLayout blayout(const pfl_params* p, int count) {
   L.stage = off;
   off = align256(off + (maxN + 16) * sizeof(double));
   L.red = off;
-  off = align256(off + (DIAG_BLOCKS * 9 + 16) * sizeof(double));
+  off = align256(off + (DIAG_BLOCKS * 10 + 32) * sizeof(double));
   L.total = off;
   return L;
 }
 
 template <int PREC>
-void launch_class_step(pfl_batch* b, const ClassPlan& c) {
+void launch_class_step(pfl_batch* b, const ClassPlan& c, int cls) {
   if (c.ntiles == 0) return;
   const int g = c.shape.grid;
-  if (c.shape.threads == 128) {
-    if (b->swapped)
-      k_batch_step<PREC, 1, 128><<<g, 128, 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->cur, b->d_tick);
+  if (cls == 0) {
+    if (c.shape.ty == 4)
+      k_batch_zm<PREC, 4, 1><<<g, dim3(ZM_TX, 4), 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->ab);
     else
-      k_batch_step<PREC, 0, 128><<<g, 128, 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->cur, b->d_tick);
+      k_batch_zm<PREC, 8, 1><<<g, dim3(ZM_TX, 8), 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->ab);
   } else {
-    if (b->swapped)
-      k_batch_step<PREC, 1, 256><<<g, 256, 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->cur, b->d_tick);
-    else
-      k_batch_step<PREC, 0, 256><<<g, 256, 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->cur, b->d_tick);
+    k_batch_zm<PREC, 8, 0><<<g, dim3(ZM_TX, 8), 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->ab);
   }
 }
 
-template <int PREC>
-void launch_class_phi(pfl_batch* b, const ClassPlan& c, unsigned* tick) {
-  if (c.ntiles == 0) return;
-  const int g = c.shape.grid;
-  // after the step kernel flipped `swapped`: READ_ODD = swapped
-  if (c.shape.threads == 128) {
-    if (b->swapped)
-      k_batch_phi<PREC, 1, 128><<<g, 128, 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->cur, tick);
-    else
-      k_batch_phi<PREC, 0, 128><<<g, 128, 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->cur, tick);
-  } else {
-    if (b->swapped)
-      k_batch_phi<PREC, 1, 256><<<g, 256, 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->cur, tick);
-    else
-      k_batch_phi<PREC, 0, 256><<<g, 256, 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->cur, tick);
-  }
-}
-
-// one lattice step of every instance: stream-collide of all classes, then phi
+// one lattice step of every instance: the fused step of both classes
 template <int PREC>
 void batch_step_once(pfl_batch* b) {
-  for (int k = 0; k < NCLASS; ++k) launch_class_step<PREC>(b, b->cls[k]);
-  b->swapped ^= 1;
-  int last = -1;
-  for (int k = 0; k < NCLASS; ++k)
-    if (b->cls[k].ntiles) last = k;
-  for (int k = 0; k < NCLASS; ++k) launch_class_phi<PREC>(b, b->cls[k], k == last ? b->d_tick : nullptr);
-  b->cur = 1 - b->cur;
+  for (int k = 0; k < NCLASS; ++k) launch_class_step<PREC>(b, b->cls[k], k);
+  b->ab ^= 1;
   b->t += 1;
 }
 
 void batch_step_dispatch(pfl_batch* b) {
-  switch (b->prec) {
-    case PFL_FP64: batch_step_once<0>(b); break;
-    case PFL_FP32: batch_step_once<1>(b); break;
-    default: batch_step_once<2>(b); break;
-  }
+  if (b->prec == PFL_FP64)
+    batch_step_once<0>(b);
+  else
+    batch_step_once<1>(b);
 }
 
-// Work list of one class for a given tile size (threads per block).
-pfl_status build_tiles(pfl_batch* b, ClassPlan& c, int threads, BTile* dst) {
+// Work list of one class for a shape: every instance's (xy tile, z chunk)
+// tiles, larger instances first (their tiles start early in the walk).
+pfl_status build_tiles(pfl_batch* b, ClassPlan& c, const Shape& sh, BTile* dst) {
   std::vector<BTile> v;
-  // larger instances first: their tiles start early in the grid-stride walk
   std::vector<int> order = c.members;
   std::sort(order.begin(), order.end(), [&](int a, int q) { return b->inst[a].geo.N > b->inst[q].geo.N; });
-  for (int i : order)
-    for (unsigned c0 = 0; c0 < b->inst[i].geo.N; c0 += threads) v.push_back(BTile{i, c0});
+  for (int i : order) {
+    const Geo32& g = b->inst[i].geo;
+    const int zc = sh.zc > 0 && sh.zc < (int)g.nz ? sh.zc : (int)g.nz;
+    b->inst[i].zc = zc;
+    const int nbx = (g.nx + ZM_TX - 1) / ZM_TX, nby = (g.ny + sh.ty - 1) / sh.ty, nbz = (g.nz + zc - 1) / zc;
+    for (int bz = 0; bz < nbz; ++bz)
+      for (int by = 0; by < nby; ++by)
+        for (int bx = 0; bx < nbx; ++bx)
+          v.push_back(BTile{i, (unsigned short)bx, (unsigned short)by, (unsigned short)bz, 0});
+  }
   c.tiles = dst;
   c.ntiles = (int)v.size();
   if (!v.empty())
     BTRY(cudaMemcpyAsync(dst, v.data(), v.size() * sizeof(BTile), cudaMemcpyHostToDevice, b->stream));
+  BTRY(cudaMemcpyAsync(b->d_inst, b->inst.data(), b->count * sizeof(BInst), cudaMemcpyHostToDevice, b->stream));
   BTRY(cudaStreamSynchronize(b->stream));
   return PFL_OK;
 }
@@ -261,20 +253,27 @@ void launch_init_one(pfl_batch* b, int i, long long c0, long long cnt, const dou
   geo.nz = b->p[i].nz;
   for (int a = 0; a < 3; ++a) geo.wall[a] = b->p[i].bc[2 * a] == PFL_NOSLIP;
   geo.N = b->inst[i].geo.N;
-  k_init<PREC, 15><<<blocks_for(cnt, 256), 256, 0, b->stream>>>(geo, (typename Store<PREC>::S*)b->inst[i].h,
-                                                            (typename Store<PREC>::S*)b->inst[i].g, c0, cnt, phi0, ux,
+  k_init<PREC, 15><<<blocks_for(cnt, 256), 256, 0, b->stream>>>(geo, (typename Store<PREC>::S*)b->inst[i].h[0],
+                                                            (typename Store<PREC>::S*)b->inst[i].g[0], c0, cnt, phi0, ux,
                                                             uy, uz, p0);
 }
 
+// phi of the current state of instance i (pair `ab`) into its phic buffer
 template <int PREC>
-void launch_phi_one(pfl_batch* b, int i) {
+void launch_phi_one(pfl_batch* b, int i, int ab) {
   const BInst& I = b->inst[i];
   k_phi32<PREC, 15, 0><<<blocks_for(I.geo.N, 256), 256, 0, b->stream>>>(
-      I.geo, (const typename Store<PREC>::S*)I.h, (const typename Store<PREC>::PhiT*)I.phi[1],
-      (typename Store<PREC>::PhiT*)I.phi[0]);
+      I.geo, (const typename Store<PREC>::S*)I.h[ab], nullptr, (typename Store<PREC>::PhiT*)I.phic);
 }
 
-// Equilibrium start of every instance (zero shifts in phi[1], phi into phi[0]).
+void phi_one(pfl_batch* b, int i, int ab) {
+  if (b->prec == PFL_FP64)
+    launch_phi_one<0>(b, i, ab);
+  else
+    launch_phi_one<1>(b, i, ab);
+}
+
+// Equilibrium start of every instance in pair 0.
 pfl_status initial_state(pfl_batch* b, const double* const* phi0, const double* const* u0, const double* const* p0) {
   double* st = (double*)(b->ws + b->stage_off);
   for (int i = 0; i < b->count; ++i) {
@@ -291,87 +290,109 @@ pfl_status initial_state(pfl_batch* b, const double* const* phi0, const double* 
         BTRY(cudaMemcpyAsync(st + 3 * cnt, u + 2 * N + c0, cnt * 8, cudaMemcpyDefault, b->stream));
       }
       if (pp) BTRY(cudaMemcpyAsync(st + 4 * cnt, pp + c0, cnt * 8, cudaMemcpyDefault, b->stream));
-      switch (b->prec) {
-        case PFL_FP64:
-          launch_init_one<0>(b, i, c0, cnt, st, u ? st + cnt : nullptr, u ? st + 2 * cnt : nullptr,
-                             u ? st + 3 * cnt : nullptr, pp ? st + 4 * cnt : nullptr);
-          break;
-        case PFL_FP32:
-          launch_init_one<1>(b, i, c0, cnt, st, u ? st + cnt : nullptr, u ? st + 2 * cnt : nullptr,
-                             u ? st + 3 * cnt : nullptr, pp ? st + 4 * cnt : nullptr);
-          break;
-        default:
-          launch_init_one<2>(b, i, c0, cnt, st, u ? st + cnt : nullptr, u ? st + 2 * cnt : nullptr,
-                             u ? st + 3 * cnt : nullptr, pp ? st + 4 * cnt : nullptr);
-          break;
-      }
+      if (b->prec == PFL_FP64)
+        launch_init_one<0>(b, i, c0, cnt, st, u ? st + cnt : nullptr, u ? st + 2 * cnt : nullptr,
+                           u ? st + 3 * cnt : nullptr, pp ? st + 4 * cnt : nullptr);
+      else
+        launch_init_one<1>(b, i, c0, cnt, st, u ? st + cnt : nullptr, u ? st + 2 * cnt : nullptr,
+                           u ? st + 3 * cnt : nullptr, pp ? st + 4 * cnt : nullptr);
       BTRY(cudaGetLastError());
       BTRY(cudaStreamSynchronize(b->stream));
     }
-    BTRY(cudaMemsetAsync(b->inst[i].phi[1], 0, (size_t)N * phi_bytes(b->prec), b->stream));
-    switch (b->prec) {
-      case PFL_FP64: launch_phi_one<0>(b, i); break;
-      case PFL_FP32: launch_phi_one<1>(b, i); break;
-      default: launch_phi_one<2>(b, i); break;
-    }
-    BTRY(cudaGetLastError());
   }
-  b->cur = 0;
-  b->swapped = 0;
+  b->ab = 0;
   b->t = 0;
-  BTRY(cudaMemsetAsync(b->d_tick, 0, sizeof(unsigned), b->stream));
   BTRY(cudaStreamSynchronize(b->stream));
   return PFL_OK;
 }
 
-int resident_blocks(int prec, int threads) {
+int resident_blocks(int prec, int ty, int flat) {
   int nb = 0;
   const void* fn = nullptr;
   if (prec == PFL_FP64)
-    fn = threads == 128 ? (const void*)k_batch_step<0, 1, 128> : (const void*)k_batch_step<0, 1, 256>;
-  else if (prec == PFL_FP32)
-    fn = threads == 128 ? (const void*)k_batch_step<1, 1, 128> : (const void*)k_batch_step<1, 1, 256>;
+    fn = flat ? (ty == 4 ? (const void*)k_batch_zm<0, 4, 1> : (const void*)k_batch_zm<0, 8, 1>)
+              : (const void*)k_batch_zm<0, 8, 0>;
   else
-    fn = threads == 128 ? (const void*)k_batch_step<2, 1, 128> : (const void*)k_batch_step<2, 1, 256>;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, 0) != cudaSuccess) {
+    fn = flat ? (ty == 4 ? (const void*)k_batch_zm<1, 4, 1> : (const void*)k_batch_zm<1, 8, 1>)
+              : (const void*)k_batch_zm<1, 8, 0>;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ZM_TX * ty, 0) != cudaSuccess) {
     cudaGetLastError();
     nb = 1;
   }
   return nb < 1 ? 1 : nb;
 }
 
-// Autotuner: for each class, time every (threads, grid) candidate over two
-// lattice steps of the whole batch (other classes at their current shape) and
-// keep the fastest.  Grids are multiples of the SM count times the resident
-// blocks per SM, capped by the tile count.
+// Default shape of a class: tile height 4 (one z plane) or 8, the z chunk by
+// the cost model of the single-lattice step (waves of resident blocks times
+// zc + 1/2, over the class's largest instance), grid = SMs x resident blocks.
+Shape default_shape(pfl_batch* b, int k) {
+  Shape sh{k == 0 ? 4 : 8, 0, 0};
+  if (k == 1) {
+    int big = -1;
+    for (int i : b->cls[k].members)
+      if (big < 0 || b->inst[i].geo.N > b->inst[big].geo.N) big = i;
+    if (big >= 0) {
+      const Geo32& g = b->inst[big].geo;
+      const long long slots = (long long)b->sms * resident_blocks(b->prec, 8, 0);
+      const long long bxy = (long long)((g.nx + ZM_TX - 1) / ZM_TX) * ((g.ny + 7) / 8);
+      double best = 1e300;
+      for (int zc = (int)g.nz; zc >= 1; --zc) {
+        const long long blocks = bxy * ((g.nz + zc - 1) / zc);
+        const double cost = (double)((blocks + slots - 1) / slots) * (zc + 0.5);
+        if (cost < best * (1 - 1e-9)) {
+          best = cost;
+          sh.zc = zc;
+        }
+      }
+    }
+  }
+  sh.grid = b->sms * resident_blocks(b->prec, sh.ty, k == 0);
+  return sh;
+}
+
+// Autotuner: for each class, time every candidate shape over two lattice
+// steps of the whole batch (the other class at its current shape) and keep
+// the fastest.  Candidates: tile height 4 or 8 (one z plane) or the z chunk
+// (the cost model's, 8, 16, 32, the whole lattice) in 3-D, each with grids of
+// 1, 2 and 4 x SMs x resident blocks, capped by the tile count.
 pfl_status tune(pfl_batch* b) {
-  BTile* tiles_base = (BTile*)(b->ws + b->tiles_off);
-  size_t tile_cursor = 0;
+  BTile* dst[NCLASS];
+  BTile* base = (BTile*)(b->ws + b->tiles_off);
+  size_t cursor = 0;
+  for (int k = 0; k < NCLASS; ++k) {
+    dst[k] = base + cursor;
+    for (int i : b->cls[k].members) cursor += tiles_of(b->p[i], 4, 1);
+  }
   cudaEvent_t e0, e1;
   BTRY(cudaEventCreate(&e0));
   BTRY(cudaEventCreate(&e1));
-  // default shapes first (so every class can run while another is tuned)
-  BTile* dst[NCLASS];
   for (int k = 0; k < NCLASS; ++k) {
-    dst[k] = tiles_base + tile_cursor;
-    size_t worst = 0;
-    for (int i : b->cls[k].members) worst += (b->inst[i].geo.N + 127) / 128;
-    tile_cursor += worst;
-    pfl_status s = build_tiles(b, b->cls[k], 128, dst[k]);
+    b->cls[k].shape = default_shape(b, k);
+    pfl_status s = build_tiles(b, b->cls[k], b->cls[k].shape, dst[k]);
     if (s != PFL_OK) return s;
-    b->cls[k].shape = Shape{128, std::min(b->cls[k].ntiles, b->sms * resident_blocks(b->prec, 128))};
   }
   for (int k = 0; k < NCLASS; ++k) {
     ClassPlan& c = b->cls[k];
     if (c.members.empty()) continue;
+    std::vector<Shape> cand;
+    const Shape d = c.shape;
+    if (k == 0) {
+      for (int ty : {4, 8}) cand.push_back(Shape{ty, 0, 0});
+    } else {
+      for (int zc : {d.zc, 8, 16, 32, 0}) {
+        bool dup = false;
+        for (const Shape& q : cand) dup |= q.zc == zc;
+        if (!dup) cand.push_back(Shape{8, zc, 0});
+      }
+    }
     float best = 1e30f;
-    Shape best_shape = c.shape;
-    for (int threads : {128, 256}) {
-      pfl_status s = build_tiles(b, c, threads, dst[k]);
+    Shape best_shape = d;
+    for (Shape sh : cand) {
+      pfl_status s = build_tiles(b, c, sh, dst[k]);
       if (s != PFL_OK) return s;
-      const int res = resident_blocks(b->prec, threads);
+      const int res = resident_blocks(b->prec, sh.ty, k == 0);
       for (int mult : {1, 2, 4}) {
-        Shape sh{threads, std::max(1, std::min(c.ntiles, mult * b->sms * res))};
+        sh.grid = std::max(1, std::min(c.ntiles, mult * b->sms * res));
         c.shape = sh;
         batch_step_dispatch(b);  // warm-up
         batch_step_dispatch(b);
@@ -390,7 +411,7 @@ pfl_status tune(pfl_batch* b) {
         if (sh.grid == c.ntiles) break;  // larger grids are the same launch
       }
     }
-    pfl_status s = build_tiles(b, c, best_shape.threads, dst[k]);
+    pfl_status s = build_tiles(b, c, best_shape, dst[k]);
     if (s != PFL_OK) return s;
     c.shape = best_shape;
   }
@@ -401,11 +422,11 @@ pfl_status tune(pfl_batch* b) {
 }
 
 pfl_status capture_graph(pfl_batch* b) {
-  // 2 * GRAPH_PAIRS steps starting at parity 0 / buffer 0 return there.  The
-  // caller's stream may be the legacy default stream, which cannot be
-  // captured: capture on a private stream, replay on the caller's.
+  // 2 * GRAPH_PAIRS steps starting at pair 0 return there.  The caller's
+  // stream may be the legacy default stream, which cannot be captured:
+  // capture on a private stream, replay on the caller's.
   cudaGraph_t g;
-  const int cur0 = b->cur, sw0 = b->swapped;
+  const int ab0 = b->ab;
   const long long t0 = b->t;
   cudaStream_t user = b->stream, cap;
   BTRY(cudaStreamSynchronize(user));
@@ -418,8 +439,7 @@ pfl_status capture_graph(pfl_batch* b) {
   }
   b->stream = user;
   cudaStreamDestroy(cap);
-  b->cur = cur0;
-  b->swapped = sw0;
+  b->ab = ab0;
   b->t = t0;
   if (e != cudaSuccess) return bfail(PFL_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
   e = cudaGraphInstantiate(&b->graph, g, 0);
@@ -437,7 +457,7 @@ size_t pfl_batch_workspace_bytes(const pfl_params* params, int count) {
   for (int i = 0; i < count; ++i) {
     if (!check_params(&params[i]).empty()) return 0;
     if (params[i].precision != params[0].precision || params[i].collision != PFL_MRT) return 0;
-    if (qh_of(&params[i]) != 15 || params[i].solids) return 0;
+    if (qh_of(&params[i]) != 15 || params[i].solids || params[i].precision == PFL_FP16S) return 0;
     if (27ull * params[i].nx * params[i].ny * params[i].nz >= (1ull << 32)) return 0;
   }
   return blayout(params, count).total;
@@ -457,6 +477,7 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
     if (params[i].collision != PFL_MRT) return bfail(PFL_ERR_ARG, "the batch runs the MRT collision");
     if (qh_of(&params[i]) != 15) return bfail(PFL_ERR_ARG, "the batch steps D3Q15 phase fields only");
     if (params[i].solids) return bfail(PFL_ERR_ARG, "the batch takes no solid cells");
+    if (params[i].precision == PFL_FP16S) return bfail(PFL_ERR_ARG, "the batch runs FP64 or FP32 storage");
     if (27ull * params[i].nx * params[i].ny * params[i].nz >= (1ull << 32))
       return bfail(PFL_ERR_ARG, "instance " + std::to_string(i) + " too large for 32-bit indices");
     if (!phi0[i]) return bfail(PFL_ERR_ARG, "phi0 of instance " + std::to_string(i) + " is NULL");
@@ -483,9 +504,10 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
   b->stage_off = L.stage;
   b->red_off = L.red;
   b->d_inst = (BInst*)(b->ws + L.table);
-  b->d_tick = (unsigned*)(b->ws + L.table + align256((size_t)count * sizeof(BInst)));
   b->graph = nullptr;
   b->tuned = 0;
+  b->ab = 0;
+  b->t = 0;
   cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, device);
   const size_t S = pop_bytes(b->prec), P = phi_bytes(b->prec);
   for (int i = 0; i < count; ++i) {
@@ -504,16 +526,20 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
       return bfail(PFL_ERR_STATE, "integer divider self-check failed");
     }
     I.ph = phys_of(&q);
-    char* base = b->ws + L.off[i];
-    I.h = base;
-    I.g = base + align256(15 * (size_t)N * S);
-    I.phi[0] = base + align256(15 * (size_t)N * S) + align256(27 * (size_t)N * S);
-    I.phi[1] = (char*)I.phi[0] + align256((size_t)N * P);
+    char* at = b->ws + L.off[i];
+    for (int pr = 0; pr < 2; ++pr) {
+      I.h[pr] = at;
+      at += align256(15 * (size_t)N * S);
+      I.g[pr] = at;
+      at += align256(27 * (size_t)N * S);
+    }
+    I.phi = at;
+    I.phic = at + align256((size_t)N * P);
+    I.zc = q.nz;
     I.active = 1;
-    I.frozen_cur = 0;
-    I.frozen_swapped = 0;
+    I.frozen_ab = 0;
     b->inst.push_back(I);
-    b->cls[N < SMALL_CELLS ? 0 : 1].members.push_back(i);
+    b->cls[q.nz == 1 ? 0 : 1].members.push_back(i);
   }
   pfl_status s = PFL_OK;
   cudaError_t e = cudaMemcpyAsync(b->d_inst, b->inst.data(), count * sizeof(BInst), cudaMemcpyHostToDevice, b->stream);
@@ -524,13 +550,13 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
       s = tune(b);
       if (s == PFL_OK) s = initial_state(b, phi0, u0, p0);  // the timing steps moved the state
     } else {
-      // default shapes without timing: 128 threads, grid = SMs x resident blocks
       BTile* base = (BTile*)(b->ws + b->tiles_off);
       size_t cursor = 0;
       for (int k = 0; k < NCLASS && s == PFL_OK; ++k) {
-        s = build_tiles(b, b->cls[k], 128, base + cursor);
-        for (int i : b->cls[k].members) cursor += (b->inst[i].geo.N + 127) / 128;
-        b->cls[k].shape = Shape{128, std::max(1, std::min(b->cls[k].ntiles, b->sms * resident_blocks(b->prec, 128)))};
+        b->cls[k].shape = default_shape(b, k);
+        s = build_tiles(b, b->cls[k], b->cls[k].shape, base + cursor);
+        for (int i : b->cls[k].members) cursor += tiles_of(b->p[i], 4, 1);
+        b->cls[k].shape.grid = std::max(1, std::min(b->cls[k].ntiles, b->cls[k].shape.grid));
       }
     }
   }
@@ -548,8 +574,8 @@ pfl_status pfl_batch_step(pfl_batch* b, int n) {
   if (n < 0) return bfail(PFL_ERR_ARG, "n_steps must be >= 0");
   BTRY(cudaSetDevice(b->device));
   int done = 0;
-  // whole graphs only from the graph's starting roles (even parity, buffer 0)
-  while (n - done >= 2 * GRAPH_PAIRS && b->swapped == 0 && b->cur == 0) {
+  // whole graphs only from the graph's starting roles (pair 0 current)
+  while (n - done >= 2 * GRAPH_PAIRS && b->ab == 0) {
     BTRY(cudaGraphLaunch(b->graph, b->stream));
     b->t += 2 * GRAPH_PAIRS;
     done += 2 * GRAPH_PAIRS;
@@ -564,8 +590,7 @@ pfl_status pfl_batch_fields(pfl_batch* b, int i, double* phi, double* rho, doubl
   if (i < 0 || i >= b->count) return bfail(PFL_ERR_ARG, "instance index out of range");
   BTRY(cudaSetDevice(b->device));
   const BInst& I = b->inst[i];
-  const int cur = I.active ? b->cur : I.frozen_cur;
-  const int swapped = I.active ? b->swapped : I.frozen_swapped;
+  const int ab = I.active ? b->ab : I.frozen_ab;
   Geo geo;
   geo.nx = (int)I.geo.nx;
   geo.ny = (int)I.geo.ny;
@@ -573,6 +598,8 @@ pfl_status pfl_batch_fields(pfl_batch* b, int i, double* phi, double* rho, doubl
   for (int a = 0; a < 3; ++a) geo.wall[a] = I.geo.wall[a];
   geo.N = I.geo.N;
   const long long N = geo.N;
+  phi_one(b, i, ab);
+  BTRY(cudaGetLastError());
   double* want[6] = {phi, rho, p, u, u ? u + N : nullptr, u ? u + 2 * N : nullptr};
   double* st = (double*)(b->ws + b->stage_off);
   for (int k = 0; k < 6; ++k) {
@@ -581,21 +608,12 @@ pfl_status pfl_batch_fields(pfl_batch* b, int i, double* phi, double* rho, doubl
     double* o[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     o[k] = dev ? want[k] : st;
     const unsigned nb = blocks_for(N, 256);
-#define BF(PREC)                                                                                                  \
-  if (swapped)                                                                                                    \
-    k_fields<PREC, 15, 1><<<nb, 256, 0, b->stream>>>(geo, I.ph, (const Store<PREC>::S*)I.g,                           \
-                                                 (const Store<PREC>::PhiT*)I.phi[cur], o[0], o[1],                 \
-                                                 o[2], o[3], o[4], o[5]);                                         \
-  else                                                                                                            \
-    k_fields<PREC, 15, 0><<<nb, 256, 0, b->stream>>>(geo, I.ph, (const Store<PREC>::S*)I.g,                           \
-                                                 (const Store<PREC>::PhiT*)I.phi[cur], o[0], o[1],                 \
-                                                 o[2], o[3], o[4], o[5]);
-    switch (b->prec) {
-      case PFL_FP64: BF(0) break;
-      case PFL_FP32: BF(1) break;
-      default: BF(2) break;
-    }
-#undef BF
+    if (b->prec == PFL_FP64)
+      k_fields<0, 15, 0><<<nb, 256, 0, b->stream>>>(geo, I.ph, (const Store<0>::S*)I.g[ab], (const Store<0>::PhiT*)I.phic,
+                                                    o[0], o[1], o[2], o[3], o[4], o[5]);
+    else
+      k_fields<1, 15, 0><<<nb, 256, 0, b->stream>>>(geo, I.ph, (const Store<1>::S*)I.g[ab], (const Store<1>::PhiT*)I.phic,
+                                                    o[0], o[1], o[2], o[3], o[4], o[5]);
     BTRY(cudaGetLastError());
     if (!dev) BTRY(cudaMemcpyAsync(want[k], st, N * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     BTRY(cudaStreamSynchronize(b->stream));
@@ -608,6 +626,8 @@ pfl_status pfl_batch_diag(pfl_batch* b, double* out, long long* nonfinite) {
   BTRY(cudaSetDevice(b->device));
   double* part = (double*)(b->ws + b->red_off);
   double* res = part + DIAG_BLOCKS * 9;
+  double* upart = part + DIAG_BLOCKS * 9 + 16;
+  double* ures = part + DIAG_BLOCKS * 10 + 16;
   int bad = 0;
   bool table_dirty = false;
   for (int i = 0; i < b->count; ++i) {
@@ -616,28 +636,35 @@ pfl_status pfl_batch_diag(pfl_batch* b, double* out, long long* nonfinite) {
     geo.nx = (int)I.geo.nx;
     geo.ny = (int)I.geo.ny;
     geo.nz = (int)I.geo.nz;
-    geo.wall[0] = geo.wall[1] = geo.wall[2] = 0;
+    for (int a = 0; a < 3; ++a) geo.wall[a] = I.geo.wall[a];
     geo.N = I.geo.N;
-    const int cur = I.active ? b->cur : I.frozen_cur;
-    if (b->prec == PFL_FP64)
-      k_diag<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, b->stream>>>(geo, (const double*)I.phi[cur], part);
-    else
-      k_diag<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, b->stream>>>(geo, (const float*)I.phi[cur], part);
+    const int ab = I.active ? b->ab : I.frozen_ab;
+    phi_one(b, i, ab);
+    if (b->prec == PFL_FP64) {
+      k_diag<double><<<DIAG_BLOCKS, DIAG_THREADS, 0, b->stream>>>(geo, (const double*)I.phic, part);
+      k_umax<0, 15, 0><<<DIAG_BLOCKS, DIAG_THREADS, 0, b->stream>>>(geo, I.ph, (const Store<0>::S*)I.g[ab],
+                                                                    (const Store<0>::PhiT*)I.phic, upart);
+    } else {
+      k_diag<float><<<DIAG_BLOCKS, DIAG_THREADS, 0, b->stream>>>(geo, (const float*)I.phic, part);
+      k_umax<1, 15, 0><<<DIAG_BLOCKS, DIAG_THREADS, 0, b->stream>>>(geo, I.ph, (const Store<1>::S*)I.g[ab],
+                                                                    (const Store<1>::PhiT*)I.phic, upart);
+    }
     k_diag_final<<<9, 32, 0, b->stream>>>(part, DIAG_BLOCKS, res);
+    k_max_final<<<1, 32, 0, b->stream>>>(upart, DIAG_BLOCKS, ures);
     BTRY(cudaGetLastError());
-    double h[9];
+    double h[9], umax = 0.0;
     BTRY(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, b->stream));
+    BTRY(cudaMemcpyAsync(&umax, ures, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     BTRY(cudaStreamSynchronize(b->stream));
     if (out)
       for (int k = 0; k < 8; ++k) out[8 * i + k] = h[k];
     const long long nf = (long long)h[8];
     if (nonfinite) nonfinite[i] = nf;
-    if (nf > 0) {
+    if (nf > 0 || !(umax <= PFL_SPEED_LIMIT)) {
       ++bad;
       if (I.active) {  // an unstable instance stops; the others go on
         I.active = 0;
-        I.frozen_cur = b->cur;
-        I.frozen_swapped = b->swapped;
+        I.frozen_ab = b->ab;
         table_dirty = true;
       }
     }
@@ -646,14 +673,16 @@ pfl_status pfl_batch_diag(pfl_batch* b, double* out, long long* nonfinite) {
     BTRY(cudaMemcpyAsync(b->d_inst, b->inst.data(), b->count * sizeof(BInst), cudaMemcpyHostToDevice, b->stream));
     BTRY(cudaStreamSynchronize(b->stream));
   }
-  if (bad) return bfail(PFL_ERR_UNSTABLE, std::to_string(bad) + " instances hold non-finite phi and were stopped");
+  if (bad)
+    return bfail(PFL_ERR_UNSTABLE, std::to_string(bad) +
+                                       " instances hold non-finite phi or a flow speed above the limit and were stopped");
   return PFL_OK;
 }
 
 pfl_status pfl_batch_shapes(const pfl_batch* b, int* threads, int* grid, int* ntiles) {
   if (!b) return bfail(PFL_ERR_ARG, "batch is NULL");
   for (int k = 0; k < NCLASS; ++k) {
-    if (threads) threads[k] = b->cls[k].shape.threads;
+    if (threads) threads[k] = ZM_TX * b->cls[k].shape.ty;
     if (grid) grid[k] = b->cls[k].shape.grid;
     if (ntiles) ntiles[k] = b->cls[k].ntiles;
   }
