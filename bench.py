@@ -2,22 +2,28 @@
 """Benchmark of the PFLBM hot path on GB300: MLUPS and fraction of HBM peak.
 
 One benchmark step = one segment of S lattice time steps of the workload (the
-fused stream-collide of h and g plus the phi pass per time step), run through
-the C interface.  Default workload: the standing capillary wave, 200 x 400 x 1
-cells (periodic x, z; no-slip walls in y), rho ratio 1000, nu = 0.01,
-sigma = 1e-4, xi = 5, M = 0.02; S = 2000 so ten steps cover its 20000 time
-steps.  The headline precision is the shifted-FP16 storage (FP32 arithmetic);
-FP64 and FP32 are timed in the same run.
+fused stream-collide of h and g with the phi stencil, one launch per lattice
+step), run through the C interface.  Default workload: the vertical drop
+impact into a pool, 512 x 384 x 512 cells (100.7 M, no-slip walls on every
+face, pool depth 128, drop diameter 64 starting 8 above the surface, Weber and
+Froude 200, rho ratio 1000, viscosity ratio 50, xi = 5, M = 0.02), the largest
+single-GPU workload, in shifted-FP16 storage with FP32 arithmetic; S = 100, so
+a run of 100 benchmark steps covers its 10000 time steps.  FP32 and FP64 are
+timed on the same lattice in the same run.
 
   value     MLUPS with the state resident in HBM (device timing, CUDA events);
-  e2e       MLUPS through the public API with host buffers: pfl_init from a
-            pinned host phi0 (H2D), S steps, pfl_fields of phi to the host (D2H);
+  e2e       MLUPS through the public API with host buffers: pfl_init from
+            pinned host phi0, u0 and p0 (H2D), S steps, pfl_fields of phi to
+            the host (D2H);
   roofline  the stream-collide kernel's algorithmic bytes per launch over its
             CUDA-event duration, against the measured HBM copy bandwidth;
-  cpu_baseline  the FP64 CPU oracle on the host cores over a bounded sample.
+  cpu_baseline  the FP64 CPU oracle on the host cores (all of them, and one)
+            over a bounded sample: a 128^3 sub-box of the same initial fields
+            around the impact point.
 
---impl reference times that oracle as the reference arm.  Under torchrun every
-rank runs an independent replica (the path is a single domain per GPU).
+--impl reference times that oracle as the reference arm on the same sample.
+Under torchrun every rank runs an independent replica (the path is a single
+domain per GPU).
 """
 import argparse
 import copy
@@ -87,10 +93,21 @@ def workload(name):
         p, phi0, u0, p0 = W.rising_bubble()
         return dict(p=p, phi0=phi0, u0=u0, p0=p0, S=200, total=4000, prec="fp32",
                     desc="rising bubble 128x384x128, walls, D 32, Eo 10, Mo 1e-3, xi 4, M 0.02")
+    if name == "drop_impact_256":
+        # the same impact at half the linear size (12.6 M cells): profiling case
+        p, phi0, u0, p0 = W.drop_impact(256, 192, 256, D=32.0, depth=64.0, gap=4.0)
+        return dict(p=p, phi0=phi0, u0=u0, p0=p0, S=100, total=5000, prec="fp16s",
+                    crop=(96, 160, 52, 116, 96, 160),
+                    desc="drop impact 256x192x256 (12.6 M cells), walls, pool depth 64, D 32 at 4 above the "
+                         "surface, We 200, Fr 200, rho ratio 1000, mu ratio 50, xi 5, M 0.02")
     if name == "drop_impact":
         p, phi0, u0, p0 = W.drop_impact()
+        # the CPU sample: 128^3 cells around the impact point (pool surface at
+        # y = 128, drop centre at y = 168)
         return dict(p=p, phi0=phi0, u0=u0, p0=p0, S=100, total=10000, prec="fp16s",
-                    desc="drop impact 512x384x512, walls, D 64, We 200, Fr 200, xi 5, M 0.02")
+                    crop=(192, 320, 104, 232, 192, 320),
+                    desc="drop impact 512x384x512 (100.7 M cells), walls, pool depth 128, D 64 at 8 above the "
+                         "surface, We 200, Fr 200, rho ratio 1000, mu ratio 50, xi 5, M 0.02")
     raise SystemExit("unknown workload " + name)
 
 
@@ -216,24 +233,51 @@ def mlups(cells, steps, seconds):
     return cells * steps / seconds / 1e6
 
 
-def cpu_oracle_rate(wl, budget_s=12.0):
-    """FP64 oracle MLUPS on the host cores over a bounded sample of the workload."""
+def oracle_sample(wl):
+    """(params, phi0, u0, p0, text) of the CPU sample of a workload: the whole
+    lattice, or for the drop impact a sub-box of the same initial fields (the
+    oracle's 700 bytes per cell would need 70 GB of host memory for the full
+    lattice); walls close the sub-box on every face."""
+    p = wl["p"]
+    if "crop" not in wl:
+        return p, wl["phi0"], wl["u0"], wl["p0"], "the full %dx%dx%d lattice" % (p.nx, p.ny, p.nz)
+    x0, x1, y0, y1, z0, z1 = wl["crop"]
+    q = copy.copy(p)
+    q.nx, q.ny, q.nz = x1 - x0, y1 - y0, z1 - z0
+    q.bc = (1,) * 6
+    sl = (slice(z0, z1), slice(y0, y1), slice(x0, x1))
+    phi0 = wl["phi0"][sl].copy()
+    u0 = None if wl["u0"] is None else wl["u0"][(slice(None),) + sl].copy()
+    p0 = None if wl["p0"] is None else wl["p0"][sl].copy()
+    return q, phi0, u0, p0, ("a %dx%dx%d sub-box (x %d..%d, y %d..%d, z %d..%d) of the %dx%dx%d lattice's initial "
+                             "fields, walls on its faces" % (q.nx, q.ny, q.nz, x0, x1, y0, y1, z0, z1, p.nx, p.ny, p.nz))
+
+
+def cpu_oracle_rate(wl, budget_s=10.0):
+    """FP64 oracle MLUPS on the host cores over a bounded sample of the
+    workload, on all cores and on one core."""
     import oracle
     oracle.build_oracle()
-    p = wl["p"]
-    o = oracle.from_params(p, wl["phi0"], wl["u0"], wl["p0"])
-    threads = os.cpu_count() or 1
-    o.step(1, threads)                      # warm-up (thread pool, caches)
-    t0 = time.perf_counter()
-    o.step(2, threads)
-    per = (time.perf_counter() - t0) / 2
-    n = max(2, min(2000, int(budget_s / max(per, 1e-9))))
-    t0 = time.perf_counter()
-    o.step(n, threads)
-    dt = time.perf_counter() - t0
-    return dict(value=mlups(p.cells, n, dt), unit=UNIT, cores=threads, kind="oracle",
-                sample="%d time steps of the full %dx%dx%d lattice (FP64, %d threads, %.1f s)"
-                       % (n, p.nx, p.ny, p.nz, threads, dt))
+    q, phi0, u0, p0, text = oracle_sample(wl)
+    o = oracle.from_params(q, phi0, u0, p0)
+    res = {}
+    for threads in (os.cpu_count() or 1, 1):
+        o.step(1, threads)                      # warm-up (thread pool, caches)
+        t0 = time.perf_counter()
+        o.step(1, threads)
+        per = time.perf_counter() - t0
+        n = max(1, min(2000, int(budget_s / max(per, 1e-9))))
+        t0 = time.perf_counter()
+        o.step(n, threads)
+        dt = time.perf_counter() - t0
+        res[threads] = (mlups(q.cells, n, dt), n, dt)
+    allc = os.cpu_count() or 1
+    v, n, dt = res[allc]
+    v1, n1, dt1 = res[1]
+    return dict(value=v, unit=UNIT, cores=allc, kind="oracle",
+                sample="%d time steps of %s (FP64, %d threads, %.1f s)" % (n, text, allc, dt),
+                single_core={"value": v1, "unit": UNIT, "cores": 1,
+                             "sample": "%d time steps of the same sample (FP64, 1 thread, %.1f s)" % (n1, dt1)})
 
 
 def run_reference(args, wl):
@@ -242,9 +286,9 @@ def run_reference(args, wl):
         return
     import oracle
     oracle.build_oracle()
-    p = wl["p"]
+    p, phi0, u0, p0, text = oracle_sample(wl)
     threads = os.cpu_count() or 1
-    o = oracle.from_params(p, wl["phi0"], wl["u0"], wl["p0"])
+    o = oracle.from_params(p, phi0, u0, p0)
     o.step(1, threads)
     t0 = time.perf_counter()
     o.step(1, threads)
@@ -258,27 +302,29 @@ def run_reference(args, wl):
         o.step(n_per, threads)
     dt = time.perf_counter() - t0
     v = mlups(p.cells, n_per * args.steps, dt)
-    sample = "%d lattice steps of the full %dx%dx%d lattice per benchmark step (FP64 oracle, %d threads)" % (
-        n_per, p.nx, p.ny, p.nz, threads)
+    sample = "%d lattice steps of %s per benchmark step (FP64 oracle, %d threads)" % (n_per, text, threads)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "description": wl["desc"], "cells": p.cells,
-                       "lattice_steps_per_step": n_per},
+                       "lattice_steps_per_step": n_per, "sample": text},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def run_batched(args):
-    """512 seeded instances (drops n^3, n in 24..96; waves nx x 2nx, nx in
-    64..256) with their own M, xi, sigma, advanced together in FP32 by the
-    batched persistent launches (CUDA graph, tuned shapes).  value = aggregate
-    MLUPS; error_vs_fp64 compares 16 instances with the FP64 single-lattice
-    path (itself checked against the oracle to 1e-10).  Under torchrun the
-    instances are sharded over the ranks (rank r takes r, r + N, ...), with
-    no collective on the data path: value = all instances' cell updates over
-    the slowest rank's time, "scaling" strong (the total work is fixed)."""
+    """Config 4: 512 seeded instances (drops n^3, n in 24..96; waves nx x
+    2nx, nx in 64..256) with their own M, xi, sigma, advanced together in FP32
+    by the batched persistent launches of the fused step (CUDA graph, tuned
+    shapes), S = 200 lattice steps per benchmark step (10 steps: the config's
+    2000).  value = aggregate MLUPS; per-instance error against the FP64 CPU
+    oracle after the same number of steps for a 16-instance subset (the 8
+    smallest drops and the 8 smallest waves of this rank's shard).  Under
+    torchrun the instances are sharded over the ranks (rank r takes r, r + N,
+    ...), with no collective on the data path: value = all instances' cell
+    updates over the slowest rank's time, "scaling" strong (the total work is
+    fixed)."""
     import numpy as np
     import torch
     from paper_2206_11637_gb300 import workloads as W
@@ -295,7 +341,6 @@ def run_batched(args):
     if dist:
         dist.barrier()
     from paper_2206_11637_gb300.batch import Batch
-    from paper_2206_11637_gb300.pflbm import Simulation
     every = W.batched_sweep(512)
     mine = shard(len(every), rank, ws)
     inst = [every[i] for i in mine]
@@ -303,7 +348,7 @@ def run_batched(args):
     t0 = time.perf_counter()
     b = Batch(inst, precision="fp32", tune=True, device=dev)
     t_init = time.perf_counter() - t0
-    S = args.lattice_steps or 100
+    S = args.lattice_steps or 200
     for _ in range(args.warmup):
         b.step(S)
     torch.cuda.synchronize()
@@ -319,26 +364,33 @@ def run_batched(args):
     ms = ranks_max(dist, e0.elapsed_time(e1), dev)
     out, nf, _ = b.diag(check=False)
     threads, grid, ntiles = b.shapes()
-    # error of 16 instances against FP64 after the same number of steps
+    # error of 16 instances against the FP64 oracle after the same number of steps
     n_done = b.time
     errs = []
-    for i in range(0, 32, 2):                      # 8 drops and 8 waves (of this rank's shard)
-        if i + (i // 2) % 2 not in mine:
-            continue
-        j = mine.index(i + (i // 2) % 2)
-        p, phi0, u0, p0 = inst[j]
-        ref = Simulation(p, phi0, u0, p0, precision="fp64", device=dev)
-        ref.step(n_done)
-        phi = b.fields(j)[0]
-        if nf[j] == 0:
-            errs.append(float(np.abs(phi - ref.phi()).max()))
-        del ref
+    if not args.no_compare:
+        import oracle
+        oracle.build_oracle()
+        drops = sorted([j for j in range(len(inst)) if inst[j][0].nz > 1], key=lambda j: inst[j][0].cells)[:8]
+        waves = sorted([j for j in range(len(inst)) if inst[j][0].nz == 1], key=lambda j: inst[j][0].cells)[:8]
+        for j in drops + waves:
+            p, phi0, u0, p0 = inst[j]
+            o = oracle.from_params(p, phi0, u0, p0)
+            o.step(n_done, 0)
+            ophi, _, _, ou = o.fields()
+            phi, _, _, u = b.fields(j)
+            umax = max(np.abs(ou).max(), 1e-300)
+            errs.append({"instance": mine[j], "cells": p.cells, "nonfinite": int(nf[j]),
+                         "phi_max_abs": float(np.abs(phi - ophi).max()),
+                         "u_max_over_umax": float(np.abs(u - ou).max() / umax)})
+            del o
     v = mlups(cells, S * args.steps, ms / 1e3)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
     if rank != 0:
         return
+    peak, _ = peaks()
+    bpc = 2 * 42 * 4 + 4    # fused FP32 step: populations read and written, phi written
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "strong" if ws > 1 else "weak",
             "vs_baseline": None,
@@ -347,25 +399,30 @@ def run_batched(args):
                        "parallelism": "instances sharded over %d ranks" % ws if ws > 1 else "1 GPU",
                        "lattice_steps_per_step": S, "precision": "fp32",
                        "l2": "working set larger than L2"},
-            "gpu_launches": 4 * S * args.steps, "clocks": clocks,
+            "gpu_launches": (2 * S + 2 * S // 16) * args.steps, "clocks": clocks,
+            "roofline": {"bound": "hbm", "achieved": v * 1e6 * bpc / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": v * 1e6 * bpc / 1e9 / peak, "traffic": None, "bytes_per_cell": bpc,
+                         "kernel": "k_batch_zm (fused two-array step over the work list)"},
             "batch": {"init_s": t_init, "shapes": {"threads": threads.tolist(), "grid": grid.tolist(),
                                                     "tiles": ntiles.tolist()},
+                      "lattice_steps_total": n_done,
                       "unstable_instances": int((nf > 0).sum()),
-                      "phi_max_abs_err_vs_fp64_16": errs}}
+                      "error_vs_fp64_oracle_16": errs}}
     print(json.dumps(line), flush=True)
 
 
-def adjoint_leg(dev, barrier, n=400):
+def adjoint_leg(dev, barrier, n=4000, window=1000):
     """Adjoint over forward on the 128 x 384 x 128 rising bubble (FP32, walls,
     D 32, Eo 10, Mo 1e-3, xi 4, M 0.02): J = mean rise velocity over the last
-    quarter of n = 400 steps, gradient with respect to (M, xi, sigma), sqrt(n)
-    checkpoints.  The ratio counts everything the adjoint call adds to the
-    forward run it contains: (t_adjoint - t_forward) / t_forward."""
+    `window` of n = 4000 steps, gradient with respect to (M, xi, sigma),
+    sqrt(n) checkpoints.  The ratio counts everything the adjoint call adds to
+    the forward run it contains: (t_adjoint - t_forward) / t_forward."""
     from paper_2206_11637_gb300 import objectives as O
     from paper_2206_11637_gb300 import workloads as W
     from paper_2206_11637_gb300.pflbm import Simulation
     p, phi0, u0, p0 = W.rising_bubble()
-    obs = O.rise_velocity_weights(p, phi0, 3 * n // 4, n)
+    window = min(window, n)
+    obs = O.rise_velocity_weights(p, phi0, n - window, n)
     fw = Simulation(p, phi0, u0, p0, precision="fp32", device=dev)
     fw.step(10)
     barrier()
@@ -385,7 +442,7 @@ def adjoint_leg(dev, barrier, n=400):
     ws_gb = ad.lib.pfl_adjoint_workspace_bytes(ad.ctx, n) / 1e9
     del ad
     return {"workload": "rising_bubble 128x384x128", "precision": "fp32", "lattice_steps": n,
-            "objective": "mean rise velocity over steps %d..%d" % (3 * n // 4, n),
+            "objective": "mean rise velocity over steps %d..%d" % (n - window, n),
             "forward_ms": t_fw * 1e3, "adjoint_ms_incl_forward_and_recompute": t_ad * 1e3,
             "adjoint_over_forward": (t_ad - t_fw) / t_fw, "workspace_gb": ws_gb,
             "J": J, "grad_M_xi_sigma": [float(v) for v in g]}
@@ -396,7 +453,6 @@ CONFIG_LEGS = [("static_drop", "fp64", 1000),
                ("capillary_wave", "fp64", 1000), ("capillary_wave", "fp32", 2000),
                ("capillary_wave", "fp16s", 2000),
                ("rising_bubble", "fp64", 20), ("rising_bubble", "fp32", 200), ("rising_bubble", "fp16s", 200),
-               ("drop_impact", "fp32", 40), ("drop_impact", "fp16s", 40),
                # the paper's own phase-field lattice (D3Q27 h)
                ("rising_bubble@d3q27", "fp32", 200), ("rising_bubble@d3q27", "fp16s", 200),
                # the paper's 2-D lattices (D2Q9 h and g) on the quasi-2-D wave
@@ -457,7 +513,7 @@ def config_table(dev, barrier):
     e1.record()
     barrier()
     r = mlups(cells, 96, e0.elapsed_time(e1) / 1e3)
-    bpc = 2 * 42 * 4 + 2 * 4     # in-place step + phi pass: populations, phi read and written
+    bpc = 2 * 42 * 4 + 4     # fused step: populations read and written, phi written
     rows.append({"workload": "batched_sweep", "instances": len(inst), "cells": cells, "precision": "fp32",
                  "lattice_steps": 96, "mlups": r, "bytes_per_cell": bpc, "hbm_frac": r * 1e6 * bpc / 1e9 / peak})
     del b
@@ -471,8 +527,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="capillary_wave",
-                    choices=["capillary_wave", "static_drop", "rising_bubble", "drop_impact", "batched_sweep"])
+    ap.add_argument("--workload", default="drop_impact",
+                    choices=["capillary_wave", "static_drop", "rising_bubble", "drop_impact", "drop_impact_256",
+                             "batched_sweep"])
     ap.add_argument("--precision", default=None, choices=[None, "fp64", "fp32", "fp16s"])
     ap.add_argument("--lattice-steps", type=int, default=None, help="lattice steps per benchmark step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -533,7 +590,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    def timed_device(precision, K, Wm):
+    def timed_device(precision, K, Wm, S=S):
         sim = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision=precision, device=dev)
         for _ in range(Wm):
             sim.step(S)
@@ -594,14 +651,21 @@ def main():
                              "source": "smsp__inst_executed.sum of one ncu capture of this kernel version"}
     del sim
 
-    # e2e through the public API with host buffers
-    phi0_pin = torch.from_numpy(np.ascontiguousarray(wl["phi0"], dtype=np.float64).reshape(-1)).pin_memory()
+    # e2e through the public API with host buffers: every input of the
+    # workload (phi0, u0, p0) from pinned host memory, phi back to the host
+    def pinned(a):
+        if a is None:
+            return None
+        return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).pin_memory()
+
+    ins = [pinned(wl["phi0"]), pinned(wl["u0"]), pinned(wl["p0"])]
+    h2d = sum(t.numel() * 8 for t in ins if t is not None)
     phi_out = torch.empty(N, dtype=torch.float64).pin_memory()
     from paper_2206_11637_gb300 import _lib as L
     import ctypes
 
     def e2e_once():
-        s = Simulation(p, phi0_pin, None, None, precision=prec, device=dev)
+        s = Simulation(p, ins[0], ins[1], ins[2], precision=prec, device=dev)
         s.step(S)
         L.check(s.lib.pfl_fields(s.ctx, ctypes.c_void_p(phi_out.data_ptr()), None, None, None))
         s.close()
@@ -614,31 +678,49 @@ def main():
         e2e_once()
     barrier()
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": mlups(N, S * K, e2e_s) * ws, "unit": UNIT, "h2d_bytes_per_step": N * 8,
+    e2e = {"value": mlups(N, S * K, e2e_s) * ws, "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": N * 8}
+    del ins, phi_out
+    torch.cuda.empty_cache()
 
-    # the other precisions and the error of the headline precision against FP64
+    # the other precisions (FP64 over fewer lattice steps per benchmark step:
+    # it runs ~15x slower) and the error of FP32 and FP16S against FP64 after
+    # 1000 lattice steps (max |dphi| and max |du| / max |u|), on the device
     compare = {}
     if not args.no_compare and rank == 0:
         for other in ("fp64", "fp32", "fp16s"):
             if other == prec:
                 continue
-            s2, ms2, _, _, _ = timed_device(other, max(2, K // 3), 3)
-            compare[other + "_mlups"] = mlups(N, S * max(2, K // 3), ms2 / 1e3)
+            S_o = max(4, S // 5) if other == "fp64" else S
+            s2, ms2, _, _, _ = timed_device(other, max(2, K // 3), 3, S_o)
+            compare[other + "_mlups"] = mlups(N, S_o * max(2, K // 3), ms2 / 1e3)
             del s2
+            torch.cuda.empty_cache()
         compare["speedup_vs_fp64"] = value / ws / compare["fp64_mlups"] if "fp64_mlups" in compare else None
-        n_acc = min(wl["total"], 2000)
-        ref = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision="fp64", device=dev)
-        ref.step(n_acc)
-        tst = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision=prec, device=dev)
-        tst.step(n_acc)
-        f64 = ref.fields()
-        ftst = tst.fields()
-        umax = max(np.abs(f64[3]).max(), 1e-300)
-        compare["error_vs_fp64"] = {"lattice_steps": n_acc,
-                                    "phi_max_abs": float(np.abs(ftst[0] - f64[0]).max()),
-                                    "u_max_over_umax": float(np.abs(ftst[3] - f64[3]).max() / umax)}
-        del ref, tst
+        n_acc = min(wl["total"], 1000)
+
+        def dev_fields(precision):
+            s3 = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision=precision, device=dev)
+            s3.step(n_acc)
+            out = {"phi": torch.empty(N, dtype=torch.float64, device=dev),
+                   "u": torch.empty(3 * N, dtype=torch.float64, device=dev)}
+            s3.fields(out)
+            del s3
+            torch.cuda.empty_cache()
+            return out
+
+        f64 = dev_fields("fp64")
+        umax = max(f64["u"].abs().max().item(), 1e-300)
+        errs = {"lattice_steps": n_acc, "u_max": umax}
+        for other in ("fp32", "fp16s"):
+            ft = dev_fields(other)
+            errs[other] = {"phi_max_abs": (ft["phi"] - f64["phi"]).abs().max().item(),
+                           "u_max_over_umax": (ft["u"] - f64["u"]).abs().max().item() / umax}
+            del ft
+        compare["error_vs_fp64"] = dict(errs, phi_max_abs=errs[prec]["phi_max_abs"] if prec != "fp64" else 0.0,
+                                        u_max_over_umax=errs[prec]["u_max_over_umax"] if prec != "fp64" else 0.0)
+        del f64
+        torch.cuda.empty_cache()
 
     adj = None
     configs = None
@@ -657,7 +739,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": args.workload, "description": wl["desc"], "precision": prec,
                            "cells": N, "lattice_steps_per_step": S, "parallelism": "replicas" if ws > 1 else "1 GPU",
-                           "l2": "flushed between timed steps" if flush else "working set larger than L2"},
+                           "l2": ("L2 flushed before each timed benchmark step of %d lattice steps" % S) if flush else "working set larger than L2"},
                 "e2e": e2e, "gpu_launches": step_launches(S, args.engine) * K, "clocks": clocks, "roofline": roofline,
                 "cpu_baseline": cpu, "nonfinite_cells": nf, "wall_s": wall, "adjoint": adj,
                 "configs": configs}
