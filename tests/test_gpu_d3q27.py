@@ -87,14 +87,41 @@ def test_fp64_parity_d3q27(name):
     assert rel(h, oh) < tol and rel(g, og) < tol
 
 
+# Reduced precision after 1000 steps of the noisy static drop at the stated
+# bars (FP32 1e-5, FP16S 1e-3; phi and u / u_max).  phi meets them; FP32 misses
+# on u / u_max (measured 5.3e-5: the flow is the decay of seeded noise, u_max ~
+# 1e-4), an expected failure (strict) with its measured level held by a second
+# test; FP16S meets its bar (u / u_max 9.8e-4).
+_q27_cache = {}
+
+
+def q27_errors(precision):
+    if precision not in _q27_cache:
+        p, phi0, u0, _ = q27(W.static_drop(32, 10.0, u_noise=1e-3, seed=1234))
+        s = sim(p, phi0, u0, None, precision)
+        o = oracle.from_params(p, phi0, u0, None)
+        s.step(1000)
+        o.step(1000, THREADS)
+        phi, _, _, u = s.fields()
+        ophi, _, _, ou = o.fields()
+        _q27_cache[precision] = (float(np.abs(phi - ophi).max()), rel(u, ou))
+    return _q27_cache[precision]
+
+
 @pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16s", 1e-3)])
 def test_reduced_precision_parity_d3q27(precision, tol):
-    p, phi0, u0, _ = q27(W.static_drop(32, 10.0, u_noise=1e-3, seed=1234))
-    s = sim(p, phi0, u0, None, precision)
-    o = oracle.from_params(p, phi0, u0, None)
-    s.step(1000)
-    o.step(1000, THREADS)
-    assert rel(s.fields()[0], o.fields()[0]) <= tol
+    assert q27_errors(precision)[0] <= tol
+
+
+@pytest.mark.parametrize("precision,tol", [
+    pytest.param("fp32", 1e-5, marks=pytest.mark.xfail(strict=True, reason="u / u_max measured 5.3e-5, bar 1e-5")),
+    ("fp16s", 1e-3)])
+def test_reduced_precision_u_d3q27(precision, tol):
+    assert q27_errors(precision)[1] <= tol
+
+
+def test_reduced_precision_u_d3q27_fp32_measured_level():
+    assert q27_errors("fp32")[1] <= 1.1e-4
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])

@@ -26,6 +26,9 @@ def rel(a, b):
     return np.abs(a - b).max() / (s if s > 0 else 1.0)
 
 
+UBAR = {"fp64": 1e-12, "fp32": 1e-5, "fp16s": 1e-3}   # u / u_max bars
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("fp16s", 2e-3)])
 def test_capillary_wave_200x400_one_step(precision, tol):
     from paper_2206_11637_gb300.pflbm import Simulation
@@ -40,7 +43,7 @@ def test_capillary_wave_200x400_one_step(precision, tol):
     phi, _, pr, u = s.fields()
     ophi, _, opr, ou = o.fields()
     assert rel(phi, ophi) < tol
-    assert rel(u, ou) < tol * 50
+    assert rel(u, ou) < UBAR[precision]
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16s"])
@@ -56,25 +59,46 @@ def test_rising_bubble_full_size_properties(precision):
     assert abs(out[0] - m0) / m0 < tol
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-6), ("fp16s", 2e-3)])
+_bubble_cache = {}
+
+
+def bubble_one_step(precision):
+    """(phi rel. error, u / u_max error) of one step of the full bubble."""
+    if precision not in _bubble_cache:
+        from paper_2206_11637_gb300.pflbm import Simulation
+        p, phi0, u0, p0 = W.rising_bubble()
+        s = Simulation(p, phi0, u0, p0, precision=precision)
+        s.step(11)
+        h, g = s.populations()
+        o = oracle.from_params(p, phi0, u0, p0)
+        o.set_populations(h, g)
+        del h, g
+        s.step(1)
+        o.step(1, 0)
+        phi, _, _, u = s.fields()
+        ophi, _, _, ou = o.fields()
+        assert np.all(np.isfinite(phi))
+        _bubble_cache[precision] = (rel(phi, ophi), rel(u, ou))
+    return _bubble_cache[precision]
+
+
+@pytest.mark.parametrize("precision,tol", [
+    ("fp64", 1e-12), ("fp32", 2e-6),
+    pytest.param("fp16s", 2e-3, marks=pytest.mark.xfail(strict=True, reason="u / u_max measured 1.14e-3, bar 1e-3"))])
 def test_rising_bubble_128x384x128_one_step(precision, tol):
     """The full 6.29 M-cell bubble (walls everywhere, gravity, hydrostatic
-    start): one GPU step against one oracle step from the same populations."""
-    from paper_2206_11637_gb300.pflbm import Simulation
-    p, phi0, u0, p0 = W.rising_bubble()
-    s = Simulation(p, phi0, u0, p0, precision=precision)
-    s.step(11)
-    h, g = s.populations()
-    o = oracle.from_params(p, phi0, u0, p0)
-    o.set_populations(h, g)
-    del h, g
-    s.step(1)
-    o.step(1, 0)
-    phi, _, _, u = s.fields()
-    ophi, _, _, ou = o.fields()
-    assert np.all(np.isfinite(phi))
-    assert rel(phi, ophi) < tol
-    assert rel(u, ou) < tol * 50
+    start): one GPU step against one oracle step from the same populations.
+    FP16S misses the u bar in the gas by a hair (one step of FP16 rounding
+    where the gas moves fastest); its phi meets the bar."""
+    e_phi, e_u = bubble_one_step(precision)
+    assert e_phi < tol
+    assert e_u < UBAR[precision]
+
+
+def test_rising_bubble_128x384x128_one_step_fp16s_levels():
+    e_phi, e_u = bubble_one_step("fp16s")
+    assert e_phi < 2e-3
+    assert e_u < 2.5e-3
 
 
 @pytest.mark.parametrize("precision", ["fp32", "fp16s"])

@@ -3,7 +3,7 @@
 Tolerances: FP64 storage and arithmetic agree with the oracle to 1e-10 (max
 relative error: max |gpu - oracle| / max |oracle| per field) after many steps;
 FP32 to 1e-5 on phi and u / u_max; FP16-shifted storage with FP32 arithmetic
-to 1e-3.  Sizes span many 256-cell blocks and a ragged tail; the edge cases
+to 1e-3 (the measured misses on u / u_max are marked below).  Sizes span many 256-cell blocks and a ragged tail; the edge cases
 are single-cell-thick (quasi-2D) lattices, walls on every face, BGK mode and
 the set/get population round trip.
 """
@@ -132,17 +132,71 @@ def test_single_cell_thick_directions():
         compare_fields(s, o, 1e-10, 1e-10, 1e-10)
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16s", 1e-3)])
-def test_reduced_precision_parity(precision, tol):
-    p, phi0, u0, _ = W.static_drop(32, 10.0, u_noise=1e-3, seed=1234)
-    s = sim(p, phi0, u0, None, precision)
-    o = oracle.from_params(p, phi0, u0, None)
-    s.step(1000)
-    o.step(1000, THREADS)
-    phi, _, _, u = s.fields()
-    ophi, _, _, ou = o.fields()
-    assert rel(phi, ophi) <= tol
-    assert rel(u, ou) <= tol * 10   # u / u_max: spurious currents are tiny here
+# Reduced precision against the oracle after many steps, at the stated bars:
+# FP32 1e-5 and shifted FP16 1e-3 on phi (max abs) and on u / u_max.  phi meets
+# them on every case.  u / u_max misses them where the flow is only the decay
+# of seeded noise and spurious currents (u_max ~ 1e-4) or a slow wave: the
+# values below were measured on a GB300 (the FP64 run started from the rounded
+# initial state stays at 1e-8 to 1e-5, so the misses come from the rounding of
+# every step, not from the start).  Those cases are expected failures (strict:
+# meeting the bar fails them, so the marks stay true), and a second test holds
+# each at twice its measured level, so a regression still shows.
+BARS = {"fp32": 1e-5, "fp16s": 1e-3}
+RP_CASES = {
+    "static_drop_32": (lambda: W.static_drop(32, 10.0, u_noise=1e-3, seed=1234), 1000),
+    "wave_walls_40x48": (lambda: W.capillary_wave(40, ny=48, a0=1.5, xi=5.0, sigma=1e-4, nu=0.01), 400),
+    "impact_64x48x64": (lambda: W.drop_impact(64, 48, 64, D=12.0, depth=16.0, gap=2.0), 300),
+}
+U_MISSES = {("static_drop_32", "fp32"): 6.5e-5, ("static_drop_32", "fp16s"): 1.3e-3,
+            ("wave_walls_40x48", "fp16s"): 2.2e-3}
+_rp_cache = {}
+
+
+def rp_errors(name, precision):
+    """(max |dphi|, max |du| / max |u|) of a case against the oracle."""
+    key = (name, precision)
+    if key not in _rp_cache:
+        build, steps = RP_CASES[name]
+        if name not in _rp_cache:
+            p, phi0, u0, p0 = build()
+            o = oracle.from_params(p, phi0, u0, p0)
+            o.step(steps, THREADS)
+            _rp_cache[name] = o.fields()
+        p, phi0, u0, p0 = build()
+        s = sim(p, phi0, u0, p0, precision)
+        s.step(steps)
+        phi, _, _, u = s.fields()
+        ophi, _, _, ou = _rp_cache[name]
+        assert np.all(np.isfinite(phi)) and np.all(np.isfinite(u))
+        _rp_cache[key] = (float(np.abs(phi - ophi).max()), rel(u, ou))
+    return _rp_cache[key]
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16s"])
+@pytest.mark.parametrize("name", list(RP_CASES))
+def test_reduced_precision_phi(name, precision):
+    assert rp_errors(name, precision)[0] <= BARS[precision]
+
+
+def _u_params():
+    out = []
+    for name in RP_CASES:
+        for prec in ("fp32", "fp16s"):
+            miss = U_MISSES.get((name, prec))
+            marks = [pytest.mark.xfail(strict=True, reason="u / u_max measured %.1e, bar %.0e" % (miss, BARS[prec]))] \
+                if miss else []
+            out.append(pytest.param(name, prec, marks=marks, id="%s-%s" % (name, prec)))
+    return out
+
+
+@pytest.mark.parametrize("name,precision", _u_params())
+def test_reduced_precision_u(name, precision):
+    assert rp_errors(name, precision)[1] <= BARS[precision]
+
+
+@pytest.mark.parametrize("name,precision", list(U_MISSES))
+def test_reduced_precision_u_measured_level(name, precision):
+    assert rp_errors(name, precision)[1] <= 2 * U_MISSES[(name, precision)]
 
 
 def test_mass_conservation_gpu_fp64():
@@ -184,7 +238,7 @@ def test_population_roundtrip_and_one_step(precision):
     o.set_populations(h2, g2)   # same rounded start on both sides
     o.step(1, THREADS)
     tol = {"fp64": 1e-12, "fp32": 1e-6, "fp16s": 1e-3}[precision]
-    compare_fields(s, o, tol, tol * 10, None)
+    compare_fields(s, o, tol, {"fp64": 1e-12, "fp32": 1e-5, "fp16s": 1e-3}[precision], None)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
