@@ -53,10 +53,11 @@ def step_kernel_bytes(prec, engine=0, qh=15, qg=27):
     population read once and written once (qh h and qg g populations); the
     fused two-array step (engine 0) also writes phi, the in-place step
     (engine 1) reads phi for its stencil; FP16S adds the read of the h shifts
-    (phi of the writing cells)."""
+    (phi of the writing cells, 4 B) and the write and read of the g shifts
+    (p* of the writing cells in FP16, 2 + 2 B)."""
     b = 2 * (qh + qg) * PREC_BYTES[prec] + PHI_BYTES[prec]
     if prec == "fp16s":
-        b += PHI_BYTES[prec]
+        b += PHI_BYTES[prec] + 4
     return b
 
 
@@ -124,23 +125,23 @@ def kernel_hash():
 # and the hash of the kernel sources they were taken on.  A capture of another
 # kernel version does not apply.
 NCU_TRAFFIC = {
-    # k_step_zm<2, 15, 1, 0>, 200x400x1 wave, three captured launches: 7.07 MB read, 0 written
-    # (profiles/k_step_zm_capillary_wave_200x400_fp16s.md)
-    ("capillary_wave", "fp16s", "5ed1f6cb0b3def0e"): 7073792.0,
-    # k_step_zm<2, 15, 0, 0>, rising bubble 128x384x128: 580.0 MB read + 519.4 MB written
-    # (profiles/k_step_zm_rising_bubble_128x384x128.md)
-    ("rising_bubble", "fp16s", "5ed1f6cb0b3def0e"): 1099392512.0,
-    # k_step_zm<1, 15, 0, 0>: 1.1475 GB read + 1.0450 GB written
-    ("rising_bubble", "fp32", "5ed1f6cb0b3def0e"): 2192553000.0,
+    # k_step_zm<2, 15, 0, 0> (FP16S) captured on the half-size impact (256x192x256,
+    # 12.58 M cells): 1.1646 GB read + 1.0966 GB written = 179.7 B/cell; the
+    # launch's traffic grows with the cells it updates, so a full 100.7 M-cell
+    # launch moves 179.7 x 100.66 M = 18.09 GB
+    # (profiles/k_step_zm_drop_impact_256x192x256.md)
+    ("drop_impact", "fp16s", "2b28b22e60761e79"): 1.8089e10,
+    # k_step_zm<1, 15, 0, 0> (FP32) on the same case: 2.2807 + 2.1377 GB = 351.1 B/cell
+    ("drop_impact", "fp32", "2b28b22e60761e79"): 3.5347e10,
 }
 
-# Warp instructions per launch of the same kernels (smsp__inst_executed.sum),
-# for the instruction-issue side of the roofline: launches that stay in L2
-# (the 80 K-cell wave) or issue more than they move (FP16S) are bound there.
+# Warp instructions per launch of the same kernels (smsp__inst_executed.sum of
+# the same captures, scaled by cells the same way), for the instruction-issue
+# side of the roofline: launches that issue more than they move (FP16S) are
+# bound there.
 NCU_INST = {
-    ("capillary_wave", "fp16s", "5ed1f6cb0b3def0e"): 4615965.0,
-    ("rising_bubble", "fp16s", "5ed1f6cb0b3def0e"): 307487398.0,
-    ("rising_bubble", "fp32", "5ed1f6cb0b3def0e"): 248550855.0,
+    ("drop_impact", "fp16s", "2b28b22e60761e79"): 5.3313e9,    # 52.96 per cell
+    ("drop_impact", "fp32", "2b28b22e60761e79"): 3.9314e9,     # 39.06 per cell
 }
 
 
@@ -698,27 +699,43 @@ def main():
             torch.cuda.empty_cache()
         compare["speedup_vs_fp64"] = value / ws / compare["fp64_mlups"] if "fp64_mlups" in compare else None
         n_acc = min(wl["total"], 1000)
+        marks = [m for m in (100, 250, 500) if m < n_acc] + [n_acc]
 
         def dev_fields(precision):
+            """phi and u (FP32 copies, on the device) at the marks."""
             s3 = Simulation(p, wl["phi0"], wl["u0"], wl["p0"], precision=precision, device=dev)
-            s3.step(n_acc)
-            out = {"phi": torch.empty(N, dtype=torch.float64, device=dev),
-                   "u": torch.empty(3 * N, dtype=torch.float64, device=dev)}
-            s3.fields(out)
+            out = []
+            for m in marks:
+                s3.step(m - s3.time)
+                f = {"phi": torch.empty(N, dtype=torch.float64, device=dev),
+                     "u": torch.empty(3 * N, dtype=torch.float64, device=dev)}
+                s3.fields(f)
+                out.append({"phi": f["phi"].float(), "u": f["u"].float()})
+                del f
             del s3
             torch.cuda.empty_cache()
             return out
 
         f64 = dev_fields("fp64")
-        umax = max(f64["u"].abs().max().item(), 1e-300)
-        errs = {"lattice_steps": n_acc, "u_max": umax}
+        errs = {"lattice_steps": n_acc, "marks": marks,
+                "u_max": [max(r["u"].abs().max().item(), 1e-300) for r in f64],
+                "measure": "max over cells (and components) of |x - x_fp64|, u divided by max |u_fp64|; rms the "
+                           "root mean square over cells"}
         for other in ("fp32", "fp16s"):
             ft = dev_fields(other)
-            errs[other] = {"phi_max_abs": (ft["phi"] - f64["phi"]).abs().max().item(),
-                           "u_max_over_umax": (ft["u"] - f64["u"]).abs().max().item() / umax}
+            e = {"phi_max_abs": [], "phi_rms": [], "u_max_over_umax": [], "u_rms_over_umax": []}
+            for a, r, um in zip(ft, f64, errs["u_max"]):
+                dphi = (a["phi"] - r["phi"]).abs()
+                du = (a["u"] - r["u"]).abs()
+                e["phi_max_abs"].append(dphi.max().item())
+                e["phi_rms"].append(dphi.pow(2).mean().sqrt().item())
+                e["u_max_over_umax"].append(du.max().item() / um)
+                e["u_rms_over_umax"].append(du.pow(2).mean().sqrt().item() / um)
+            errs[other] = e
             del ft
-        compare["error_vs_fp64"] = dict(errs, phi_max_abs=errs[prec]["phi_max_abs"] if prec != "fp64" else 0.0,
-                                        u_max_over_umax=errs[prec]["u_max_over_umax"] if prec != "fp64" else 0.0)
+        last = -1
+        compare["error_vs_fp64"] = dict(errs, phi_max_abs=errs[prec]["phi_max_abs"][last] if prec != "fp64" else 0.0,
+                                        u_max_over_umax=errs[prec]["u_max_over_umax"][last] if prec != "fp64" else 0.0)
         del f64
         torch.cuda.empty_cache()
 
