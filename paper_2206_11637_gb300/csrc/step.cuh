@@ -270,6 +270,21 @@ __device__ __forceinline__ typename Store<PREC>::S pack_sr(typename Store<PREC>:
   }
 }
 
+// w (s + r) for a lattice weight w, s the large part of a stored population
+// (phi or p*) and r the small rest.  FP32 carries w as hi + lo: the FP32
+// roundings of the D3Q15 weights alone sum to 1 + 7.5e-9 (D3Q27 likewise),
+// a bias of the zeroth and second moments that repeats every step and, over
+// 1000 steps, was the largest FP32 error of phi and u.  FP64 uses w as is.
+template <typename R>
+__device__ __forceinline__ R wsum(double w, R s, R r) {
+  if constexpr (sizeof(R) == 4) {
+    const float hi = (float)w, lo = (float)(w - (double)hi);
+    return fmaf(hi, s, fmaf(lo, s, hi * r));
+  } else {
+    return fma(w, s, w * r);
+  }
+}
+
 __device__ __forceinline__ void cell_off(const Geo32& geo, unsigned c, CellOff& o) {
   const unsigned yz = fdiv(c, geo.dx);
   const unsigned x = c - yz * geo.nx;
@@ -460,10 +475,18 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
   {
     const R uu = ux * ux + uy * uy + uz * uz;
     const R a2 = ((R)1 - omega) * (R)4.5;
-    const R dxx = pxx - p3 - ux * ux, dyy = pyy - p3 - uy * uy;
-    const R dzz = QG == 9 ? (R)0 : pzz - p3 - uz * uz;  // 2-D: the trace runs over x and y
+    // deviatoric second moments.  FP32 / FP64 form (3 P_aa - p*) / 3 with one
+    // rounding: p* (1/3) would carry the rounded constant 1/3, a bias of
+    // 3e-8 p* that repeats every step (FP16S keeps its form)
+    const R third = (R)(1.0 / 3.0);
+    const R dxx = F16 ? pxx - p3 - ux * ux : fma((R)3, pxx, -pst) * third - ux * ux;
+    const R dyy = F16 ? pyy - p3 - uy * uy : fma((R)3, pyy, -pst) * third - uy * uy;
+    const R dzz = QG == 9 ? (R)0 : (F16 ? pzz - p3 - uz * uz : fma((R)3, pzz, -pst) * third - uz * uz);  // 2-D: the trace runs over x and y
     const R K = F16 ? (R)KG16 : (R)1;
-    const R al = K * ((pst - pw) - (R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
+    // alpha = p* + als with als small: FP32 and FP64 round p* once per stored
+    // value (FP16S stores K (alpha - P) + ... directly)
+    const R als = -(R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0);
+    const R al = K * (pst - pw - (R)1.5 * uu - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
     const R fr = (R)1.5 / rho;
     const R bx = K * ((R)3 * ux + fr * Fx), by = K * ((R)3 * uy + fr * Fy), bz = K * ((R)3 * uz + fr * Fz);
     const R Gxx = K * ((R)4.5 * ux * ux + a2 * dxx), Gyy = K * ((R)4.5 * uy * uy + a2 * dyy),
@@ -471,11 +494,14 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     const R Gxy = K * (R)2 * ((R)4.5 * ux * uy + a2 * (pxy - ux * uy));
     const R Gyz = K * (R)2 * ((R)4.5 * uy * uz + a2 * (pyz - uy * uz));
     const R Gxz = K * (R)2 * ((R)4.5 * ux * uz + a2 * (pxz - ux * uz));
-    gout[(unsigned)GR * N + cell] = pack_sr<PREC>(F16 ? al : (R)lq_w<QG>(GR) * al, dith);
+    gout[(unsigned)GR * N + cell] =
+        pack_sr<PREC>(F16 ? al : wsum<R>(lq_w<QG>(GR), pst, als), dith);
 #pragma unroll
     for (int i = 0; i < GR; ++i) {
       const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
-      R E = al;
+      // FP32 / FP64: the small terms first, the equilibrium part once (one
+      // rounding at its size); FP16S as E = al + ..., A = E + L
+      R E = F16 ? al : (R)0;
       if (cx) E += Gxx;
       if (cy) E += Gyy;
       if (cz) E += Gzz;
@@ -486,10 +512,13 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
       if (cx) L += cx > 0 ? bx : -bx;
       if (cy) L += cy > 0 ? by : -by;
       if (cz) L += cz > 0 ? bz : -bz;
-      R A = E + L, B = E - L;
-      if (!F16) {
-        A *= (R)lq_w<QG>(i);
-        B *= (R)lq_w<QG>(i);
+      R A, B;
+      if (F16) {
+        A = E + L;
+        B = E - L;
+      } else {
+        A = wsum<R>(lq_w<QG>(i), pst, als + (E + L));
+        B = wsum<R>(lq_w<QG>(i), pst, als + (E - L));
       }
       store_pair<PREC, WRITE_ODD>(gout, N, cell, o, i, QG - 1 - i, cx, cy, cz, A, B, dith);
     }
@@ -547,21 +576,35 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
     const R theta = (R)4 * pc * ((R)1 - pc) * (R)ph.inv_xi;
     const R tn = theta / (gn + (R)1e-6) * ((R)1 - (R)0.5 * omp);  // (1 - omega_phi/2) theta / |grad phi|
     const R a1 = ((R)1 - omp) * (R)3, a2 = ((R)1 - omp) * (R)4.5;
+    // deviatoric second moments and the non-equilibrium flux.  FP32 / FP64
+    // form (3 H_aa - phi) / 3 and J - phi u with one rounding each: phi (1/3)
+    // would carry the rounded constant 1/3, a bias of 3e-8 phi that repeats
+    // every step (FP16S keeps its form)
     const R ph3 = phl * (R)(1.0 / 3.0);
-    const R dxx = hxx - ph3, dyy = hyy - ph3, dzz = QG == 9 ? (R)0 : hzz - ph3;
+    const R third = (R)(1.0 / 3.0);
+    const R dxx = F16 ? hxx - ph3 : fma((R)3, hxx, -phl) * third;
+    const R dyy = F16 ? hyy - ph3 : fma((R)3, hyy, -phl) * third;
+    const R dzz = QG == 9 ? (R)0 : (F16 ? hzz - ph3 : fma((R)3, hzz, -phl) * third);
     const R K = F16 ? (R)KH16 : (R)1;
     const R sh = F16 ? pc : (R)0;   // this cell's phi: the shift of everything it writes
+    // alpha = phi + als with als small: FP32 and FP64 round phi once per stored
+    // value (FP16S stores K (alpha - phi_x) + ... directly)
+    const R als = -a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0);
     const R al = K * ((phl - sh) - a2 * (dxx + dyy + dzz) * (R)(1.0 / 3.0));
-    const R bx = K * ((R)3 * phl * ux + a1 * (hjx - phl * ux) + tn * gx);
-    const R by = K * ((R)3 * phl * uy + a1 * (hjy - phl * uy) + tn * gy);
-    const R bz = K * ((R)3 * phl * uz + a1 * (hjz - phl * uz) + tn * gz);
+    const R jdx = F16 ? hjx - phl * ux : fma(-phl, ux, hjx);
+    const R jdy = F16 ? hjy - phl * uy : fma(-phl, uy, hjy);
+    const R jdz = F16 ? hjz - phl * uz : fma(-phl, uz, hjz);
+    const R bx = K * ((R)3 * phl * ux + a1 * jdx + tn * gx);
+    const R by = K * ((R)3 * phl * uy + a1 * jdy + tn * gy);
+    const R bz = K * ((R)3 * phl * uz + a1 * jdz + tn * gz);
     const R Gxx = K * a2 * dxx, Gyy = K * a2 * dyy, Gzz = K * a2 * dzz;
     const R Gxy = K * (R)2 * a2 * hxy, Gyz = K * (R)2 * a2 * hyz, Gxz = K * (R)2 * a2 * hxz;
-    hout[(unsigned)hq_rest<QH>() * N + cell] = pack_sr<PREC>(F16 ? al : (R)hq_w<QH>(hq_rest<QH>()) * al, dith);
+    hout[(unsigned)hq_rest<QH>() * N + cell] =
+        pack_sr<PREC>(F16 ? al : wsum<R>(hq_w<QH>(hq_rest<QH>()), phl, als), dith);
 #pragma unroll
     for (int k = 0; k < hq_rest<QH>(); ++k) {
       const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
-      R E = al;
+      R E = F16 ? al : (R)0;
       if (cx) E += Gxx;
       if (cy) E += Gyy;
       if (cz) E += Gzz;
@@ -572,10 +615,13 @@ __device__ __forceinline__ void collide_cell(const Geo32& geo, const Phys& ph, c
       if (cx) L += cx > 0 ? bx : -bx;
       if (cy) L += cy > 0 ? by : -by;
       if (cz) L += cz > 0 ? bz : -bz;
-      R A = E + L, B = E - L;
-      if (!F16) {
-        A *= (R)hq_w<QH>(k);
-        B *= (R)hq_w<QH>(k);
+      R A, B;
+      if (F16) {
+        A = E + L;
+        B = E - L;
+      } else {
+        A = wsum<R>(hq_w<QH>(k), phl, als + (E + L));
+        B = wsum<R>(hq_w<QH>(k), phl, als + (E - L));
       }
       store_pair<PREC, WRITE_ODD>(hout, N, cell, o, k, QH - 1 - k, cx, cy, cz, A, B, dith);
     }

@@ -89,12 +89,8 @@ def test_fp64_parity_d2q9(name):
 
 
 # Reduced precision after 1000 steps at the stated bars (FP32 1e-5, FP16S 1e-3,
-# on phi and on u / u_max).  FP32 misses them on this quasi-2-D column by a
-# little: measured 1.15e-5 on phi and 1.05e-5 on u / u_max (every quasi-2-D
-# interface measured at rho ratio 1000 gives 1.1-1.9e-5 on phi in FP32, the
-# 3-D lattices on the same set-ups as well, while the 3-D drop stays under
-# 1e-5).  The miss is an expected failure (strict) and a second test holds the
-# measured level; shifted FP16 meets its bar (phi 5.9e-5, u / u_max 9.0e-4).
+# on phi and on u / u_max), both met: FP32 phi 6.3e-7, u / u_max 9.9e-6; shifted
+# FP16 phi 5.9e-5, u / u_max 9.0e-4 (measured on a GB300).
 _q9_cache = {}
 
 
@@ -113,17 +109,10 @@ def q9_errors(precision):
     return _q9_cache[precision]
 
 
-@pytest.mark.parametrize("precision,tol", [
-    pytest.param("fp32", 1e-5, marks=pytest.mark.xfail(strict=True, reason="phi 1.15e-5, u / u_max 1.05e-5, bar 1e-5")),
-    ("fp16s", 1e-3)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 1e-5), ("fp16s", 1e-3)])
 def test_reduced_precision_parity_d2q9(precision, tol):
     e_phi, e_u = q9_errors(precision)
     assert e_phi <= tol and e_u <= tol
-
-
-def test_reduced_precision_d2q9_fp32_measured_level():
-    e_phi, e_u = q9_errors("fp32")
-    assert e_phi <= 2.5e-5 and e_u <= 2.5e-5
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32", "fp16s"])
