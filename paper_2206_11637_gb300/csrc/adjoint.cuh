@@ -28,12 +28,19 @@
 namespace pfl {
 
 constexpr int ADJ_THREADS = 128;
-// Resident blocks of k_adj_local per SM the compiler is asked for (0: no bound,
-// 158 registers, 3 blocks).  On the 128x384x128 FP32 bubble (400 steps) the
-// adjoint took 832 ms unbounded, 880 / 856 / 871 ms at 4 / 5 / 6 blocks.
-#ifndef PFL_ADJ_MINB
-#define PFL_ADJ_MINB 0
+// Resident blocks of k_adj_local per SM the compiler is asked for, FP32 (FP64
+// is left unbounded: it runs on the FP64 units, and 5 blocks already spill 0.5
+// KB).  On the 128x384x128 FP32 bubble (400 steps, lambda gathered first),
+// adjoint / forward was 3.43 unbounded (128 registers, 4 blocks), 3.33 at 5
+// (96, no spill), 3.24 at 6 (80, 56 B of spill), 3.22 at 7, 3.20 at 8 (64, 156
+// B); 6 keeps the spill small on every lattice.
+#ifndef PFL_ADJ_MINB32
+#define PFL_ADJ_MINB32 6
 #endif
+template <int PREC>
+constexpr int adj_minb() {
+  return PREC == 1 ? PFL_ADJ_MINB32 : 0;
+}
 // (An L1 prefetch of the lambda gathers on entry, to overlap them with the
 // forward recomputation, doubled the adjoint's time on the same bubble: 831 ->
 // 1691 ms.  It is not used.)
@@ -67,7 +74,7 @@ __device__ __forceinline__ R block_sum3_to(R a, R b, R c, double* out3) {
 }
 
 template <int PREC, int QH, int READ_ODD>
-__global__ void __launch_bounds__(ADJ_THREADS, PFL_ADJ_MINB) k_adj_local(Geo32 geo, Phys ph, AdjPar ap,
+__global__ void __launch_bounds__(ADJ_THREADS, adj_minb<PREC>()) k_adj_local(Geo32 geo, Phys ph, AdjPar ap,
                                                            const typename Store<PREC>::S* __restrict__ h,
                                                            const typename Store<PREC>::S* __restrict__ g,
                                                            const typename Store<PREC>::PhiT* __restrict__ phi,
@@ -87,6 +94,66 @@ __global__ void __launch_bounds__(ADJ_THREADS, PFL_ADJ_MINB) k_adj_local(Geo32 g
     const unsigned N = geo.N;
     CellOff o;
     cell_off(geo, cell, o);
+    // ---------------- adjoints of the post-collision populations
+    // Gathered first: they depend on lambda and the offsets only, so their
+    // loads overlap those of the saved state, and the twenty sums they reduce
+    // to are all that stays live through the forward recomputation (158 -> 128
+    // registers at no bound; adjoint / forward on the 128x384x128 FP32 bubble,
+    // 400 steps: 3.96 -> 3.43).
+    // g: lambda+ of population i of this cell sits where streaming put it
+    R b_al = 0, b_bx = 0, b_by = 0, b_bz = 0, b_Gxx = 0, b_Gyy = 0, b_Gzz = 0, b_Gxy = 0, b_Gyz = 0, b_Gxz = 0;
+    const R* lg = lam_in + (unsigned)QH * N;
+    b_al = (R)lq_w<QG>(GR) * lg[(unsigned)GR * N + cell];
+#pragma unroll
+    for (int i = 0; i < GR; ++i) {
+      const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
+      const int oi = QG - 1 - i;
+      // direction c (index i) went to x + c (slot i) or bounced into slot oi of x
+      const R la = o.valid(cx, cy, cz) ? lg[(unsigned)i * N + cell + (unsigned)o.off(cx, cy, cz)]
+                                       : lg[(unsigned)oi * N + cell];
+      const R lb = o.valid(-cx, -cy, -cz) ? lg[(unsigned)oi * N + cell + (unsigned)o.off(-cx, -cy, -cz)]
+                                          : lg[(unsigned)i * N + cell];
+      const R w = (R)lq_w<QG>(i);
+      const R S = w * (la + lb), D = w * (la - lb);
+      b_al += S;
+      if (cx) b_bx += cx > 0 ? D : -D;
+      if (cy) b_by += cy > 0 ? D : -D;
+      if (cz) b_bz += cz > 0 ? D : -D;
+      if (cx) b_Gxx += S;
+      if (cy) b_Gyy += S;
+      if (cz) b_Gzz += S;
+      if (cx && cy) b_Gxy += (cx * cy > 0) ? S : -S;
+      if (cy && cz) b_Gyz += (cy * cz > 0) ? S : -S;
+      if (cx && cz) b_Gxz += (cx * cz > 0) ? S : -S;
+    }
+    // h
+    R c_al = (R)hq_w<QH>(hq_rest<QH>()) * (lam_in[(unsigned)hq_rest<QH>() * N + cell] + acc_in[cell]), c_bx = 0,
+      c_by = 0, c_bz = 0;
+    R c_Gxx = 0, c_Gyy = 0, c_Gzz = 0, c_Gxy = 0, c_Gyz = 0, c_Gxz = 0;
+#pragma unroll
+    for (int k = 0; k < hq_rest<QH>(); ++k) {
+      const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
+      const int ok = QH - 1 - k;
+      // the slot read and the cell holding it (whose acc belongs to every h slot)
+      const bool va = o.valid(cx, cy, cz), vb = o.valid(-cx, -cy, -cz);
+      const unsigned ya = va ? cell + (unsigned)o.off(cx, cy, cz) : cell;
+      const unsigned yb = vb ? cell + (unsigned)o.off(-cx, -cy, -cz) : cell;
+      const R la = lam_in[(va ? (unsigned)k : (unsigned)ok) * N + ya] + acc_in[ya];
+      const R lb = lam_in[(vb ? (unsigned)ok : (unsigned)k) * N + yb] + acc_in[yb];
+      const R w = (R)hq_w<QH>(k);
+      const R S = w * (la + lb), D = w * (la - lb);
+      c_al += S;
+      if (cx) c_bx += cx > 0 ? D : -D;
+      if (cy) c_by += cy > 0 ? D : -D;
+      if (cz) c_bz += cz > 0 ? D : -D;
+      if (cx) c_Gxx += S;
+      if (cy) c_Gyy += S;
+      if (cz) c_Gzz += S;
+      if (cx && cy) c_Gxy += (cx * cy > 0) ? S : -S;
+      if (cy && cz) c_Gyz += (cy * cz > 0) ? S : -S;
+      if (cx && cz) c_Gxz += (cx * cz > 0) ? S : -S;
+    }
+
     // ---------------- forward recomputation (as in k_step_mrt)
     const R pc = (R)phi[cell];
     R gx = 0, gy = 0, gz = 0, lap = 0;
@@ -183,61 +250,6 @@ __global__ void __launch_bounds__(ADJ_THREADS, PFL_ADJ_MINB) k_adj_local(Geo32 g
     const R a1h = ((R)1 - omp) * (R)3, a2h = ((R)1 - omp) * (R)4.5;
     const R ph3 = phl * (R)(1.0 / 3.0);
     const R dhxx = hxx - ph3, dhyy = hyy - ph3, dhzz = QG == 9 ? (R)0 : hzz - ph3;
-
-    // ---------------- adjoints of the post-collision populations
-    // g: lambda+ of population i of this cell sits where streaming put it
-    R b_al = 0, b_bx = 0, b_by = 0, b_bz = 0, b_Gxx = 0, b_Gyy = 0, b_Gzz = 0, b_Gxy = 0, b_Gyz = 0, b_Gxz = 0;
-    const R* lg = lam_in + (unsigned)QH * N;
-    b_al = (R)lq_w<QG>(GR) * lg[(unsigned)GR * N + cell];
-#pragma unroll
-    for (int i = 0; i < GR; ++i) {
-      const int cx = q27_cx(lq_to27<QG>(i)), cy = q27_cy(lq_to27<QG>(i)), cz = q27_cz(lq_to27<QG>(i));
-      const int oi = QG - 1 - i;
-      // direction c (index i) went to x + c (slot i) or bounced into slot oi of x
-      const R la = o.valid(cx, cy, cz) ? lg[(unsigned)i * N + cell + (unsigned)o.off(cx, cy, cz)]
-                                       : lg[(unsigned)oi * N + cell];
-      const R lb = o.valid(-cx, -cy, -cz) ? lg[(unsigned)oi * N + cell + (unsigned)o.off(-cx, -cy, -cz)]
-                                          : lg[(unsigned)i * N + cell];
-      const R w = (R)lq_w<QG>(i);
-      const R S = w * (la + lb), D = w * (la - lb);
-      b_al += S;
-      if (cx) b_bx += cx > 0 ? D : -D;
-      if (cy) b_by += cy > 0 ? D : -D;
-      if (cz) b_bz += cz > 0 ? D : -D;
-      if (cx) b_Gxx += S;
-      if (cy) b_Gyy += S;
-      if (cz) b_Gzz += S;
-      if (cx && cy) b_Gxy += (cx * cy > 0) ? S : -S;
-      if (cy && cz) b_Gyz += (cy * cz > 0) ? S : -S;
-      if (cx && cz) b_Gxz += (cx * cz > 0) ? S : -S;
-    }
-    // h
-    R c_al = (R)hq_w<QH>(hq_rest<QH>()) * (lam_in[(unsigned)hq_rest<QH>() * N + cell] + acc_in[cell]), c_bx = 0,
-      c_by = 0, c_bz = 0;
-    R c_Gxx = 0, c_Gyy = 0, c_Gzz = 0, c_Gxy = 0, c_Gyz = 0, c_Gxz = 0;
-#pragma unroll
-    for (int k = 0; k < hq_rest<QH>(); ++k) {
-      const int cx = hq_cx<QH>(k), cy = hq_cy<QH>(k), cz = hq_cz<QH>(k);
-      const int ok = QH - 1 - k;
-      // the slot read and the cell holding it (whose acc belongs to every h slot)
-      const bool va = o.valid(cx, cy, cz), vb = o.valid(-cx, -cy, -cz);
-      const unsigned ya = va ? cell + (unsigned)o.off(cx, cy, cz) : cell;
-      const unsigned yb = vb ? cell + (unsigned)o.off(-cx, -cy, -cz) : cell;
-      const R la = lam_in[(va ? (unsigned)k : (unsigned)ok) * N + ya] + acc_in[ya];
-      const R lb = lam_in[(vb ? (unsigned)ok : (unsigned)k) * N + yb] + acc_in[yb];
-      const R w = (R)hq_w<QH>(k);
-      const R S = w * (la + lb), D = w * (la - lb);
-      c_al += S;
-      if (cx) c_bx += cx > 0 ? D : -D;
-      if (cy) c_by += cy > 0 ? D : -D;
-      if (cz) c_bz += cz > 0 ? D : -D;
-      if (cx) c_Gxx += S;
-      if (cy) c_Gyy += S;
-      if (cz) c_Gzz += S;
-      if (cx && cy) c_Gxy += (cx * cy > 0) ? S : -S;
-      if (cy && cz) c_Gyz += (cy * cz > 0) ? S : -S;
-      if (cx && cz) c_Gxz += (cx * cz > 0) ? S : -S;
-    }
 
     // ---------------- reverse sweep of the local map
     // adjoint accumulators of the inputs
