@@ -126,13 +126,13 @@ def kernel_hash():
 # kernel version does not apply.
 NCU_TRAFFIC = {
     # k_step_zm<2, 15, 0, 0> (FP16S) captured on the half-size impact (256x192x256,
-    # 12.58 M cells): 1.1638 GB read + 1.0972 GB written = 179.7 B/cell; the
+    # 12.58 M cells): 1.1640 GB read + 1.0975 GB written = 179.7 B/cell; the
     # launch's traffic grows with the cells it updates, so a full 100.7 M-cell
     # launch moves 179.7 x 100.66 M = 18.09 GB
     # (profiles/k_step_zm_drop_impact_256x192x256.md)
-    ("drop_impact", "fp16s", "fdf79eeaa4a12fa9"): 1.8088e10,
-    # k_step_zm<1, 15, 0, 0> (FP32) on the same case: 2.2611 + 2.1341 GB = 349.3 B/cell
-    ("drop_impact", "fp32", "fdf79eeaa4a12fa9"): 3.5161e10,
+    ("drop_impact", "fp16s", "8f1ed78088adb18e"): 1.8092e10,
+    # k_step_zm<1, 15, 0, 0> (FP32) on the same case: 2.2597 + 2.1340 GB = 349.2 B/cell
+    ("drop_impact", "fp32", "8f1ed78088adb18e"): 3.5149e10,
 }
 
 # Warp instructions per launch of the same kernels (smsp__inst_executed.sum of
@@ -140,8 +140,8 @@ NCU_TRAFFIC = {
 # side of the roofline: launches that issue more than they move (FP16S) are
 # bound there.
 NCU_INST = {
-    ("drop_impact", "fp16s", "fdf79eeaa4a12fa9"): 5.3313e9,    # 52.96 per cell
-    ("drop_impact", "fp32", "fdf79eeaa4a12fa9"): 4.3670e9,     # 43.38 per cell
+    ("drop_impact", "fp16s", "8f1ed78088adb18e"): 5.3313e9,    # 52.96 per cell
+    ("drop_impact", "fp32", "8f1ed78088adb18e"): 4.3670e9,     # 43.38 per cell
 }
 
 

@@ -295,6 +295,17 @@ pfl_status pfl_batch_fields(pfl_batch* b, int i, double* phi, double* rho, doubl
  * kept) and the call returns PFL_ERR_UNSTABLE.  Synchronises. */
 pfl_status pfl_batch_diag(pfl_batch* b, double* out, long long* nonfinite);
 
+/* Launch shape of class cls (0: one z plane, 1: 3-D), in place of the one
+ * the tuner or the default chose: tiles of tile_x x tile_y cells, one block of
+ * tile_x x tile_y threads each (class 0: 32x4, 32x8, and in FP32 16x8; class
+ * 1: 32x8, 16x8, and in FP32 16x16); z_chunk planes per tile (class 1; 0: the
+ * whole lattice); grid blocks of the persistent launch (0: SMs x resident
+ * blocks; capped by the tile count).  Rebuilds the class's work list and the
+ * CUDA graph; results do not depend on the shape (every cell's arithmetic is
+ * the same).  PFL_ERR_ARG for a shape the class and precision do not have.
+ * Synchronises. */
+pfl_status pfl_batch_set_shape(pfl_batch* b, int cls, int tile_x, int tile_y, int z_chunk, int grid);
+
 /* Launch shape chosen for each of the two classes (0: one z plane, 1: 3-D):
  * threads per block, grid blocks and work-list tiles (each array of 2, may be
  * NULL). */

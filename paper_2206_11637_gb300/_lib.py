@@ -98,6 +98,8 @@ def load():
     lib.pfl_batch_diag.argtypes = [P, P, P]
     lib.pfl_batch_shapes.restype = I
     lib.pfl_batch_shapes.argtypes = [P, P, P, P]
+    lib.pfl_batch_set_shape.restype = I
+    lib.pfl_batch_set_shape.argtypes = [P, I, I, I, I, I]
     lib.pfl_batch_time.restype = ctypes.c_longlong
     lib.pfl_batch_time.argtypes = [P]
     lib.pfl_batch_destroy.restype = None

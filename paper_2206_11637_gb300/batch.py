@@ -99,3 +99,9 @@ class Batch:
         n = np.zeros(2, dtype=np.int32)
         L.check(self.lib.pfl_batch_shapes(self.b, _ptr(t), _ptr(g), _ptr(n)))
         return t, g, n
+
+    def set_shape(self, cls, tile_x, tile_y, z_chunk=0, grid=0):
+        """Launch shape of class cls (0: one z plane, 1: 3-D): tile_x x tile_y
+        tiles, z_chunk planes per tile (0: whole lattice), grid blocks (0: SMs x
+        resident blocks)."""
+        L.check(self.lib.pfl_batch_set_shape(self.b, int(cls), int(tile_x), int(tile_y), int(z_chunk), int(grid)))

@@ -64,11 +64,23 @@ struct BTile {
 constexpr int NCLASS = 2;     // class 0: one z plane (quasi-2-D), class 1: 3-D
 constexpr int GRAPH_PAIRS = 8;  // a graph holds 2 * GRAPH_PAIRS lattice steps
 
+// Tiles are handed out by a counter (PFL_BATCH_DYNAMIC = 1): a block takes the
+// next tile of the list when it finishes one, so the large-first list ends
+// with small tiles on every SM; 0 walks the list with a fixed stride.
+#ifndef PFL_BATCH_DYNAMIC
+#define PFL_BATCH_DYNAMIC 1
+#endif
+
 // One lattice step of the instances of one class: a persistent walk over the
-// class's work list (ab: the array pair holding the current state).
-template <int PREC, int TY, int FLAT>
-__global__ void __launch_bounds__(ZM_TX * TY, (PREC == 0 ? PFL_ZM_MINB_FP64 : PFL_ZM_MINB) * ZM_TY / TY)
-    k_batch_zm(const BInst* __restrict__ inst, const BTile* __restrict__ tiles, int ntiles, int ab) {
+// class's work list (ab: the array pair holding the current state), by blocks
+// of TX x TY threads, resident like the single-lattice step's (the same
+// threads per SM).  ctr: the class's two counters (next tile, blocks done),
+// zero at launch; the last block to finish zeroes them for the next launch,
+// which stream order puts after this one.
+template <int PREC, int TX, int TY, int FLAT>
+__global__ void __launch_bounds__(TX * TY, (PREC == 0 ? PFL_ZM_MINB_FP64 : PFL_ZM_MINB) * ZM_TX * ZM_TY / (TX * TY))
+    k_batch_zm(const BInst* __restrict__ inst, const BTile* __restrict__ tiles, int ntiles, int ab,
+               unsigned* __restrict__ ctr) {
   typedef typename Store<PREC>::S S;
   typedef typename Store<PREC>::PhiT PhiT;
   __shared__ Geo32 sgeo;
@@ -76,9 +88,16 @@ __global__ void __launch_bounds__(ZM_TX * TY, (PREC == 0 ? PFL_ZM_MINB_FP64 : PF
   __shared__ int sact;
   __shared__ void* sptr[5];
   __shared__ int szc;
+  __shared__ int snext;
   if (PFL_ZM_PDL) asm volatile("griddepcontrol.wait;" ::: "memory");
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  for (int t = blockIdx.x;; t += gridDim.x) {
+    if (PFL_BATCH_DYNAMIC) {
+      if (tid == 0) snext = (int)atomicAdd(ctr, 1u);
+      __syncthreads();
+      t = snext;
+    }
+    if (t >= ntiles) break;
     const BTile tile = tiles[t];
     if (tid == 0) {
       const BInst* I = inst + tile.inst;
@@ -94,21 +113,34 @@ __global__ void __launch_bounds__(ZM_TX * TY, (PREC == 0 ? PFL_ZM_MINB_FP64 : PF
     }
     __syncthreads();
     if (sact)
-      zm_tile<PREC, 15, TY, FLAT, 0>(sgeo, sph, (const S*)sptr[0], (const S*)sptr[1], (S*)sptr[2], (S*)sptr[3], nullptr,
+      zm_tile<PREC, 15, TY, FLAT, 0, TX>(sgeo, sph, (const S*)sptr[0], (const S*)sptr[1], (S*)sptr[2], (S*)sptr[3], nullptr,
                                      (PhiT*)sptr[4], szc, 0u, nullptr, nullptr, nullptr, tile.bx, tile.by, tile.bz);
-    __syncthreads();  // the next tile refills the shared rings and the instance slot
+    __syncthreads();  // the next tile refills the shared rings, the instance slot and snext
+  }
+  if (PFL_BATCH_DYNAMIC && tid == 0 && atomicAdd(ctr + 1, 1u) == gridDim.x - 1) {
+    ctr[0] = 0;  // every block has taken its last ticket
+    ctr[1] = 0;
   }
 }
 
 struct Shape {
-  int ty;    // tile height (threads per block = ZM_TX * ty); 4 or 8 for one z plane, 8 in 3-D
+  int tx;    // tile width: 32, or 16 (FP32) for instances a few tiles wide
+  int ty;    // tile height (threads per block = tx * ty): 4 or 8 for one z plane, 8 or 16 in 3-D
   int zc;    // z planes per tile (3-D class; 0 = the whole lattice)
   int grid;  // blocks of the persistent launch
 };
 
+// Tile shapes (tx, ty) of each class: every precision takes the first two, FP32
+// also the third.  A 16-wide tile leaves fewer threads idle on lattices that
+// are not a multiple of 32 wide (a 40-wide drop fills 40 of 64 columns in
+// 32-wide tiles, 40 of 48 in 16-wide ones) for a larger share of ring cells.
+constexpr int NSHAPE = 3;
+constexpr int SHAPES[NCLASS][NSHAPE][2] = {{{32, 4}, {32, 8}, {16, 8}}, {{32, 8}, {16, 8}, {16, 16}}};
+constexpr int shapes_for(int prec) { return prec == PFL_FP32 ? 3 : 2; }
+
 struct ClassPlan {
   std::vector<int> members;
-  Shape shape{8, 0, 0};
+  Shape shape{32, 8, 0, 0};
   BTile* tiles = nullptr;  // device
   int ntiles = 0;
 };
@@ -140,7 +172,7 @@ struct pfl_batch {
   std::vector<pfl_params> p;
   std::vector<BInst> inst;     // host copy of the table
   std::vector<size_t> off;     // workspace offset of each instance's buffers
-  size_t table_off, tiles_off, stage_off, red_off;
+  size_t table_off, tiles_off, stage_off, red_off, ctr_off;
   BInst* d_inst;
   ClassPlan cls[NCLASS];
   int ab;                      // the array pair holding the current state
@@ -153,7 +185,7 @@ namespace {
 
 struct BLayout {
   std::vector<size_t> off;
-  size_t table, tiles, stage, red, total;
+  size_t table, tiles, stage, red, ctr, total;
 };
 
 size_t inst_bytes(const pfl_params& p) {
@@ -162,10 +194,10 @@ size_t inst_bytes(const pfl_params& p) {
          2 * align256(N * phi_bytes(p.precision));
 }
 
-// tiles of one instance for a tile height and z chunk
-size_t tiles_of(const pfl_params& p, int ty, int zc) {
+// tiles of one instance for a tile shape and z chunk
+size_t tiles_of(const pfl_params& p, int tx, int ty, int zc) {
   const size_t zc_ = zc > 0 && zc < p.nz ? (size_t)zc : (size_t)p.nz;
-  return (size_t)((p.nx + ZM_TX - 1) / ZM_TX) * ((p.ny + ty - 1) / ty) * ((p.nz + zc_ - 1) / zc_);
+  return (size_t)((p.nx + tx - 1) / tx) * ((p.ny + ty - 1) / ty) * ((p.nz + zc_ - 1) / zc_);
 }
 
 BLayout blayout(const pfl_params* p, int count) {
@@ -176,7 +208,7 @@ BLayout blayout(const pfl_params* p, int count) {
     off += inst_bytes(p[i]);
     const size_t N = (size_t)p[i].nx * p[i].ny * p[i].nz;
     maxN = std::max(maxN, N);
-    tiles += tiles_of(p[i], 4, 1);  // the most tiles any shape takes
+    tiles += tiles_of(p[i], 16, 4, 1);  // at least as many as any shape takes
   }
   L.table = off;
   off = align256(off + (size_t)count * sizeof(BInst) + 256);
@@ -186,22 +218,53 @@ BLayout blayout(const pfl_params* p, int count) {
   off = align256(off + (maxN + 16) * sizeof(double));
   L.red = off;
   off = align256(off + (DIAG_BLOCKS * 10 + 32) * sizeof(double));
+  L.ctr = off;  // tile counters of the two classes
+  off = align256(off + 2 * NCLASS * sizeof(unsigned));
   L.total = off;
   return L;
+}
+
+int shape_index(int cls, const Shape& sh) {
+  for (int j = 0; j < NSHAPE; ++j)
+    if (SHAPES[cls][j][0] == sh.tx && SHAPES[cls][j][1] == sh.ty) return j;
+  return -1;
+}
+
+// kernel function of (precision, class, shape); FP64 has the first two shapes only
+template <int PREC, int CLS>
+const void* batch_fn(int j) {
+  if (j == 0) return (const void*)k_batch_zm<PREC, SHAPES[CLS][0][0], SHAPES[CLS][0][1], CLS == 0>;
+  if (j == 1) return (const void*)k_batch_zm<PREC, SHAPES[CLS][1][0], SHAPES[CLS][1][1], CLS == 0>;
+  if constexpr (PREC == 1) {
+    if (j == 2) return (const void*)k_batch_zm<PREC, SHAPES[CLS][2][0], SHAPES[CLS][2][1], CLS == 0>;
+  }
+  return nullptr;
+}
+
+template <int PREC, int CLS, int J>
+void launch_shape(pfl_batch* b, const ClassPlan& c) {
+  k_batch_zm<PREC, SHAPES[CLS][J][0], SHAPES[CLS][J][1], CLS == 0>
+      <<<c.shape.grid, dim3(SHAPES[CLS][J][0], SHAPES[CLS][J][1]), 0, b->stream>>>(
+          b->d_inst, c.tiles, c.ntiles, b->ab, (unsigned*)(b->ws + b->ctr_off) + 2 * CLS);
+}
+
+template <int PREC, int CLS>
+void launch_class(pfl_batch* b, const ClassPlan& c) {
+  const int j = shape_index(CLS, c.shape);
+  if (j == 0) launch_shape<PREC, CLS, 0>(b, c);
+  if (j == 1) launch_shape<PREC, CLS, 1>(b, c);
+  if constexpr (PREC == 1) {
+    if (j == 2) launch_shape<PREC, CLS, 2>(b, c);
+  }
 }
 
 template <int PREC>
 void launch_class_step(pfl_batch* b, const ClassPlan& c, int cls) {
   if (c.ntiles == 0) return;
-  const int g = c.shape.grid;
-  if (cls == 0) {
-    if (c.shape.ty == 4)
-      k_batch_zm<PREC, 4, 1><<<g, dim3(ZM_TX, 4), 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->ab);
-    else
-      k_batch_zm<PREC, 8, 1><<<g, dim3(ZM_TX, 8), 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->ab);
-  } else {
-    k_batch_zm<PREC, 8, 0><<<g, dim3(ZM_TX, 8), 0, b->stream>>>(b->d_inst, c.tiles, c.ntiles, b->ab);
-  }
+  if (cls == 0)
+    launch_class<PREC, 0>(b, c);
+  else
+    launch_class<PREC, 1>(b, c);
 }
 
 // one lattice step of every instance: the fused step of both classes
@@ -229,7 +292,7 @@ pfl_status build_tiles(pfl_batch* b, ClassPlan& c, const Shape& sh, BTile* dst) 
     const Geo32& g = b->inst[i].geo;
     const int zc = sh.zc > 0 && sh.zc < (int)g.nz ? sh.zc : (int)g.nz;
     b->inst[i].zc = zc;
-    const int nbx = (g.nx + ZM_TX - 1) / ZM_TX, nby = (g.ny + sh.ty - 1) / sh.ty, nbz = (g.nz + zc - 1) / zc;
+    const int nbx = (g.nx + sh.tx - 1) / sh.tx, nby = (g.ny + sh.ty - 1) / sh.ty, nbz = (g.nz + zc - 1) / zc;
     for (int bz = 0; bz < nbz; ++bz)
       for (int by = 0; by < nby; ++by)
         for (int bx = 0; bx < nbx; ++bx)
@@ -306,35 +369,31 @@ pfl_status initial_state(pfl_batch* b, const double* const* phi0, const double* 
   return PFL_OK;
 }
 
-int resident_blocks(int prec, int ty, int flat) {
+int resident_blocks(int prec, int cls, const Shape& sh) {
   int nb = 0;
-  const void* fn = nullptr;
-  if (prec == PFL_FP64)
-    fn = flat ? (ty == 4 ? (const void*)k_batch_zm<0, 4, 1> : (const void*)k_batch_zm<0, 8, 1>)
-              : (const void*)k_batch_zm<0, 8, 0>;
-  else
-    fn = flat ? (ty == 4 ? (const void*)k_batch_zm<1, 4, 1> : (const void*)k_batch_zm<1, 8, 1>)
-              : (const void*)k_batch_zm<1, 8, 0>;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, ZM_TX * ty, 0) != cudaSuccess) {
+  const int j = shape_index(cls, sh);
+  const void* fn = prec == PFL_FP64 ? (cls == 0 ? batch_fn<0, 0>(j) : batch_fn<0, 1>(j))
+                                    : (cls == 0 ? batch_fn<1, 0>(j) : batch_fn<1, 1>(j));
+  if (!fn || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, sh.tx * sh.ty, 0) != cudaSuccess) {
     cudaGetLastError();
     nb = 1;
   }
   return nb < 1 ? 1 : nb;
 }
 
-// Default shape of a class: tile height 4 (one z plane) or 8, the z chunk by
+// Default shape of a class: 32 x 4 tiles (one z plane) or 32 x 8, the z chunk by
 // the cost model of the single-lattice step (waves of resident blocks times
 // zc + 1/2, over the class's largest instance), grid = SMs x resident blocks.
 Shape default_shape(pfl_batch* b, int k) {
-  Shape sh{k == 0 ? 4 : 8, 0, 0};
+  Shape sh{32, k == 0 ? 4 : 8, 0, 0};
   if (k == 1) {
     int big = -1;
     for (int i : b->cls[k].members)
       if (big < 0 || b->inst[i].geo.N > b->inst[big].geo.N) big = i;
     if (big >= 0) {
       const Geo32& g = b->inst[big].geo;
-      const long long slots = (long long)b->sms * resident_blocks(b->prec, 8, 0);
-      const long long bxy = (long long)((g.nx + ZM_TX - 1) / ZM_TX) * ((g.ny + 7) / 8);
+      const long long slots = (long long)b->sms * resident_blocks(b->prec, 1, sh);
+      const long long bxy = (long long)((g.nx + sh.tx - 1) / sh.tx) * ((g.ny + sh.ty - 1) / sh.ty);
       double best = 1e300;
       for (int zc = (int)g.nz; zc >= 1; --zc) {
         const long long blocks = bxy * ((g.nz + zc - 1) / zc);
@@ -346,22 +405,23 @@ Shape default_shape(pfl_batch* b, int k) {
       }
     }
   }
-  sh.grid = b->sms * resident_blocks(b->prec, sh.ty, k == 0);
+  sh.grid = b->sms * resident_blocks(b->prec, k, sh);
   return sh;
 }
 
 // Autotuner: for each class, time every candidate shape over two lattice
 // steps of the whole batch (the other class at its current shape) and keep
-// the fastest.  Candidates: tile height 4 or 8 (one z plane) or the z chunk
-// (the cost model's, 8, 16, 32, the whole lattice) in 3-D, each with grids of
-// 1, 2 and 4 x SMs x resident blocks, capped by the tile count.
+// the fastest.  Candidates: the class's tile shapes (SHAPES; FP64 the 32-wide
+// ones), in 3-D each with the z chunks of the cost model, 8, 16, 32 and the
+// whole lattice, and each with grids of 1, 2 and 4 x SMs x resident blocks,
+// capped by the tile count.
 pfl_status tune(pfl_batch* b) {
   BTile* dst[NCLASS];
   BTile* base = (BTile*)(b->ws + b->tiles_off);
   size_t cursor = 0;
   for (int k = 0; k < NCLASS; ++k) {
     dst[k] = base + cursor;
-    for (int i : b->cls[k].members) cursor += tiles_of(b->p[i], 4, 1);
+    for (int i : b->cls[k].members) cursor += tiles_of(b->p[i], 16, 4, 1);
   }
   cudaEvent_t e0, e1;
   BTRY(cudaEventCreate(&e0));
@@ -376,13 +436,16 @@ pfl_status tune(pfl_batch* b) {
     if (c.members.empty()) continue;
     std::vector<Shape> cand;
     const Shape d = c.shape;
-    if (k == 0) {
-      for (int ty : {4, 8}) cand.push_back(Shape{ty, 0, 0});
-    } else {
-      for (int zc : {d.zc, 8, 16, 32, 0}) {
-        bool dup = false;
-        for (const Shape& q : cand) dup |= q.zc == zc;
-        if (!dup) cand.push_back(Shape{8, zc, 0});
+    for (int j = 0; j < shapes_for(b->prec); ++j) {
+      const int tx = SHAPES[k][j][0], ty = SHAPES[k][j][1];
+      if (k == 0) {
+        cand.push_back(Shape{tx, ty, 0, 0});
+      } else {
+        for (int zc : {d.zc, 8, 16, 32, 0}) {
+          bool dup = false;
+          for (const Shape& q : cand) dup |= q.tx == tx && q.ty == ty && q.zc == zc;
+          if (!dup) cand.push_back(Shape{tx, ty, zc, 0});
+        }
       }
     }
     float best = 1e30f;
@@ -390,7 +453,7 @@ pfl_status tune(pfl_batch* b) {
     for (Shape sh : cand) {
       pfl_status s = build_tiles(b, c, sh, dst[k]);
       if (s != PFL_OK) return s;
-      const int res = resident_blocks(b->prec, sh.ty, k == 0);
+      const int res = resident_blocks(b->prec, k, sh);
       for (int mult : {1, 2, 4}) {
         sh.grid = std::max(1, std::min(c.ntiles, mult * b->sms * res));
         c.shape = sh;
@@ -503,6 +566,7 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
   b->tiles_off = L.tiles;
   b->stage_off = L.stage;
   b->red_off = L.red;
+  b->ctr_off = L.ctr;
   b->d_inst = (BInst*)(b->ws + L.table);
   b->graph = nullptr;
   b->tuned = 0;
@@ -543,6 +607,7 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
   }
   pfl_status s = PFL_OK;
   cudaError_t e = cudaMemcpyAsync(b->d_inst, b->inst.data(), count * sizeof(BInst), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->ws + b->ctr_off, 0, 2 * NCLASS * sizeof(unsigned), b->stream);
   if (e != cudaSuccess) s = bfail(PFL_ERR_CUDA, cudaGetErrorString(e));
   if (s == PFL_OK) s = initial_state(b, phi0, u0, p0);
   if (s == PFL_OK) {
@@ -555,7 +620,7 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
       for (int k = 0; k < NCLASS && s == PFL_OK; ++k) {
         b->cls[k].shape = default_shape(b, k);
         s = build_tiles(b, b->cls[k], b->cls[k].shape, base + cursor);
-        for (int i : b->cls[k].members) cursor += tiles_of(b->p[i], 4, 1);
+        for (int i : b->cls[k].members) cursor += tiles_of(b->p[i], 16, 4, 1);
         b->cls[k].shape.grid = std::max(1, std::min(b->cls[k].ntiles, b->cls[k].shape.grid));
       }
     }
@@ -679,10 +744,40 @@ pfl_status pfl_batch_diag(pfl_batch* b, double* out, long long* nonfinite) {
   return PFL_OK;
 }
 
+pfl_status pfl_batch_set_shape(pfl_batch* b, int cls, int tile_x, int tile_y, int z_chunk, int grid) {
+  if (!b) return bfail(PFL_ERR_ARG, "batch is NULL");
+  if (cls < 0 || cls >= NCLASS) return bfail(PFL_ERR_ARG, "class must be 0 (one z plane) or 1 (3-D)");
+  if (z_chunk < 0 || grid < 0) return bfail(PFL_ERR_ARG, "z_chunk and grid must be >= 0");
+  Shape sh{tile_x, tile_y, cls == 1 ? z_chunk : 0, 0};
+  const int j = shape_index(cls, sh);
+  if (j < 0 || j >= shapes_for(b->prec))
+    return bfail(PFL_ERR_ARG, "tile " + std::to_string(tile_x) + " x " + std::to_string(tile_y) +
+                                  " is not a shape of this class and precision");
+  BTRY(cudaSetDevice(b->device));
+  BTRY(cudaStreamSynchronize(b->stream));
+  ClassPlan& c = b->cls[cls];
+  if (!c.tiles) return PFL_OK;  // no instance of this class
+  pfl_status s = build_tiles(b, c, sh, c.tiles);
+  if (s != PFL_OK) return s;
+  sh.grid = grid > 0 ? grid : b->sms * resident_blocks(b->prec, cls, sh);
+  sh.grid = std::max(1, std::min(c.ntiles, sh.grid));
+  c.shape = sh;
+  // the graph holds the old launches; capture it again from pair 0
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  const int ab = b->ab;
+  b->ab = 0;
+  s = capture_graph(b);
+  b->ab = ab;
+  return s;
+}
+
 pfl_status pfl_batch_shapes(const pfl_batch* b, int* threads, int* grid, int* ntiles) {
   if (!b) return bfail(PFL_ERR_ARG, "batch is NULL");
   for (int k = 0; k < NCLASS; ++k) {
-    if (threads) threads[k] = ZM_TX * b->cls[k].shape.ty;
+    if (threads) threads[k] = b->cls[k].shape.tx * b->cls[k].shape.ty;
     if (grid) grid[k] = b->cls[k].shape.grid;
     if (ntiles) ntiles[k] = b->cls[k].ntiles;
   }

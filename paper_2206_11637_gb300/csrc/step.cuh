@@ -725,26 +725,26 @@ __host__ __device__ constexpr int zm_ty(int flat) { return flat ? ZM_TY_FLAT : Z
 
 // FLAT: a single plane, its own z neighbour (periodic) -- every cz reads the
 // plane itself, so the compiler loads each in-plane value once.
-template <int PREC, int FLAT = 0>
+template <int PREC, int FLAT = 0, int PW = ZM_TX + 2>
 struct SmemPhi {
-  const typename Store<PREC>::PhiT* plane[3];  // planes z - 1, z, z + 1 of (ZM_TY + 2) x (ZM_TX + 2) values
+  const typename Store<PREC>::PhiT* plane[3];  // planes z - 1, z, z + 1 of (tile height + 2) x PW values
   int i0;                 // index of this thread's column in a plane
   unsigned blk = 0;       // blocked links: a solid neighbour reads as this cell (neutral wetting)
   __device__ __forceinline__ typename Store<PREC>::R operator()(int cx, int cy, int cz) const {
     if (blk & link_bit(cx, cy, cz)) return (typename Store<PREC>::R)plane[1][i0];
-    return (typename Store<PREC>::R)plane[FLAT ? 1 : 1 + cz][i0 + cy * (ZM_TX + 2) + cx];
+    return (typename Store<PREC>::R)plane[FLAT ? 1 : 1 + cz][i0 + cy * PW + cx];
   }
 };
 
 // p* shift of the writer of a g population from the ring of P planes z - 1,
 // z, z + 1 of the fused step (tile plus a one-cell ring, like SmemPhi): the
 // neighbour at (dx, dy, dz), or the cell itself after a bounce-back.
-template <int FLAT = 0>
+template <int FLAT = 0, int PW = ZM_TX + 2>
 struct SmemShift {
   const float* plane[3];
   int i0;
   __device__ __forceinline__ float operator()(unsigned, int dx, int dy, int dz, bool valid) const {
-    return valid ? plane[FLAT ? 1 : 1 + dz][i0 + dy * (ZM_TX + 2) + dx] : plane[1][i0];
+    return valid ? plane[FLAT ? 1 : 1 + dz][i0 + dy * PW + dx] : plane[1][i0];
   }
 };
 
@@ -898,10 +898,11 @@ __device__ __forceinline__ void frame_pos(int r, int W, int H, int& i, int& j) {
 // tclock (launches replayed from a CUDA graph): the FP16 rounding seed comes
 // from the step count *tclock + tofs in device memory instead of `seed`, the
 // same function of the step count as the host's.
-// One tile of the fused step: the xy tile (bx, by) of ZM_TX x TY columns and
+// One tile of the fused step: the xy tile (bx, by) of TX x TY columns and
 // the z chunk bz of zc planes (the grid of k_step_zm, or an entry of the
-// batched engine's work list).  The caller has waited for the previous step.
-template <int PREC, int QH, int TY, int FLAT, int SOLID>
+// batched engine's work list), run by a block of TX x TY threads.  The caller
+// has waited for the previous step.
+template <int PREC, int QH, int TY, int FLAT, int SOLID, int TX = ZM_TX>
 __device__ __forceinline__ void zm_tile(const Geo32& geo, const Phys& ph, const typename Store<PREC>::S* __restrict__ hA,
                                         const typename Store<PREC>::S* __restrict__ gA,
                                         typename Store<PREC>::S* __restrict__ hB, typename Store<PREC>::S* __restrict__ gB,
@@ -911,8 +912,8 @@ __device__ __forceinline__ void zm_tile(const Geo32& geo, const Phys& ph, const 
                                         __half* __restrict__ pg_out, int bx, int by, int bz) {
   typedef typename Store<PREC>::PhiT PhiT;
   typedef typename Store<PREC>::R R;
-  constexpr int NT = ZM_TX * TY;
-  constexpr int PW = ZM_TX + 2, PH = TY + 2, PS = PW * PH;
+  constexpr int NT = TX * TY;
+  constexpr int PW = TX + 2, PH = TY + 2, PS = PW * PH;
   constexpr int NRING = 2 * (PW + PH) - 4;
   static_assert(NRING <= NT, "one thread per ring position");
   // phi planes z - 1, z, z + 1 and the one being filled: with four slots the
@@ -925,8 +926,8 @@ __device__ __forceinline__ void zm_tile(const Geo32& geo, const Phys& ph, const 
   __shared__ R hmom[FLAT ? 1 : 2][10 * NT];  // h moments of the tile's own cells
   constexpr bool F16 = PREC == 2;
   __shared__ float pring[F16 ? NS : 1][F16 ? PS : 1];  // FP16S: p* shifts of the stored g, ring like phi
-  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * ZM_TX + tx;
-  const int x0 = bx * ZM_TX, y0 = by * TY;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * TX + tx;
+  const int x0 = bx * TX, y0 = by * TY;
   const int z0 = bz * zc;
   const int z1 = min(z0 + zc, (int)geo.nz);
   const int x = x0 + tx, y = y0 + ty;
@@ -988,7 +989,7 @@ __device__ __forceinline__ void zm_tile(const Geo32& geo, const Phys& ph, const 
       phi_out[cell] = (PhiT)0;  // solid cells are not updated; their populations stay zero
     } else if (active) {
       const typename OffOf<INT>::T o = OffOf<INT>::at(geo, (unsigned)x, (unsigned)y, (unsigned)z, blk);
-      SmemPhi<PREC, FLAT> at;
+      SmemPhi<PREC, FLAT, PW> at;
       if (FLAT) {
         at.plane[0] = at.plane[1] = at.plane[2] = ring[0];
       } else {
@@ -999,7 +1000,7 @@ __device__ __forceinline__ void zm_tile(const Geo32& geo, const Phys& ph, const 
       // with one z plane the z neighbours are the plane itself (periodic or mirrored)
       at.i0 = (ty + 1) * PW + (tx + 1);
       at.blk = blk;
-      SmemShift<FLAT> psh;
+      SmemShift<FLAT, PW> psh;
       if constexpr (F16) {
         if (FLAT) {
           psh.plane[0] = psh.plane[1] = psh.plane[2] = pring[0];
@@ -1011,14 +1012,14 @@ __device__ __forceinline__ void zm_tile(const Geo32& geo, const Phys& ph, const 
         psh.i0 = at.i0;
       }
       phi_out[cell] = (PhiT)at(0, 0, 0);
-      collide_cell<PREC, QH, 0, 1, SmemPhi<PREC, FLAT>, 1, SmemShift<FLAT>, typename OffOf<INT>::T>(
+      collide_cell<PREC, QH, 0, 1, SmemPhi<PREC, FLAT, PW>, 1, SmemShift<FLAT, PW>, typename OffOf<INT>::T>(
           geo, ph, o, hA, gA, hB, gB, at, phi_shift, cell, seed, &hmom[FLAT ? 0 : ((z - z0) & 1)][tid], NT, psh,
           pg_out);
     }
     if (NS == 3) __syncthreads();
   }
   };
-  const bool interior = !SOLID && PFL_ZM_INTERIOR && x0 >= 2 && x0 + ZM_TX + 1 < (int)geo.nx && y0 >= 2 &&
+  const bool interior = !SOLID && PFL_ZM_INTERIOR && x0 >= 2 && x0 + TX + 1 < (int)geo.nx && y0 >= 2 &&
                         y0 + TY + 1 < (int)geo.ny && (FLAT || (z0 >= 2 && z1 + 1 < (int)geo.nz));
   if (interior)
     march(std::integral_constant<int, 1>());

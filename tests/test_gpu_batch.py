@@ -2,9 +2,10 @@
 
 Each instance of a batch evolves exactly like the same lattice run alone
 (same per-cell code, FP64: bitwise), through both the graph replay and the
-direct-launch remainder; tuned and untuned launch shapes agree; FP32
-instances stay within the FP32 tolerance of the oracle; an instance that goes
-unstable is stopped while the others continue.
+direct-launch remainder; tuned and untuned launch shapes agree, and so does
+every tile shape a class offers (16- and 32-wide, FP32 bitwise against single
+runs); FP32 instances stay within the FP32 tolerance of the oracle; an
+instance that goes unstable is stopped while the others continue.
 """
 import numpy as np
 import pytest
@@ -53,6 +54,44 @@ def test_batch_equals_single_runs(tune):
         r = s.fields()
         for x, y in zip(a, r):
             assert np.array_equal(x, y), i
+
+
+# every tile shape of each class (FP32 adds the 16-wide ones); one pair of
+# shapes per batch, the same steps through graph replays and direct launches
+SHAPE_PAIRS = [((32, 4), (32, 8)), ((32, 8), (16, 8)), ((16, 8), (16, 16))]
+
+
+@pytest.mark.parametrize("shapes", SHAPE_PAIRS, ids=["%dx%d-%dx%d" % (a + b) for a, b in SHAPE_PAIRS])
+def test_batch_tile_shapes_equal_single_runs_fp32(shapes):
+    from paper_2206_11637_gb300.batch import Batch
+    from paper_2206_11637_gb300.pflbm import Simulation
+    inst = mixed()
+    b = Batch(inst, precision="fp32", tune=False)
+    (tx0, ty0), (tx1, ty1) = shapes
+    b.set_shape(0, tx0, ty0)
+    b.set_shape(1, tx1, ty1, z_chunk=7)    # a ragged last chunk on the 20- and 44-deep lattices
+    t, g, n = b.shapes()
+    assert list(t) == [tx0 * ty0, tx1 * ty1] and n[0] > 0 and n[1] > 0
+    steps = 37
+    b.step(steps)
+    for i, (p, phi0, u0, p0) in enumerate(inst):
+        s = Simulation(p, phi0, u0, p0, precision="fp32")
+        s.step(steps)
+        for x, y in zip(b.fields(i), s.fields()):
+            assert np.array_equal(x, y), (shapes, i)
+
+
+def test_batch_set_shape_refusals():
+    from paper_2206_11637_gb300 import _lib as L
+    from paper_2206_11637_gb300.batch import Batch
+    inst = mixed(count=2)
+    b = Batch(inst, precision="fp64", tune=False)
+    for args in [(0, 16, 8), (1, 16, 16), (2, 32, 8), (1, 32, 4), (0, 32, 16), (1, 32, 8, -1)]:
+        with pytest.raises(L.PFLError):
+            b.set_shape(*args)
+    b.set_shape(1, 16, 8, 5, 100)          # FP64 has the 16 x 8 tile in 3-D
+    t, g, n = b.shapes()
+    assert t[1] == 128 and g[1] == min(100, n[1])
 
 
 def test_batch_fp32_against_oracle():
