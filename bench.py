@@ -446,7 +446,49 @@ def adjoint_leg(dev, barrier, n=4000, window=1000):
             "objective": "mean rise velocity over steps %d..%d" % (n - window, n),
             "forward_ms": t_fw * 1e3, "adjoint_ms_incl_forward_and_recompute": t_ad * 1e3,
             "adjoint_over_forward": (t_ad - t_fw) / t_fw, "workspace_gb": ws_gb,
-            "J": J, "grad_M_xi_sigma": [float(v) for v in g]}
+            "J": J, "grad_M_xi_sigma": [float(v) for v in g],
+            "fd_check": adjoint_fd_check(dev, p, phi0, u0, p0, 2000) if n >= 2000 else None}
+
+
+def adjoint_fd_check(dev, p, phi0, u0, p0, n, rel=1e-2):
+    """The adjoint gradient of the same bubble and objective over n steps (J
+    over the last quarter) against central differences of forward FP32 runs
+    with relative step rel.  Over 4000 steps J is no longer smooth in the
+    parameters (finite differences do not converge as the step shrinks), so the
+    check runs at a horizon where it is."""
+    import copy
+    import torch
+    from paper_2206_11637_gb300 import objectives as O
+    from paper_2206_11637_gb300.pflbm import Simulation
+    obs = O.rise_velocity_weights(p, phi0, n - n // 4, n)
+    wd = [(t, torch.from_numpy(w).to(dev)) for t, w in obs]
+
+    def forward_J(q):
+        s = Simulation(q, phi0, u0, p0, precision="fp32", device=dev)
+        J = 0.0
+        for t, w in sorted(wd, key=lambda a: a[0]):
+            s.step(t - s.time)
+            f = {"phi": torch.empty(s.N, dtype=torch.float64, device=dev)}
+            s.fields(f)
+            J += float(torch.dot(w, f["phi"]).item())
+        del s
+        torch.cuda.empty_cache()
+        return J
+
+    s = Simulation(p, phi0, u0, p0, precision="fp32", device=dev)
+    _, g = s.adjoint(n, obs)
+    del s
+    torch.cuda.empty_cache()
+    fd = []
+    for name in ("mobility", "xi", "sigma"):
+        v = getattr(p, name)
+        pp, pm = copy.copy(p), copy.copy(p)
+        setattr(pp, name, v * (1 + rel))
+        setattr(pm, name, v * (1 - rel))
+        fd.append((forward_J(pp) - forward_J(pm)) / (2 * rel * v))
+    return {"lattice_steps": n, "objective": "mean rise velocity over steps %d..%d" % (n - n // 4, n),
+            "relative_step": rel, "adjoint": [float(v) for v in g], "central_differences": fd,
+            "rel_err": [abs(float(a) - b) / abs(b) for a, b in zip(g, fd)]}
 
 
 # (workload, precision, lattice steps timed) of the per-config table
