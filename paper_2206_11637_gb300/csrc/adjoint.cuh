@@ -45,24 +45,71 @@ constexpr int adj_minb() {
 // forward recomputation, doubled the adjoint's time on the same bubble: 831 ->
 // 1691 ms.  It is not used.)
 
+// The step's parameters in the arithmetic type R, converted once on the host:
+// converting the doubles of Phys in every thread kept the FP64 pipe (1/64 of
+// the FP32 rate on this part) three quarters busy in k_adj_local.  (The fused
+// forward step keeps Phys: the same change there measured 2.6 % slower in
+// FP16S and 0.9 % in FP32, its schedule losing more to load latency than the
+// conversions cost.)
+template <typename R>
+struct PhysR {
+  R rho_l, drho, tau_l, dtau, beta, kappa, inv_xi, omega_phi, gx, gy, gz;
+};
+
+template <typename R>
+inline PhysR<R> phys_r(const Phys& p) {
+  PhysR<R> q;
+  q.rho_l = (R)p.rho_l;
+  q.drho = (R)(p.rho_h - p.rho_l);
+  q.tau_l = (R)p.tau_l;
+  q.dtau = (R)(p.tau_h - p.tau_l);
+  q.beta = (R)p.beta;
+  q.kappa = (R)p.kappa;
+  q.inv_xi = (R)p.inv_xi;
+  q.omega_phi = (R)p.omega_phi;
+  q.gx = (R)p.gx;
+  q.gy = (R)p.gy;
+  q.gz = (R)p.gz;
+  return q;
+}
+
 // Parameters of the reverse sweep that the forward step folds into Phys.
 struct AdjPar {
   double M, xi, sigma;
 };
 
+// The chain-rule factors of (M, xi, sigma) in the arithmetic type, formed once
+// on the host: beta = 12 sigma / xi, kappa = 1.5 sigma xi, 1 / xi.
+template <typename R>
+struct AdjParR {
+  R xi2;        // xi^2
+  R beta_sig;   // d beta / d sigma = 12 / xi
+  R kappa_sig;  // d kappa / d sigma = 1.5 xi
+  R beta_xi;    // d beta / d xi = -12 sigma / xi^2
+  R kappa_xi;   // d kappa / d xi = 1.5 sigma
+};
+
+template <typename R>
+inline AdjParR<R> adj_par_r(const AdjPar& a) {
+  return AdjParR<R>{(R)(a.xi * a.xi), (R)(12.0 / a.xi), (R)(1.5 * a.xi), (R)(-12.0 * a.sigma / (a.xi * a.xi)),
+                    (R)(1.5 * a.sigma)};
+}
+
 template <typename R>
 __device__ __forceinline__ R block_sum3_to(R a, R b, R c, double* out3) {
-  // FP64 block reduction of three values, added to out3[0..2]: each block owns
-  // its three slots and accumulates over the reverse sweep's steps.
+  // Block reduction of three values, added in FP64 to out3[0..2]: each block
+  // owns its three slots and accumulates over the reverse sweep's steps.  The
+  // 32 lanes of a warp sum in the arithmetic type, the warps' sums in FP64
+  // (FP64 shuffles of every thread's value kept the FP64 pipe busy).
   __shared__ double sm[ADJ_THREADS / 32][3];
-  double v[3] = {(double)a, (double)b, (double)c};
+  R v[3] = {a, b, c};
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    double s = v[k];
+    R s = v[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) sm[wid][k] = s;
+    if (lane == 0) sm[wid][k] = (double)s;
   }
   __syncthreads();
   if (threadIdx.x < 3) {
@@ -74,7 +121,8 @@ __device__ __forceinline__ R block_sum3_to(R a, R b, R c, double* out3) {
 }
 
 template <int PREC, int QH, int READ_ODD>
-__global__ void __launch_bounds__(ADJ_THREADS, adj_minb<PREC>()) k_adj_local(Geo32 geo, Phys ph, AdjPar ap,
+__global__ void __launch_bounds__(ADJ_THREADS, adj_minb<PREC>()) k_adj_local(Geo32 geo, PhysR<typename Store<PREC>::R> ph,
+                                                           AdjParR<typename Store<PREC>::R> ap,
                                                            const typename Store<PREC>::S* __restrict__ h,
                                                            const typename Store<PREC>::S* __restrict__ g,
                                                            const typename Store<PREC>::PhiT* __restrict__ phi,
@@ -213,18 +261,18 @@ __global__ void __launch_bounds__(ADJ_THREADS, adj_minb<PREC>()) k_adj_local(Geo
       if (cx && cz) hxz += (cx * cz > 0) ? S : -S;
     }
 
-    const R drho = (R)(ph.rho_h - ph.rho_l);
-    const R dtau = (R)(ph.tau_h - ph.tau_l);
-    const R rho = (R)ph.rho_l + pc * drho;
-    const R tau = (R)ph.tau_l + pc * dtau;
+    const R drho = ph.drho;
+    const R dtau = ph.dtau;
+    const R rho = ph.rho_l + pc * drho;
+    const R tau = ph.tau_l + pc * dtau;
     const R omega = (R)1 / tau;
     const R nu = (tau - (R)0.5) * (R)(1.0 / 3.0);
-    const R beta = (R)ph.beta, kappa = (R)ph.kappa;
+    const R beta = ph.beta, kappa = ph.kappa;
     const R dw = pc * (pc - (R)1) * (pc - (R)0.5);
     const R mu = (R)4 * beta * dw - kappa * lap;
     const R inv2rho = (R)0.5 / rho;
     const R cp = -pst * (R)(1.0 / 3.0) * drho;
-    const R Gx = (R)ph.gx, Gy = (R)ph.gy, Gz = (R)ph.gz;
+    const R Gx = ph.gx, Gy = ph.gy, Gz = ph.gz;
     const R F0x = (mu + cp) * gx + rho * Gx, F0y = (mu + cp) * gy + rho * Gy, F0z = (mu + cp) * gz + rho * Gz;
     const R p3 = pst * (R)(1.0 / 3.0);
     const R u0x = jx + F0x * inv2rho, u0y = jy + F0y * inv2rho, u0z = jz + F0z * inv2rho;
@@ -241,10 +289,10 @@ __global__ void __launch_bounds__(ADJ_THREADS, adj_minb<PREC>()) k_adj_local(Geo
     const R dzz = QG == 9 ? (R)0 : pzz - p3 - uz * uz;  // 2-D: the trace runs over x and y
     const R fr = (R)1.5 / rho;
     // phase field
-    const R omp = (R)ph.omega_phi;
+    const R omp = ph.omega_phi;
     const R gn = sqrt(gx * gx + gy * gy + gz * gz);
     const R den = gn + (R)1e-6;
-    const R theta = (R)4 * pc * ((R)1 - pc) * (R)ph.inv_xi;
+    const R theta = (R)4 * pc * ((R)1 - pc) * ph.inv_xi;
     const R sfac = (R)1 - (R)0.5 * omp;
     const R tn = theta / den * sfac;
     const R a1h = ((R)1 - omp) * (R)3, a2h = ((R)1 - omp) * (R)4.5;
@@ -354,9 +402,9 @@ __global__ void __launch_bounds__(ADJ_THREADS, adj_minb<PREC>()) k_adj_local(Geo
         b_gz += gz / gn * b_den;
       }
       // theta = 4 pc (1 - pc) / xi
-      b_pc += (R)4 * ((R)1 - (R)2 * pc) * (R)ph.inv_xi * b_theta;
+      b_pc += (R)4 * ((R)1 - (R)2 * pc) * ph.inv_xi * b_theta;
       const R b_invxi = (R)4 * pc * ((R)1 - pc) * b_theta;
-      bXi += -b_invxi / (R)(ap.xi * ap.xi);
+      bXi += -b_invxi / ap.xi2;
       // omega_phi -> M
       const R b_omp = (R)-3 * b_a1h - (R)4.5 * b_a2h - (R)0.5 * b_sfac;
       bM += (R)-3 * omp * omp * b_omp;
@@ -418,8 +466,8 @@ __global__ void __launch_bounds__(ADJ_THREADS, adj_minb<PREC>()) k_adj_local(Geo
       const R b_beta = (R)4 * dw * b_mcp;
       const R b_kappa = -lap * b_mcp;
       // beta = 12 sigma / xi, kappa = 1.5 sigma xi
-      bSig += (R)(12.0 / ap.xi) * b_beta + (R)(1.5 * ap.xi) * b_kappa;
-      bXi += (R)(-12.0 * ap.sigma / (ap.xi * ap.xi)) * b_beta + (R)(1.5 * ap.sigma) * b_kappa;
+      bSig += ap.beta_sig * b_beta + ap.kappa_sig * b_kappa;
+      bXi += ap.beta_xi * b_beta + ap.kappa_xi * b_kappa;
       // inv2rho = 0.5 / rho ; nu = (tau - 0.5) / 3 ; omega = 1 / tau
       b_rho += (R)-0.5 / (rho * rho) * b_inv2rho;
       R b_tau = b_nu * (R)(1.0 / 3.0) - omega * omega * b_omega;

@@ -1163,16 +1163,17 @@ void launch_adj_step(pfl_ctx* c, const AdjLayout& A, char* aws, char* slot, int 
   const typename Store<PREC>::S* g = (const typename Store<PREC>::S*)(slot + align256((size_t)QH * N * S));
   const typename Store<PREC>::PhiT* phi =
       (const typename Store<PREC>::PhiT*)(slot + align256((size_t)QH * N * S) + align256((size_t)qg_of<QH>() * N * S));
-  AdjPar ap{c->p.mobility, c->p.xi, c->p.sigma};
+  const AdjParR<R> ap = adj_par_r<R>(AdjPar{c->p.mobility, c->p.xi, c->p.sigma});
+  const PhysR<R> phr = phys_r<R>(c->ph);
   double* part = (double*)(aws + A.part);
   R* aux = (R*)(aws + A.aux);
   R* acc = (R*)(aws + A.acc);
   const unsigned nb = blocks_for(c->geo.N, ADJ_THREADS);
   if (swapped)
-    k_adj_local<PREC, QH, 1><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
+    k_adj_local<PREC, QH, 1><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, phr, ap, h, g, phi, (const R*)lam_in,
                                                              acc, (R*)lam_out, aux, part);
   else
-    k_adj_local<PREC, QH, 0><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, c->ph, ap, h, g, phi, (const R*)lam_in,
+    k_adj_local<PREC, QH, 0><<<nb, ADJ_THREADS, 0, c->stream>>>(c->g32, phr, ap, h, g, phi, (const R*)lam_in,
                                                              acc, (R*)lam_out, aux, part);
   const dim3 grid((c->p.nx + ZM_TX - 1) / ZM_TX, (c->p.ny + ZM_TY - 1) / ZM_TY, (c->p.nz + c->zc - 1) / c->zc);
   k_adj_phi<R, qg_of<QH>()><<<grid, dim3(ZM_TX, ZM_TY), 0, c->stream>>>(c->g32, aux, acc, W, c->zc);
