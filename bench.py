@@ -412,16 +412,17 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def adjoint_leg(dev, barrier, n=4000, window=1000):
+def adjoint_leg(dev, barrier, n=4000, window=1000, ny=384):
     """Adjoint over forward on the 128 x 384 x 128 rising bubble (FP32, walls,
     D 32, Eo 10, Mo 1e-3, xi 4, M 0.02): J = mean rise velocity over the last
     `window` of n = 4000 steps, gradient with respect to (M, xi, sigma),
     sqrt(n) checkpoints.  The ratio counts everything the adjoint call adds to
-    the forward run it contains: (t_adjoint - t_forward) / t_forward."""
+    the forward run it contains: (t_adjoint - t_forward) / t_forward.  ny < 384
+    runs the same bubble in a shorter box (a profiling case)."""
     from paper_2206_11637_gb300 import objectives as O
     from paper_2206_11637_gb300 import workloads as W
     from paper_2206_11637_gb300.pflbm import Simulation
-    p, phi0, u0, p0 = W.rising_bubble()
+    p, phi0, u0, p0 = W.rising_bubble() if ny == 384 else W.rising_bubble(128, ny, 128)
     window = min(window, n)
     obs = O.rise_velocity_weights(p, phi0, n - window, n)
     fw = Simulation(p, phi0, u0, p0, precision="fp32", device=dev)
@@ -442,12 +443,12 @@ def adjoint_leg(dev, barrier, n=4000, window=1000):
     t_ad = time.perf_counter() - t0
     ws_gb = ad.lib.pfl_adjoint_workspace_bytes(ad.ctx, n) / 1e9
     del ad
-    return {"workload": "rising_bubble 128x384x128", "precision": "fp32", "lattice_steps": n,
+    return {"workload": "rising_bubble 128x%dx128" % ny, "precision": "fp32", "lattice_steps": n,
             "objective": "mean rise velocity over steps %d..%d" % (n - window, n),
             "forward_ms": t_fw * 1e3, "adjoint_ms_incl_forward_and_recompute": t_ad * 1e3,
             "adjoint_over_forward": (t_ad - t_fw) / t_fw, "workspace_gb": ws_gb,
             "J": J, "grad_M_xi_sigma": [float(v) for v in g],
-            "fd_check": adjoint_fd_check(dev, p, phi0, u0, p0, 2000) if n >= 2000 else None}
+            "fd_check": adjoint_fd_check(dev, p, phi0, u0, p0, 2000) if n >= 2000 and ny == 384 else None}
 
 
 def adjoint_fd_check(dev, p, phi0, u0, p0, n, rel=1e-2):
@@ -579,6 +580,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true", help="skip timing the other precisions")
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="N",
                     help="run only the adjoint leg over N steps and print its JSON (profiling)")
+    ap.add_argument("--adjoint-ny", type=int, default=384, metavar="NY",
+                    help="height of the adjoint leg's bubble box (384: the config; less for profiling)")
     ap.add_argument("--engine", type=int, default=0, choices=[0, 1],
                     help="0: fused two-array step (default), 1: in-place AA step + phi pass")
     args = ap.parse_args()
@@ -589,7 +592,7 @@ def main():
         from paper_2206_11637_gb300 import build as B
         B.build_library()
         torch.cuda.set_device(0)
-        r = adjoint_leg(torch.device("cuda", 0), torch.cuda.synchronize, args.adjoint_only)
+        r = adjoint_leg(torch.device("cuda", 0), torch.cuda.synchronize, args.adjoint_only, ny=args.adjoint_ny)
         print(json.dumps(r), flush=True)
         return
     if args.workload == "batched_sweep":
