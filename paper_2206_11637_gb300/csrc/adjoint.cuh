@@ -589,32 +589,76 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY) k_adj_phi(Geo32 geo, const R* _
     }
   };
 
+  // The weights factor per axis, w(o) = w1(o_x) w1(o_y) w1(o_z) with w1 = 1/6,
+  // 2/3, 1/6 (D2Q9: w1(o_x) w1(o_y)), so with o = -c the sum is
+  //   acc = aux_pc - 6 aux_lap(x) + 6 sum_o w(o) lap(x + o)
+  //         - 3 sum_o w(o) (o_x g_x + o_y g_y + o_z g_z)(x + o),
+  // formed as four 3x3 sums in each plane (lap with w1 w1, g_x with o_x w1 w1,
+  // g_y with w1 o_y w1, g_z with w1 w1) and their combination over the planes
+  // z - 1, z, z + 1 (weights w1, or o_z w1 for g_z), kept in registers as the
+  // march goes: 30 shared-memory reads per cell instead of 80.
+  constexpr bool FLAT2 = QG == 9;
+  const R w1e = (R)(1.0 / 6.0), w1c = (R)(2.0 / 3.0);
+  const int i0 = (ty + 1) * PW + (tx + 1);
+  auto plane_sums = [&](int slot, R out[4]) {
+    const R* L = ring[slot][3];
+    const R* GX = ring[slot][0];
+    const R* GY = ring[slot][1];
+    const R* GZ = ring[slot][2];
+    // rows y - 1, y, y + 1 of lap and g_z, smoothed along x (w1); g_x differenced along x
+    R la[3], gz[3], gx[3], gyr[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const int r = i0 + (j - 1) * PW;
+      la[j] = w1e * (L[r - 1] + L[r + 1]) + w1c * L[r];
+      gz[j] = w1e * (GZ[r - 1] + GZ[r + 1]) + w1c * GZ[r];
+      gx[j] = w1e * (GX[r + 1] - GX[r - 1]);
+      gyr[j] = (j == 1) ? (R)0 : w1e * (GY[r - 1] + GY[r + 1]) + w1c * GY[r];
+    }
+    out[0] = w1e * (la[0] + la[2]) + w1c * la[1];      // lap, w1 w1
+    out[1] = w1e * (gx[0] + gx[2]) + w1c * gx[1];      // g_x, o_x w1 . w1
+    out[2] = w1e * (gyr[2] - gyr[0]);                  // g_y, w1 . o_y w1
+    out[3] = w1e * (gz[0] + gz[2]) + w1c * gz[1];      // g_z, w1 w1
+  };
+
   fill(z0 - 1, 0);
   fill(z0, 1);
+  __syncthreads();
+  R Sm[4] = {0, 0, 0, 0}, S0[4], Sp[4];
+  if (!FLAT2) plane_sums(0, Sm);
+  plane_sums(1, S0);
   for (int z = z0; z < z1; ++z) {
     const int b = z - (z0 - 1);
-    fill(z + 1, (b + 1) % 3);
+    // plane z + 1 goes into the slot of plane z - 2, whose sums were taken two
+    // planes ago (barriers since); plane z's slot stays for its centre value
+    if (!FLAT2) fill(z + 1, (b + 1) % 3);
     __syncthreads();
+    if (!FLAT2) plane_sums((b + 1) % 3, Sp);
     if (active) {
       const unsigned cell = (unsigned)x + geo.nx * ((unsigned)y + geo.ny * (unsigned)z);
-      const int i0 = (ty + 1) * PW + (tx + 1);
-      const int sl[3] = {(b + 2) % 3, b % 3, (b + 1) % 3};  // planes z - 1, z, z + 1
-      R acc = aux[4u * N + cell] - (R)(6.0 * (1.0 - lq_w<QG>((QG - 1) / 2))) * ring[sl[1]][3][i0];
-#pragma unroll
-      for (int q = 0; q < QG; ++q) {
-        if (q == (QG - 1) / 2) continue;
-        const int cx = q27_cx(lq_to27<QG>(q)), cy = q27_cy(lq_to27<QG>(q)), cz = q27_cz(lq_to27<QG>(q));
-        const int s = sl[1 - cz], r = i0 - cx - cy * PW;   // reader y = x - c
-        R v = (R)6 * ring[s][3][r];
-        if (cx) v += (R)(3 * cx) * ring[s][0][r];
-        if (cy) v += (R)(3 * cy) * ring[s][1][r];
-        if (cz) v += (R)(3 * cz) * ring[s][2][r];
-        acc += (R)lq_w<QG>(q) * v;
+      R sl, sx, sy, sz;
+      if (FLAT2) {
+        sl = S0[0];
+        sx = S0[1];
+        sy = S0[2];
+        sz = 0;
+      } else {
+        sl = w1e * (Sm[0] + Sp[0]) + w1c * S0[0];
+        sx = w1e * (Sm[1] + Sp[1]) + w1c * S0[1];
+        sy = w1e * (Sm[2] + Sp[2]) + w1c * S0[2];
+        sz = w1e * (Sp[3] - Sm[3]);
       }
+      R acc = aux[4u * N + cell] - (R)6 * ring[b % 3][3][i0] + (R)6 * sl - (R)3 * (sx + sy + sz);
       if (W) acc += (R)W[cell];
       acc_out[cell] = acc;
     }
-    __syncthreads();
+    if (!FLAT2) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        Sm[k] = S0[k];
+        S0[k] = Sp[k];
+      }
+    }
   }
 }
 
