@@ -572,21 +572,45 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY) k_adj_phi(Geo32 geo, const R* _
     return (unsigned)(((p % n) + n) % n);
   };
 
-  auto fill = [&](int zp, int slot) {
+  // The four aux fields of plane zp at this thread's ring positions (tid and
+  // tid + NT) into registers, then into a ring slot: a plane's loads are
+  // issued one plane ahead, so they are in flight over the barrier and the
+  // sums of the plane before.
+  constexpr int NPOS = (PS + NT - 1) / NT;
+  R pre[NPOS][4];
+  auto load_plane = [&](int zp) {
     bool fz;
     const unsigned sz = src(zp, (int)geo.nz, geo.wall[2], fz);
-    for (int r = tid; r < PS; r += NT) {
-      const int i = r % PW, j = r / PW;
-      bool fx, fy;
-      const unsigned sx = src(x0 - 1 + i, (int)geo.nx, geo.wall[0], fx);
-      const unsigned sy = src(y0 - 1 + j, (int)geo.ny, geo.wall[1], fy);
-      const unsigned c = sx + geo.nx * (sy + geo.ny * sz);
-      const R a0 = aux[c], a1 = aux[N + c], a2 = aux[2u * N + c];
-      ring[slot][0][r] = fx ? -a0 : a0;
-      ring[slot][1][r] = fy ? -a1 : a1;
-      ring[slot][2][r] = fz ? -a2 : a2;
-      ring[slot][3][r] = aux[3u * N + c];
+#pragma unroll
+    for (int k = 0; k < NPOS; ++k) {
+      const int r = tid + k * NT;
+      if (r < PS) {
+        const int i = r % PW, j = r / PW;
+        bool fx, fy;
+        const unsigned sx = src(x0 - 1 + i, (int)geo.nx, geo.wall[0], fx);
+        const unsigned sy = src(y0 - 1 + j, (int)geo.ny, geo.wall[1], fy);
+        const unsigned c = sx + geo.nx * (sy + geo.ny * sz);
+        const R a0 = aux[c], a1 = aux[N + c], a2 = aux[2u * N + c];
+        pre[k][0] = fx ? -a0 : a0;
+        pre[k][1] = fy ? -a1 : a1;
+        pre[k][2] = fz ? -a2 : a2;
+        pre[k][3] = aux[3u * N + c];
+      }
     }
+  };
+  auto store_plane = [&](int slot) {
+#pragma unroll
+    for (int k = 0; k < NPOS; ++k) {
+      const int r = tid + k * NT;
+      if (r < PS) {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) ring[slot][f][r] = pre[k][f];
+      }
+    }
+  };
+  auto fill = [&](int zp, int slot) {
+    load_plane(zp);
+    store_plane(slot);
   };
 
   // The weights factor per axis, w(o) = w1(o_x) w1(o_y) w1(o_z) with w1 = 1/6,
@@ -623,15 +647,20 @@ __global__ void __launch_bounds__(ZM_TX * ZM_TY) k_adj_phi(Geo32 geo, const R* _
 
   fill(z0 - 1, 0);
   fill(z0, 1);
+  if (!FLAT2) load_plane(z0 + 1);
   __syncthreads();
   R Sm[4] = {0, 0, 0, 0}, S0[4], Sp[4];
   if (!FLAT2) plane_sums(0, Sm);
   plane_sums(1, S0);
   for (int z = z0; z < z1; ++z) {
     const int b = z - (z0 - 1);
-    // plane z + 1 goes into the slot of plane z - 2, whose sums were taken two
-    // planes ago (barriers since); plane z's slot stays for its centre value
-    if (!FLAT2) fill(z + 1, (b + 1) % 3);
+    // plane z + 1 (loaded one plane ago) goes into the slot of plane z - 2,
+    // whose sums were taken two planes ago (barriers since); plane z's slot
+    // stays for its centre value; plane z + 2's loads go out now
+    if (!FLAT2) {
+      store_plane((b + 1) % 3);
+      if (z + 2 <= z1) load_plane(z + 2);
+    }
     __syncthreads();
     if (!FLAT2) plane_sums((b + 1) % 3, Sp);
     if (active) {
