@@ -120,3 +120,15 @@ def test_d2q9_lattice():
     G = M @ np.diag(w) @ M.T
     assert np.abs(G - np.diag(np.diag(G))).max() < 1e-14
     assert [int(np.sum(deg == k)) for k in range(5)] == [1, 2, 3, 2, 1]
+
+
+@pytest.mark.parametrize("q", [27, 9])
+def test_stencil_weights_factor_per_axis(q):
+    """The weights of the phi stencil (D3Q27 in 3-D, D2Q9 in 2-D) are products
+    of one 1-D weight per axis, w1(0) = 2/3 and w1(+-1) = 1/6: the property the
+    adjoint's transposed stencil uses to sum plane by plane."""
+    t = oracle.tables(q)
+    w1 = {-1: 1.0 / 6.0, 0: 2.0 / 3.0, 1: 1.0 / 6.0}
+    dims = 3 if q == 27 else 2
+    for ci, wi in zip(t["c"], t["w"]):
+        assert abs(wi - np.prod([w1[int(ci[a])] for a in range(dims)])) < 1e-16
