@@ -11,7 +11,7 @@ the readings it follows.  ``tangent`` runs the same arithmetic in dual numbers
 for the exact derivative of a phi functional with respect to M, xi or sigma.
 """
 from .oracle import (Oracle, from_params, tables, mrt_collide, build_oracle, tangent, COLL_MRT, COLL_BGK,
-                     COLL_MRT_ALL_EQUAL)
+                     COLL_MRT_ALL_EQUAL, SCHED_CONCURRENT, SCHED_SEQUENTIAL)
 
 __all__ = ["Oracle", "from_params", "tables", "mrt_collide", "build_oracle", "tangent", "COLL_MRT", "COLL_BGK",
-           "COLL_MRT_ALL_EQUAL"]
+           "COLL_MRT_ALL_EQUAL", "SCHED_CONCURRENT", "SCHED_SEQUENTIAL"]

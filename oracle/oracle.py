@@ -10,6 +10,9 @@ _SRC = os.path.join(_HERE, "pflbm_oracle.cpp")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 COLL_MRT, COLL_BGK, COLL_MRT_ALL_EQUAL = 0, 1, 2
+# order of the two collisions in a step: both at phi^t (the reading used
+# everywhere), or the phase field first and the hydrodynamics at phi^{t+1}
+SCHED_CONCURRENT, SCHED_SEQUENTIAL = 0, 1
 
 _lib = None
 
@@ -73,13 +76,16 @@ class Oracle:
     """
 
     def __init__(self, nx, ny, nz, bc, rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi,
-                 gravity=(0.0, 0.0, 0.0), phi0=None, u0=None, p0=None, collision=COLL_MRT, h_lattice=15):
+                 gravity=(0.0, 0.0, 0.0), phi0=None, u0=None, p0=None, collision=COLL_MRT, h_lattice=15,
+                 schedule=SCHED_CONCURRENT):
         self.lib = _load()
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         self.qh = {27: 27, 9: 9}.get(h_lattice, 15)
         self.qg = 9 if self.qh == 9 else 27
-        ip = np.array([nx, ny, nz] + list(bc) + [collision, self.qh], dtype=np.int32)
+        if schedule not in (SCHED_CONCURRENT, SCHED_SEQUENTIAL):
+            raise ValueError("unknown schedule %r" % (schedule,))
+        ip = np.array([nx, ny, nz] + list(bc) + [collision, self.qh, schedule], dtype=np.int32)
         dp = np.array([rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi] + list(gravity), dtype=np.float64)
         self._phi0 = _f64(phi0, self.N)
         self._u0 = _f64(u0, 3 * self.N)
@@ -150,10 +156,11 @@ def mrt_collide(q, f, feq, src, rates):
     return out
 
 
-def from_params(p, phi0, u0=None, p0=None):
+def from_params(p, phi0, u0=None, p0=None, schedule=SCHED_CONCURRENT):
     """Oracle built from a ``workloads.Params``-like object (duck-typed)."""
     o = Oracle(p.nx, p.ny, p.nz, p.bc, p.rho_h, p.rho_l, p.nu_h, p.nu_l, p.sigma, p.mobility, p.xi,
-               p.gravity, phi0, u0, p0, collision=p.collision, h_lattice=getattr(p, "h_lattice", 15))
+               p.gravity, phi0, u0, p0, collision=p.collision, h_lattice=getattr(p, "h_lattice", 15),
+               schedule=schedule)
     if getattr(p, "solid", None) is not None:
         o.set_solid(p.solid)
     return o
@@ -169,7 +176,7 @@ def tangent(p, phi0, u0, p0, n, obs, param, threads=0):
     lib = _load()
     N = p.nx * p.ny * p.nz
     qh = {27: 27, 9: 9}.get(getattr(p, "h_lattice", 15), 15)
-    ip = np.array([p.nx, p.ny, p.nz] + list(p.bc) + [p.collision, qh], dtype=np.int32)
+    ip = np.array([p.nx, p.ny, p.nz] + list(p.bc) + [p.collision, qh, SCHED_CONCURRENT], dtype=np.int32)
     dp = np.array([p.rho_h, p.rho_l, p.nu_h, p.nu_l, p.sigma, p.mobility, p.xi] + list(p.gravity),
                   dtype=np.float64)
     steps = np.array([int(t) for t, _ in obs], dtype=np.int32)

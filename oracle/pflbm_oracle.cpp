@@ -37,7 +37,9 @@
 //     the stencil, so that n stays well conditioned where grad(phi) -> 0.
 //
 // Schedule per step: both collisions use phi^t and its stencil, u^t from g in
-// the same cell; then both sets stream; then phi^{t+1} = sum h.
+// the same cell; then both sets stream; then phi^{t+1} = sum h.  A sequential
+// order (phase field first, the hydrodynamics at phi^{t+1}) is kept as an
+// option for studies of how much that reading matters.
 //
 // Built with -O2 -ffp-contract=off so the arithmetic is plain IEEE FP64.
 #include <cmath>
@@ -224,11 +226,20 @@ const Lattice& Q15() {
 // ------------------------------------------------------------------ model --
 enum { COLL_MRT = 0, COLL_BGK = 1, COLL_MRT_ALL_EQUAL = 2 };
 
+// Order of the two collisions within a step (the paper does not state it).
+// CONCURRENT: both collisions at t use phi^t, its stencil and u^t; then both
+// sets stream; then phi^{t+1} = sum h.  SEQUENTIAL (for sensitivity studies
+// of that reading only): the phase field goes first -- h collides with phi^t
+// and u^t, streams, phi^{t+1} = sum h -- and the hydrodynamic collision then
+// takes phi^{t+1} and its stencil (rho, tau, every force) with g^t.
+enum { SCHED_CONCURRENT = 0, SCHED_SEQUENTIAL = 1 };
+
 struct Params {
   int nx, ny, nz;
   int bc[6];  // -x,+x,-y,+y,-z,+z : 0 periodic, 1 no-slip
   int collision;
   int qh;     // phase-field lattice: 15 (D3Q15), 27 (D3Q27) or 9 (D2Q9, with D2Q9 for g)
+  int schedule;  // SCHED_CONCURRENT (the reading used throughout) or SCHED_SEQUENTIAL
   double rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, g[3];
 };
 
@@ -420,90 +431,138 @@ void compute_phi(Sim<T>& S) {
   }
 }
 
+// Hydrodynamic collision of cell (x, y, z) from its macroscopic state cs and
+// populations gc, pushed into S.gn (periodic wrap or halfway bounce-back).
 template <typename T>
-void do_step(Sim<T>& S) {
-  using std::sqrt;
+void g_update(Sim<T>& S, int x, int y, int z, const CellState<T>& cs, const T* gc) {
   const Params& P = S.P;
   const Lattice& L27 = g_lattice(P);
+  const long N = S.N;
+  const long c0 = cell_index(P, x, y, z);
+  T geq[27], G[27], gpost[27], s27[27];
+  geq_of(L27, cs.pstar, cs.u, geq);
+  for (int i = 0; i < L27.q; ++i) {
+    T cF = L27.c[3 * i] * cs.F[0] + L27.c[3 * i + 1] * cs.F[1] + L27.c[3 * i + 2] * cs.F[2];
+    G[i] = L27.w[i] * cF / (CS2 * cs.rho);
+  }
+  if (P.collision == COLL_BGK) {
+    for (int i = 0; i < L27.q; ++i)
+      gpost[i] = gc[i] - cs.omega * (gc[i] - geq[i]) + (1.0 - 0.5 * cs.omega) * G[i];
+  } else {
+    for (int k = 0; k < L27.q; ++k) s27[k] = rate_g(P, L27.degree[k], cs.omega);
+    mrt_collide(L27, gc, geq, G, s27, gpost);
+  }
+  for (int i = 0; i < L27.q; ++i) {
+    int xt, yt, zt;
+    bool ok = neighbour(x, L27.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
+              neighbour(y, L27.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
+              neighbour(z, L27.c[3 * i + 2], P.nz, P.bc[4], P.bc[5], zt);
+    if (ok && !S.solid.empty() && S.solid[cell_index(P, xt, yt, zt)]) ok = false;  // bounce at a solid cell
+    if (ok)
+      S.gn[(size_t)i * N + cell_index(P, xt, yt, zt)] = gpost[i];
+    else
+      S.gn[(size_t)L27.opp[i] * N + c0] = gpost[i];
+  }
+}
+
+// Phase-field collision of cell (x, y, z) from cs (phi, its gradient and u)
+// and populations hc, pushed into S.hn.
+template <typename T>
+void h_update(Sim<T>& S, int x, int y, int z, const CellState<T>& cs, const T* hc) {
+  using std::sqrt;
+  const Params& P = S.P;
   const Lattice& LH = h_lattice(P);  // phase-field lattice
   const long N = S.N;
+  const long c0 = cell_index(P, x, y, z);
   const T omega_phi = 1.0 / (S.mobility / CS2 + 0.5);
-#pragma omp parallel for collapse(2) schedule(static)
-  for (int z = 0; z < P.nz; ++z) {
-    for (int y = 0; y < P.ny; ++y)
-      for (int x = 0; x < P.nx; ++x) {
-        long c0 = cell_index(P, x, y, z);
-        if (!S.solid.empty() && S.solid[c0]) continue;  // solid cells are not updated
-        T gc[27], hc[27];
-        for (int i = 0; i < L27.q; ++i) gc[i] = S.g[(size_t)i * N + c0];
-        for (int i = 0; i < LH.q; ++i) hc[i] = S.h[(size_t)i * N + c0];
-        CellState<T> cs;
-        cell_macro(S, x, y, z, gc, cs);
-
-        // hydrodynamic collision
-        T geq[27], G[27], gpost[27], s27[27];
-        geq_of(L27, cs.pstar, cs.u, geq);
-        for (int i = 0; i < L27.q; ++i) {
-          T cF = L27.c[3 * i] * cs.F[0] + L27.c[3 * i + 1] * cs.F[1] + L27.c[3 * i + 2] * cs.F[2];
-          G[i] = L27.w[i] * cF / (CS2 * cs.rho);
-        }
-        if (P.collision == COLL_BGK) {
-          for (int i = 0; i < L27.q; ++i)
-            gpost[i] = gc[i] - cs.omega * (gc[i] - geq[i]) + (1.0 - 0.5 * cs.omega) * G[i];
-        } else {
-          for (int k = 0; k < L27.q; ++k) s27[k] = rate_g(P, L27.degree[k], cs.omega);
-          mrt_collide(L27, gc, geq, G, s27, gpost);
-        }
-
-        // phase-field collision
-        T gnorm = sqrt(cs.gradphi[0] * cs.gradphi[0] + cs.gradphi[1] * cs.gradphi[1] +
-                       cs.gradphi[2] * cs.gradphi[2]);
-        T n[3];
-        for (int a = 0; a < 3; ++a) n[a] = cs.gradphi[a] / (gnorm + 1e-6);
-        T theta = 4.0 * cs.phi * (1.0 - cs.phi) / S.xi;
-        T heq[27], Sh[27], hpost[27], sh_rates[27];
-        for (int i = 0; i < LH.q; ++i) {
-          T cu = LH.c[3 * i] * cs.u[0] + LH.c[3 * i + 1] * cs.u[1] + LH.c[3 * i + 2] * cs.u[2];
-          T cn = LH.c[3 * i] * n[0] + LH.c[3 * i + 1] * n[1] + LH.c[3 * i + 2] * n[2];
-          heq[i] = LH.w[i] * cs.phi * (1.0 + cu / CS2);
-          Sh[i] = LH.w[i] * theta * cn;
-        }
-        if (P.collision == COLL_BGK) {
-          for (int i = 0; i < LH.q; ++i)
-            hpost[i] = hc[i] - omega_phi * (hc[i] - heq[i]) + (1.0 - 0.5 * omega_phi) * Sh[i];
-        } else {
-          for (int k = 0; k < LH.q; ++k) sh_rates[k] = rate_h(P, LH.degree[k], omega_phi);
-          mrt_collide(LH, hc, heq, Sh, sh_rates, hpost);
-        }
-
-        // streaming (push) with periodic wrap / halfway bounce-back
-        for (int i = 0; i < L27.q; ++i) {
-          int xt, yt, zt;
-          bool ok = neighbour(x, L27.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
-                    neighbour(y, L27.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
-                    neighbour(z, L27.c[3 * i + 2], P.nz, P.bc[4], P.bc[5], zt);
-          if (ok && !S.solid.empty() && S.solid[cell_index(P, xt, yt, zt)]) ok = false;  // bounce at a solid cell
-          if (ok)
-            S.gn[(size_t)i * N + cell_index(P, xt, yt, zt)] = gpost[i];
-          else
-            S.gn[(size_t)L27.opp[i] * N + c0] = gpost[i];
-        }
-        for (int i = 0; i < LH.q; ++i) {
-          int xt, yt, zt;
-          bool ok = neighbour(x, LH.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
-                    neighbour(y, LH.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
-                    neighbour(z, LH.c[3 * i + 2], P.nz, P.bc[4], P.bc[5], zt);
-          if (ok && !S.solid.empty() && S.solid[cell_index(P, xt, yt, zt)]) ok = false;
-          if (ok)
-            S.hn[(size_t)i * N + cell_index(P, xt, yt, zt)] = hpost[i];
-          else
-            S.hn[(size_t)LH.opp[i] * N + c0] = hpost[i];
-        }
-      }
+  T gnorm = sqrt(cs.gradphi[0] * cs.gradphi[0] + cs.gradphi[1] * cs.gradphi[1] + cs.gradphi[2] * cs.gradphi[2]);
+  T n[3];
+  for (int a = 0; a < 3; ++a) n[a] = cs.gradphi[a] / (gnorm + 1e-6);
+  T theta = 4.0 * cs.phi * (1.0 - cs.phi) / S.xi;
+  T heq[27], Sh[27], hpost[27], sh_rates[27];
+  for (int i = 0; i < LH.q; ++i) {
+    T cu = LH.c[3 * i] * cs.u[0] + LH.c[3 * i + 1] * cs.u[1] + LH.c[3 * i + 2] * cs.u[2];
+    T cn = LH.c[3 * i] * n[0] + LH.c[3 * i + 1] * n[1] + LH.c[3 * i + 2] * n[2];
+    heq[i] = LH.w[i] * cs.phi * (1.0 + cu / CS2);
+    Sh[i] = LH.w[i] * theta * cn;
   }
-  std::swap(S.g, S.gn);
-  std::swap(S.h, S.hn);
-  compute_phi(S);
+  if (P.collision == COLL_BGK) {
+    for (int i = 0; i < LH.q; ++i)
+      hpost[i] = hc[i] - omega_phi * (hc[i] - heq[i]) + (1.0 - 0.5 * omega_phi) * Sh[i];
+  } else {
+    for (int k = 0; k < LH.q; ++k) sh_rates[k] = rate_h(P, LH.degree[k], omega_phi);
+    mrt_collide(LH, hc, heq, Sh, sh_rates, hpost);
+  }
+  for (int i = 0; i < LH.q; ++i) {
+    int xt, yt, zt;
+    bool ok = neighbour(x, LH.c[3 * i], P.nx, P.bc[0], P.bc[1], xt) &&
+              neighbour(y, LH.c[3 * i + 1], P.ny, P.bc[2], P.bc[3], yt) &&
+              neighbour(z, LH.c[3 * i + 2], P.nz, P.bc[4], P.bc[5], zt);
+    if (ok && !S.solid.empty() && S.solid[cell_index(P, xt, yt, zt)]) ok = false;
+    if (ok)
+      S.hn[(size_t)i * N + cell_index(P, xt, yt, zt)] = hpost[i];
+    else
+      S.hn[(size_t)LH.opp[i] * N + c0] = hpost[i];
+  }
+}
+
+// One time step in the order of P.schedule.
+template <typename T>
+void do_step(Sim<T>& S) {
+  const Params& P = S.P;
+  const Lattice& L27 = g_lattice(P);
+  const Lattice& LH = h_lattice(P);
+  const long N = S.N;
+  // the state of a fluid cell at the current phi: populations and macroscopic values
+  auto load = [&](int x, int y, int z, T* gc, T* hc, CellState<T>& cs) {
+    const long c0 = cell_index(P, x, y, z);
+    for (int i = 0; i < L27.q; ++i) gc[i] = S.g[(size_t)i * N + c0];
+    for (int i = 0; i < LH.q; ++i) hc[i] = S.h[(size_t)i * N + c0];
+    cell_macro(S, x, y, z, gc, cs);
+  };
+  auto fluid = [&](int x, int y, int z) { return S.solid.empty() || !S.solid[cell_index(P, x, y, z)]; };
+  if (P.schedule == SCHED_CONCURRENT) {
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < P.nz; ++z)
+      for (int y = 0; y < P.ny; ++y)
+        for (int x = 0; x < P.nx; ++x) {
+          if (!fluid(x, y, z)) continue;  // solid cells are not updated
+          T gc[27], hc[27];
+          CellState<T> cs;
+          load(x, y, z, gc, hc, cs);
+          g_update(S, x, y, z, cs, gc);
+          h_update(S, x, y, z, cs, hc);
+        }
+    std::swap(S.g, S.gn);
+    std::swap(S.h, S.hn);
+    compute_phi(S);
+  } else {
+    // phase field first: h at phi^t and u^t, then phi^{t+1} = sum h
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < P.nz; ++z)
+      for (int y = 0; y < P.ny; ++y)
+        for (int x = 0; x < P.nx; ++x) {
+          if (!fluid(x, y, z)) continue;
+          T gc[27], hc[27];
+          CellState<T> cs;
+          load(x, y, z, gc, hc, cs);
+          h_update(S, x, y, z, cs, hc);
+        }
+    std::swap(S.h, S.hn);
+    compute_phi(S);
+    // then the hydrodynamics with g^t at phi^{t+1}
+#pragma omp parallel for collapse(2) schedule(static)
+    for (int z = 0; z < P.nz; ++z)
+      for (int y = 0; y < P.ny; ++y)
+        for (int x = 0; x < P.nx; ++x) {
+          if (!fluid(x, y, z)) continue;
+          T gc[27], hc[27];
+          CellState<T> cs;
+          load(x, y, z, gc, hc, cs);
+          g_update(S, x, y, z, cs, gc);
+        }
+    std::swap(S.g, S.gn);
+  }
   S.step += 1;
 }
 
@@ -518,6 +577,7 @@ void init_sim(Sim<T>& S, const int* ip, const double* dp, const double* phi0, co
   for (int k = 0; k < 6; ++k) P.bc[k] = ip[3 + k];
   P.collision = ip[9];
   P.qh = ip[10] == 27 ? 27 : (ip[10] == 9 ? 9 : 15);
+  P.schedule = ip[11] == SCHED_SEQUENTIAL ? SCHED_SEQUENTIAL : SCHED_CONCURRENT;
   P.rho_h = dp[0];
   P.rho_l = dp[1];
   P.nu_h = dp[2];
@@ -562,7 +622,8 @@ typedef Sim<double> SimD;
 
 extern "C" {
 
-// iparams: nx, ny, nz, bc[6], collision, h lattice (15, 27, or 9 for D2Q9 h and g)   (11 ints)
+// iparams: nx, ny, nz, bc[6], collision, h lattice (15, 27, or 9 for D2Q9 h and g),
+//          schedule (0 concurrent, 1 sequential)   (12 ints)
 // dparams: rho_h, rho_l, nu_h, nu_l, sigma, mobility, xi, gx, gy, gz (10 doubles)
 // phi0 (N), u0 (3N SoA, nullable), p0 (N, nullable): initial state; the
 // populations start at their equilibria h^eq(phi0, u0), g^eq(p0, u0).

@@ -1,0 +1,139 @@
+"""The order of the two collisions within a step, a reading of the paper
+(section "Conservative Allen-Cahn model" states both lattice Boltzmann
+equations but not which goes first).  Oracle and CUDA path both take the
+concurrent order: both collisions at t use phi^t.  The oracle also runs the
+sequential order (phase field first, the hydrodynamic collision at phi^{t+1})
+so that the reading's weight can be measured.
+
+Pins of the sequential order against the concurrent oracle and the physics:
+- one sequential step is the composition of the concurrent oracle's halves:
+  its h equals a concurrent step's h, its g equals a concurrent step taken
+  from (h^{t+1}, g^t) -- the hydrodynamic collision at phi^{t+1} with g^t;
+- with the phases decoupled (equal densities and viscosities, no surface
+  tension, no gravity) the hydrodynamics does not see phi, and both orders
+  give bitwise the same populations;
+- phi mass is conserved to 1e-12;
+- a static column reaches the same Laplace equilibrium in both orders, since
+  at steady state phi^{t+1} = phi^t.
+
+Measured sensitivities (the readings' table of the design notes quotes them):
+the Laplace jump moves 1e-6 relative, the capillary wave's frequency 1e-4.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2206_11637_gb300 import workloads as W
+import analytic as A
+
+THREADS = min(8, os.cpu_count() or 1)
+SEQ, CONC = oracle.SCHED_SEQUENTIAL, oracle.SCHED_CONCURRENT
+
+
+def _fitted_omega(t, a, a0, w0):
+    """Angular frequency of A exp(-g t) cos(w t + psi) + c fitted to a(t)."""
+    from scipy.optimize import curve_fit
+    f = lambda t, A0, g, w, ph, c: A0 * np.exp(-g * t) * np.cos(w * t + ph) + c
+    popt, _ = curve_fit(f, t, a, p0=[a0, 1e-5, w0, 0.0, 0.0], maxfev=20000)
+    return popt[2]
+
+
+def _drop(qh=15):
+    p, phi0, u0, _ = W.static_drop(12, 3.0, u_noise=1e-3, seed=7)
+    p.h_lattice = qh
+    if qh == 9:
+        p, phi0, u0, _ = W.static_cylinder(16, 4.0, nu=1 / 6)
+        p.h_lattice = 9
+        u0 = np.random.default_rng(7).uniform(-1e-3, 1e-3, (3,) + phi0.shape)
+        u0[2] = 0.0
+    return p, phi0, u0
+
+
+@pytest.mark.parametrize("qh", [15, 27, 9])
+def test_sequential_step_is_the_composition_of_the_halves(qh):
+    p, phi0, u0 = _drop(qh)
+    p.gravity = (0.0, -1e-5, 0.0)
+    pre = oracle.from_params(p, phi0, u0)
+    pre.step(7, THREADS)              # a state with flow and a moved interface
+    h0, g0 = pre.populations()
+
+    seq = oracle.from_params(p, phi0, u0, schedule=SEQ)
+    seq.set_populations(h0, g0)
+    seq.step(1, THREADS)
+    hs, gs = seq.populations()
+
+    conc = oracle.from_params(p, phi0, u0)
+    conc.set_populations(h0, g0)
+    conc.step(1, THREADS)
+    hc, gc = conc.populations()
+    assert np.array_equal(hs, hc)      # the phase field sees phi^t and u^t in both orders
+
+    aux = oracle.from_params(p, phi0, u0)
+    aux.set_populations(hc, g0)        # phi^{t+1} = sum h^{t+1}, with g^t
+    aux.step(1, THREADS)
+    _, ga = aux.populations()
+    assert np.array_equal(gs, ga)      # the hydrodynamics at phi^{t+1}
+    assert np.abs(gs - gc).max() > 1e-12   # and that is not the concurrent g
+
+
+@pytest.mark.parametrize("qh", [15, 9])
+def test_orders_agree_bitwise_when_the_phases_are_decoupled(qh):
+    p, phi0, u0 = _drop(qh)
+    p.rho_l, p.nu_l, p.sigma = p.rho_h, p.nu_h, 0.0
+    a = oracle.from_params(p, phi0, u0, schedule=CONC)
+    b = oracle.from_params(p, phi0, u0, schedule=SEQ)
+    a.step(30, THREADS)
+    b.step(30, THREADS)
+    ha, ga = a.populations()
+    hb, gb = b.populations()
+    assert np.array_equal(ha, hb) and np.array_equal(ga, gb)
+    assert np.abs(a.fields()[3]).max() > 1e-5    # the flow is not trivial
+
+
+@pytest.mark.parametrize("qh", [15, 27])
+def test_sequential_order_conserves_mass(qh):
+    p, phi0, u0 = _drop(qh)
+    p.bc = (1, 1, 1, 1, 0, 0)
+    o = oracle.from_params(p, phi0, u0, schedule=SEQ)
+    m0 = o.fields()[0].sum()
+    o.step(150, THREADS)
+    phi = o.fields()[0]
+    assert np.all(np.isfinite(phi))
+    assert abs(phi.sum() - m0) <= 1e-12 * m0
+
+
+def test_orders_share_the_laplace_equilibrium():
+    R = 16.0
+    p, phi0, _, _ = W.static_cylinder(64, R, nu=1 / 6)
+    p.h_lattice = 9
+    jumps = []
+    for sched in (CONC, SEQ):
+        o = oracle.from_params(p, phi0, schedule=sched)
+        o.step(2500, THREADS)
+        pr = o.fields()[2]
+        jumps.append((pr[0, 30:34, 30:34].mean() - pr[0, 0:2, 0:2].mean()) / (p.sigma / R))
+    assert abs(jumps[0] - 1) < 0.02 and abs(jumps[1] - 1) < 0.02
+    assert abs(jumps[1] / jumps[0] - 1) < 1e-4       # measured 1.3e-6
+
+
+def test_order_moves_the_capillary_wave_frequency_little():
+    L, sigma, nu, a0 = 32, 1e-4, 0.002, 0.5
+    k = 2 * np.pi / L
+    p, phi0, _, _ = W.capillary_wave(L, ny=L, a0=a0, xi=4.0, M=0.02, sigma=sigma, nu=nu)
+    p.h_lattice = 9
+    T = 2 * np.pi / A.capillary_omega0(sigma, k, 1.0, 1e-3)
+    dt = int(T / 60)
+    series = []
+    for sched in (CONC, SEQ):
+        o = oracle.from_params(p, phi0, schedule=sched)
+        ts, amps = [], []
+        while o.time < 1.6 * T:
+            ts.append(o.time)
+            amps.append(A.interface_height(o.fields()[0][0, :, 0]) - (L - 1) / 2)
+            o.step(dt, THREADS)
+        series.append((np.array(ts, float), np.array(amps)))
+    omegas = [_fitted_omega(t, a, a0, 2 * np.pi / T) for t, a in series]
+    assert abs(omegas[1] / omegas[0] - 1) < 1e-3      # measured 1e-4
+    assert np.abs(series[1][1] - series[0][1]).max() < 0.01 * a0
