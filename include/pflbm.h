@@ -28,6 +28,10 @@
  *   - Heavy phase phi = 1 (rho_h), light phase phi = 0 (rho_l).
  *   - All device work is queued on the stream passed to pfl_init; calls that
  *     return data to the host synchronise that stream.
+ *   - A context lives on the device that holds its workspace.  Each call makes
+ *     that device current while it runs and gives the caller's current device
+ *     back before it returns, on every path; a NULL stream is that device's
+ *     legacy default stream.  The same holds for batches.
  *
  * Memory ownership: the library never allocates device memory.  The caller
  * allocates one device buffer of pfl_workspace_bytes() bytes (for example a

@@ -552,7 +552,8 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
                                   std::to_string(L.total));
   int device = 0;
   if (!is_device_ptr(workspace, &device)) return bfail(PFL_ERR_ARG, "workspace is not device memory");
-  BTRY(cudaSetDevice(device));
+  DeviceScope on_device;
+  BTRY(on_device.enter(device));
 
   pfl_batch* b = new pfl_batch();
   b->count = count;
@@ -637,7 +638,8 @@ pfl_status pfl_batch_init(const pfl_params* params, int count, const double* con
 pfl_status pfl_batch_step(pfl_batch* b, int n) {
   if (!b) return bfail(PFL_ERR_ARG, "batch is NULL");
   if (n < 0) return bfail(PFL_ERR_ARG, "n_steps must be >= 0");
-  BTRY(cudaSetDevice(b->device));
+  DeviceScope on_device;
+  BTRY(on_device.enter(b->device));
   int done = 0;
   // whole graphs only from the graph's starting roles (pair 0 current)
   while (n - done >= 2 * GRAPH_PAIRS && b->ab == 0) {
@@ -653,7 +655,8 @@ pfl_status pfl_batch_step(pfl_batch* b, int n) {
 pfl_status pfl_batch_fields(pfl_batch* b, int i, double* phi, double* rho, double* p, double* u) {
   if (!b) return bfail(PFL_ERR_ARG, "batch is NULL");
   if (i < 0 || i >= b->count) return bfail(PFL_ERR_ARG, "instance index out of range");
-  BTRY(cudaSetDevice(b->device));
+  DeviceScope on_device;
+  BTRY(on_device.enter(b->device));
   const BInst& I = b->inst[i];
   const int ab = I.active ? b->ab : I.frozen_ab;
   Geo geo;
@@ -688,7 +691,8 @@ pfl_status pfl_batch_fields(pfl_batch* b, int i, double* phi, double* rho, doubl
 
 pfl_status pfl_batch_diag(pfl_batch* b, double* out, long long* nonfinite) {
   if (!b) return bfail(PFL_ERR_ARG, "batch is NULL");
-  BTRY(cudaSetDevice(b->device));
+  DeviceScope on_device;
+  BTRY(on_device.enter(b->device));
   double* part = (double*)(b->ws + b->red_off);
   double* res = part + DIAG_BLOCKS * 9;
   double* upart = part + DIAG_BLOCKS * 9 + 16;
@@ -753,7 +757,8 @@ pfl_status pfl_batch_set_shape(pfl_batch* b, int cls, int tile_x, int tile_y, in
   if (j < 0 || j >= shapes_for(b->prec))
     return bfail(PFL_ERR_ARG, "tile " + std::to_string(tile_x) + " x " + std::to_string(tile_y) +
                                   " is not a shape of this class and precision");
-  BTRY(cudaSetDevice(b->device));
+  DeviceScope on_device;
+  BTRY(on_device.enter(b->device));
   BTRY(cudaStreamSynchronize(b->stream));
   ClassPlan& c = b->cls[cls];
   if (!c.tiles) return PFL_OK;  // no instance of this class
@@ -788,6 +793,8 @@ long long pfl_batch_time(const pfl_batch* b) { return b ? b->t : -1; }
 
 void pfl_batch_destroy(pfl_batch* b) {
   if (!b) return;
+  DeviceScope on_device;  // the stream (NULL: the legacy stream) is the batch's device's
+  on_device.enter(b->device);
   cudaStreamSynchronize(b->stream);
   if (b->graph) cudaGraphExecDestroy(b->graph);
   delete b;

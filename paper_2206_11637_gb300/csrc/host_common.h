@@ -11,6 +11,33 @@
 
 namespace pfl_host {
 
+// The device of a context (the one that holds its workspace) is made current
+// for the duration of a library call, and the caller's current device is
+// given back when the call returns, on every return path, so that the
+// caller's own CUDA calls keep going to the device it chose.  Nothing is
+// switched when the two are the same device.
+class DeviceScope {
+ public:
+  DeviceScope() = default;
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+  cudaError_t enter(int device) {
+    cudaError_t e = cudaGetDevice(&saved_);
+    if (e != cudaSuccess) {
+      saved_ = -1;
+      return e;
+    }
+    return saved_ == device ? cudaSuccess : cudaSetDevice(device);
+  }
+  ~DeviceScope() {
+    int now = -1;
+    if (saved_ >= 0 && cudaGetDevice(&now) == cudaSuccess && now != saved_) cudaSetDevice(saved_);
+  }
+
+ private:
+  int saved_ = -1;
+};
+
 inline size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 inline size_t pop_bytes(int prec) { return prec == PFL_FP64 ? 8 : prec == PFL_FP32 ? 4 : 2; }

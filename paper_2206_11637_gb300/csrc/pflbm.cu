@@ -564,7 +564,8 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
                                  std::to_string(L.total));
   int device = 0;
   if (!is_device_ptr(workspace, &device)) return fail(PFL_ERR_ARG, "workspace is not device memory");
-  CUDA_TRY(cudaSetDevice(device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(device));
 
   pfl_ctx* c = new pfl_ctx();
   c->p = *p;
@@ -724,7 +725,8 @@ pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, c
 
 pfl_status pfl_step(pfl_ctx* c, int n) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   if (n < 0) return fail(PFL_ERR_ARG, "n_steps must be >= 0");
   if (n == 0) return PFL_OK;
   if (c->zm && c->graph_k > 0 && n >= c->graph_k) {
@@ -746,7 +748,8 @@ pfl_status pfl_step(pfl_ctx* c, int n) {
 pfl_status pfl_set_graph_steps(pfl_ctx* c, int k) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
   if (k < 0 || k % 2 != 0 || k > 4096) return fail(PFL_ERR_ARG, "graph steps must be 0 or even in [2, 4096]");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   drop_graphs(c);
   c->graph_k = k;
@@ -755,7 +758,8 @@ pfl_status pfl_set_graph_steps(pfl_ctx* c, int k) {
 
 pfl_status pfl_fields(pfl_ctx* c, double* phi, double* rho, double* p, double* u) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   const long long N = c->geo.N;
   double* want[6] = {phi, rho, p, u, u ? u + N : nullptr, u ? u + 2 * N : nullptr};
   double* dev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
@@ -786,7 +790,8 @@ pfl_status pfl_fields(pfl_ctx* c, double* phi, double* rho, double* p, double* u
 
 pfl_status pfl_populations(pfl_ctx* c, double* h, double* g) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   DISPATCH(c, ensure_phi, c);
   const long long N = c->geo.N;
   for (int set = 0; set < 2; ++set) {
@@ -810,7 +815,8 @@ pfl_status pfl_populations(pfl_ctx* c, double* h, double* g) {
 
 pfl_status pfl_set_populations(pfl_ctx* c, const double* h, const double* g) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   if (!h || !g) return fail(PFL_ERR_ARG, "both population sets are required");
   const long long N = c->geo.N;
   // read the complete current state first when only part would change: not
@@ -883,7 +889,8 @@ pfl_status pfl_save(pfl_ctx* c, void* buf, size_t bytes) {
   if (bytes < pfl_state_bytes(c))
     return fail(PFL_ERR_ARG, "buffer holds " + std::to_string(bytes) + " bytes, a state needs " +
                                  std::to_string(pfl_state_bytes(c)));
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   SavedHeader hd;
   std::memset(&hd, 0, sizeof hd);
   std::memcpy(hd.magic, "PFLSTATE", 8);
@@ -919,7 +926,8 @@ pfl_status pfl_load(pfl_ctx* c, const void* buf, size_t bytes) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
   if (!buf) return fail(PFL_ERR_ARG, "buffer is NULL");
   if (bytes < sizeof(SavedHeader)) return fail(PFL_ERR_ARG, "buffer is shorter than a state header");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   SavedHeader hd;
   CUDA_TRY(cudaMemcpy(&hd, buf, sizeof hd, cudaMemcpyDefault));
   if (std::memcmp(hd.magic, "PFLSTATE", 8) != 0 || hd.version != 2)
@@ -966,7 +974,8 @@ pfl_status pfl_set_solid(pfl_ctx* c, const unsigned char* mask) {
   if (!mask) return fail(PFL_ERR_ARG, "mask is NULL");
   if (!c->p.solids) return fail(PFL_ERR_STATE, "the context was created without solids (pfl_params.solids = 0)");
   if (c->t != 0) return fail(PFL_ERR_STATE, "solid cells are set before the first step");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   const long long N = c->geo.N;
   unsigned char* st = (unsigned char*)stage(c);  // N bytes fit the N + 16 doubles of the staging area
   CUDA_TRY(cudaMemcpyAsync(st, mask, (size_t)N, cudaMemcpyDefault, c->stream));
@@ -988,7 +997,8 @@ static pfl_status queue_speed(pfl_ctx* c, double* res) {
 
 pfl_status pfl_diag(pfl_ctx* c, double out[8], long long* nonfinite) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   double* part = (double*)(c->ws + c->L.red);
   double* res = part + DIAG_BLOCKS * 9;
   double* ures = part + DIAG_BLOCKS * 10 + 16;
@@ -1015,7 +1025,8 @@ pfl_status pfl_diag(pfl_ctx* c, double out[8], long long* nonfinite) {
 pfl_status pfl_max_speed(pfl_ctx* c, double* umax) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
   if (!umax) return fail(PFL_ERR_ARG, "umax is NULL");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   double* ures = (double*)(c->ws + c->L.red) + DIAG_BLOCKS * 10 + 16;
   pfl_status st = queue_speed(c, ures);
   if (st != PFL_OK) return st;
@@ -1028,7 +1039,8 @@ pfl_status pfl_interface_height(pfl_ctx* c, int x, int z, double* y) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
   if (!y) return fail(PFL_ERR_ARG, "y is NULL");
   if (x < 0 || x >= c->p.nx || z < 0 || z >= c->p.nz) return fail(PFL_ERR_ARG, "column (x, z) outside the lattice");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   DISPATCH(c, ensure_phi, c);
   double* res = (double*)(c->ws + c->L.red) + DIAG_BLOCKS * 9 + 9;  // a spare word after the diag results
   DISPATCH_PREC(c, launch_iface, c, x, z, res);
@@ -1041,7 +1053,8 @@ pfl_status pfl_interface_height(pfl_ctx* c, int x, int z, double* y) {
 pfl_status pfl_kernel_times(pfl_ctx* c, int n, double ms[2]) {
   if (!c) return fail(PFL_ERR_ARG, "context is NULL");
   if (n <= 0 || !ms) return fail(PFL_ERR_ARG, "n_steps must be > 0 and ms non-NULL");
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   cudaEvent_t ev[3];
   for (int k = 0; k < 3; ++k) CUDA_TRY(cudaEventCreate(&ev[k]));
   double acc[2] = {0, 0};
@@ -1410,7 +1423,8 @@ pfl_status pfl_adjoint(pfl_ctx* c, int n_steps, int n_obs, const int* obs_steps,
   if (adj_bytes < A.total)
     return fail(PFL_ERR_OOM, "adjoint workspace holds " + std::to_string(adj_bytes) + " bytes, needs " +
                                  std::to_string(A.total));
-  CUDA_TRY(cudaSetDevice(c->device));
+  DeviceScope on_device;
+  CUDA_TRY(on_device.enter(c->device));
   char* aws = (char*)adj_workspace;
   const size_t N = (size_t)c->geo.N;
   ObsTable obs;
@@ -1439,6 +1453,8 @@ pfl_status pfl_adjoint(pfl_ctx* c, int n_steps, int n_obs, const int* obs_steps,
 
 void pfl_destroy(pfl_ctx* c) {
   if (!c) return;
+  DeviceScope on_device;  // the stream (NULL: the legacy stream) is the context's device's
+  on_device.enter(c->device);
   cudaStreamSynchronize(c->stream);
   drop_graphs(c);
   if (c->cap) cudaStreamDestroy(c->cap);
