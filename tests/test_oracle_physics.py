@@ -266,8 +266,10 @@ def test_capillary_wave_period_converges_in_L():
     zero crossings of the interface height at x = 0, against the same
     crossings of Prosperetti's a(t), is 16.5 %, 12.4 % and 8.1 % long at
     L = 24, 32 and 48: first order in xi / L.  The test asks for a monotone
-    fall, an error below 10 % at L = 48 and a ratio err(24) / err(48) in
-    [1.6, 2.6] (2 for first order)."""
+    fall, an error below 10 % at L = 48, a ratio err(24) / err(48) in
+    [1.6, 2.6] (2 for first order), and that the error extrapolated linearly
+    in 1 / L to a sharp interface (L -> infinity) vanishes within 2 %: the
+    oracle's period converges to the dispersion relation's."""
     sigma, nu, xi = 1e-3, 0.002, 4.0
     errs = []
     for L in (24, 32, 48):
@@ -294,6 +296,10 @@ def test_capillary_wave_period_converges_in_L():
     assert errs[0] > errs[1] > errs[2] > 0, errs
     assert errs[2] < 0.10, errs
     assert 1.6 < errs[0] / errs[2] < 2.6, errs
+    # err = a + b / L by least squares: the limit L -> infinity (a sharp
+    # interface) lands on Prosperetti's period (a = -0.3 % measured)
+    b, a = np.polyfit(1.0 / np.array([24.0, 32.0, 48.0]), errs, 1)
+    assert abs(a) < 0.02, (a, b, errs)
 
 
 def _period_mean_pressure(o, n, period):
