@@ -122,6 +122,21 @@ typedef enum { PFL_ENGINE_AUTO = 0, PFL_ENGINE_INPLACE = 1 } pfl_engine;
 /* Device bytes the workspace must hold for these parameters (0 if invalid). */
 size_t pfl_workspace_bytes(const pfl_params* p);
 
+/* The hydrostatic start of pfl_init, on the host: the normalised pressure
+ * p* = p / (rho(phi0) c_s^2) of the fluid at rest under gravity, from which
+ * the paper starts its gravity cases (sections "Gravity wave", "Rising
+ * bubble", "Drop impact").  The same numbers pfl_init uses with
+ * pfl_params.hydrostatic = 1 and p0 == NULL: along every line of cells
+ * parallel to the gravity axis s, dp/ds = rho(phi0) g_s integrated by the
+ * trapezoid rule between cell centres, p = 0 at s = p->p_level (linear
+ * interpolation between the two cells around it).  A caller can inspect or
+ * amend it (a bubble's Laplace jump, another gauge) and pass it as p0.
+ *   phi0: N host doubles, x-fastest; pstar: N host doubles, written.
+ * Needs no GPU and no context; p->hydrostatic is not read.  PFL_ERR_ARG for
+ * NULL or device arrays, invalid parameters, gravity not along exactly one
+ * axis, or a non-finite p_level. */
+pfl_status pfl_hydrostatic_pstar(const pfl_params* p, const double* phi0, double* pstar);
+
 /* Create a context and write the initial state.
  *   phi0: N doubles, required.  u0: 3N doubles SoA or NULL (zero).  p0: N
  *   doubles of initial normalised pressure p* or NULL: zero, or with
@@ -360,7 +375,8 @@ void pfl_destroy(pfl_ctx* ctx);
 /* Message of the last failed call on this thread ("" if none). */
 const char* pfl_last_error(void);
 
-/* Library interface version (2: pfl_params carries hydrostatic and p_level). */
+/* Library interface version (2: pfl_params carries hydrostatic and p_level;
+ * 3: pfl_hydrostatic_pstar). */
 int pfl_version(void);
 
 #ifdef __cplusplus

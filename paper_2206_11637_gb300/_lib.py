@@ -54,6 +54,8 @@ def load():
     PP = ctypes.POINTER(pfl_params)
     lib.pfl_workspace_bytes.restype = S
     lib.pfl_workspace_bytes.argtypes = [PP]
+    lib.pfl_hydrostatic_pstar.restype = I
+    lib.pfl_hydrostatic_pstar.argtypes = [PP, P, P]
     lib.pfl_init.restype = I
     lib.pfl_init.argtypes = [PP, P, P, P, P, S, P, ctypes.POINTER(P)]
     lib.pfl_step.restype = I

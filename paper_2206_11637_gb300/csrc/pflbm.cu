@@ -5,6 +5,7 @@
 //   [h populations | g populations | phi (two buffers) | FP64 staging (N) | reduction scratch]
 // each section 256-byte aligned.  All kernels are queued on the caller's
 // stream; calls returning data to the host synchronise that stream.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -540,13 +541,26 @@ pfl_status graph_steps(pfl_ctx* c) {
 
 extern "C" {
 
-int pfl_version(void) { return 2; }
+int pfl_version(void) { return 3; }
 
 const char* pfl_last_error(void) { return g_err.c_str(); }
 
 size_t pfl_workspace_bytes(const pfl_params* p) {
   if (!check_params(p).empty()) return 0;
   return layout_of(p).total;
+}
+
+pfl_status pfl_hydrostatic_pstar(const pfl_params* p, const double* phi0, double* pstar) {
+  if (!p || !phi0 || !pstar) return fail(PFL_ERR_ARG, "params, phi0 and pstar must not be NULL");
+  pfl_params q = *p;
+  q.hydrostatic = 1;  // the checks of the hydrostatic start apply
+  const std::string why = check_params(&q);
+  if (!why.empty()) return fail(PFL_ERR_ARG, why);
+  if (is_device_ptr(phi0) || is_device_ptr(pstar)) return fail(PFL_ERR_ARG, "phi0 and pstar must be host arrays");
+  std::vector<double> out;
+  hydrostatic_pstar(&q, phi0, out);
+  std::copy(out.begin(), out.end(), pstar);
+  return PFL_OK;
 }
 
 pfl_status pfl_init(const pfl_params* p, const double* phi0, const double* u0, const double* p0, void* workspace,

@@ -45,6 +45,19 @@ def workspace_bytes(p, precision):
     return L.load().pfl_workspace_bytes(ctypes.byref(s))
 
 
+def hydrostatic_pstar(p, phi0):
+    """The library's hydrostatic start (pfl_hydrostatic_pstar, on the host):
+    p* of the fluid at rest under p.gravity, zero pressure at p.p_level along
+    the gravity axis; phi0 and the result are (nz, ny, nx) FP64 arrays."""
+    s = _params_struct(p, L.PFL_FP64)
+    phi0 = np.ascontiguousarray(np.asarray(phi0, dtype=np.float64))
+    if phi0.size != p.nx * p.ny * p.nz:
+        raise ValueError("phi0 must hold one value per cell")
+    out = np.empty((p.nz, p.ny, p.nx))
+    L.check(L.load().pfl_hydrostatic_pstar(ctypes.byref(s), _ptr(phi0), _ptr(out)))
+    return out
+
+
 class Simulation:
     """One PFLBM domain on the GPU.
 

@@ -21,7 +21,7 @@ def test_exports_every_declared_symbol(lib):
     assert {"pfl_init", "pfl_step", "pfl_fields", "pfl_diag"} <= set(names)
     for n in names:
         assert hasattr(lib, n), n
-    assert lib.pfl_version() == 2
+    assert lib.pfl_version() == 3
 
 
 def test_workspace_size(lib):
@@ -117,3 +117,39 @@ def test_hydrostatic_start_needs_gravity_along_one_axis(lib):
 
 def test_null_context_speed(lib):
     assert lib.pfl_max_speed(None, None) == L.PFL_ERR_ARG
+
+
+def test_host_hydrostatic_start(lib):
+    """pfl_hydrostatic_pstar (host only): equal to the caller-side column
+    integration for gravity along -y; gravity along z gives the y result of
+    the transposed field (the integration follows the gravity axis, whichever
+    it is); the refusals."""
+    import numpy as np
+    p, phi0, _, _ = W.gravity_wave(24)
+    p.p_level = 11.5
+    ours = pflbm.hydrostatic_pstar(p, phi0)
+    ref = W.column_hydrostatic_pstar(p, phi0, 11.5)
+    assert np.allclose(ours, ref, rtol=1e-13, atol=1e-15)
+
+    p3, _, _, _ = W.rising_bubble(12, 20, 8, D=5.0, hydrostatic=False)
+    rng = np.random.Generator(np.random.PCG64(3))
+    phi = rng.uniform(0.0, 1.0, p3.shape)                  # (nz, ny, nx)
+    p3.gravity, p3.p_level = (0.0, -2e-5, 0.0), 7.25
+    along_y = pflbm.hydrostatic_pstar(p3, phi)
+    pz = W.Params(p3.nx, p3.nz, p3.ny, p3.bc, p3.rho_h, p3.rho_l, p3.nu_h, p3.nu_l, p3.sigma, p3.mobility, p3.xi,
+                  (0.0, 0.0, -2e-5))                       # y and z swapped
+    pz.p_level = 7.25
+    along_z = pflbm.hydrostatic_pstar(pz, np.ascontiguousarray(phi.transpose(1, 0, 2)))
+    assert np.array_equal(along_z.transpose(1, 0, 2), along_y)
+    # flipping gravity flips the pressure
+    p3.gravity = (0.0, 2e-5, 0.0)
+    assert np.allclose(pflbm.hydrostatic_pstar(p3, phi), -along_y, rtol=1e-14, atol=0)
+
+    out = np.empty(p3.shape)
+    s = pflbm._params_struct(p3, 0)
+    assert lib.pfl_hydrostatic_pstar(ctypes.byref(s), None, out.ctypes.data_as(ctypes.c_void_p)) == L.PFL_ERR_ARG
+    p3.gravity = (1e-6, 1e-6, 0.0)
+    s = pflbm._params_struct(p3, 0)
+    assert lib.pfl_hydrostatic_pstar(ctypes.byref(s), phi.ctypes.data_as(ctypes.c_void_p),
+                                     out.ctypes.data_as(ctypes.c_void_p)) == L.PFL_ERR_ARG
+    assert "one axis" in lib.pfl_last_error().decode()
