@@ -733,7 +733,19 @@ def main():
     # it runs ~15x slower) and the error of FP32 and FP16S against FP64 after
     # 1000 lattice steps (max |dphi| and max |du| / max |u|), on the device
     compare = {}
-    if not args.no_compare and rank == 0:
+    leg_errors = {}
+
+    def leg(name, fn):
+        """Run an auxiliary leg after the headline measurement; a failure is
+        recorded in the line (leg_errors) instead of losing the line."""
+        try:
+            return fn()
+        except Exception as e:  # noqa: BLE001 -- reported, not hidden
+            leg_errors[name] = "%s: %s" % (type(e).__name__, e)
+            torch.cuda.empty_cache()
+            return None
+
+    def compare_leg():
         for other in ("fp64", "fp32", "fp16s"):
             if other == prec:
                 continue
@@ -787,12 +799,13 @@ def main():
     adj = None
     configs = None
     if not args.no_compare and rank == 0:
-        adj = adjoint_leg(dev, barrier)
-        configs = config_table(dev, barrier)
+        leg("compare", compare_leg)
+        adj = leg("adjoint", lambda: adjoint_leg(dev, barrier))
+        configs = leg("configs", lambda: config_table(dev, barrier))
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        cpu = cpu_oracle_rate(wl)
+        cpu = leg("cpu_baseline", lambda: cpu_oracle_rate(wl))
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
@@ -805,6 +818,8 @@ def main():
                 "e2e": e2e, "gpu_launches": step_launches(S, args.engine) * K, "clocks": clocks, "roofline": roofline,
                 "cpu_baseline": cpu, "nonfinite_cells": nf, "wall_s": wall, "adjoint": adj,
                 "configs": configs}
+        if leg_errors:
+            line["leg_errors"] = leg_errors
         line.update(compare)
         print(json.dumps(line), flush=True)
     if dist:
